@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the differentiable Gaussian rasterizer on GB300.
+
+Workload (the headline configuration): a 500k-Gaussian synthetic sub-map
+(room_scene(500_000, seed=3): 6 x 5 x 3 m room + 40 boxes, surface Gaussians)
+seen by one 1200x680 RGB-D keyframe (sub-map view 5, ~326k visible).  One
+step is one single-view mapping iteration through the C ABI (gsr_map_step):
+projection + binning, blend forward, fused L1/SSIM/depth loss, blend
+backward, projection backward, Adam with the isotropic regulariser; the
+iteration is a captured CUDA graph.  The optimised copy starts from the
+ground truth plus noise; targets are renders of the ground truth.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (one
+horizontal band of 1/8 of the frame per step, scaled to full-frame
+iterations/s).  Under torchrun each rank runs an independent replica
+(no collective: the mapping step of one keyframe does not exchange data).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd render iters/s at 1200×680, 500k Gaussians; % HBM roofline"
+N_GAUSS = 500_000
+BAND_FRACTION = 8  # the CPU sample is 1/8 of the frame (85 rows)
+
+# algorithmic FP32 flops per pixel-Gaussian evaluation (FMA = 2), see the design doc
+FLOPS_FWD_EVAL = 22
+FLOPS_BWD_EVAL = 61
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm=d["hbm_gbs"], sm_mhz=d.get("sm_max_mhz", 2070.0), src="measured")
+    return dict(hbm=6800.0, sm_mhz=2070.0, src="fallback")
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ------------------------------------------------------------------ oracle
+_BAND_TARGETS = {}
+_ADAM = {}
+
+
+def oracle_band_step(sc64, q, t, spec, band_index=0):
+    """One step of the FP64 oracle on a horizontal band (1/8) of the frame:
+    render, mapping loss against the band of a target, backward, Adam.  The
+    target is a perturbed render of the band, made once per band."""
+    import oracle as O
+    h = spec.height // BAND_FRACTION
+    cam = O.Camera(spec.width, h, spec.fx, spec.fy, spec.cx, spec.cy - band_index * h)
+    if band_index not in _BAND_TARGETS:
+        tr = O.render(sc64, q, t, cam)
+        _BAND_TARGETS[band_index] = (np.clip(tr["rgb"] * 0.97 + 0.01, 0, 1), tr["depth"] * 1.01)
+    rgb_t, depth_t = _BAND_TARGETS[band_index]
+    r = O.render(sc64, q, t, cam)
+    lm = O.loss_map(r["rgb"], r["depth"], rgb_t, depth_t)
+    g = O.render_backward(sc64, q, t, cam, lm["d_rgb"], lm["d_depth"], None)
+    _, gl = O.lreg(sc64.log_scale)
+    for k in ("mean", "log_scale", "quat", "opacity_logit", "rgb"):
+        p = getattr(sc64, k)
+        gk = np.ascontiguousarray(g[k] + (gl if k == "log_scale" else 0))
+        m, v, st = _ADAM.setdefault(k, (np.zeros_like(p), np.zeros_like(p), [0]))
+        st[0] += 1
+        O.adam(p, gk, m, v, st[0], 1e-4, 0.9, 0.999, 1e-15)
+    return lm["loss"]
+
+
+def cpu_baseline(budget_s=30.0):
+    """The oracle as it stands, on the host cores: the bands of the frame in
+    turn (each a full step on 1/8 of the pixels) until all 8 ran or the
+    budget is spent; iters/s scaled to the full frame."""
+    import oracle as O
+    from paper_2312_10070_gb300 import synth as S
+    O.build()
+    sc64 = O.Scene.from_dict(S.room_scene(N_GAUSS, seed=3))
+    q, t = S.submap_views()[S.HEADLINE_VIEW]
+    spec = S.camera_room()
+    for b in range(BAND_FRACTION):  # targets are inputs, made outside the timing
+        h = spec.height // BAND_FRACTION
+        cam = O.Camera(spec.width, h, spec.fx, spec.fy, spec.cx, spec.cy - b * h)
+        tr = O.render(sc64, q, t, cam)
+        _BAND_TARGETS[b] = (np.clip(tr["rgb"] * 0.97 + 0.01, 0, 1), tr["depth"] * 1.01)
+    t0 = time.perf_counter()
+    done = 0
+    for b in range(BAND_FRACTION):
+        oracle_band_step(sc64, q, t, spec, b)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=done / (BAND_FRACTION * dt), unit="iters/s", cores=O.num_threads(), kind="oracle",
+                sample=f"{done} of the 8 1200x85 bands of view {S.HEADLINE_VIEW} (each band: all 500k Gaussians "
+                       f"projected, render, loss, backward, Adam); iters/s = bands / (8 x seconds)",
+                seconds=dt)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2312_10070_gb300 import synth as S
+    O.build()
+    sc64 = O.Scene.from_dict(S.room_scene(N_GAUSS, seed=3))
+    q, t = S.submap_views()[S.HEADLINE_VIEW]
+    spec = S.camera_room()
+    for i in range(args.warmup):
+        oracle_band_step(sc64, q, t, spec, i % BAND_FRACTION)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle_band_step(sc64, q, t, spec, i % BAND_FRACTION)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    value = 1.0 / (dt * BAND_FRACTION)
+    line = dict(impl="reference", metric=METRIC, value=value, unit="iters/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=dt * BAND_FRACTION * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=config_dict(None, None),
+                cpu_baseline=dict(kind="oracle", cores=O.num_threads(), value=value, unit="iters/s",
+                                  sample="each step: the FP64 oracle on one 1200x85 band (1/8 frame, bands in "
+                                         f"turn) of view {S.HEADLINE_VIEW}; value scaled x1/8 to full-frame "
+                                         "iters/s"),
+                e2e=dict(value=value, unit="iters/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(stats, flops_info):
+    from paper_2312_10070_gb300 import synth as S
+    c = dict(workload=f"sub-map mapping iteration, 1 keyframe: 1200x680 RGB-D, {N_GAUSS} Gaussians "
+                      f"(room_scene seed 3, view {S.HEADLINE_VIEW})",
+             width=1200, height=680, gaussians=N_GAUSS,
+             step="projection+binning, blend fwd, fused L1+SSIM+depth loss, blend bwd, projection bwd, "
+                  "Adam+L_reg (CUDA graph)",
+             l2="flushed between timed steps (256 MB write)", parallelism="replicas")
+    if stats:
+        c.update(visible=int(stats["n_visible"]), instances=int(stats["n_instances"]))
+    return c
+
+
+# -------------------------------------------------------------------- GPU
+def run_gpu(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2312_10070_gb300 import api, synth as S
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = S.camera_room()
+    cam = api.camera_from_spec(spec)
+    sc_gt = S.room_scene(N_GAUSS, seed=3)
+    q, t = S.submap_views()[S.HEADLINE_VIEW]
+    pose = api.make_pose(q, t)
+    ctx = api.Context()
+    g_gt = api.GaussianParams.from_numpy(sc_gt, dev)
+    tgt = api.render_forward(ctx, g_gt, cam, pose)
+    rgb_t, depth_t = tgt["rgb"].clone(), tgt["depth"].clone()
+    g = api.GaussianParams.from_numpy(S.noisy_copy(sc_gt, seed=3), dev)
+    state = api.AdamMoments(g)
+    cfg = api.MapConfig()
+    kf = [(pose, rgb_t, depth_t)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        api.map_step(ctx, g, state, cam, kf, None, 1, cfg, want_stats=False)
+
+    api.profile_enable(ctx, True)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    # counters of the current parameters (outside the timed region)
+    probe = api.render_forward(ctx, g, cam, pose)
+    stats = api.frame_stats(ctx)
+    e_bwd = int((probe["last_idx"].to(torch.int64) + 1).sum())
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phase_ms = {k: [] for k in api.PHASES}
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.kernel_launches
+    sampler.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        step()
+        ev[i][1].record()
+        ph = api.profile_read(ctx)  # synchronises; the events of this replay
+        for k, v in ph.items():
+            phase_ms[k].append(v)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = ctx.kernel_launches - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(tt)
+    value = world * args.steps / (total_ms / 1e3)
+
+    # end-to-end through the public API with host buffers
+    rgb_h = rgb_t.cpu().pin_memory()
+    depth_h = depth_t.cpu().pin_memory()
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rgb_t.copy_(rgb_h, non_blocking=True)
+        depth_t.copy_(depth_h, non_blocking=True)
+        api.map_step(ctx, g, state, cam, kf, None, 1, cfg, want_stats=True)  # reads the loss back
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt)
+    e2e = dict(value=world * e2e_steps / e2e_s, unit="iters/s",
+               h2d_bytes_per_step=int(rgb_h.numel() * 4 + depth_h.numel() * 4 + 28), d2h_bytes_per_step=8)
+
+    if rank != 0:
+        return
+    pk = peaks()
+    avg = {k: float(np.mean([x for x in v if x >= 0])) if any(x >= 0 for x in v) else None
+           for k, v in phase_ms.items()}
+    dom = max((k for k in avg if avg[k] is not None), key=lambda k: avg[k])
+    n, V, I, P = N_GAUSS, stats["n_visible"], stats["n_instances"], 1200 * 680
+    step_bytes = 68 * n + 388 * V + 52 * I + 132 * P + 392 * n
+    ms_per_step = total_ms / args.steps
+    hbm = dict(bound="hbm", achieved=step_bytes / (ms_per_step / 1e3) / 1e9, peak=pk["hbm"], unit="GB/s",
+               traffic_model_bytes=step_bytes, note=f"whole step, algorithmic bytes 460N+388V+52I+132P; peak "
+                                                    f"{pk['src']}")
+    hbm["frac"] = hbm["achieved"] / hbm["peak"]
+    peak_tf = fp32_peak_tflops(pk["sm_mhz"])
+    if dom in ("blend_bwd", "blend_fwd"):
+        fl = (FLOPS_BWD_EVAL if dom == "blend_bwd" else FLOPS_FWD_EVAL) * e_bwd
+        ach = fl / (avg[dom] / 1e3) / 1e12
+        roof = dict(bound="alu", kernel=dom, achieved=ach, peak=peak_tf, unit="TFLOP/s", frac=ach / peak_tf,
+                    traffic=None, units=f"{e_bwd} pixel-Gaussian evaluations x "
+                                       f"{FLOPS_BWD_EVAL if dom == 'blend_bwd' else FLOPS_FWD_EVAL} flops",
+                    peak_note=f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_mhz']:.0f} MHz (derived)")
+    else:
+        per = {"bin": 68 * n + 96 * V + 44 * I, "loss": 56 * P, "project_bwd": 56 * n + 152 * V,
+               "adam": 392 * n}.get(dom, step_bytes)
+        ach = per / (avg[dom] / 1e3) / 1e9
+        roof = dict(bound="hbm", kernel=dom, achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
+                    traffic=None)
+    line = dict(metric=METRIC, value=value, unit="iters/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+                data="synthetic", config=config_dict(stats, None), roofline=roof, hbm_roofline_step=hbm,
+                phases_ms=avg, e2e=e2e, gpu_launches=int(launches), clocks=clocks)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -56,6 +56,7 @@ typedef struct {
                          bit1: a gradient clamp is near its threshold */
     int vis_amb;      /* the cull decision itself is near its threshold */
     int ox0, oy0, ox1, oy1, ix0, iy0, ix1, iy1; /* outer / inner possible tile rectangles */
+    double err_z, err_u, err_v; /* bounds of the float32 rounding error of p_z, u, v */
     int clamp_x, clamp_y;
     double u, v, depth, opacity;
     double cov[3];    /* Sigma^I + eps I:   a b c */
@@ -123,8 +124,14 @@ static void project_one(const orc_camera *c, const double Rcw[9], const double t
         o->p[i] = Rcw[3 * i] * mean[0] + Rcw[3 * i + 1] * mean[1] + Rcw[3 * i + 2] * mean[2] + tcw[i];
     double px = o->p[0], py = o->p[1], pz = o->p[2];
     o->depth = pz;
-    if (fabs(pz - c->z_near) <= 1e-6) { o->amb |= 1; o->vis_amb = 2; }
-    if (pz <= c->z_near) return;
+    /* Error model of a float32 implementation that evaluates p = R mu + t
+     * faithfully rounded (compensated products): |error| < 1 ulp of p, bounded
+     * here by 2.4e-7 |p|.  The margins below derive from it: a decision closer
+     * to its threshold than the bound is flagged as ambiguous, not compared. */
+    o->err_z = 2.4e-7 * fabs(pz) + 1e-12;
+    int z_amb = fabs(pz - c->z_near) <= o->err_z;
+    if (z_amb) { o->amb |= 1; o->vis_amb = 1; } /* its tiles (computed below) are marked */
+    if (pz <= c->z_near && !z_amb) return;
 
     /* Sigma_cam = R_wc Sigma R_wc^T */
     double T1[9], Rt[9];
@@ -174,16 +181,19 @@ static void project_one(const orc_camera *c, const double Rcw[9], const double t
     /* pinhole projection; pixel (i, j) has its centre at (i + 0.5, j + 0.5) */
     o->u = c->fx * px / pz + c->cx;
     o->v = c->fy * py / pz + c->cy;
+    /* u = fx (p_x / p_z) + c_x in float: ~4 ulp on the ratio, 0.5 ulp on u */
+    o->err_u = 5e-7 * c->fx * fabs(px / pz) + 1.2e-7 * fabs(o->u) + 1e-6;
+    o->err_v = 5e-7 * c->fy * fabs(py / pz) + 1.2e-7 * fabs(o->v) + 1e-6;
 
     /* tile rectangle, inclusive, clamped to the tile grid */
     int tiles_x = (c->width + c->tile_w - 1) / c->tile_w;
     int tiles_y = (c->height + c->tile_h - 1) / c->tile_h;
     double ex[4] = {o->u - rad, o->u + rad, o->v - rad, o->v + rad};
-    const double m = 2e-4; /* pixel margin of the rectangle edges */
+    const double mu_ = o->err_u, mv_ = o->err_v; /* pixel margins of the rectangle edges */
     int empty = ex[1] < 0 || ex[0] >= c->width || ex[3] < 0 || ex[2] >= c->height;
-    if (fabs(o->u + rad_lo) <= m || fabs(o->u + rad_hi) <= m || fabs(o->u - rad_lo - c->width) <= m
-        || fabs(o->u - rad_hi - c->width) <= m || fabs(o->v + rad_lo) <= m || fabs(o->v + rad_hi) <= m
-        || fabs(o->v - rad_lo - c->height) <= m || fabs(o->v - rad_hi - c->height) <= m
+    if (fabs(o->u + rad_lo) <= mu_ || fabs(o->u + rad_hi) <= mu_ || fabs(o->u - rad_lo - c->width) <= mu_
+        || fabs(o->u - rad_hi - c->width) <= mu_ || fabs(o->v + rad_lo) <= mv_ || fabs(o->v + rad_hi) <= mv_
+        || fabs(o->v - rad_lo - c->height) <= mv_ || fabs(o->v - rad_hi - c->height) <= mv_
         || (rad_lo != rad_hi && ((o->u + rad_lo < 0) != (o->u + rad_hi < 0)
                                  || (o->u - rad_lo >= c->width) != (o->u - rad_hi >= c->width)
                                  || (o->v + rad_lo < 0) != (o->v + rad_hi < 0)
@@ -192,16 +202,16 @@ static void project_one(const orc_camera *c, const double Rcw[9], const double t
         o->vis_amb = 1;
     }
     /* possible edge tiles under the margins */
-    o->ox0 = imax(0, (int)floor((o->u - rad_hi - m) / c->tile_w));
-    o->ix0 = imax(0, (int)floor((o->u - rad_lo + m) / c->tile_w));
-    o->ix1 = imin(tiles_x - 1, (int)floor((o->u + rad_lo - m) / c->tile_w));
-    o->ox1 = imin(tiles_x - 1, (int)floor((o->u + rad_hi + m) / c->tile_w));
-    o->oy0 = imax(0, (int)floor((o->v - rad_hi - m) / c->tile_h));
-    o->iy0 = imax(0, (int)floor((o->v - rad_lo + m) / c->tile_h));
-    o->iy1 = imin(tiles_y - 1, (int)floor((o->v + rad_lo - m) / c->tile_h));
-    o->oy1 = imin(tiles_y - 1, (int)floor((o->v + rad_hi + m) / c->tile_h));
+    o->ox0 = imax(0, (int)floor((o->u - rad_hi - mu_) / c->tile_w));
+    o->ix0 = imax(0, (int)floor((o->u - rad_lo + mu_) / c->tile_w));
+    o->ix1 = imin(tiles_x - 1, (int)floor((o->u + rad_lo - mu_) / c->tile_w));
+    o->ox1 = imin(tiles_x - 1, (int)floor((o->u + rad_hi + mu_) / c->tile_w));
+    o->oy0 = imax(0, (int)floor((o->v - rad_hi - mv_) / c->tile_h));
+    o->iy0 = imax(0, (int)floor((o->v - rad_lo + mv_) / c->tile_h));
+    o->iy1 = imin(tiles_y - 1, (int)floor((o->v + rad_lo - mv_) / c->tile_h));
+    o->oy1 = imin(tiles_y - 1, (int)floor((o->v + rad_hi + mv_) / c->tile_h));
     if (o->ox0 != o->ix0 || o->ox1 != o->ix1 || o->oy0 != o->iy0 || o->oy1 != o->iy1) o->amb |= 1;
-    if (empty) return;
+    if (empty || pz <= c->z_near) return;
     o->x0 = imax(0, (int)floor(ex[0] / c->tile_w));
     o->x1 = imin(tiles_x - 1, (int)floor(ex[1] / c->tile_w));
     o->y0 = imax(0, (int)floor(ex[2] / c->tile_h));
@@ -279,15 +289,11 @@ static void free_lists(olists *L)
     free(L->gid);
 }
 
-/* float depths within 4 ulp are flagged as an order near-tie */
-static int depth_near_tie(double a, double b)
+/* two depths whose order a float32 evaluation may swap: within the sum of
+ * their error bounds plus 2 ulp of float */
+static int depth_near_tie(double a, double ea, double b, double eb)
 {
-    float fa = (float)a, fb = (float)b;
-    int32_t ia, ib;
-    memcpy(&ia, &fa, 4);
-    memcpy(&ib, &fb, 4);
-    int64_t d = (int64_t)ia - (int64_t)ib;
-    return d <= 4 && d >= -4;
+    return fabs(a - b) <= ea + eb + 2.5e-7 * fmax(fabs(a), fabs(b));
 }
 
 /* Tiles whose list membership may differ because a projection decision is
@@ -364,7 +370,8 @@ int64_t orc_bin(int64_t n, const double *mean, const double *log_scale, const do
         if (near_tie)
             for (int64_t t = 0; t < L.n_tiles; ++t)
                 for (int64_t k = L.start[t]; k < L.start[t + 1]; ++k)
-                    near_tie[k] = (k > L.start[t]) && depth_near_tie(P[L.gid[k]].depth, P[L.gid[k - 1]].depth);
+                    near_tie[k] = (k > L.start[t]) && depth_near_tie(P[L.gid[k]].depth, P[L.gid[k]].err_z,
+                                                                     P[L.gid[k - 1]].depth, P[L.gid[k - 1]].err_z);
     } else {
         total = -1;
     }
@@ -393,7 +400,7 @@ static void blend_pixel(const orc_camera *cam, const oproj *P, const double *rgb
     int32_t lastpos = -1, nc = 0;
     int64_t ne = 0;
     int a = 0, have_prev = 0;
-    double prev_depth = 0, eps = cam->amb_rel;
+    double prev_depth = 0, prev_err = 0, eps = cam->amb_rel;
     C[0] = C[1] = C[2] = 0;
     *D = 0;
     for (int64_t k = 0; k < len; ++k) {
@@ -407,17 +414,22 @@ static void blend_pixel(const orc_camera *cam, const oproj *P, const double *rgb
         if (sigma < 0) continue;
         double ex = exp(-sigma);
         double G = g->opacity * ex; /* alpha_j = o_j exp(-sigma_j) */
-        if (fabs(G - ALPHA_MIN) <= eps * ALPHA_MIN) a |= 1;
-        if (fabs(G - ALPHA_MAX) <= eps * ALPHA_MAX) a |= 2;
+        /* relative error bound of G from the float32 error of (u, v) */
+        double es = fabs(g->conic[0] * dx + g->conic[1] * dy) * g->err_u
+                  + fabs(g->conic[1] * dx + g->conic[2] * dy) * g->err_v;
+        double mg = eps + es;
+        if (fabs(G - ALPHA_MIN) <= mg * ALPHA_MIN) a |= 1;
+        if (fabs(G - ALPHA_MAX) <= mg * ALPHA_MAX) a |= 2;
         int clamped = G > ALPHA_MAX;
         double alpha = clamped ? ALPHA_MAX : G;
         if (alpha < ALPHA_MIN) continue;
         double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - T_STOP) <= eps * T_STOP) a |= 1;
+        if (fabs(Tn - T_STOP) <= (eps + mg * alpha / (1.0 - alpha)) * T_STOP) a |= 1;
         if (Tn < T_STOP) break;
         a |= g->amb & 2;
-        if (have_prev && depth_near_tie(prev_depth, g->depth)) a |= 1;
+        if (have_prev && depth_near_tie(prev_depth, prev_err, g->depth, g->err_z)) a |= 1;
         prev_depth = g->depth;
+        prev_err = g->err_z;
         have_prev = 1;
         if (trace) {
             ocontrib *t = &trace[nc];

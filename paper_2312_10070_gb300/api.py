@@ -1,0 +1,336 @@
+"""Python binding of the C ABI (include/gsr.h) over PyTorch tensors.
+
+Functions carry the names of the C entry points (without the ``gsr_``
+prefix).  PyTorch supplies device memory and the current CUDA stream; all
+computation happens in libgsr.so.  Tensors must be float32 (int32 where
+stated), contiguous and on the context's CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """Owns a gsr_ctx (scratch, tile lists, graphs) on the current device."""
+
+    def __init__(self, tile=(16, 16), batch=256, memory_saving=False, fixed_capacity=False, max_gaussians=0,
+                 max_instances=0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the GB300 rasterizer needs a CUDA device; there is no CPU fallback")
+        self.lib = L.load()
+        o = L.Options()
+        self.lib.gsr_default_options(ctypes.byref(o))
+        o.tile_w, o.tile_h = tile
+        o.batch = batch
+        o.memory_saving = int(memory_saving)
+        o.fixed_capacity = int(fixed_capacity)
+        o.max_gaussians = max_gaussians
+        o.max_instances = max_instances
+        self.options = o
+        h = ctypes.c_void_p()
+        L.check(self.lib.gsr_create(ctypes.byref(h), ctypes.byref(o)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.gsr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, status):
+        L.check(status, self.handle)
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.gsr_kernel_launches(self.handle))
+
+
+PHASES = ("bin", "blend_fwd", "loss", "blend_bwd", "project_bwd", "adam")
+
+
+def profile_enable(ctx: Context, on: bool = True):
+    ctx.check(ctx.lib.gsr_profile_enable(ctx.handle, int(on)))
+
+
+def profile_read(ctx: Context) -> dict:
+    """Elapsed ms of each phase in its latest execution (gsr_profile_read)."""
+    ms = (ctypes.c_float * len(PHASES))()
+    ctx.check(ctx.lib.gsr_profile_read(ctx.handle, ms, len(PHASES), _stream()))
+    return {k: float(v) for k, v in zip(PHASES, ms)}
+
+
+def make_camera(width, height, fx, fy, cx, cy, z_near=0.2, eps2d=0.3) -> L.Camera:
+    return L.Camera(int(width), int(height), float(fx), float(fy), float(cx), float(cy), float(z_near), float(eps2d))
+
+
+def camera_from_spec(spec, **kw) -> L.Camera:
+    return make_camera(spec.width, spec.height, spec.fx, spec.fy, spec.cx, spec.cy, **kw)
+
+
+def make_pose(q, t) -> L.Pose:
+    q = [float(x) for x in np.asarray(q, np.float64).reshape(4)]
+    t = [float(x) for x in np.asarray(t, np.float64).reshape(3)]
+    return L.Pose((ctypes.c_float * 4)(*q), (ctypes.c_float * 3)(*t))
+
+
+@dataclass
+class GaussianParams:
+    """Gaussian parameters (SoA, float32, CUDA)."""
+    mean: torch.Tensor
+    log_scale: torch.Tensor
+    quat: torch.Tensor
+    opacity_logit: torch.Tensor
+    rgb: torch.Tensor
+
+    NAMES = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
+
+    @classmethod
+    def from_numpy(cls, d: dict, device="cuda"):
+        return cls(*[torch.as_tensor(np.ascontiguousarray(d[k]), dtype=torch.float32, device=device)
+                     for k in cls.NAMES])
+
+    @property
+    def n(self) -> int:
+        return int(self.mean.shape[0])
+
+    def tensors(self):
+        return [getattr(self, k) for k in self.NAMES]
+
+    def clone(self):
+        return GaussianParams(*[t.clone() for t in self.tensors()])
+
+    def zeros_like(self):
+        return GaussianParams(*[torch.zeros_like(t) for t in self.tensors()])
+
+    def c(self) -> L.Gaussians:
+        return L.Gaussians(*[_ptr(t) for t in self.tensors()], self.n)
+
+    def c_mut(self) -> L.GaussiansMut:
+        return L.GaussiansMut(*[_ptr(t) for t in self.tensors()], self.n)
+
+    def c_grads(self) -> L.GaussianGrads:
+        return L.GaussianGrads(*[_ptr(t) for t in self.tensors()])
+
+
+def render_forward(ctx: Context, g: GaussianParams, cam: L.Camera, pose: L.Pose, want_n_contrib=False) -> dict:
+    """gsr_render_forward: rgb [3,H,W], depth, alpha, final_T, last_idx (int32)."""
+    H, W = cam.height, cam.width
+    dev = g.mean.device
+    out = dict(rgb=torch.empty((3, H, W), device=dev), depth=torch.empty((H, W), device=dev),
+               alpha=torch.empty((H, W), device=dev), final_T=torch.empty((H, W), device=dev),
+               last_idx=torch.empty((H, W), dtype=torch.int32, device=dev),
+               n_contrib=torch.empty((H, W), dtype=torch.int32, device=dev) if want_n_contrib else None)
+    ro = L.RenderOut(*[_ptr(out[k]) for k in ("rgb", "depth", "alpha", "final_T", "last_idx", "n_contrib")])
+    ctx.check(ctx.lib.gsr_render_forward(ctx.handle, ctypes.byref(g.c()), ctypes.byref(cam), ctypes.byref(pose),
+                                         ctypes.byref(ro), _stream()))
+    return out
+
+
+def frame_stats(ctx: Context) -> dict:
+    st = L.FrameStats()
+    ctx.check(ctx.lib.gsr_frame_stats_get(ctx.handle, ctypes.byref(st), _stream()))
+    return dict(n_visible=st.n_visible, n_instances=st.n_instances, n_tiles=st.n_tiles,
+                capacity_instances=st.capacity_instances)
+
+
+def tile_lists(ctx: Context, n_tiles: int, n_gaussians: int, capacity: int = None):
+    """gsr_tile_lists_get: (ranges uint32 [n_tiles, 2], gids int32 [I], depth bits uint32 [n])."""
+    st = frame_stats(ctx)
+    cap = int(st["n_instances"]) if capacity is None else capacity
+    ranges = np.zeros((n_tiles, 2), np.uint32)
+    gids = np.zeros(max(cap, 1), np.int32)
+    dbits = np.zeros(max(n_gaussians, 1), np.uint32)
+    ni = ctypes.c_int64()
+    ctx.check(ctx.lib.gsr_tile_lists_get(ctx.handle, ranges.ctypes.data_as(ctypes.c_void_p),
+                                         gids.ctypes.data_as(ctypes.c_void_p), cap,
+                                         dbits.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ni), _stream()))
+    return ranges, gids[:ni.value], dbits[:n_gaussians]
+
+
+def render_backward(ctx: Context, g: GaussianParams, cam: L.Camera, pose: L.Pose, saved: dict, d_rgb=None,
+                    d_depth=None, d_alpha=None, want_params=True, want_pose=True, out: GaussianParams = None):
+    """gsr_render_backward: returns (GaussianParams of gradients or None, pose6 tensor or None)."""
+    grads = None
+    if want_params:
+        grads = out if out is not None else g.zeros_like()
+    pose6 = torch.empty(6, device=g.mean.device) if want_pose else None
+    ro = L.RenderOut(None, None, None, _ptr(saved["final_T"]), _ptr(saved["last_idx"]), None)
+    gg = grads.c_grads() if grads is not None else None
+    ctx.check(ctx.lib.gsr_render_backward(ctx.handle, ctypes.byref(g.c()), ctypes.byref(cam), ctypes.byref(pose),
+                                          ctypes.byref(ro), _ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha),
+                                          ctypes.byref(gg) if gg is not None else None, _ptr(pose6), _stream()))
+    return grads, pose6
+
+
+def loss_map(ctx: Context, rgb, depth, rgb_t, depth_t, lambda_ssim=0.2, w_color=1.0, w_depth=1.0, scale=1.0):
+    """gsr_loss_map: returns (loss [1] device tensor, d_rgb, d_depth)."""
+    _, H, W = rgb.shape
+    d_rgb, d_depth = torch.empty_like(rgb), torch.empty_like(depth)
+    loss = torch.empty(1, device=rgb.device)
+    ctx.check(ctx.lib.gsr_loss_map(ctx.handle, W, H, _ptr(rgb), _ptr(depth), _ptr(rgb_t), _ptr(depth_t),
+                                   lambda_ssim, w_color, w_depth, scale, _ptr(d_rgb), _ptr(d_depth), _ptr(loss),
+                                   _stream()))
+    return loss, d_rgb, d_depth
+
+
+def loss_track(ctx: Context, rgb, depth, alpha, rgb_t, depth_t, lambda_c=0.5, k_median=50.0, alpha_pow=3.0):
+    """gsr_loss_track: returns (loss [1], median [1], d_rgb, d_depth)."""
+    _, H, W = rgb.shape
+    d_rgb, d_depth = torch.empty_like(rgb), torch.empty_like(depth)
+    loss = torch.empty(1, device=rgb.device)
+    med = torch.empty(1, device=rgb.device)
+    ctx.check(ctx.lib.gsr_loss_track(ctx.handle, W, H, _ptr(rgb), _ptr(depth), _ptr(alpha), _ptr(rgb_t),
+                                     _ptr(depth_t), lambda_c, k_median, alpha_pow, _ptr(d_rgb), _ptr(d_depth),
+                                     _ptr(loss), _ptr(med), _stream()))
+    return loss, med, d_rgb, d_depth
+
+
+@dataclass
+class AdamConfig:
+    """Learning rates per parameter group (the paper names none; these are
+    configurable defaults), betas, eps and the L_reg weight (1, Sec. 4)."""
+    lr_mean: float = 1e-4
+    lr_log_scale: float = 5e-3
+    lr_quat: float = 1e-3
+    lr_opacity: float = 5e-2
+    lr_rgb: float = 2.5e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+    w_reg: float = 1.0
+
+    def c(self) -> L.AdamOpts:
+        return L.AdamOpts(self.lr_mean, self.lr_log_scale, self.lr_quat, self.lr_opacity, self.lr_rgb,
+                          self.beta1, self.beta2, self.eps, self.w_reg)
+
+
+class AdamMoments:
+    """First/second moments (same layout as the parameters) and a device step."""
+
+    def __init__(self, g: GaussianParams):
+        self.m = g.zeros_like()
+        self.v = g.zeros_like()
+        self.step = torch.zeros(1, dtype=torch.int32, device=g.mean.device)
+
+    def c(self) -> L.AdamState:
+        return L.AdamState(*[_ptr(t) for t in self.m.tensors()], *[_ptr(t) for t in self.v.tensors()],
+                           _ptr(self.step))
+
+
+def adam_step(ctx: Context, g: GaussianParams, grads: GaussianParams, state: AdamMoments, cfg: AdamConfig,
+              loss_reg=None):
+    """gsr_adam_step (in place).  loss_reg: optional [1] tensor that receives += w_reg L_reg."""
+    ctx.check(ctx.lib.gsr_adam_step(ctx.handle, ctypes.byref(g.c_mut()), ctypes.byref(grads.c_grads()),
+                                    ctypes.byref(state.c()), ctypes.byref(cfg.c()), _ptr(loss_reg), _stream()))
+
+
+@dataclass
+class TrackConfig:
+    lambda_c: float = 0.5
+    k_median: float = 50.0
+    alpha_pow: float = 3.0
+    lr_rho: float = 2e-3
+    lr_phi: float = 2e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+    use_graph: bool = True
+
+    def c(self) -> L.TrackOpts:
+        return L.TrackOpts(self.lambda_c, self.k_median, self.alpha_pow, self.lr_rho, self.lr_phi, self.beta1,
+                           self.beta2, self.eps, int(self.use_graph))
+
+
+def track_step(ctx: Context, g: GaussianParams, cam: L.Camera, rgb_in, depth_in, pose: L.Pose, n_iters: int,
+               cfg: TrackConfig = None):
+    """gsr_track_step: returns (pose after tracking, dict of stats).  Synchronising."""
+    cfg = cfg or TrackConfig()
+    p = L.Pose(pose.q, pose.t)
+    st = L.TrackStats()
+    ctx.check(ctx.lib.gsr_track_step(ctx.handle, ctypes.byref(g.c()), ctypes.byref(cam), _ptr(rgb_in),
+                                     _ptr(depth_in), ctypes.byref(p), int(n_iters), ctypes.byref(cfg.c()),
+                                     ctypes.byref(st), _stream()))
+    return p, dict(loss_first=st.loss_first, loss_last=st.loss_last, iters=st.iters)
+
+
+@dataclass
+class MapConfig:
+    lambda_ssim: float = 0.2
+    w_color: float = 1.0
+    w_depth: float = 1.0
+    adam: AdamConfig = field(default_factory=AdamConfig)
+    use_graph: bool = True
+
+    def c(self) -> L.MapOpts:
+        return L.MapOpts(self.lambda_ssim, self.w_color, self.w_depth, self.adam.c(), int(self.use_graph))
+
+
+def map_step(ctx: Context, g: GaussianParams, state: AdamMoments, cam: L.Camera, keyframes, weights=None,
+             n_iters: int = 1, cfg: MapConfig = None, want_stats=True):
+    """gsr_map_step over keyframes = [(pose, rgb [3,H,W], depth [H,W]), ...]."""
+    cfg = cfg or MapConfig()
+    kfs = (L.Keyframe * len(keyframes))()
+    for i, (pose, rgb, depth) in enumerate(keyframes):
+        kfs[i] = L.Keyframe(pose, _ptr(rgb), _ptr(depth))
+    w = None
+    if weights is not None:
+        w = (ctypes.c_float * len(keyframes))(*[float(x) for x in weights])
+    st = L.MapStats()
+    ctx.check(ctx.lib.gsr_map_step(ctx.handle, ctypes.byref(g.c_mut()), ctypes.byref(state.c()), ctypes.byref(cam),
+                                   kfs, len(keyframes), ctypes.cast(w, ctypes.c_void_p) if w is not None else None,
+                                   int(n_iters), ctypes.byref(cfg.c()), ctypes.byref(st) if want_stats else None,
+                                   _stream()))
+    return dict(loss_last=st.loss_last, iters=st.iters) if want_stats else None
+
+
+# ----------------------------------------------------------- pose helpers
+def quat_mul(a, b):
+    aw, ax, ay, az = a
+    bw, bx, by, bz = b
+    return np.array([aw * bw - ax * bx - ay * by - az * bz, aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx, aw * bz + ax * by - ay * bx + az * bw])
+
+
+def pose_exp_left(q, t, xi):
+    """exp(xi^) T on the host (xi = (rho, phi)); used by the autograd wrapper."""
+    xi = np.asarray(xi, np.float64)
+    rho, phi = xi[:3], xi[3:]
+    th = float(np.linalg.norm(phi))
+    K = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+    if th < 1e-8:
+        A, B, C = 1.0, 0.5, 1.0 / 6.0
+        dq = np.array([1.0, *(0.5 * phi)])
+    else:
+        A, B, C = math.sin(th) / th, (1 - math.cos(th)) / th ** 2, (th - math.sin(th)) / th ** 3
+        dq = np.array([math.cos(th / 2), *(math.sin(th / 2) / th * phi)])
+    Rd = np.eye(3) + A * K + B * K @ K
+    V = np.eye(3) + B * K + C * K @ K
+    qn = quat_mul(dq, np.asarray(q, np.float64))
+    qn /= np.linalg.norm(qn)
+    if qn[0] < 0:
+        qn = -qn
+    return qn, Rd @ np.asarray(t, np.float64) + V @ rho

@@ -1,0 +1,195 @@
+// adam.cu -- optimiser steps.
+//
+// Gaussians: bias-corrected Adam on the 14 parameters of every Gaussian with
+// the gradient of the isotropic regulariser L_reg (Sec. 3.4) fused in:
+//   L_reg = (1/n) sum_k |s_k - mean(s_k)|_1,  s = exp(log_scale).
+// The step counter lives in device memory so that a captured CUDA graph can
+// be replayed: a one-thread kernel advances it and writes the bias
+// corrections before the update kernel reads them.
+//
+// Pose (tracking, Sec. 3.5): Adam on the twist of a left perturbation, then
+// the retraction T <- exp(delta^) T with the closed-form SE(3) exponential.
+#include <math.h>
+
+#include "gsr_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ float sgnf(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
+
+__global__ void k_adam_prep(int32_t *step, float b1, float b2, float *bc)
+{
+    int t = *step + 1;
+    *step = t;
+    bc[0] = 1.f - powf(b1, (float)t);
+    bc[1] = 1.f - powf(b2, (float)t);
+}
+
+__device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, float lr, float b1, float b2, float eps,
+                                      float bc1, float bc2)
+{
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+}
+
+__global__ void __launch_bounds__(256) k_adam(gsr_gaussians_mut g, gsr_gaussian_grads gr, gsr_adam_state st,
+                                              gsr_adam_opts o, const float *__restrict__ bc, float *__restrict__ part)
+{
+    int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    float lreg = 0.f;
+    if (i < g.n) {
+        const float bc1 = bc[0], bc2 = bc[1];
+        // isotropic regulariser on the activated scales
+        float s[3], sb = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            s[k] = expf(g.log_scale[3 * i + k]);
+            sb += s[k];
+        }
+        sb *= (1.f / 3.f);
+        float sg[3], ssum = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lreg += fabsf(s[k] - sb);
+            sg[k] = sgnf(s[k] - sb);
+            ssum += sg[k];
+        }
+        const float rw = o.w_reg / (float)g.n;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            int64_t j = 3 * i + k;
+            adam1(g.mean[j], gr.mean[j], st.m_mean[j], st.v_mean[j], o.lr_mean, o.beta1, o.beta2, o.eps, bc1, bc2);
+            float gl = gr.log_scale[j] + rw * (sg[k] - ssum * (1.f / 3.f)) * s[k];
+            adam1(g.log_scale[j], gl, st.m_log_scale[j], st.v_log_scale[j], o.lr_log_scale, o.beta1, o.beta2, o.eps,
+                  bc1, bc2);
+            adam1(g.rgb[j], gr.rgb[j], st.m_rgb[j], st.v_rgb[j], o.lr_rgb, o.beta1, o.beta2, o.eps, bc1, bc2);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int64_t j = 4 * i + k;
+            adam1(g.quat[j], gr.quat[j], st.m_quat[j], st.v_quat[j], o.lr_quat, o.beta1, o.beta2, o.eps, bc1, bc2);
+        }
+        adam1(g.opacity_logit[i], gr.opacity_logit[i], st.m_opacity_logit[i], st.v_opacity_logit[i], o.lr_opacity,
+              o.beta1, o.beta2, o.eps, bc1, bc2);
+    }
+    if (part) {
+        __shared__ float red[8];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) lreg += __shfl_down_sync(0xffffffffu, lreg, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lreg;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int k = 0; k < 8; ++k) t += red[k];
+            part[blockIdx.x] = t;
+        }
+    }
+}
+
+__global__ void k_lreg_final(const float *__restrict__ part, int nb, float scale, float *out)
+{
+    __shared__ float red[32];
+    float v = 0.f;
+    for (int b = threadIdx.x; b < nb; b += 1024) v += part[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int k = 0; k < 32; ++k) t += red[k];
+        *out += scale * t;
+    }
+}
+
+// Adam on the 6-vector twist, then T <- exp(delta^) T (q, t stored on device)
+__global__ void k_pose_adam(float *pose, const float *__restrict__ g6, float *m6, float *v6, int32_t *step,
+                            float lr_rho, float lr_phi, float b1, float b2, float eps)
+{
+    const int t = *step + 1;
+    *step = t;
+    const float bc1 = 1.f - powf(b1, (float)t), bc2 = 1.f - powf(b2, (float)t);
+    float d[6];
+    for (int k = 0; k < 6; ++k) {
+        float g = g6[k];
+        m6[k] = b1 * m6[k] + (1.f - b1) * g;
+        v6[k] = b2 * v6[k] + (1.f - b2) * g * g;
+        float lr = k < 3 ? lr_rho : lr_phi;
+        d[k] = -lr * (m6[k] / bc1) / (sqrtf(v6[k] / bc2) + eps);
+    }
+    // SE(3) exponential: rotation quaternion of phi, V = I + B [phi]x + C [phi]x^2
+    const float wx = d[3], wy = d[4], wz = d[5];
+    const float th2 = wx * wx + wy * wy + wz * wz, th = sqrtf(th2);
+    float B, C, qs, qv;
+    if (th < 1e-4f) {
+        B = 0.5f - th2 / 24.f;
+        C = 1.f / 6.f - th2 / 120.f;
+        qs = 1.f - th2 / 8.f;
+        qv = 0.5f - th2 / 48.f;
+    } else {
+        B = (1.f - cosf(th)) / th2;
+        C = (th - sinf(th)) / (th2 * th);
+        qs = cosf(0.5f * th);
+        qv = sinf(0.5f * th) / th;
+    }
+    const float dq[4] = {qs, qv * wx, qv * wy, qv * wz};
+    float Rd[9];
+    quat_rot(dq[0], dq[1], dq[2], dq[3], Rd);
+    const float K[9] = {0.f, -wz, wy, wz, 0.f, -wx, -wy, wx, 0.f};
+    float K2[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) K2[3 * r + c] = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+    float tn[3];
+    for (int r = 0; r < 3; ++r) {
+        float vr = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            float Vrc = (r == c ? 1.f : 0.f) + B * K[3 * r + c] + C * K2[3 * r + c];
+            vr += Vrc * d[c];
+        }
+        tn[r] = Rd[3 * r] * pose[4] + Rd[3 * r + 1] * pose[5] + Rd[3 * r + 2] * pose[6] + vr;
+    }
+    // q <- dq * q (Hamilton product), renormalised
+    const float aw = dq[0], ax = dq[1], ay = dq[2], az = dq[3];
+    const float bw = pose[0], bx = pose[1], by = pose[2], bz = pose[3];
+    float q[4] = {aw * bw - ax * bx - ay * by - az * bz, aw * bx + ax * bw + ay * bz - az * by,
+                  aw * by - ax * bz + ay * bw + az * bx, aw * bz + ax * by - ay * bx + az * bw};
+    float inv = 1.f / sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (q[0] < 0.f) inv = -inv;
+    for (int k = 0; k < 4; ++k) pose[k] = q[k] * inv;
+    for (int k = 0; k < 3; ++k) pose[4 + k] = tn[k];
+    pose_rotation_split(pose);
+}
+
+} // namespace
+
+gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads *gr, gsr_adam_state *st,
+                    const gsr_adam_opts *o, float *loss_reg_dev, cudaStream_t s)
+{
+    const unsigned nb = (unsigned)ceil_div(g->n > 0 ? g->n : 1, 256);
+    GSR_TRY(ensure_buf(ctx, ctx->small, 256 * sizeof(float)));
+    float *bc = (float *)ctx->small.p;  // [0..1] bias corrections
+    float *part = nullptr;
+    if (loss_reg_dev) {
+        GSR_TRY(ensure_buf(ctx, ctx->pose_part, sizeof(float) * 6 * nb));
+        part = (float *)ctx->pose_part.p;
+    }
+    k_adam_prep<<<1, 1, 0, s>>>(st->step, o->beta1, o->beta2, bc);
+    k_adam<<<nb, 256, 0, s>>>(*g, *gr, *st, *o, bc, part);
+    ctx->launches += 2;
+    if (loss_reg_dev) {
+        k_lreg_final<<<1, 1024, 0, s>>>(part, (int)nb, o->w_reg / (float)(g->n > 0 ? g->n : 1), loss_reg_dev);
+        ctx->launches += 1;
+    }
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+gsr_status run_pose_adam(gsr_ctx *ctx, float *d_pose, const float *d_grad6, float *m6, float *v6, int32_t *step,
+                         float lr_rho, float lr_phi, float b1, float b2, float eps, cudaStream_t s)
+{
+    k_pose_adam<<<1, 1, 0, s>>>(d_pose, d_grad6, m6, v6, step, lr_rho, lr_phi, b1, b2, eps);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}

@@ -1,0 +1,231 @@
+// gsr_internal.cuh -- internal declarations of the GB300 (sm_103a) rasterizer.
+// Not part of the ABI; the public interface is include/gsr.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gsr.h"
+
+typedef uint32_t u32;
+
+// ----------------------------------------------------------------- constants
+// Blend decisions (the same constants in forward and backward).
+#define GSR_ALPHA_MIN (1.0f / 255.0f)
+#define GSR_ALPHA_MAX 0.99f
+#define GSR_T_STOP 1e-4f
+#define GSR_GUARD 1.3f
+
+// Device status word bits.
+#define GSR_FLAG_CAPACITY 1u
+#define GSR_FLAG_NONFINITE 2u
+
+// Counters block layout (u32 words in ctx->counters).
+enum {
+    CNT_VISIBLE = 0,   // V of the current view
+    CNT_INSTANCES = 1, // I (before clamping to capacity)
+    CNT_SORTN = 2,     // min(I, capacity): instances actually sorted
+    CNT_STATUS = 3,    // sticky status bits
+    CNT_NVALID = 4,    // valid target depth pixels of the last mapping loss
+    CNT_TRACK_N = 5,   // valid pixels of the tracking loss
+    CNT_SEL = 6,       // radix-select state: [6] prefix bits, [7] remaining rank
+    CNT_WORDS = 16
+};
+
+// --------------------------------------------------------------- scratch
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Per-view scratch of the projection/binning/blend pipeline.
+struct ViewScratch {
+    DevBuf rec;         // float4 x3 per Gaussian id: (u,v,ca,cb) (cc,o,z,rect_lo) (r,g,b,rect_hi)
+    DevBuf flag;        // u32 per Gaussian id: 1 = visible
+    DevBuf compact;     // u32 per Gaussian id: exclusive scan of flag
+    DevBuf rank_of_gid; // int32 per Gaussian id: depth rank, -1 = culled
+    DevBuf dkeys[2];    // u32 depth keys (ping-pong)
+    DevBuf dvals[2];    // u32 Gaussian ids
+    DevBuf rec_sorted;  // float4 x3 per depth rank
+    DevBuf tcount;      // u32 tiles touched per rank
+    DevBuf inst_off;    // u32 exclusive scan of tcount
+    DevBuf tkeys[2];    // u32 tile id per instance
+    DevBuf tvals[2];    // u32 depth rank per instance
+    DevBuf ranges;      // uint2 per tile
+    DevBuf g2d;         // float x12 per rank: image-space gradients
+    DevBuf counters;    // u32[CNT_WORDS]
+    DevBuf pose;        // float[8]: q(4), t(3)
+    int64_t cap_n = 0, cap_i = 0, cap_t = 0;
+    // identity of the last forward, to decide whether the saved lists are valid
+    uint64_t generation = 0;
+};
+
+struct gsr_ctx {
+    gsr_options opt;
+    int device = 0;
+    std::string err;
+    int64_t launches = 0;
+    uint64_t generation = 0;
+    ViewScratch view;
+    // generic scratch
+    DevBuf scan_tmp;     // block sums of device scans
+    DevBuf radix_hist;   // per-block digit histograms
+    DevBuf pose_part;    // per-block pose partial sums
+    DevBuf loss_part;    // per-block loss partial sums
+    DevBuf loss_maps;    // SSIM adjoint maps [9,H,W] / tracking residual
+    DevBuf img_tmp;      // images of iterative loops
+    DevBuf small;        // misc device scalars (losses, Adam state of the pose)
+    DevBuf grads;        // gradients of map_step [n,14]
+    // forward identity
+    const float *fwd_ptrs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int64_t fwd_n = -1;
+    gsr_camera fwd_cam{};
+    gsr_pose fwd_pose{};
+    // graphs
+    cudaGraphExec_t track_graph = nullptr;
+    uint64_t track_key = 0;
+    cudaGraphExec_t map_graph = nullptr;
+    uint64_t map_key = 0, map_sized_key = 0;
+    int64_t track_graph_kernels = 0, map_graph_kernels = 0;
+    // per-phase CUDA events (profiling mode)
+    bool prof = false;
+    cudaEvent_t prof_ev[2 * 8] = {};
+    u32 *host_pinned = nullptr; // small pinned readback buffer
+};
+
+// -------------------------------------------------------------- host helpers
+gsr_status gsr_fail(gsr_ctx *ctx, gsr_status s, const std::string &msg);
+gsr_status gsr_cuda_check(gsr_ctx *ctx, cudaError_t e, const char *what);
+gsr_status ensure_buf(gsr_ctx *ctx, DevBuf &b, size_t bytes);
+void free_buf(DevBuf &b);
+
+#define GSR_TRY(expr)                          \
+    do {                                       \
+        gsr_status _s = (expr);                \
+        if (_s != GSR_OK) return _s;           \
+    } while (0)
+#define GSR_CUDA(ctx, expr) GSR_TRY(gsr_cuda_check((ctx), (expr), #expr))
+#define GSR_LAUNCHED(ctx) GSR_TRY(gsr_cuda_check((ctx), cudaGetLastError(), "kernel launch"))
+
+static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// --------------------------------------------------------- scan / radix sort
+// Device-wide exclusive scan of u32.  The element count is min(*d_n, n_cap)
+// when d_n is given, else n_cap.  The total is written to *d_total (nullable).
+gsr_status scan_exclusive(gsr_ctx *ctx, const u32 *in, u32 *out, int64_t n_cap, const u32 *d_n,
+                          u32 *d_total, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on key bits [0, bits), 8 bits
+// per pass.  The element count is read on the device from *d_n (<= n_cap).
+// The sorted pairs end in keys[0]/vals[0].
+gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_cap, const u32 *d_n,
+                            int bits, cudaStream_t s);
+
+// ------------------------------------------------------------ device math
+struct CamK {
+    int W, H, tw, th, tiles_x, tiles_y;
+    float fx, fy, cx, cy, z_near, eps2d, limx, limy;
+};
+
+CamK make_camk(const gsr_camera &c, int tw, int th);
+
+__device__ __forceinline__ void quat_rot(float qw, float qx, float qy, float qz, float R[9])
+{
+    R[0] = 1.f - 2.f * (qy * qy + qz * qz);
+    R[1] = 2.f * (qx * qy - qw * qz);
+    R[2] = 2.f * (qx * qz + qw * qy);
+    R[3] = 2.f * (qx * qy + qw * qz);
+    R[4] = 1.f - 2.f * (qx * qx + qz * qz);
+    R[5] = 2.f * (qy * qz - qw * qx);
+    R[6] = 2.f * (qx * qz - qw * qy);
+    R[7] = 2.f * (qy * qz + qw * qx);
+    R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+}
+
+// Device pose record: q(4) t(3) pad(1) R_hi(9) R_lo(9); see project.cu.
+#define GSR_POSE_WORDS 32
+
+// Forms R(q/|q|) in double precision from pose[0..3] and stores its float
+// hi/lo split in pose[8..25] (one thread).
+__device__ __forceinline__ void pose_rotation_split(float *pose)
+{
+    double w = pose[0], x = pose[1], y = pose[2], z = pose[3];
+    double n = sqrt(w * w + x * x + y * y + z * z);
+    w /= n;
+    x /= n;
+    y /= n;
+    z /= n;
+    double R[9] = {1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z),       2.0 * (x * z + w * y),
+                   2.0 * (x * y + w * z),       1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x),
+                   2.0 * (x * z - w * y),       2.0 * (y * z + w * x),       1.0 - 2.0 * (x * x + y * y)};
+    for (int k = 0; k < 9; ++k) {
+        float hi = (float)R[k];
+        pose[8 + k] = hi;
+        pose[17 + k] = (float)(R[k] - (double)hi);
+    }
+}
+
+// Image-space evaluation of one Gaussian at one pixel.  Every operation is an
+// explicitly rounded intrinsic so that the forward and the backward kernels,
+// which both call it, take bit-identical skip decisions.
+struct Eval {
+    float dx, dy, ex, G, alpha;
+    bool use;  // composited (before the transmittance test)
+};
+
+__device__ __forceinline__ Eval eval_gaussian(float px, float py, float u, float v, float ca, float cb,
+                                              float cc, float op)
+{
+    Eval e;
+    e.dx = __fsub_rn(px, u);
+    e.dy = __fsub_rn(py, v);
+    float q = __fmaf_rn(ca, __fmul_rn(e.dx, e.dx), __fmul_rn(cc, __fmul_rn(e.dy, e.dy)));
+    float sigma = __fmaf_rn(cb, __fmul_rn(e.dx, e.dy), __fmul_rn(0.5f, q));
+    e.ex = __expf(-sigma);
+    e.G = __fmul_rn(op, e.ex);
+    e.alpha = fminf(GSR_ALPHA_MAX, e.G);
+    e.use = (sigma >= 0.f) && (e.alpha >= GSR_ALPHA_MIN);
+    return e;
+}
+
+// --------------------------------------------------------------- launchers
+struct Params {
+    const float *mean, *log_scale, *quat, *opacity_logit, *rgb;
+    int64_t n;
+};
+
+gsr_status launch_set_pose(gsr_ctx *ctx, float *d_pose, const gsr_pose &p, cudaStream_t s);
+// Projection + binning into ctx->view; returns after enqueueing (no sync)
+gsr_status run_binning(gsr_ctx *ctx, const Params &P, const CamK &ck, const float *d_pose,
+                       bool allow_grow, cudaStream_t s);
+gsr_status run_blend_forward(gsr_ctx *ctx, const Params &P, const CamK &ck, gsr_render_out *out,
+                             cudaStream_t s);
+gsr_status run_blend_backward(gsr_ctx *ctx, const CamK &ck, const gsr_render_out *saved,
+                              const float *d_rgb, const float *d_depth, const float *d_alpha,
+                              bool pose_only, cudaStream_t s);
+// chain image-space gradients to parameters; accumulate = add w * grad into
+// the outputs instead of overwriting them.
+gsr_status run_project_backward(gsr_ctx *ctx, const Params &P, const CamK &ck, const float *d_pose,
+                                gsr_gaussian_grads *dg, float *d_pose6, bool accumulate,
+                                float weight, cudaStream_t s);
+gsr_status run_loss_map(gsr_ctx *ctx, int W, int H, const float *rgb, const float *depth,
+                        const float *rgb_t, const float *depth_t, float lam, float wc, float wd,
+                        float scale, float *d_rgb, float *d_depth, float *loss_dev, bool accumulate_loss,
+                        cudaStream_t s);
+gsr_status run_loss_track(gsr_ctx *ctx, int W, int H, const float *rgb, const float *depth,
+                          const float *alpha, const float *rgb_t, const float *depth_t, float lam_c,
+                          float k_med, float apow, float *d_rgb, float *d_depth, float *loss_dev,
+                          float *median_dev, cudaStream_t s);
+gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads *gr,
+                    gsr_adam_state *st, const gsr_adam_opts *o, float *loss_reg_dev, cudaStream_t s);
+gsr_status run_pose_adam(gsr_ctx *ctx, float *d_pose, const float *d_grad6, float *m6, float *v6,
+                         int32_t *step, float lr_rho, float lr_phi, float b1, float b2, float eps,
+                         cudaStream_t s);
+gsr_status copy_tile_lists(gsr_ctx *ctx, int64_t n, int64_t n_tiles, u32 *ranges_h, int32_t *gids_h,
+                           int64_t capacity, u32 *depth_h, int64_t *n_inst, cudaStream_t s);
+
+// profiling phases
+enum { PROF_BIN = 0, PROF_FWD = 1, PROF_LOSS = 2, PROF_BWD = 3, PROF_PBWD = 4, PROF_ADAM = 5, PROF_NSLOT = 6 };
+// records the start (end = false) or end event of a phase on `s` when profiling
+gsr_status prof_mark(gsr_ctx *ctx, int phase, bool end, cudaStream_t s);

@@ -1,0 +1,411 @@
+// loss.cu -- fused per-pixel losses and their image gradients.
+//
+// Mapping (Sec. 3.4, Eqs. (depth_loss), (color_loss), (joint_loss)):
+//   L = w_c [(1-lam) mean|I^-I| + lam (1 - SSIM)] + w_d mean_valid |D^-D|
+// SSIM uses the 11x11 Gaussian window (sigma 1.5) of Wang et al. with zero
+// padding, C1 = 0.01^2, C2 = 0.03^2, averaged over pixels and channels.  Two
+// kernels: the first forms the five window sums per channel from a 26x26
+// shared-memory tile (separable passes), the SSIM value and the adjoint maps
+// dS/dmu_x, dS/dE[x^2], dS/dE[xy]; the second blurs the adjoint maps with the
+// same (symmetric) window and assembles dL/dI^ and dL/dD^.
+//
+// Tracking (Sec. 3.5, supplementary Sec. B):
+//   L = sum M_inlier alpha^3 (lam_c sum_ch |I^-I| + (1-lam_c)|D^-D|)
+// with the lower median of |D^-D| over valid pixels found exactly by a
+// 4-pass 8-bit radix select on the float bits.
+//
+// Reductions are deterministic: per-block partials, then one ordered pass.
+#include <algorithm>
+
+#include "gsr_internal.cuh"
+
+namespace {
+
+constexpr int ST = 16;            // output tile
+constexpr int SHALO = 5;          // window radius
+constexpr int SW = ST + 2 * SHALO;
+
+__device__ __forceinline__ float sgnf(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
+
+__device__ __forceinline__ void load_window(float *wk)
+{
+    // 11 taps of exp(-k^2 / (2 * 1.5^2)), normalised to sum 1
+    if (threadIdx.x < 11) {
+        float k = (float)threadIdx.x - 5.f;
+        wk[threadIdx.x] = expf(-k * k / 4.5f);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int k = 0; k < 11; ++k) s += wk[k];
+        for (int k = 0; k < 11; ++k) wk[k] /= s;
+    }
+    __syncthreads();
+}
+
+// block sum of NV values over 256 threads; thread 0 gets the totals
+template <int NV>
+__device__ __forceinline__ void block_sum256(float (&v)[NV])
+{
+    __shared__ float red[NV][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float x = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[i][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            float x = 0.f;
+            for (int k = 0; k < 8; ++k) x += red[i][k];
+            v[i] = x;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ssim_fwd(int W, int H, const float *__restrict__ x, const float *__restrict__ y,
+                                                  const float *__restrict__ dep, const float *__restrict__ dep_t,
+                                                  float gscale, float *__restrict__ P, float *__restrict__ part,
+                                                  u32 *__restrict__ nvalid)
+{
+    __shared__ float wk[11];
+    __shared__ float sx[SW][SW], sy[SW][SW];
+    __shared__ float hq[5][SW][ST];
+    load_window(wk);
+    const int ox = blockIdx.x * ST, oy = blockIdx.y * ST;
+    const int r = threadIdx.x / ST, c = threadIdx.x % ST;
+    const int gx = ox + c, gy = oy + r;
+    const bool inside = gx < W && gy < H;
+    const int64_t HW = (int64_t)W * H, p = (int64_t)gy * W + gx;
+    const float C1 = 1e-4f, C2 = 9e-4f;
+    float acc[3] = {0.f, 0.f, 0.f};  // SSIM sum, |x - y| sum, valid |D^ - D| sum
+    for (int ch = 0; ch < 3; ++ch) {
+        for (int i = threadIdx.x; i < SW * SW; i += 256) {
+            int rr = i / SW, cc = i % SW;
+            int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
+            bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
+            int64_t q = (int64_t)ch * HW + (int64_t)yy * W + xx;
+            sx[rr][cc] = ok ? x[q] : 0.f;
+            sy[rr][cc] = ok ? y[q] : 0.f;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < SW * ST; i += 256) {
+            int rr = i / ST, cc = i % ST;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                float xv = sx[rr][cc + k], yv = sy[rr][cc + k], w = wk[k];
+                a0 = fmaf(w, xv, a0);
+                a1 = fmaf(w, yv, a1);
+                a2 = fmaf(w, xv * xv, a2);
+                a3 = fmaf(w, yv * yv, a3);
+                a4 = fmaf(w, xv * yv, a4);
+            }
+            hq[0][rr][cc] = a0;
+            hq[1][rr][cc] = a1;
+            hq[2][rr][cc] = a2;
+            hq[3][rr][cc] = a3;
+            hq[4][rr][cc] = a4;
+        }
+        __syncthreads();
+        float m1 = 0.f, m2 = 0.f, e11 = 0.f, e22 = 0.f, e12 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            float w = wk[k];
+            m1 = fmaf(w, hq[0][r + k][c], m1);
+            m2 = fmaf(w, hq[1][r + k][c], m2);
+            e11 = fmaf(w, hq[2][r + k][c], e11);
+            e22 = fmaf(w, hq[3][r + k][c], e22);
+            e12 = fmaf(w, hq[4][r + k][c], e12);
+        }
+        if (inside) {
+            float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * (e12 - m1 * m2) + C2;
+            float B1 = m1 * m1 + m2 * m2 + C1, B2 = (e11 - m1 * m1) + (e22 - m2 * m2) + C2;
+            float iB = 1.f / (B1 * B2);
+            float S = A1 * A2 * iB;
+            acc[0] += S;
+            float xv = sx[r + SHALO][c + SHALO], yv = sy[r + SHALO][c + SHALO];
+            acc[1] += fabsf(xv - yv);
+            P[(3 * ch + 0) * HW + p] = gscale * (2.f * m2 * (A2 - A1) * iB - 2.f * m1 * S * (1.f / B1 - 1.f / B2));
+            P[(3 * ch + 1) * HW + p] = gscale * (-S / B2);
+            P[(3 * ch + 2) * HW + p] = gscale * (2.f * A1 * iB);
+        }
+        __syncthreads();
+    }
+    bool valid = false;
+    if (inside) {
+        float dt = dep_t[p];
+        valid = dt > 0.f;
+        if (valid) acc[2] = fabsf(dep[p] - dt);
+    }
+    u32 bal = __ballot_sync(0xffffffffu, valid);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(nvalid, (u32)__popc(bal));
+    block_sum256<3>(acc);
+    if (threadIdx.x == 0) {
+        int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        part[3 * b] = acc[0];
+        part[3 * b + 1] = acc[1];
+        part[3 * b + 2] = acc[2];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ssim_bwd(int W, int H, const float *__restrict__ x, const float *__restrict__ y,
+                                                  const float *__restrict__ dep, const float *__restrict__ dep_t,
+                                                  const float *__restrict__ P, float l1s, float dscale,
+                                                  const u32 *__restrict__ nvalid, float *__restrict__ d_rgb,
+                                                  float *__restrict__ d_dep)
+{
+    __shared__ float wk[11];
+    __shared__ float sp[3][SW][SW];
+    __shared__ float hq[3][SW][ST];
+    load_window(wk);
+    const int ox = blockIdx.x * ST, oy = blockIdx.y * ST;
+    const int r = threadIdx.x / ST, c = threadIdx.x % ST;
+    const int gx = ox + c, gy = oy + r;
+    const bool inside = gx < W && gy < H;
+    const int64_t HW = (int64_t)W * H, p = (int64_t)gy * W + gx;
+    for (int ch = 0; ch < 3; ++ch) {
+        for (int i = threadIdx.x; i < SW * SW; i += 256) {
+            int rr = i / SW, cc = i % SW;
+            int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
+            bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
+            int64_t q = (int64_t)yy * W + xx;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) sp[m][rr][cc] = ok ? P[(3 * ch + m) * HW + q] : 0.f;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < SW * ST; i += 256) {
+            int rr = i / ST, cc = i % ST;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                float w = wk[k];
+                a0 = fmaf(w, sp[0][rr][cc + k], a0);
+                a1 = fmaf(w, sp[1][rr][cc + k], a1);
+                a2 = fmaf(w, sp[2][rr][cc + k], a2);
+            }
+            hq[0][rr][cc] = a0;
+            hq[1][rr][cc] = a1;
+            hq[2][rr][cc] = a2;
+        }
+        __syncthreads();
+        float b1 = 0.f, b2 = 0.f, b3 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            float w = wk[k];
+            b1 = fmaf(w, hq[0][r + k][c], b1);
+            b2 = fmaf(w, hq[1][r + k][c], b2);
+            b3 = fmaf(w, hq[2][r + k][c], b3);
+        }
+        if (inside) {
+            float xv = x[ch * HW + p], yv = y[ch * HW + p];
+            d_rgb[ch * HW + p] = l1s * sgnf(xv - yv) + b1 + 2.f * xv * b2 + yv * b3;
+        }
+        __syncthreads();
+    }
+    if (inside) {
+        u32 nv = *nvalid;
+        float dt = dep_t[p];
+        d_dep[p] = (dt > 0.f && nv > 0) ? dscale * sgnf(dep[p] - dt) / (float)nv : 0.f;
+    }
+}
+
+__global__ void k_loss_map_final(const float *__restrict__ part, int nb, const u32 *__restrict__ nvalid, float inv3hw,
+                                 float lam, float wc, float wd, float scale, float *loss, int accumulate,
+                                 u32 *status)
+{
+    __shared__ float red[3][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 3 warps
+    float v = 0.f;
+    for (int b = lane; b < nb; b += 32) v += part[3 * b + w];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w][0] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float ssim = red[0][0] * inv3hw, l1c = red[1][0] * inv3hw;
+        u32 nv = *nvalid;
+        float l1d = nv > 0 ? red[2][0] / (float)nv : 0.f;
+        float L = scale * (wc * ((1.f - lam) * l1c + lam * (1.f - ssim)) + wd * l1d);
+        if (!isfinite(L)) atomicOr(status, GSR_FLAG_NONFINITE);
+        if (loss) {
+            if (accumulate) *loss += L;
+            else *loss = L;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- tracking
+__global__ void k_track_resid(int64_t HW, const float *__restrict__ dep, const float *__restrict__ dep_t,
+                              u32 *__restrict__ ebits, u32 *__restrict__ nvalid)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = false;
+    if (p < HW) {
+        float dt = dep_t[p];
+        valid = dt > 0.f;
+        ebits[p] = valid ? __float_as_uint(fabsf(dep[p] - dt)) : 0xffffffffu;
+    }
+    u32 bal = __ballot_sync(0xffffffffu, valid);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(nvalid, (u32)__popc(bal));
+}
+
+// state: sel[0] = prefix bits, sel[1] = remaining rank
+__global__ void k_sel_init(const u32 *__restrict__ nvalid, u32 *__restrict__ sel, u32 *__restrict__ hist)
+{
+    u32 n = *nvalid;
+    if (threadIdx.x == 0) {
+        sel[0] = 0u;
+        sel[1] = n > 0 ? (n - 1u) / 2u : 0u;
+    }
+    hist[threadIdx.x] = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_sel_hist(int64_t HW, const u32 *__restrict__ ebits, int shift,
+                                                  const u32 *__restrict__ sel, u32 *__restrict__ hist)
+{
+    __shared__ u32 h[256];
+    h[threadIdx.x] = 0u;
+    __syncthreads();
+    const u32 prefix = sel[0];
+    const u32 hmask = shift == 24 ? 0u : (0xffffffffu << (shift + 8));
+    for (int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x; p < HW; p += (int64_t)gridDim.x * 256) {
+        u32 b = ebits[p];
+        if (b != 0xffffffffu && (b & hmask) == (prefix & hmask)) atomicAdd(&h[(b >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) k_sel_pick(int shift, u32 *__restrict__ sel, u32 *__restrict__ hist)
+{
+    __shared__ u32 s[256];
+    const u32 v = hist[threadIdx.x];
+    s[threadIdx.x] = v;
+    __syncthreads();
+    // inclusive scan (Hillis-Steele, 256 entries)
+    for (int o = 1; o < 256; o <<= 1) {
+        u32 t = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0u;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    const u32 k = sel[1];
+    const u32 incl = s[threadIdx.x], excl = incl - v;
+    __syncthreads();
+    if (v > 0 && excl <= k && k < incl) {
+        sel[0] |= (u32)threadIdx.x << shift;
+        sel[1] = k - excl;
+    }
+    hist[threadIdx.x] = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_track_loss(int64_t HW, const float *__restrict__ rgb, const float *__restrict__ dep,
+                                                    const float *__restrict__ alpha, const float *__restrict__ rgb_t,
+                                                    const float *__restrict__ dep_t, const u32 *__restrict__ sel,
+                                                    const u32 *__restrict__ nvalid, float lam_c, float k_med,
+                                                    float apow, float *__restrict__ d_rgb, float *__restrict__ d_dep,
+                                                    float *__restrict__ part)
+{
+    int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    float acc[1] = {0.f};
+    if (p < HW) {
+        const float med = *nvalid > 0 ? __uint_as_float(sel[0]) : 0.f;
+        float dt = dep_t[p], dh = dep[p];
+        float e = fabsf(dh - dt);
+        bool in = dt > 0.f && e <= k_med * med;
+        float a = alpha[p];
+        float w = 0.f;
+        if (in) w = (apow == 3.f) ? a * a * a : powf(a, apow);
+        float lc = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float diff = rgb[ch * HW + p] - rgb_t[ch * HW + p];
+            lc += fabsf(diff);
+            d_rgb[ch * HW + p] = w * lam_c * sgnf(diff);
+        }
+        d_dep[p] = w * (1.f - lam_c) * sgnf(dh - dt);
+        acc[0] = w * (lam_c * lc + (1.f - lam_c) * e);
+    }
+    block_sum256<1>(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
+}
+
+__global__ void k_track_final(const float *__restrict__ part, int nb, const u32 *__restrict__ sel,
+                              const u32 *__restrict__ nvalid, float *loss, float *median, u32 *status)
+{
+    __shared__ float red[32];
+    float v = 0.f;
+    for (int b = threadIdx.x; b < nb; b += 1024) v += part[b];
+    // fixed-order block reduction over 1024 threads
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float L = 0.f;
+        for (int k = 0; k < 32; ++k) L += red[k];
+        if (!isfinite(L)) atomicOr(status, GSR_FLAG_NONFINITE);
+        if (loss) *loss = L;
+        if (median) *median = *nvalid > 0 ? __uint_as_float(sel[0]) : 0.f;
+    }
+}
+
+} // namespace
+
+gsr_status run_loss_map(gsr_ctx *ctx, int W, int H, const float *rgb, const float *depth, const float *rgb_t,
+                        const float *depth_t, float lam, float wc, float wd, float scale, float *d_rgb,
+                        float *d_depth, float *loss_dev, bool accumulate_loss, cudaStream_t s)
+{
+    const int64_t HW = (int64_t)W * H;
+    dim3 grid((unsigned)ceil_div(W, ST), (unsigned)ceil_div(H, ST));
+    const int nb = (int)(grid.x * grid.y);
+    GSR_TRY(ensure_buf(ctx, ctx->loss_maps, sizeof(float) * 9 * (size_t)HW));
+    GSR_TRY(ensure_buf(ctx, ctx->loss_part, sizeof(float) * 3 * (size_t)nb));
+    GSR_TRY(ensure_buf(ctx, ctx->view.counters, sizeof(u32) * CNT_WORDS));
+    u32 *cnt = (u32 *)ctx->view.counters.p;
+    GSR_CUDA(ctx, cudaMemsetAsync(cnt + CNT_NVALID, 0, sizeof(u32), s));
+    const float inv3hw = 1.f / (3.f * (float)HW);
+    k_ssim_fwd<<<grid, 256, 0, s>>>(W, H, rgb, rgb_t, depth, depth_t, -scale * wc * lam * inv3hw,
+                                    (float *)ctx->loss_maps.p, (float *)ctx->loss_part.p, cnt + CNT_NVALID);
+    k_ssim_bwd<<<grid, 256, 0, s>>>(W, H, rgb, rgb_t, depth, depth_t, (float *)ctx->loss_maps.p,
+                                    scale * wc * (1.f - lam) * inv3hw, scale * wd, cnt + CNT_NVALID, d_rgb, d_depth);
+    k_loss_map_final<<<1, 96, 0, s>>>((float *)ctx->loss_part.p, nb, cnt + CNT_NVALID, inv3hw, lam, wc, wd, scale,
+                                      loss_dev, accumulate_loss ? 1 : 0, cnt + CNT_STATUS);
+    ctx->launches += 3;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+gsr_status run_loss_track(gsr_ctx *ctx, int W, int H, const float *rgb, const float *depth, const float *alpha,
+                          const float *rgb_t, const float *depth_t, float lam_c, float k_med, float apow,
+                          float *d_rgb, float *d_depth, float *loss_dev, float *median_dev, cudaStream_t s)
+{
+    const int64_t HW = (int64_t)W * H;
+    const unsigned nb = (unsigned)ceil_div(HW, 256);
+    GSR_TRY(ensure_buf(ctx, ctx->loss_maps, sizeof(u32) * (size_t)HW + sizeof(u32) * 256));
+    GSR_TRY(ensure_buf(ctx, ctx->loss_part, sizeof(float) * nb));
+    GSR_TRY(ensure_buf(ctx, ctx->view.counters, sizeof(u32) * CNT_WORDS));
+    u32 *cnt = (u32 *)ctx->view.counters.p;
+    u32 *ebits = (u32 *)ctx->loss_maps.p;
+    u32 *hist = ebits + HW;
+    GSR_CUDA(ctx, cudaMemsetAsync(cnt + CNT_TRACK_N, 0, sizeof(u32), s));
+    k_track_resid<<<nb, 256, 0, s>>>(HW, depth, depth_t, ebits, cnt + CNT_TRACK_N);
+    k_sel_init<<<1, 256, 0, s>>>(cnt + CNT_TRACK_N, cnt + CNT_SEL, hist);
+    const unsigned hb = (unsigned)std::min<int64_t>(nb, 1216);
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        k_sel_hist<<<hb, 256, 0, s>>>(HW, ebits, shift, cnt + CNT_SEL, hist);
+        k_sel_pick<<<1, 256, 0, s>>>(shift, cnt + CNT_SEL, hist);
+    }
+    k_track_loss<<<nb, 256, 0, s>>>(HW, rgb, depth, alpha, rgb_t, depth_t, cnt + CNT_SEL, cnt + CNT_TRACK_N, lam_c,
+                                    k_med, apow, d_rgb, d_depth, (float *)ctx->loss_part.p);
+    k_track_final<<<1, 1024, 0, s>>>((float *)ctx->loss_part.p, (int)nb, cnt + CNT_SEL, cnt + CNT_TRACK_N, loss_dev,
+                                     median_dev, cnt + CNT_STATUS);
+    ctx->launches += 12;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}

@@ -1,0 +1,611 @@
+// project.cu -- per-Gaussian projection (Sec. 3.1), tile binning glue and
+// the projection backward with the 6-DoF pose adjoint.
+//
+// Numerics: the 2D covariance is formed as Sigma' = T T^T + eps I with
+// T = J W M (M = R diag(s), W = R_wc), so a and c are sums of squares and
+// det(Sigma') = |T_0 x T_1|^2 + eps (|T_0|^2 + |T_1|^2) + eps^2 (Lagrange's
+// identity) is a sum of positive terms: no cancellation for thin Gaussians.
+#include "gsr_internal.cuh"
+
+CamK make_camk(const gsr_camera &c, int tw, int th)
+{
+    CamK k;
+    k.W = c.width;
+    k.H = c.height;
+    k.tw = tw;
+    k.th = th;
+    k.tiles_x = (c.width + tw - 1) / tw;
+    k.tiles_y = (c.height + th - 1) / th;
+    k.fx = c.fx;
+    k.fy = c.fy;
+    k.cx = c.cx;
+    k.cy = c.cy;
+    k.z_near = c.z_near;
+    k.eps2d = c.eps2d;
+    k.limx = GSR_GUARD * 0.5f * (float)c.width / c.fx;
+    k.limy = GSR_GUARD * 0.5f * (float)c.height / c.fy;
+    return k;
+}
+
+namespace {
+
+// Device pose record (float[GSR_POSE_WORDS]): q (4), t (3), pad, then the
+// rotation R(q / |q|) formed in double precision and split into float
+// hi + lo parts (9 + 9).  The camera transform p = R mu + t is evaluated as
+// a compensated dot product on the FP32 pipe, so p is faithfully rounded:
+// the depth keys equal the float rounding of the exact depth except within
+// one ulp, and u, v carry no cancellation error from large world coordinates.
+struct PoseR {
+    float R[9], Rlo[9], t[3];
+};
+
+__device__ __forceinline__ PoseR load_pose(const float *__restrict__ pose)
+{
+    PoseR P;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        P.R[k] = pose[8 + k];
+        P.Rlo[k] = pose[17 + k];
+    }
+    P.t[0] = pose[4];
+    P.t[1] = pose[5];
+    P.t[2] = pose[6];
+    return P;
+}
+
+// error-free transformations (Knuth two-sum, FMA two-product)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (R_hi + R_lo) . x + t, compensated (Ogita-Rump-Oishi Dot2 with the lo parts)
+__device__ __forceinline__ float dot3_comp(const float *Rh, const float *Rl, float x0, float x1, float x2, float t)
+{
+    float p = __fmul_rn(Rh[0], x0);
+    float s = __fmaf_rn(Rh[0], x0, -p);
+    float h, r, q;
+    h = __fmul_rn(Rh[1], x1);
+    r = __fmaf_rn(Rh[1], x1, -h);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, r));
+    h = __fmul_rn(Rh[2], x2);
+    r = __fmaf_rn(Rh[2], x2, -h);
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, r));
+    two_sum(p, t, p, q);
+    s = __fadd_rn(s, q);
+    s = __fmaf_rn(Rl[0], x0, s);
+    s = __fmaf_rn(Rl[1], x1, s);
+    s = __fmaf_rn(Rl[2], x2, s);
+    return __fadd_rn(p, s);
+}
+
+// Full forward state of one Gaussian, recomputed by the backward.
+struct GProj {
+    float p[3];       // camera-space mean
+    float R[9];       // Gaussian rotation (normalised quaternion)
+    float qh[4], qn;  // normalised quaternion and |q|
+    float s[3];       // scales
+    float A[9];       // W M
+    float J[6];
+    float T[6];       // J W M (2x3)
+    float tx, ty;
+    bool clx, cly;
+    float a, b, c;    // Sigma' entries (with eps)
+    float det;
+    float op;
+};
+
+// returns false when culled by depth
+__device__ __forceinline__ bool project_core(const CamK &ck, const PoseR &P, const float *__restrict__ mean,
+                                             const float *__restrict__ ls, const float *__restrict__ quat,
+                                             float logit, int64_t i, GProj &g)
+{
+    float mx = mean[3 * i], my = mean[3 * i + 1], mz = mean[3 * i + 2];
+    g.p[0] = dot3_comp(P.R, P.Rlo, mx, my, mz, P.t[0]);
+    g.p[1] = dot3_comp(P.R + 3, P.Rlo + 3, mx, my, mz, P.t[1]);
+    g.p[2] = dot3_comp(P.R + 6, P.Rlo + 6, mx, my, mz, P.t[2]);
+    g.op = 1.f / (1.f + expf(-logit));
+    if (!(g.p[2] > ck.z_near)) return false;
+    float qw = quat[4 * i], qx = quat[4 * i + 1], qy = quat[4 * i + 2], qz = quat[4 * i + 3];
+    g.qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    float inv = 1.f / g.qn;
+    g.qh[0] = qw * inv;
+    g.qh[1] = qx * inv;
+    g.qh[2] = qy * inv;
+    g.qh[3] = qz * inv;
+    quat_rot(g.qh[0], g.qh[1], g.qh[2], g.qh[3], g.R);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g.s[k] = expf(ls[3 * i + k]);
+    // A = W R diag(s)
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            g.A[3 * r + k] = (P.R[3 * r] * g.R[k] + P.R[3 * r + 1] * g.R[3 + k] + P.R[3 * r + 2] * g.R[6 + k]) * g.s[k];
+    float iz = 1.f / g.p[2];
+    float tx = g.p[0] * iz, ty = g.p[1] * iz;
+    g.clx = fabsf(tx) > ck.limx;
+    g.cly = fabsf(ty) > ck.limy;
+    g.tx = fminf(fmaxf(tx, -ck.limx), ck.limx);
+    g.ty = fminf(fmaxf(ty, -ck.limy), ck.limy);
+    g.J[0] = ck.fx * iz;
+    g.J[1] = 0.f;
+    g.J[2] = -ck.fx * g.tx * iz;
+    g.J[3] = 0.f;
+    g.J[4] = ck.fy * iz;
+    g.J[5] = -ck.fy * g.ty * iz;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        g.T[k] = fmaf(g.J[0], g.A[k], g.J[2] * g.A[6 + k]);
+        g.T[3 + k] = fmaf(g.J[4], g.A[3 + k], g.J[5] * g.A[6 + k]);
+    }
+    float a0 = g.T[0] * g.T[0] + g.T[1] * g.T[1] + g.T[2] * g.T[2];
+    float c0 = g.T[3] * g.T[3] + g.T[4] * g.T[4] + g.T[5] * g.T[5];
+    g.a = a0 + ck.eps2d;
+    g.c = c0 + ck.eps2d;
+    g.b = g.T[0] * g.T[3] + g.T[1] * g.T[4] + g.T[2] * g.T[5];
+    float x0 = g.T[1] * g.T[5] - g.T[2] * g.T[4];
+    float x1 = g.T[2] * g.T[3] - g.T[0] * g.T[5];
+    float x2 = g.T[0] * g.T[4] - g.T[1] * g.T[3];
+    g.det = (x0 * x0 + x1 * x1 + x2 * x2) + ck.eps2d * (a0 + c0) + ck.eps2d * ck.eps2d;
+    return true;
+}
+
+__global__ void k_set_pose(float *d, gsr_pose p)
+{
+    d[0] = p.q[0];
+    d[1] = p.q[1];
+    d[2] = p.q[2];
+    d[3] = p.q[3];
+    d[4] = p.t[0];
+    d[5] = p.t[1];
+    d[6] = p.t[2];
+    d[7] = 0.f;
+    pose_rotation_split(d);
+}
+
+// K1: projection, culling, radius, tile rectangle.  rec[gid] holds
+// (u, v, conic a, conic b) (conic c, opacity, depth, rect lo) (r, g, b, rect hi).
+__global__ void __launch_bounds__(256) k_project(Params P, CamK ck, const float *__restrict__ pose,
+                                                 float4 *__restrict__ rec, u32 *__restrict__ flag,
+                                                 int32_t *__restrict__ rank_of_gid)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    PoseR pr = load_pose(pose);
+    GProj g;
+    u32 vis = 0;
+    rank_of_gid[i] = -1;
+    if (project_core(ck, pr, P.mean, P.log_scale, P.quat, P.opacity_logit[i], i, g) && g.det > 0.f) {
+        float idet = 1.f / g.det;
+        float hm = 0.5f * (g.a + g.c), hd = 0.5f * (g.a - g.c);
+        float lmax = hm + sqrtf(hd * hd + g.b * g.b);
+        float r = ceilf(3.f * sqrtf(lmax));
+        float iz = 1.f / g.p[2];
+        float u = fmaf(ck.fx, g.p[0] * iz, ck.cx);
+        float v = fmaf(ck.fy, g.p[1] * iz, ck.cy);
+        if (!(u + r < 0.f || u - r >= (float)ck.W || v + r < 0.f || v - r >= (float)ck.H)) {
+            int x0 = max(0, (int)floorf((u - r) / (float)ck.tw));
+            int x1 = min(ck.tiles_x - 1, (int)floorf((u + r) / (float)ck.tw));
+            int y0 = max(0, (int)floorf((v - r) / (float)ck.th));
+            int y1 = min(ck.tiles_y - 1, (int)floorf((v + r) / (float)ck.th));
+            vis = 1;
+            rec[3 * i] = make_float4(u, v, g.c * idet, -g.b * idet);
+            rec[3 * i + 1] = make_float4(g.a * idet, g.op, g.p[2], __uint_as_float((u32)x0 | ((u32)y0 << 16)));
+            rec[3 * i + 2] = make_float4(P.rgb[3 * i], P.rgb[3 * i + 1], P.rgb[3 * i + 2],
+                                         __uint_as_float((u32)x1 | ((u32)y1 << 16)));
+        }
+    }
+    flag[i] = vis;
+}
+
+// stable compaction of visible Gaussians: depth key + id
+__global__ void k_compact(int64_t n, const u32 *__restrict__ flag, const u32 *__restrict__ off,
+                          const float4 *__restrict__ rec, u32 *__restrict__ keys, u32 *__restrict__ vals)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flag[i]) return;
+    u32 o = off[i];
+    keys[o] = __float_as_uint(rec[3 * i + 1].z);  // positive depth: bit order = value order
+    vals[o] = (u32)i;
+}
+
+// records in depth order; tiles touched per rank
+__global__ void k_gather(int64_t cap, const u32 *__restrict__ d_v, const u32 *__restrict__ vals,
+                         const float4 *__restrict__ rec, float4 *__restrict__ rec_sorted,
+                         int32_t *__restrict__ rank_of_gid, u32 *__restrict__ tcount)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= cap || r >= (int64_t)*d_v) return;
+    u32 gid = vals[r];
+    float4 a = rec[3 * (int64_t)gid], b = rec[3 * (int64_t)gid + 1], c = rec[3 * (int64_t)gid + 2];
+    rec_sorted[3 * r] = a;
+    rec_sorted[3 * r + 1] = b;
+    rec_sorted[3 * r + 2] = c;
+    rank_of_gid[gid] = (int32_t)r;
+    u32 lo = __float_as_uint(b.w), hi = __float_as_uint(c.w);
+    u32 w = (hi & 0xffffu) - (lo & 0xffffu) + 1u, h = (hi >> 16) - (lo >> 16) + 1u;
+    tcount[r] = w * h;
+}
+
+// one instance (tile id, depth rank) per tile of each rectangle; the stream is
+// in depth order, so a stable sort on the tile id yields depth-ordered lists
+__global__ void k_emit(int64_t cap_v, const u32 *__restrict__ d_v, const float4 *__restrict__ rec_sorted,
+                       const u32 *__restrict__ off, int tiles_x, int64_t cap_i, u32 *__restrict__ tkeys,
+                       u32 *__restrict__ tvals, u32 *__restrict__ counters)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) {
+        u32 total = counters[CNT_INSTANCES];
+        counters[CNT_SORTN] = (int64_t)total > cap_i ? (u32)cap_i : total;
+        if ((int64_t)total > cap_i) atomicOr(&counters[CNT_STATUS], GSR_FLAG_CAPACITY);
+    }
+    if (r >= cap_v || r >= (int64_t)*d_v) return;
+    u32 lo = __float_as_uint(rec_sorted[3 * r + 1].w), hi = __float_as_uint(rec_sorted[3 * r + 2].w);
+    int x0 = lo & 0xffff, y0 = lo >> 16, x1 = hi & 0xffff, y1 = hi >> 16;
+    int64_t o = off[r];
+    for (int y = y0; y <= y1; ++y)
+        for (int x = x0; x <= x1; ++x, ++o)
+            if (o < cap_i) {
+                tkeys[o] = (u32)(y * tiles_x + x);
+                tvals[o] = (u32)r;
+            }
+}
+
+__global__ void k_ranges(int64_t cap_i, const u32 *__restrict__ d_n, const u32 *__restrict__ tkeys,
+                         uint2 *__restrict__ ranges)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t n = *d_n;
+    if (i >= n || i >= cap_i) return;
+    u32 t = tkeys[i];
+    if (i == 0 || tkeys[i - 1] != t) ranges[t].x = (u32)i;
+    if (i == n - 1 || tkeys[i + 1] != t) ranges[t].y = (u32)(i + 1);
+}
+
+// --------------------------------------------------------------- backward
+// K6: image-space gradients g2 = (u, v, conic a, b, c, opacity, r, g, b, z)
+// -> parameter gradients and per-Gaussian pose adjoint (left perturbation).
+template <bool WANT_PARAMS>
+__global__ void __launch_bounds__(256) k_project_bwd(Params P, CamK ck, const float *__restrict__ pose,
+                                                     const int32_t *__restrict__ rank_of_gid,
+                                                     const float *__restrict__ g2d, gsr_gaussian_grads dg,
+                                                     int accumulate, float weight,
+                                                     float *__restrict__ pose_part)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float gpose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < P.n) {
+        int32_t r = rank_of_gid[i];
+        float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+        float glog = 0.f, grgb[3] = {0.f, 0.f, 0.f};
+        if (r >= 0) {
+            PoseR pr = load_pose(pose);
+            GProj g;
+            project_core(ck, pr, P.mean, P.log_scale, P.quat, P.opacity_logit[i], i, g);
+            const float4 *G4 = reinterpret_cast<const float4 *>(g2d + 12 * (int64_t)r);
+            float4 q0 = G4[0], q1 = G4[1], q2 = G4[2];
+            float gu = q0.x, gv = q0.y, gca = q0.z, gcb = q0.w, gcc = q1.x, gop = q1.y;
+            grgb[0] = q1.z;
+            grgb[1] = q1.w;
+            grgb[2] = q2.x;
+            float gz = q2.y;
+            glog = gop * g.op * (1.f - g.op);
+            // conic Q = S^-1: G_S = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]]
+            float idet = 1.f / g.det;
+            float Qa = g.c * idet, Qb = -g.b * idet, Qc = g.a * idet;
+            float hb = 0.5f * gcb;
+            float t00 = Qa * gca + Qb * hb, t01 = Qa * hb + Qb * gcc;
+            float t10 = Qb * gca + Qc * hb, t11 = Qb * hb + Qc * gcc;
+            float S00 = -(t00 * Qa + t01 * Qb), S01 = -(t00 * Qb + t01 * Qc);
+            float S11 = -(t10 * Qb + t11 * Qc);
+            // S = T T^T + eps I  ->  G_T = 2 G_S T
+            float GT[6];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                GT[k] = 2.f * (S00 * g.T[k] + S01 * g.T[3 + k]);
+                GT[3 + k] = 2.f * (S01 * g.T[k] + S11 * g.T[3 + k]);
+            }
+            // T = J A -> G_J = G_T A^T (only J00, J02, J11, J12 depend on p), G_A = J^T G_T
+            float GJ00 = GT[0] * g.A[0] + GT[1] * g.A[1] + GT[2] * g.A[2];
+            float GJ02 = GT[0] * g.A[6] + GT[1] * g.A[7] + GT[2] * g.A[8];
+            float GJ11 = GT[3] * g.A[3] + GT[4] * g.A[4] + GT[5] * g.A[5];
+            float GJ12 = GT[3] * g.A[6] + GT[4] * g.A[7] + GT[5] * g.A[8];
+            float GA[9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                GA[k] = g.J[0] * GT[k];
+                GA[3 + k] = g.J[4] * GT[3 + k];
+                GA[6 + k] = g.J[2] * GT[k] + g.J[5] * GT[3 + k];
+            }
+            float px = g.p[0], py = g.p[1], pz = g.p[2];
+            float iz = 1.f / pz, iz2 = iz * iz;
+            float gp0 = gu * ck.fx * iz;
+            float gp1 = gv * ck.fy * iz;
+            float gp2 = -(gu * ck.fx * px + gv * ck.fy * py) * iz2 + gz;
+            gp2 += GJ00 * (-ck.fx * iz2) + GJ02 * (ck.fx * g.tx * iz2) + GJ11 * (-ck.fy * iz2)
+                 + GJ12 * (ck.fy * g.ty * iz2);
+            float gtx = GJ02 * (-ck.fx * iz), gty = GJ12 * (-ck.fy * iz);
+            if (!g.clx) {
+                gp0 += gtx * iz;
+                gp2 -= gtx * px * iz2;
+            }
+            if (!g.cly) {
+                gp1 += gty * iz;
+                gp2 -= gty * py * iz2;
+            }
+            // pose: rho = g_p, phi = p x g_p + vee(G_W W^T), G_W W^T = G_A A^T
+            float Y[9];
+#pragma unroll
+            for (int r2 = 0; r2 < 3; ++r2)
+#pragma unroll
+                for (int c2 = 0; c2 < 3; ++c2)
+                    Y[3 * r2 + c2] = GA[3 * r2] * g.A[3 * c2] + GA[3 * r2 + 1] * g.A[3 * c2 + 1]
+                                   + GA[3 * r2 + 2] * g.A[3 * c2 + 2];
+            gpose[0] = gp0;
+            gpose[1] = gp1;
+            gpose[2] = gp2;
+            gpose[3] = py * gp2 - pz * gp1 + (Y[7] - Y[5]);
+            gpose[4] = pz * gp0 - px * gp2 + (Y[2] - Y[6]);
+            gpose[5] = px * gp1 - py * gp0 + (Y[3] - Y[1]);
+            if (WANT_PARAMS) {
+                PoseR W = pr;
+                // mean: p = W mu + t
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gm[k] = W.R[k] * gp0 + W.R[3 + k] * gp1 + W.R[6 + k] * gp2;
+                // A = W M -> G_M = W^T G_A; M = R diag(s)
+                float GM[9];
+#pragma unroll
+                for (int r2 = 0; r2 < 3; ++r2)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        GM[3 * r2 + k] = W.R[r2] * GA[k] + W.R[3 + r2] * GA[3 + k] + W.R[6 + r2] * GA[6 + k];
+                float GR[9];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    float gsk = GM[k] * g.R[k] + GM[3 + k] * g.R[3 + k] + GM[6 + k] * g.R[6 + k];
+                    gls[k] = gsk * g.s[k];
+                    GR[k] = GM[k] * g.s[k];
+                    GR[3 + k] = GM[3 + k] * g.s[k];
+                    GR[6 + k] = GM[6 + k] * g.s[k];
+                }
+                float w = g.qh[0], x = g.qh[1], y = g.qh[2], z = g.qh[3];
+                float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+                float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6]
+                                  + w * GR[7] - 2.f * x * GR[8]);
+                float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6]
+                                  + z * GR[7] - 2.f * y * GR[8]);
+                float gzq = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4]
+                                   + y * GR[5] + x * GR[6] + y * GR[7]);
+                float dot = gw * w + gx * x + gy * y + gzq * z;
+                float iq = 1.f / g.qn;
+                gq[0] = (gw - w * dot) * iq;
+                gq[1] = (gx - x * dot) * iq;
+                gq[2] = (gy - y * dot) * iq;
+                gq[3] = (gzq - z * dot) * iq;
+            }
+        }
+        if (WANT_PARAMS) {
+#define GSR_PUT(ptr, idx, val) \
+    if (ptr) { if (accumulate) (ptr)[idx] += weight * (val); else (ptr)[idx] = (val); }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                GSR_PUT(dg.mean, 3 * i + k, gm[k]);
+                GSR_PUT(dg.log_scale, 3 * i + k, gls[k]);
+                GSR_PUT(dg.rgb, 3 * i + k, grgb[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) GSR_PUT(dg.quat, 4 * i + k, gq[k]);
+            GSR_PUT(dg.opacity_logit, i, glog);
+#undef GSR_PUT
+        }
+    }
+    if (pose_part) {
+        // block reduction of the 6 pose components (deterministic order)
+        __shared__ float red[6][8];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float v = gpose[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[k][w] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            float v = 0.f;
+            for (int ww = 0; ww < 8; ++ww) v += red[threadIdx.x][ww];
+            pose_part[6 * (int64_t)blockIdx.x + threadIdx.x] = v;
+        }
+    }
+}
+
+// list entries as Gaussian ids; per-id depth bits (culled: 0xffffffff)
+__global__ void k_lists_to_gid(int64_t cap_i, const u32 *__restrict__ d_n, const u32 *__restrict__ tvals,
+                               const u32 *__restrict__ rank2gid, u32 *__restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cap_i && i < (int64_t)*d_n) out[i] = rank2gid[tvals[i]];
+}
+
+__global__ void k_depth_bits(int64_t n, const u32 *__restrict__ flag, const float4 *__restrict__ rec,
+                             u32 *__restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = flag[i] ? __float_as_uint(rec[3 * i + 1].z) : 0xffffffffu;
+}
+
+__global__ void k_pose_reduce(const float *__restrict__ part, int nb, float *__restrict__ out, int accumulate,
+                              float weight)
+{
+    __shared__ float red[6][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 6 warps? no: 192 threads = 6 warps of 32
+    // warp w reduces component w over all blocks
+    float v = 0.f;
+    for (int b = lane; b < nb; b += 32) v += part[6 * b + w];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w][0] = v;
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        if (accumulate) out[threadIdx.x] += weight * red[threadIdx.x][0];
+        else out[threadIdx.x] = red[threadIdx.x][0];
+    }
+}
+
+} // namespace
+
+gsr_status launch_set_pose(gsr_ctx *ctx, float *d_pose, const gsr_pose &p, cudaStream_t s)
+{
+    k_set_pose<<<1, 1, 0, s>>>(d_pose, p);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+static int bits_for(int64_t v)
+{
+    int b = 1;
+    while (b < 32 && ((int64_t)1 << b) < v) ++b;
+    return b;
+}
+
+gsr_status run_binning(gsr_ctx *ctx, const Params &P, const CamK &ck, const float *d_pose, bool allow_grow,
+                       cudaStream_t s)
+{
+    ViewScratch &V = ctx->view;
+    const int64_t n = P.n;
+    const int64_t tiles = (int64_t)ck.tiles_x * ck.tiles_y;
+    if (n > V.cap_n) {
+        int64_t c = n;
+        GSR_TRY(ensure_buf(ctx, V.rec, sizeof(float4) * 3 * c));
+        GSR_TRY(ensure_buf(ctx, V.flag, sizeof(u32) * c));
+        GSR_TRY(ensure_buf(ctx, V.compact, sizeof(u32) * c));
+        GSR_TRY(ensure_buf(ctx, V.rank_of_gid, sizeof(int32_t) * c));
+        for (int k = 0; k < 2; ++k) {
+            GSR_TRY(ensure_buf(ctx, V.dkeys[k], sizeof(u32) * c));
+            GSR_TRY(ensure_buf(ctx, V.dvals[k], sizeof(u32) * c));
+        }
+        GSR_TRY(ensure_buf(ctx, V.rec_sorted, sizeof(float4) * 3 * c));
+        GSR_TRY(ensure_buf(ctx, V.tcount, sizeof(u32) * c));
+        GSR_TRY(ensure_buf(ctx, V.inst_off, sizeof(u32) * c));
+        GSR_TRY(ensure_buf(ctx, V.g2d, sizeof(float) * 12 * c));
+        V.cap_n = c;
+    }
+    if (tiles > V.cap_t) {
+        GSR_TRY(ensure_buf(ctx, V.ranges, sizeof(uint2) * tiles));
+        V.cap_t = tiles;
+    }
+    GSR_TRY(ensure_buf(ctx, V.counters, sizeof(u32) * CNT_WORDS));
+    u32 *cnt = (u32 *)V.counters.p;
+    const unsigned nb = (unsigned)ceil_div(n > 0 ? n : 1, 256);
+
+    k_project<<<nb, 256, 0, s>>>(P, ck, d_pose, (float4 *)V.rec.p, (u32 *)V.flag.p, (int32_t *)V.rank_of_gid.p);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    GSR_TRY(scan_exclusive(ctx, (u32 *)V.flag.p, (u32 *)V.compact.p, n, nullptr, cnt + CNT_VISIBLE, s));
+    k_compact<<<nb, 256, 0, s>>>(n, (u32 *)V.flag.p, (u32 *)V.compact.p, (float4 *)V.rec.p, (u32 *)V.dkeys[0].p,
+                                 (u32 *)V.dvals[0].p);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    u32 *dk[2] = {(u32 *)V.dkeys[0].p, (u32 *)V.dkeys[1].p};
+    u32 *dv[2] = {(u32 *)V.dvals[0].p, (u32 *)V.dvals[1].p};
+    GSR_TRY(radix_sort_pairs(ctx, dk, dv, n, cnt + CNT_VISIBLE, 32, s));
+    k_gather<<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, dv[0], (float4 *)V.rec.p, (float4 *)V.rec_sorted.p,
+                                (int32_t *)V.rank_of_gid.p, (u32 *)V.tcount.p);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    GSR_TRY(scan_exclusive(ctx, (u32 *)V.tcount.p, (u32 *)V.inst_off.p, n, cnt + CNT_VISIBLE,
+                           cnt + CNT_INSTANCES, s));
+    if (allow_grow) {
+        // one 4-byte readback sizes the instance buffers (grow-on-demand mode)
+        GSR_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, cnt + CNT_INSTANCES, sizeof(u32), cudaMemcpyDeviceToHost, s));
+        GSR_CUDA(ctx, cudaStreamSynchronize(s));
+        int64_t need = (int64_t)ctx->host_pinned[0];
+        if (need > V.cap_i) {
+            int64_t c = need + need / 4 + 1024;
+            for (int k = 0; k < 2; ++k) {
+                GSR_TRY(ensure_buf(ctx, V.tkeys[k], sizeof(u32) * c));
+                GSR_TRY(ensure_buf(ctx, V.tvals[k], sizeof(u32) * c));
+            }
+            V.cap_i = c;
+        }
+    }
+    if (V.cap_i <= 0) return gsr_fail(ctx, GSR_ERR_CAPACITY, "instance capacity is zero in fixed-capacity mode");
+    k_emit<<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, (u32 *)V.inst_off.p, ck.tiles_x,
+                              V.cap_i, (u32 *)V.tkeys[0].p, (u32 *)V.tvals[0].p, cnt);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    u32 *tk[2] = {(u32 *)V.tkeys[0].p, (u32 *)V.tkeys[1].p};
+    u32 *tv[2] = {(u32 *)V.tvals[0].p, (u32 *)V.tvals[1].p};
+    GSR_TRY(radix_sort_pairs(ctx, tk, tv, V.cap_i, cnt + CNT_SORTN, bits_for(tiles), s));
+    GSR_CUDA(ctx, cudaMemsetAsync(V.ranges.p, 0, sizeof(uint2) * tiles, s));
+    k_ranges<<<(unsigned)ceil_div(V.cap_i, 256), 256, 0, s>>>(V.cap_i, cnt + CNT_SORTN, tk[0], (uint2 *)V.ranges.p);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+gsr_status run_project_backward(gsr_ctx *ctx, const Params &P, const CamK &ck, const float *d_pose,
+                                gsr_gaussian_grads *dg, float *d_pose6, bool accumulate, float weight,
+                                cudaStream_t s)
+{
+    ViewScratch &V = ctx->view;
+    const int64_t n = P.n;
+    const unsigned nb = (unsigned)ceil_div(n > 0 ? n : 1, 256);
+    float *part = nullptr;
+    if (d_pose6) {
+        GSR_TRY(ensure_buf(ctx, ctx->pose_part, sizeof(float) * 6 * nb));
+        part = (float *)ctx->pose_part.p;
+    }
+    gsr_gaussian_grads none{};
+    bool want = dg && (dg->mean || dg->log_scale || dg->quat || dg->opacity_logit || dg->rgb);
+    if (!want && !d_pose6) return GSR_OK;
+    if (want)
+        k_project_bwd<true><<<nb, 256, 0, s>>>(P, ck, d_pose, (int32_t *)V.rank_of_gid.p, (float *)V.g2d.p, *dg,
+                                               accumulate ? 1 : 0, weight, part);
+    else
+        k_project_bwd<false><<<nb, 256, 0, s>>>(P, ck, d_pose, (int32_t *)V.rank_of_gid.p, (float *)V.g2d.p, none,
+                                                0, weight, part);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    if (d_pose6) {
+        k_pose_reduce<<<1, 192, 0, s>>>(part, (int)nb, d_pose6, accumulate ? 1 : 0, weight);
+        ctx->launches += 1;
+        GSR_LAUNCHED(ctx);
+    }
+    return GSR_OK;
+}
+
+gsr_status copy_tile_lists(gsr_ctx *ctx, int64_t n, int64_t n_tiles, u32 *ranges_h, int32_t *gids_h,
+                           int64_t capacity, u32 *depth_h, int64_t *n_inst, cudaStream_t s)
+{
+    ViewScratch &V = ctx->view;
+    u32 *cnt = (u32 *)V.counters.p;
+    GSR_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, cnt, sizeof(u32) * 4, cudaMemcpyDeviceToHost, s));
+    GSR_CUDA(ctx, cudaStreamSynchronize(s));
+    int64_t ni = ctx->host_pinned[CNT_SORTN];
+    *n_inst = ctx->host_pinned[CNT_INSTANCES];
+    if (ranges_h) GSR_CUDA(ctx, cudaMemcpy(ranges_h, V.ranges.p, sizeof(uint2) * n_tiles, cudaMemcpyDeviceToHost));
+    if (depth_h && n > 0) {
+        // the depth-sort ping buffer 1 is free once the sort finished
+        k_depth_bits<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, (u32 *)V.flag.p, (float4 *)V.rec.p,
+                                                                (u32 *)V.dkeys[1].p);
+        GSR_LAUNCHED(ctx);
+        GSR_CUDA(ctx, cudaMemcpyAsync(depth_h, V.dkeys[1].p, sizeof(u32) * n, cudaMemcpyDeviceToHost, s));
+        GSR_CUDA(ctx, cudaStreamSynchronize(s));
+    }
+    if (*n_inst > capacity || *n_inst > ni) return gsr_fail(ctx, GSR_ERR_CAPACITY, "tile list capacity");
+    if (gids_h && ni > 0) {
+        k_lists_to_gid<<<(unsigned)ceil_div(ni, 256), 256, 0, s>>>(V.cap_i, cnt + CNT_SORTN, (u32 *)V.tvals[0].p,
+                                                                   (u32 *)V.dvals[0].p, (u32 *)V.tkeys[1].p);
+        GSR_LAUNCHED(ctx);
+        GSR_CUDA(ctx, cudaMemcpyAsync(gids_h, V.tkeys[1].p, sizeof(u32) * ni, cudaMemcpyDeviceToHost, s));
+        GSR_CUDA(ctx, cudaStreamSynchronize(s));
+    }
+    return GSR_OK;
+}

@@ -1,0 +1,93 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every
+symbol include/gsr.h declares, and the ctypes mirror matches the header's
+struct layouts (checked against gcc's own sizeof/offsetof).  No compute call
+is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2312_10070_gb300 import _build, _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gsr.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^GSR_API\s+[\w\s\*]+?\b(gsr_\w+)\s*\(", txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return _lib.load(build_if_missing=False)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.PROTOTYPES), set(names) ^ set(_lib.PROTOTYPES)
+
+
+def test_library_has_sm103a_code_and_no_torch_types():
+    txt = open(HEADER).read()
+    assert "torch" not in txt.lower().replace("pytorch type", "")
+    assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+
+
+STRUCTS = {
+    "gsr_options": _lib.Options, "gsr_camera": _lib.Camera, "gsr_pose": _lib.Pose,
+    "gsr_gaussians": _lib.Gaussians, "gsr_gaussian_grads": _lib.GaussianGrads, "gsr_render_out": _lib.RenderOut,
+    "gsr_frame_stats": _lib.FrameStats, "gsr_adam_opts": _lib.AdamOpts, "gsr_adam_state": _lib.AdamState,
+    "gsr_gaussians_mut": _lib.GaussiansMut, "gsr_track_opts": _lib.TrackOpts, "gsr_track_stats": _lib.TrackStats,
+    "gsr_keyframe": _lib.Keyframe, "gsr_map_opts": _lib.MapOpts, "gsr_map_stats": _lib.MapStats,
+}
+
+
+def test_struct_layouts_match_header(tmp_path):
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    for cname, py in STRUCTS.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-o", str(exe), str(src)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    for line in filter(None, out):
+        cname, field, val = line.split()
+        py = STRUCTS[cname]
+        if field == "size":
+            assert ctypes.sizeof(py) == int(val), cname
+        else:
+            assert getattr(py, field).offset == int(val), (cname, field)
+
+
+def test_default_options_without_gpu(lib):
+    o = _lib.Options()
+    lib.gsr_default_options(ctypes.byref(o))
+    assert (o.tile_w, o.tile_h, o.batch) == (16, 16, 256)
+    c = _lib.Camera()
+    lib.gsr_default_camera(ctypes.byref(c), 160, 120, 150.0, 150.0, 80.0, 60.0)
+    assert abs(c.z_near - 0.2) < 1e-7 and abs(c.eps2d - 0.3) < 1e-7
+    assert lib.gsr_status_string(-4) == b"GSR_ERR_CAPACITY"
+
+
+def test_invalid_arguments_are_rejected_without_gpu(lib):
+    # argument validation happens before any CUDA call
+    h = ctypes.c_void_p()
+    o = _lib.Options()
+    lib.gsr_default_options(ctypes.byref(o))
+    o.tile_w = 12
+    assert lib.gsr_create(ctypes.byref(h), ctypes.byref(o)) == -1
+    assert not h.value
+    o.tile_w, o.batch = 16, 100
+    assert lib.gsr_create(ctypes.byref(h), ctypes.byref(o)) == -1
+    assert lib.gsr_create(None, None) == -1

@@ -1,0 +1,195 @@
+"""GPU parity of the renderer: the CUDA path (through the C ABI) against the
+FP64 oracle on the same seeded inputs.
+
+Bars: tile keys / per-tile lists and per-pixel contributor counts bit-exact;
+RGB / depth / alpha within max-abs 2e-4; gradients within 1e-3 relative,
+|g - g_ref| <= 1e-3 (|g_ref| + 1e-3 rms(g_ref)).  Pixels and Gaussians whose
+discrete decisions the oracle flags as within its margin of a threshold
+(FP32 vs FP64 may legitimately decide them differently) are excluded; their
+count is asserted small.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2312_10070_gb300 import api, synth as S
+from tests.gpu_common import grad_close, ocam, tile_sequences_match, unit_inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = api.Context()
+    yield c
+    c.close()
+
+
+def run_forward(ctx, sc, spec, q, t, tile=(16, 16)):
+    g = api.GaussianParams.from_numpy(sc)
+    cam = api.camera_from_spec(spec)
+    pose = api.make_pose(q, t)
+    out = api.render_forward(ctx, g, cam, pose, want_n_contrib=True)
+    torch.cuda.synchronize()
+    return g, cam, pose, {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}, out
+
+
+def check_forward(out, ref, max_amb=0.08):
+    ok = ref["amb"] == 0
+    assert ok.mean() >= 1 - max_amb, ok.mean()
+    for k in ("depth", "alpha", "final_T"):
+        err = np.abs(out[k][ok] - ref[k][ok]).max()
+        assert err <= 2e-4, (k, err)
+    err = np.abs(out["rgb"][:, ok] - ref["rgb"][:, ok]).max()
+    assert err <= 2e-4, ("rgb", err)
+    assert np.array_equal(out["n_contrib"][ok], ref["n_contrib"][ok])
+    assert np.array_equal(out["last_idx"][ok], ref["last_idx"][ok])
+
+
+@pytest.mark.parametrize("seed,pose_seed", [(1, 2), (7, 8)])
+def test_forward_unit_matches_oracle(ctx, seed, pose_seed):
+    sc, spec, q, t = unit_inputs(seed, pose_seed)
+    _, _, _, out, _ = run_forward(ctx, sc, spec, q, t)
+    ref = O.render(O.Scene.from_dict(sc), q, t, ocam(spec))
+    check_forward(out, ref)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8), (32, 8)])
+def test_tile_lists_bit_exact(tile):
+    c = api.Context(tile=tile)
+    sc, spec, q, t = unit_inputs(3, 4)
+    g, cam, pose, out, _ = run_forward(c, sc, spec, q, t)
+    oc = ocam(spec, tile)
+    sc64 = O.Scene.from_dict(sc)
+    tx, ty = oc.tiles
+    ranges, gids, dbits = api.tile_lists(c, tx * ty, sc64.n)
+    ref = O.bin_tiles(sc64, q, t, oc)
+    pr = O.project(sc64, q, t, oc)
+    skip = (pr["amb"] & 1).astype(bool)
+    assert skip.sum() <= 10
+    assert tile_sequences_match(ranges, gids, ref["start"], ref["gid"], ref["near_tie"], skip) == 0
+    # culling decisions and depth keys
+    vis = dbits != 0xFFFFFFFF
+    assert np.array_equal(vis[~skip], pr["visible"][~skip].astype(bool))
+    f32 = pr["depth"].astype(np.float32).view(np.uint32).astype(np.int64)
+    ulp = np.abs(dbits.astype(np.int64) - f32)[vis & ~skip]
+    assert ulp.max() <= 1, ulp.max()  # faithfully rounded camera depth
+    # forward outputs at this tile size
+    check_forward(out, O.render(sc64, q, t, oc))
+    c.close()
+
+
+def test_backward_unit_matches_oracle(ctx):
+    sc, spec, q, t = unit_inputs(1, 2)
+    g, cam, pose, out, saved = run_forward(ctx, sc, spec, q, t)
+    sc64 = O.Scene.from_dict(sc)
+    ref_f = O.render(sc64, q, t, ocam(spec))
+    rng = np.random.default_rng(5)
+    H, W = spec.height, spec.width
+    w = [rng.standard_normal((3, H, W)), rng.standard_normal((H, W)), rng.standard_normal((H, W))]
+    amb = ref_f["amb"] != 0
+    for a in w:
+        a[..., amb] = 0.0
+    w = [a.astype(np.float32) for a in w]
+    grads, pose6 = api.render_backward(ctx, g, cam, pose, saved, *[torch.from_numpy(a).cuda() for a in w])
+    torch.cuda.synchronize()
+    ref = O.render_backward(sc64, q, t, ocam(spec), *w)
+    for k in api.GaussianParams.NAMES:
+        ok, worst = grad_close(getattr(grads, k).cpu().numpy(), ref[k])
+        assert ok, (k, worst)
+    ok, worst = grad_close(pose6.cpu().numpy(), ref["pose"])
+    assert ok, ("pose", worst)
+
+
+def test_pose_only_backward(ctx):
+    sc, spec, q, t = unit_inputs(11, 12)
+    g, cam, pose, out, saved = run_forward(ctx, sc, spec, q, t)
+    sc64 = O.Scene.from_dict(sc)
+    ref_f = O.render(sc64, q, t, ocam(spec))
+    rng = np.random.default_rng(6)
+    H, W = spec.height, spec.width
+    d_rgb, d_dep = rng.standard_normal((3, H, W)), rng.standard_normal((H, W))
+    amb = ref_f["amb"] != 0
+    d_rgb[:, amb] = 0
+    d_dep[amb] = 0
+    d_rgb, d_dep = d_rgb.astype(np.float32), d_dep.astype(np.float32)
+    _, pose6 = api.render_backward(ctx, g, cam, pose, saved, torch.from_numpy(d_rgb).cuda(),
+                                   torch.from_numpy(d_dep).cuda(), None, want_params=False)
+    ref = O.render_backward(sc64, q, t, ocam(spec), d_rgb, d_dep, None)
+    ok, worst = grad_close(pose6.cpu().numpy(), ref["pose"])
+    assert ok, worst
+
+
+def test_edge_cases(ctx):
+    spec = S.CameraSpec(50, 37, 40.0, 40.0, 25.0, 18.5)  # ragged: 4 x 3 tiles, partial tiles
+    cam = api.camera_from_spec(spec)
+    pose = api.make_pose(*S.IDENTITY_POSE)
+    # empty scene
+    empty = {k: np.zeros((0,) + s, np.float32) for k, s in
+             (("mean", (3,)), ("log_scale", (3,)), ("quat", (4,)), ("opacity_logit", ()), ("rgb", (3,)))}
+    g = api.GaussianParams.from_numpy(empty)
+    out = api.render_forward(ctx, g, cam, pose)
+    assert float(out["rgb"].abs().max()) == 0.0 and float(out["final_T"].min()) == 1.0
+    assert int(out["last_idx"].max()) == -1
+    grads, pose6 = api.render_backward(ctx, g, cam, pose, out, torch.ones((3, 37, 50), device="cuda"))
+    assert float(pose6.abs().max()) == 0.0
+    # everything behind the camera: all culled
+    sc = S.random_scene(300, 3, box=((-1, 1), (-1, 1), (-3, -1)))
+    g = api.GaussianParams.from_numpy(sc)
+    out = api.render_forward(ctx, g, cam, pose)
+    assert float(out["alpha"].max()) == 0.0
+    assert api.frame_stats(ctx)["n_visible"] == 0
+    # ragged image against the oracle
+    sc = S.random_scene(400, 4, box=((-0.6, 0.6), (-0.45, 0.45), (1, 3)), log_scale=(-3.0, 0.4))
+    _, _, _, out, _ = run_forward(ctx, sc, spec, *S.IDENTITY_POSE)
+    check_forward(out, O.render(O.Scene.from_dict(sc), *S.IDENTITY_POSE, ocam(spec)))
+
+
+def test_memory_saving_mode_is_bit_identical():
+    sc, spec, q, t = unit_inputs(1, 2)
+    outs = []
+    for ms in (False, True):
+        c = api.Context(memory_saving=ms)
+        g, cam, pose, out, saved = run_forward(c, sc, spec, q, t)
+        # a second forward in between: default mode then rebuilds too
+        d = torch.ones((3, spec.height, spec.width), device="cuda")
+        grads, pose6 = api.render_backward(c, g, cam, pose, saved, d, d[0], None)
+        torch.cuda.synchronize()
+        outs.append((out, grads, pose6))
+        c.close()
+    for k in ("rgb", "depth", "alpha", "final_T", "last_idx", "n_contrib"):
+        assert np.array_equal(outs[0][0][k], outs[1][0][k])
+    for k in api.GaussianParams.NAMES:
+        a, b = getattr(outs[0][1], k).cpu().numpy(), getattr(outs[1][1], k).cpu().numpy()
+        ok, worst = grad_close(a, b)  # float atomics: summation order may differ
+        assert ok, (k, worst)
+
+
+def test_full_size_room_view_matches_oracle(ctx):
+    """1200x680, 500k-Gaussian sub-map, the headline view (the bench's launch)."""
+    sc = S.room_scene(500_000, seed=3)
+    spec = S.camera_room()
+    q, t = S.submap_views()[S.HEADLINE_VIEW]
+    g, cam, pose, out, saved = run_forward(ctx, sc, spec, q, t)
+    sc64 = O.Scene.from_dict(sc)
+    ref = O.render(sc64, q, t, ocam(spec))
+    check_forward(out, ref, max_amb=0.1)
+    st = api.frame_stats(ctx)
+    pr = O.project(sc64, q, t, ocam(spec))
+    assert abs(st["n_visible"] - pr["visible"].sum()) <= (pr["amb"] & 1).sum()
+    # backward on sampled outputs: dL/dpixel nonzero on a random 2% of unambiguous pixels
+    rng = np.random.default_rng(9)
+    H, W = spec.height, spec.width
+    mask = (rng.random((H, W)) < 0.02) & (ref["amb"] == 0)
+    d_rgb = (rng.standard_normal((3, H, W)) * mask).astype(np.float32)
+    d_dep = (rng.standard_normal((H, W)) * mask).astype(np.float32)
+    grads, pose6 = api.render_backward(ctx, g, cam, pose, saved, torch.from_numpy(d_rgb).cuda(),
+                                       torch.from_numpy(d_dep).cuda(), None)
+    refb = O.render_backward(sc64, q, t, ocam(spec), d_rgb, d_dep, None)
+    for k in api.GaussianParams.NAMES:
+        ok, worst = grad_close(getattr(grads, k).cpu().numpy(), refb[k], rel=2e-3)
+        assert ok, (k, worst)
+    ok, worst = grad_close(pose6.cpu().numpy(), refb["pose"])
+    assert ok, ("pose", worst)

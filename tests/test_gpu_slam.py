@@ -1,0 +1,212 @@
+"""GPU tests of the autograd wrapper, tracking (Sec. 3.5) and sub-map mapping
+(Sec. 3.2 / Eq. (joint_loss)) built on the rasterizer."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2312_10070_gb300 import api, synth as S
+from paper_2312_10070_gb300.autograd import render
+from tests.gpu_common import grad_close, ocam, unit_inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def test_autograd_function_matches_oracle():
+    """torch.autograd backward (hand-written, saved final T + last index) for
+    every Gaussian parameter and the pose twist, against the oracle's exact
+    gradient (itself pinned to central finite differences)."""
+    ctx = api.Context()
+    sc, spec, q, t = unit_inputs(21, 22)
+    g = api.GaussianParams.from_numpy(sc)
+    for tt in g.tensors():
+        tt.requires_grad_(True)
+    xi = torch.zeros(6, device="cuda", requires_grad=True)
+    cam = api.camera_from_spec(spec)
+    rgb, depth, alpha = render(ctx, g, cam, q, t, xi)
+    ref_f = O.render(O.Scene.from_dict(sc), q, t, ocam(spec))
+    amb = torch.from_numpy(ref_f["amb"] != 0).cuda()
+    rng = np.random.default_rng(1)
+    w = [cu(rng.standard_normal(s)) for s in ((3, 120, 160), (120, 160), (120, 160))]
+    for a in w:
+        a[..., amb] = 0
+    loss = (w[0] * rgb).sum() + (w[1] * depth).sum() + (w[2] * alpha).sum()
+    loss.backward()
+    ref = O.render_backward(O.Scene.from_dict(sc), q, t, ocam(spec), *[a.cpu().numpy() for a in w])
+    for k in api.GaussianParams.NAMES:
+        ok, worst = grad_close(getattr(g, k).grad.cpu().numpy(), ref[k])
+        assert ok, (k, worst)
+    ok, worst = grad_close(xi.grad.cpu().numpy(), ref["pose"])
+    assert ok, ("xi", worst)
+    ctx.close()
+
+
+def test_track_iterations_match_oracle():
+    """Three tracking iterations (render, L_tracking, pose backward, Adam on
+    the twist, left retraction) against the same loop in the oracle."""
+    ctx = api.Context()
+    sc, spec, _, _ = unit_inputs(31, 32)
+    qg, tg = S.IDENTITY_POSE
+    sc64 = O.Scene.from_dict(sc)
+    oc = ocam(spec)
+    tgt = O.render(sc64, qg, tg, oc)
+    rgb_t, d_t = tgt["rgb"].astype(np.float32), tgt["depth"].astype(np.float32)
+    q0, t0 = S.perturbed_pose(33, 0.01, 0.5)
+    cfg = api.TrackConfig(use_graph=False, lr_rho=1e-3, lr_phi=1e-3)
+    g = api.GaussianParams.from_numpy(sc)
+    pose_gpu, st = api.track_step(ctx, g, api.camera_from_spec(spec), cu(rgb_t), cu(d_t), api.make_pose(q0, t0), 3,
+                                  cfg)
+    q, t = np.asarray(q0, np.float64), np.asarray(t0, np.float64)
+    m, v = np.zeros(6), np.zeros(6)
+    losses = []
+    for it in range(3):
+        r = O.render(sc64, q, t, oc)
+        lt = O.loss_track(r["rgb"], r["depth"], r["alpha"], rgb_t, d_t, cfg.lambda_c, cfg.k_median, cfg.alpha_pow)
+        losses.append(lt["loss"])
+        gb = O.render_backward(sc64, q, t, oc, lt["d_rgb"], lt["d_depth"], None)
+        step = np.zeros(6)
+        gpose = gb["pose"].copy()
+        for k in range(6):  # Adam on the twist, lr per block
+            pk = np.zeros(1)
+            mk, vk = m[k:k + 1].copy(), v[k:k + 1].copy()
+            O.adam(pk, np.array([gpose[k]]), mk, vk, it + 1, cfg.lr_rho if k < 3 else cfg.lr_phi, cfg.beta1,
+                   cfg.beta2, cfg.eps)
+            m[k], v[k], step[k] = mk[0], vk[0], pk[0]
+        q, t = O.pose_retract(q, t, step)
+    assert abs(st["loss_first"] - losses[0]) <= 2e-3 * abs(losses[0])
+    np.testing.assert_allclose(np.array(pose_gpu.t), t, atol=2e-5)
+    qd = np.array(pose_gpu.q)
+    assert min(np.abs(qd - q).max(), np.abs(qd + q).max()) <= 2e-5
+    ctx.close()
+
+
+def _room_frame(ctx, sc_gpu, cam, q, t, seed):
+    out = api.render_forward(ctx, sc_gpu, cam, api.make_pose(q, t))
+    rgb, dep = S.add_sensor_noise(out["rgb"].cpu().numpy(), out["depth"].cpu().numpy(),
+                                  out["alpha"].cpu().numpy(), seed=seed)
+    return cu(rgb), cu(dep)
+
+
+def _pose_error(q, t, qg, tg):
+    """(translation error of the camera centre in m, rotation error in degrees)"""
+    from scipy.spatial.transform import Rotation
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    Rg = Rotation.from_quat([qg[1], qg[2], qg[3], qg[0]]).as_matrix()
+    c, cg = -R.T @ np.asarray(t), -Rg.T @ np.asarray(tg)
+    ang = np.degrees(np.arccos(np.clip((np.trace(R @ Rg.T) - 1) / 2, -1, 1)))
+    return float(np.linalg.norm(c - cg)), float(ang)
+
+
+def test_track_step_converges_on_room_sequence():
+    """Constant-velocity start on a synthetic room trajectory; 100 pose-only
+    iterations reach the ground truth within 1 cm and 0.5 degrees."""
+    ctx = api.Context()
+    sc = S.room_scene(300_000, seed=100)
+    g = api.GaussianParams.from_numpy(sc)
+    spec = S.camera_room()
+    cam = api.camera_from_spec(spec)
+    qs, ts = S.room_trajectory(100, n_frames=12)
+    errs = []
+    for k in (3, 7, 11):
+        rgb, dep = _room_frame(ctx, g, cam, qs[k], ts[k], seed=k)
+        # constant velocity on (q, t): T_k = T_{k-1} + (T_{k-1} - T_{k-2}), q renormalised
+        q1, q2 = np.asarray(qs[k - 1], np.float64), np.asarray(qs[k - 2], np.float64)
+        if np.dot(q1, q2) < 0:
+            q2 = -q2
+        qi = 2 * q1 - q2
+        qi /= np.linalg.norm(qi)
+        ti = 2 * np.asarray(ts[k - 1], np.float64) - np.asarray(ts[k - 2], np.float64)
+        e0 = _pose_error(qi, ti, qs[k], ts[k])
+        pose, st = api.track_step(ctx, g, cam, rgb, dep, api.make_pose(qi, ti), 100, api.TrackConfig())
+        e1 = _pose_error(np.array(pose.q), np.array(pose.t), qs[k], ts[k])
+        errs.append((e0, e1, st["loss_first"], st["loss_last"]))
+        assert st["loss_last"] < st["loss_first"]
+        assert e1[0] <= 0.01 and e1[1] <= 0.5, errs
+    ctx.close()
+
+
+def test_track_graph_replay_equals_eager():
+    sc, spec, _, _ = unit_inputs(41, 42)
+    sc64 = O.Scene.from_dict(sc)
+    tgt = O.render(sc64, *S.IDENTITY_POSE, ocam(spec))
+    rgb_t, d_t = cu(tgt["rgb"]), cu(tgt["depth"])
+    q0, t0 = S.perturbed_pose(43, 0.01, 0.5)
+    res = []
+    for use_graph in (False, True):
+        ctx = api.Context()
+        g = api.GaussianParams.from_numpy(sc)
+        pose, st = api.track_step(ctx, g, api.camera_from_spec(spec), rgb_t, d_t, api.make_pose(q0, t0), 8,
+                                  api.TrackConfig(use_graph=use_graph))
+        res.append((np.array(pose.q), np.array(pose.t), st))
+        ctx.close()
+    np.testing.assert_allclose(res[0][1], res[1][1], atol=1e-6)
+    np.testing.assert_allclose(res[0][0], res[1][0], atol=1e-6)
+
+
+def _views_and_targets(ctx, g_gt, cam, idx):
+    kfs = []
+    for i in idx:
+        q, t = S.submap_views()[i]
+        out = api.render_forward(ctx, g_gt, cam, api.make_pose(q, t))
+        kfs.append((api.make_pose(q, t), out["rgb"].clone(), out["depth"].clone()))
+    return kfs
+
+
+def test_map_step_batched_gradient_is_weighted_sum():
+    """One map_step over 3 keyframes equals an Adam step on the weighted sum
+    of the single-view gradients (render_backward of the fused loss)."""
+    ctx = api.Context()
+    spec = S.scale_camera(S.camera_room(), 300, 170)
+    cam = api.camera_from_spec(spec)
+    sc_gt = S.room_scene(60_000, seed=3)
+    g_gt = api.GaussianParams.from_numpy(sc_gt)
+    kfs = _views_and_targets(ctx, g_gt, cam, (1, 4, 6))
+    w = [0.5, 0.3, 0.2]
+    noisy = S.noisy_copy(sc_gt, seed=5)
+    cfg = api.MapConfig(use_graph=False)
+    gA = api.GaussianParams.from_numpy(noisy)
+    stA = api.AdamMoments(gA)
+    api.map_step(ctx, gA, stA, cam, kfs, w, 1, cfg)
+    gB = api.GaussianParams.from_numpy(noisy)
+    stB = api.AdamMoments(gB)
+    total = gB.zeros_like()
+    for (pose, rgb_t, d_t), wk in zip(kfs, w):
+        out = api.render_forward(ctx, gB, cam, pose)
+        _, d_rgb, d_d = api.loss_map(ctx, out["rgb"], out["depth"], rgb_t, d_t, scale=wk)
+        grads, _ = api.render_backward(ctx, gB, cam, pose, out, d_rgb, d_d, None, want_pose=False)
+        for k in api.GaussianParams.NAMES:
+            getattr(total, k).add_(getattr(grads, k))
+    api.adam_step(ctx, gB, total, stB, cfg.adam)
+    for k in api.GaussianParams.NAMES:
+        a, b = getattr(gA, k).cpu().numpy(), getattr(gB, k).cpu().numpy()
+        # Adam's first step is lr * sign(g); entries whose gradient sum is ~0 may flip
+        frac = np.mean(np.abs(a - b) > 1e-6)
+        assert frac < 1e-3, (k, frac)
+    ctx.close()
+
+
+def test_map_step_graph_replay_and_loss_decrease():
+    ctx = api.Context()
+    spec = S.scale_camera(S.camera_room(), 400, 226)
+    cam = api.camera_from_spec(spec)
+    sc_gt = S.room_scene(80_000, seed=3)
+    g_gt = api.GaussianParams.from_numpy(sc_gt)
+    kfs = _views_and_targets(ctx, g_gt, cam, range(8))
+    res = []
+    for use_graph in (False, True):
+        g = api.GaussianParams.from_numpy(S.noisy_copy(sc_gt, seed=5))
+        st = api.AdamMoments(g)
+        cfg = api.MapConfig(use_graph=use_graph)
+        s0 = api.map_step(ctx, g, st, cam, kfs, None, 1, cfg)
+        s1 = api.map_step(ctx, g, st, cam, kfs, None, 30, cfg)
+        res.append((g, s0, s1))
+        assert s1["loss_last"] < 0.8 * s0["loss_last"], (s0, s1)
+    for k in api.GaussianParams.NAMES:
+        a, b = getattr(res[0][0], k).cpu().numpy(), getattr(res[1][0], k).cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-3 * (np.abs(a).max() + 1e-6), k
+    ctx.close()
