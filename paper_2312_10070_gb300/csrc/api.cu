@@ -185,13 +185,7 @@ gsr_status gsr_create(gsr_ctx **out, const gsr_options *opt)
         if (s == GSR_OK) s = ensure_buf(c, V.g2d, sizeof(float) * 12 * n);
         if (s == GSR_OK) V.cap_n = n;
     }
-    if (s == GSR_OK && o.max_instances > 0) {
-        for (int k = 0; k < 2 && s == GSR_OK; ++k) {
-            s = ensure_buf(c, V.tkeys[k], sizeof(u32) * o.max_instances);
-            if (s == GSR_OK) s = ensure_buf(c, V.tvals[k], sizeof(u32) * o.max_instances);
-        }
-        if (s == GSR_OK) V.cap_i = o.max_instances;
-    }
+    if (s == GSR_OK && o.max_instances > 0) s = grow_instance_capacity(c, o.max_instances);
     if (s != GSR_OK) {
         gsr_destroy(c);
         return s;
@@ -518,11 +512,7 @@ extern "C" gsr_status gsr_track_step(gsr_ctx *ctx, const gsr_gaussians *g, const
                 int64_t need = (int64_t)ctx->host_pinned[0];
                 int64_t c = need + need / 2 + 4096;
                 if (c > V.cap_i) {
-                    for (int k = 0; k < 2; ++k) {
-                        GSR_TRY(ensure_buf(ctx, V.tkeys[k], sizeof(u32) * c));
-                        GSR_TRY(ensure_buf(ctx, V.tvals[k], sizeof(u32) * c));
-                    }
-                    V.cap_i = c;
+                    GSR_TRY(grow_instance_capacity(ctx, c));
                     if (ctx->track_graph) cudaGraphExecDestroy(ctx->track_graph);
                     ctx->track_graph = nullptr;
                 }

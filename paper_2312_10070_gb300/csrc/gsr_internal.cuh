@@ -122,6 +122,9 @@ gsr_status scan_exclusive(gsr_ctx *ctx, const u32 *in, u32 *out, int64_t n_cap, 
 gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_cap, const u32 *d_n,
                             int bits, cudaStream_t s);
 
+// Grows the tile-instance capacity (and the sort scratch sized from it).
+gsr_status grow_instance_capacity(gsr_ctx *ctx, int64_t c);
+
 // ------------------------------------------------------------ device math
 struct CamK {
     int W, H, tw, th, tiles_x, tiles_y;

@@ -526,14 +526,7 @@ gsr_status run_binning(gsr_ctx *ctx, const Params &P, const CamK &ck, const floa
         GSR_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, cnt + CNT_INSTANCES, sizeof(u32), cudaMemcpyDeviceToHost, s));
         GSR_CUDA(ctx, cudaStreamSynchronize(s));
         int64_t need = (int64_t)ctx->host_pinned[0];
-        if (need > V.cap_i) {
-            int64_t c = need + need / 4 + 1024;
-            for (int k = 0; k < 2; ++k) {
-                GSR_TRY(ensure_buf(ctx, V.tkeys[k], sizeof(u32) * c));
-                GSR_TRY(ensure_buf(ctx, V.tvals[k], sizeof(u32) * c));
-            }
-            V.cap_i = c;
-        }
+        if (need > V.cap_i) GSR_TRY(grow_instance_capacity(ctx, need + need / 4 + 1024));
     }
     if (V.cap_i <= 0) return gsr_fail(ctx, GSR_ERR_CAPACITY, "instance capacity is zero in fixed-capacity mode");
     k_emit<<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, (u32 *)V.inst_off.p, ck.tiles_x,

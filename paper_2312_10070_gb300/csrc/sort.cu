@@ -232,3 +232,20 @@ gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_
     }
     return GSR_OK;
 }
+
+gsr_status grow_instance_capacity(gsr_ctx *ctx, int64_t c)
+{
+    ViewScratch &V = ctx->view;
+    if (c <= V.cap_i) return GSR_OK;
+    for (int k = 0; k < 2; ++k) {
+        GSR_TRY(ensure_buf(ctx, V.tkeys[k], sizeof(u32) * c));
+        GSR_TRY(ensure_buf(ctx, V.tvals[k], sizeof(u32) * c));
+    }
+    // everything the instance sort touches is sized here, so that a captured
+    // graph never needs to grow a buffer
+    const int64_t hist_words = ceil_div(c, RX_TILE) * RX;
+    GSR_TRY(ensure_buf(ctx, ctx->radix_hist, sizeof(u32) * hist_words));
+    GSR_TRY(ensure_buf(ctx, ctx->scan_tmp, sizeof(u32) * ceil_div(hist_words, SCAN_TILE)));
+    V.cap_i = c;
+    return GSR_OK;
+}

@@ -11,14 +11,21 @@ def ocam(spec, tile=(16, 16), **kw):
                     **kw)
 
 
-def grad_close(g, ref, rel=1e-3):
-    """|g - ref| <= rel * (|ref| + rel * rms(ref)) elementwise; returns (ok, worst ratio)."""
+def grad_close(g, ref, rel=1e-3, floor=0.1, rel_l2=1e-4):
+    """Gradient parity: elementwise |g - ref| <= rel (|ref| + floor max|ref|) and
+    a per-tensor relative L2 error <= rel_l2.  FP32 sums of many contributions
+    of both signs carry an error relative to the contributions, not to the sum,
+    so the elementwise floor scales with the tensor's largest entry (1e-4 of it
+    by default).  Returns (ok, worst elementwise ratio)."""
     g = np.asarray(g, np.float64)
     ref = np.asarray(ref, np.float64)
-    rms = np.sqrt(np.mean(ref ** 2)) if ref.size else 0.0
-    tol = rel * (np.abs(ref) + rel * rms) + 1e-30
+    if ref.size == 0:
+        return True, 0.0
+    mx = np.abs(ref).max()
+    tol = rel * (np.abs(ref) + floor * mx) + 1e-30
     ratio = np.abs(g - ref) / tol
-    return bool((ratio <= 1.0).all()), float(ratio.max()) if ratio.size else 0.0
+    l2 = np.linalg.norm(g - ref) / (np.linalg.norm(ref) + 1e-30)
+    return bool((ratio <= 1.0).all() and l2 <= rel_l2), float(max(ratio.max(), l2 / rel_l2))
 
 
 def tile_sequences_match(ranges, gids, ref_start, ref_gid, near_tie, skip):

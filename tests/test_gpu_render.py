@@ -3,7 +3,8 @@ FP64 oracle on the same seeded inputs.
 
 Bars: tile keys / per-tile lists and per-pixel contributor counts bit-exact;
 RGB / depth / alpha within max-abs 2e-4; gradients within 1e-3 relative,
-|g - g_ref| <= 1e-3 (|g_ref| + 1e-3 rms(g_ref)).  Pixels and Gaussians whose
+|g - g_ref| <= 1e-3 |g_ref| + 1e-4 max|g_ref| elementwise and a per-tensor
+relative L2 error <= 1e-4.  Pixels and Gaussians whose
 discrete decisions the oracle flags as within its margin of a threshold
 (FP32 vs FP64 may legitimately decide them differently) are excluded; their
 count is asserted small.
@@ -189,7 +190,7 @@ def test_full_size_room_view_matches_oracle(ctx):
                                        torch.from_numpy(d_dep).cuda(), None)
     refb = O.render_backward(sc64, q, t, ocam(spec), d_rgb, d_dep, None)
     for k in api.GaussianParams.NAMES:
-        ok, worst = grad_close(getattr(grads, k).cpu().numpy(), refb[k], rel=2e-3)
+        ok, worst = grad_close(getattr(grads, k).cpu().numpy(), refb[k])
         assert ok, (k, worst)
     ok, worst = grad_close(pose6.cpu().numpy(), refb["pose"])
     assert ok, ("pose", worst)

