@@ -203,6 +203,33 @@ GSR_API gsr_status gsr_loss_track(gsr_ctx *ctx, int32_t width, int32_t height, c
                           float alpha_pow, float *d_rgb, float *d_depth, float *loss_dev,
                           float *median_dev, void *stream);
 
+/* Largest image (width * height) gsr_loss_track_noalloc accepts: 1280 x 720. */
+#define GSR_NOALLOC_MAX_PIXELS 921600
+
+/* Allocation-free variant of gsr_loss_track (the paper has no counterpart;
+ * it is an interface for callers).  Some callers cannot call cudaMalloc: code
+ * that runs inside another framework's memory pool with a fixed budget, or a
+ * real-time tracking loop that must not meet cudaMalloc's implicit device
+ * synchronisation.  They cannot create a gsr_ctx (whose scratch is
+ * allocated), so this call needs no context and allocates nothing.  Inputs,
+ * outputs, scale and the result are those of gsr_loss_track.
+ *
+ * Its scratch (about 3.7 MB) is one static device array in libgsr.so, held
+ * by every GPU that loads the library until the process exits.  The first
+ * call on a device looks up that array's device address (with that device
+ * current), so the first call on each device should come before any stream
+ * capture.  Every call on a device shares the array, which keeps the last
+ * call's contents: calls that overlap on the GPU (different streams, or
+ * host threads) race and must be serialised by the caller.
+ *
+ * Errors: GSR_ERR_INVALID_ARG for a null pointer or a non-positive size,
+ * GSR_ERR_CAPACITY when width * height > GSR_NOALLOC_MAX_PIXELS (nothing is
+ * launched), GSR_ERR_CUDA if the address lookup or a launch fails. */
+GSR_API gsr_status gsr_loss_track_noalloc(int32_t width, int32_t height, const float *rgb, const float *depth,
+                                          const float *alpha, const float *rgb_target, const float *depth_target,
+                                          float lambda_c, float k_median, float alpha_pow, float *d_rgb,
+                                          float *d_depth, float *loss_dev, float *median_dev, void *stream);
+
 /* ------------------------------------------------------------ optimiser */
 
 typedef struct {

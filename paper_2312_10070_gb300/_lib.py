@@ -116,6 +116,8 @@ PROTOTYPES = {
                              c_vp]),
     "gsr_loss_track": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_f, c_f, c_f, c_vp, c_vp,
                                c_vp, c_vp, c_vp]),
+    "gsr_loss_track_noalloc": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_f, c_f, c_f, c_vp, c_vp, c_vp,
+                                       c_vp, c_vp]),
     "gsr_adam_step": (c_i32, [c_vp, ctypes.POINTER(GaussiansMut), ctypes.POINTER(GaussianGrads),
                               ctypes.POINTER(AdamState), ctypes.POINTER(AdamOpts), c_vp, c_vp]),
     "gsr_track_step": (c_i32, [c_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), c_vp, c_vp,

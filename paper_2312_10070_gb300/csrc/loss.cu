@@ -16,6 +16,7 @@
 //
 // Reductions are deterministic: per-block partials, then one ordered pass.
 #include <algorithm>
+#include <mutex>
 
 #include "gsr_internal.cuh"
 
@@ -407,5 +408,79 @@ gsr_status run_loss_track(gsr_ctx *ctx, int W, int H, const float *rgb, const fl
                                      median_dev, cnt + CNT_STATUS);
     ctx->launches += 12;
     GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+// ----------------------------------------------------- allocation-free variant
+// Scratch of gsr_loss_track_noalloc: one static device array, laid out as
+// [residual bits: MAXP][select histogram: 256][block partials: MAXB][counters: 16]
+// (u32 words).  It belongs to the library, not to a context, so a caller that
+// cannot allocate device memory can still run the tracking loss.
+namespace {
+constexpr int64_t NA_MAXP = GSR_NOALLOC_MAX_PIXELS;
+constexpr int64_t NA_MAXB = (NA_MAXP + 255) / 256;
+constexpr int64_t NA_HIST = NA_MAXP;
+constexpr int64_t NA_PART = NA_HIST + 256;
+constexpr int64_t NA_CNT = NA_PART + NA_MAXB;
+constexpr int64_t NA_WORDS = NA_CNT + 16;
+}  // namespace
+
+static __device__ __align__(256) u32 g_noalloc_scratch[NA_WORDS];
+
+namespace {
+std::mutex g_noalloc_mu;
+u32 *g_noalloc_ptr[256] = {};  // device address of g_noalloc_scratch per device ordinal
+}  // namespace
+
+extern "C" gsr_status gsr_loss_track_noalloc(int32_t width, int32_t height, const float *rgb, const float *depth,
+                                             const float *alpha, const float *rgb_target, const float *depth_target,
+                                             float lambda_c, float k_median, float alpha_pow, float *d_rgb,
+                                             float *d_depth, float *loss_dev, float *median_dev, void *stream)
+{
+    if (width <= 0 || height <= 0 || !rgb || !depth || !alpha || !rgb_target || !depth_target || !d_rgb || !d_depth)
+        return GSR_ERR_INVALID_ARG;
+    const int64_t HW = (int64_t)width * height;
+    if (HW > NA_MAXP) return GSR_ERR_CAPACITY;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        (void)cudaGetLastError();
+        return GSR_ERR_CUDA;
+    }
+    u32 *base = nullptr;
+    {
+        // set-up once per device: host code only knows the array's host-side
+        // stand-in; the kernels need its device address
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                (void)cudaGetLastError();
+                return GSR_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = (u32 *)p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    u32 *ebits = base, *hist = base + NA_HIST, *cnt = base + NA_CNT;
+    float *part = (float *)(base + NA_PART);
+    u32 *nvalid = cnt + 0, *sel = cnt + 1, *status = cnt + 4;
+    const unsigned nb = (unsigned)ceil_div(HW, 256);
+    // the array keeps the previous call's contents: reset what accumulates
+    if (cudaMemsetAsync(cnt, 0, 16 * sizeof(u32), s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GSR_ERR_CUDA;
+    }
+    k_track_resid<<<nb, 256, 0, s>>>(HW, depth, depth_target, ebits, nvalid);
+    k_sel_init<<<1, 256, 0, s>>>(nvalid, sel, hist);
+    const unsigned hb = (unsigned)std::min<int64_t>(nb, 1216);
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        k_sel_hist<<<hb, 256, 0, s>>>(HW, ebits, shift, sel, hist);
+        k_sel_pick<<<1, 256, 0, s>>>(shift, sel, hist);
+    }
+    k_track_loss<<<nb, 256, 0, s>>>(HW, rgb, depth, alpha, rgb_target, depth_target, sel, nvalid, lambda_c, k_median,
+                                    alpha_pow, d_rgb, d_depth, part);
+    k_track_final<<<1, 1024, 0, s>>>(part, (int)nb, sel, nvalid, loss_dev, median_dev, status);
+    if (cudaGetLastError() != cudaSuccess) return GSR_ERR_CUDA;
     return GSR_OK;
 }
