@@ -70,6 +70,9 @@ typedef struct {
     int64_t max_gaussians;   /* initial scratch capacities (0 = grow on first use) */
     int64_t max_instances;   /* tile instances (Gaussian x tile pairs) */
     int64_t max_pixels;
+    int32_t pixels_per_thread; /* pixels each blend thread owns: 1 or 2 (0 = default 2);
+                                  results do not depend on it */
+    int32_t reserved;
 } gsr_options;
 
 /* Pinhole camera and rasterizer constants. */
@@ -315,6 +318,27 @@ GSR_API gsr_status gsr_map_step(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_sta
                         const gsr_camera *cam, const gsr_keyframe *kfs, int32_t n_kf,
                         const float *kf_weights, int32_t n_iters, const gsr_map_opts *opt,
                         gsr_map_stats *out, void *stream);
+
+/* ------------------------------------------------------------ autotune */
+
+typedef struct {
+    int32_t tile_w, tile_h, batch, pixels_per_thread;
+    float ms;  /* mean time of one forward + backward over all given poses */
+} gsr_tune_result;
+
+/* Times gsr_render_forward + gsr_render_backward (all gradients, dL/dpixel
+ * = 1) of `g` at each of the n_poses poses for every configuration of tile
+ * shape {16x16, 8x8, 16x8, 32x8} x batch {32, 64, 128, 256} x pixels per
+ * thread {1, 2}, `reps` timed repetitions each after one warm-up, and keeps the
+ * fastest on the context (its captured graphs are dropped).  The tile shape
+ * changes which Gaussians a tile lists (the rectangle rule is per tile), so a
+ * context's results are reproducible for a fixed configuration; batch and
+ * pixels per thread do not change results.  *best receives the winner; all
+ * (nullable, n_all entries) the timings in the order tried.  Synchronising;
+ * the Gaussians are not modified. */
+GSR_API gsr_status gsr_autotune(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam, const gsr_pose *poses,
+                                int32_t n_poses, int32_t reps, gsr_tune_result *best, gsr_tune_result *all,
+                                int32_t n_all, void *stream);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,7 @@ STATUS = {0: "GSR_OK", -1: "GSR_ERR_INVALID_ARG", -2: "GSR_ERR_CUDA", -3: "GSR_E
 class Options(ctypes.Structure):
     _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("batch", c_i32), ("memory_saving", c_i32),
                 ("fixed_capacity", c_i32), ("max_gaussians", c_i64), ("max_instances", c_i64),
-                ("max_pixels", c_i64)]
+                ("max_pixels", c_i64), ("pixels_per_thread", c_i32), ("reserved", c_i32)]
 
 
 class Camera(ctypes.Structure):
@@ -94,6 +94,10 @@ class MapStats(ctypes.Structure):
     _fields_ = [("loss_last", c_f), ("iters", c_i32)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("batch", c_i32), ("pixels_per_thread", c_i32), ("ms", c_f)]
+
+
 # name -> (restype, argtypes); every symbol include/gsr.h declares
 PROTOTYPES = {
     "gsr_default_options": (None, [ctypes.POINTER(Options)]),
@@ -126,6 +130,8 @@ PROTOTYPES = {
     "gsr_map_step": (c_i32, [c_vp, ctypes.POINTER(GaussiansMut), ctypes.POINTER(AdamState), ctypes.POINTER(Camera),
                              ctypes.POINTER(Keyframe), c_i32, c_vp, c_i32, ctypes.POINTER(MapOpts),
                              ctypes.POINTER(MapStats), c_vp]),
+    "gsr_autotune": (c_i32, [c_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Pose), c_i32,
+                             c_i32, ctypes.POINTER(TuneResult), ctypes.POINTER(TuneResult), c_i32, c_vp]),
 }
 
 _lib = None

@@ -155,9 +155,11 @@ gsr_status gsr_create(gsr_ctx **out, const gsr_options *opt)
     if (!valid_tile(o.tile_w, o.tile_h)) return GSR_ERR_INVALID_ARG;
     if (o.batch != 32 && o.batch != 64 && o.batch != 128 && o.batch != 256) return GSR_ERR_INVALID_ARG;
     if (o.max_gaussians < 0 || o.max_instances < 0 || o.max_pixels < 0) return GSR_ERR_INVALID_ARG;
+    if (o.pixels_per_thread != 0 && o.pixels_per_thread != 1 && o.pixels_per_thread != 2) return GSR_ERR_INVALID_ARG;
     gsr_ctx *c = new (std::nothrow) gsr_ctx();
     if (!c) return GSR_ERR_OOM;
     c->opt = o;
+    c->ppt = o.pixels_per_thread ? o.pixels_per_thread : 2;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         (void)cudaGetLastError();
         delete c;
@@ -185,7 +187,7 @@ gsr_status gsr_create(gsr_ctx **out, const gsr_options *opt)
         if (s == GSR_OK) s = ensure_buf(c, V.g2d, sizeof(float) * 12 * n);
         if (s == GSR_OK) V.cap_n = n;
     }
-    if (s == GSR_OK && o.max_instances > 0) s = grow_instance_capacity(c, o.max_instances);
+    if (s == GSR_OK && o.max_instances > 0) s = grow_instance_capacity(c, c->view, o.max_instances);
     if (s != GSR_OK) {
         gsr_destroy(c);
         return s;
@@ -204,6 +206,15 @@ void gsr_destroy(gsr_ctx *c)
                       &V.ranges, &V.g2d, &V.counters, &V.pose, &c->scan_tmp, &c->radix_hist, &c->pose_part,
                       &c->loss_part, &c->loss_maps, &c->img_tmp, &c->small, &c->grads};
     for (DevBuf *b : bufs) free_buf(*b);
+    for (ViewScratch &W : c->mv) {
+        DevBuf *vb[] = {&W.rec, &W.flag, &W.compact, &W.rank_of_gid, &W.dkeys[0], &W.dkeys[1], &W.dvals[0],
+                        &W.dvals[1], &W.rec_sorted, &W.tcount, &W.inst_off, &W.tkeys[0], &W.tkeys[1], &W.tvals[0],
+                        &W.tvals[1], &W.ranges, &W.g2d, &W.counters, &W.pose};
+        for (DevBuf *b : vb) free_buf(*b);
+    }
+    DevBuf *mb[] = {&c->mv_frames, &c->mv_desc, &c->mv_pview, &c->mv_keys[0], &c->mv_keys[1], &c->mv_items[0],
+                    &c->mv_items[1], &c->mv_counter};
+    for (DevBuf *b : mb) free_buf(*b);
     if (c->track_graph) cudaGraphExecDestroy(c->track_graph);
     if (c->map_graph) cudaGraphExecDestroy(c->map_graph);
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
@@ -307,7 +318,7 @@ extern "C" gsr_status gsr_render_forward(gsr_ctx *ctx, const gsr_gaussians *g, c
     CamK ck = make_camk(*cam, ctx->opt.tile_w, ctx->opt.tile_h);
     Params P = to_params(g);
     GSR_TRY(prof_mark(ctx, PROF_BIN, false, s));
-    GSR_TRY(run_binning(ctx, P, ck, d_pose, !ctx->opt.fixed_capacity, s));
+    GSR_TRY(run_binning(ctx, ctx->view, P, ck, d_pose, !ctx->opt.fixed_capacity, s));
     GSR_TRY(prof_mark(ctx, PROF_BIN, true, s));
     GSR_TRY(prof_mark(ctx, PROF_FWD, false, s));
     GSR_TRY(run_blend_forward(ctx, P, ck, out, s));
@@ -360,7 +371,7 @@ extern "C" gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *g, 
     if (ctx->opt.memory_saving || !same_forward(ctx, g, cam, pose)) {
         // rebuild the (deterministic) tile lists instead of keeping them alive
         GSR_TRY(launch_set_pose(ctx, d_pose, *pose, s));
-        GSR_TRY(run_binning(ctx, P, ck, d_pose, !ctx->opt.fixed_capacity, s));
+        GSR_TRY(run_binning(ctx, ctx->view, P, ck, d_pose, !ctx->opt.fixed_capacity, s));
         remember_forward(ctx, g, cam, pose);
     }
     bool want_params = dg && (dg->mean || dg->log_scale || dg->quat || dg->opacity_logit || dg->rgb);
@@ -368,7 +379,7 @@ extern "C" gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *g, 
     GSR_TRY(run_blend_backward(ctx, ck, saved, d_rgb, d_depth, d_alpha, !want_params, s));
     GSR_TRY(prof_mark(ctx, PROF_BWD, true, s));
     GSR_TRY(prof_mark(ctx, PROF_PBWD, false, s));
-    GSR_TRY(run_project_backward(ctx, P, ck, d_pose, want_params ? dg : nullptr, d_pose6, false, 1.f, s));
+    GSR_TRY(run_project_backward(ctx, ctx->view, P, ck, d_pose, want_params ? dg : nullptr, d_pose6, false, 1.f, s));
     GSR_TRY(prof_mark(ctx, PROF_PBWD, true, s));
     return GSR_OK;
 }
@@ -438,12 +449,12 @@ static gsr_status track_iter(gsr_ctx *ctx, const Params &P, const CamK &ck, cons
 {
     float *sm = (float *)ctx->small.p;
     gsr_render_out ro{f.rgb, f.depth, f.alpha, f.T, f.last, nullptr};
-    GSR_TRY(run_binning(ctx, P, ck, sm + SM_POSE, grow, s));
+    GSR_TRY(run_binning(ctx, ctx->view, P, ck, sm + SM_POSE, grow, s));
     GSR_TRY(run_blend_forward(ctx, P, ck, &ro, s));
     GSR_TRY(run_loss_track(ctx, ck.W, ck.H, f.rgb, f.depth, f.alpha, rgb_in, depth_in, o->lambda_c, o->k_median,
                            o->alpha_pow, f.d_rgb, f.d_depth, loss_slot, sm + SM_MED, s));
     GSR_TRY(run_blend_backward(ctx, ck, &ro, f.d_rgb, f.d_depth, nullptr, true, s));
-    GSR_TRY(run_project_backward(ctx, P, ck, sm + SM_POSE, nullptr, sm + SM_G6, false, 1.f, s));
+    GSR_TRY(run_project_backward(ctx, ctx->view, P, ck, sm + SM_POSE, nullptr, sm + SM_G6, false, 1.f, s));
     GSR_TRY(run_pose_adam(ctx, sm + SM_POSE, sm + SM_G6, sm + SM_M6, sm + SM_V6, (int32_t *)(sm + SM_STEP),
                           o->lr_rho, o->lr_phi, o->beta1, o->beta2, o->eps, s));
     return GSR_OK;
@@ -512,7 +523,7 @@ extern "C" gsr_status gsr_track_step(gsr_ctx *ctx, const gsr_gaussians *g, const
                 int64_t need = (int64_t)ctx->host_pinned[0];
                 int64_t c = need + need / 2 + 4096;
                 if (c > V.cap_i) {
-                    GSR_TRY(grow_instance_capacity(ctx, c));
+                    GSR_TRY(grow_instance_capacity(ctx, V, c));
                     if (ctx->track_graph) cudaGraphExecDestroy(ctx->track_graph);
                     ctx->track_graph = nullptr;
                 }
@@ -552,7 +563,7 @@ static gsr_status map_iter(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *s
         gsr_render_out ro{f.rgb, f.depth, f.alpha, f.T, f.last, nullptr};
         GSR_TRY(prof_mark(ctx, PROF_BIN, false, s));
         GSR_TRY(launch_set_pose(ctx, d_pose, kfs[k].pose, s));
-        GSR_TRY(run_binning(ctx, P, ck, d_pose, grow, s));
+        GSR_TRY(run_binning(ctx, ctx->view, P, ck, d_pose, grow, s));
         GSR_TRY(prof_mark(ctx, PROF_BIN, true, s));
         GSR_TRY(prof_mark(ctx, PROF_FWD, false, s));
         GSR_TRY(run_blend_forward(ctx, P, ck, &ro, s));
@@ -565,9 +576,99 @@ static gsr_status map_iter(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *s
         GSR_TRY(run_blend_backward(ctx, ck, &ro, f.d_rgb, f.d_depth, nullptr, false, s));
         GSR_TRY(prof_mark(ctx, PROF_BWD, true, s));
         GSR_TRY(prof_mark(ctx, PROF_PBWD, false, s));
-        GSR_TRY(run_project_backward(ctx, P, ck, d_pose, &gr, nullptr, true, 1.f, s));
+        GSR_TRY(run_project_backward(ctx, ctx->view, P, ck, d_pose, &gr, nullptr, true, 1.f, s));
         GSR_TRY(prof_mark(ctx, PROF_PBWD, true, s));
     }
+    GSR_TRY(prof_mark(ctx, PROF_ADAM, false, s));
+    GSR_TRY(run_adam(ctx, g, &gr, st, &o->adam, sm + SM_MAPLOSS, s));
+    GSR_TRY(prof_mark(ctx, PROF_ADAM, true, s));
+    return GSR_OK;
+}
+
+// Batched iteration over n_kf >= 2 keyframes: every keyframe is binned into
+// its own scratch, then ONE persistent forward launch and ONE persistent
+// backward launch cover all (keyframe, tile) items, longest lists first; the
+// projection backward chains all keyframes' gradients in one pass.
+static gsr_status map_iter_multi(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *st, const CamK &ck,
+                                 const gsr_keyframe *kfs, int n_kf, const float *w, const gsr_map_opts *o, bool grow,
+                                 cudaStream_t s)
+{
+    const int64_t n = g->n, HW = (int64_t)ck.W * ck.H;
+    const int tiles = ck.tiles_x * ck.tiles_y;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    GSR_CUDA(ctx, cudaStreamIsCapturing(s, &cap));
+    const bool capturing = cap == cudaStreamCaptureStatusActive;
+    if ((int)ctx->mv.size() < n_kf) {
+        if (capturing) return gsr_fail(ctx, GSR_ERR_STATE, "keyframe scratch must exist before capture");
+        ctx->mv.resize(n_kf);
+    }
+    GSR_TRY(ensure_buf(ctx, ctx->mv_frames, sizeof(float) * 12 * (size_t)HW * n_kf));
+    GSR_TRY(ensure_buf(ctx, ctx->mv_desc, sizeof(BlendView) * n_kf));
+    GSR_TRY(ensure_buf(ctx, ctx->mv_pview, sizeof(ProjView) * n_kf));
+    for (int k = 0; k < 2; ++k) {
+        GSR_TRY(ensure_buf(ctx, ctx->mv_keys[k], sizeof(u32) * (size_t)tiles * n_kf));
+        GSR_TRY(ensure_buf(ctx, ctx->mv_items[k], sizeof(u32) * (size_t)tiles * n_kf));
+    }
+    GSR_TRY(ensure_buf(ctx, ctx->mv_counter, sizeof(u32)));
+    float *G = (float *)ctx->grads.p;
+    gsr_gaussian_grads gr{G, G + 3 * n, G + 6 * n, G + 10 * n, G + 11 * n};
+    float *sm = (float *)ctx->small.p;
+    GSR_CUDA(ctx, cudaMemsetAsync(G, 0, sizeof(float) * 14 * n, s));
+    GSR_CUDA(ctx, cudaMemsetAsync(sm + SM_MAPLOSS, 0, sizeof(float), s));
+    Params P{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, n};
+
+    GSR_TRY(prof_mark(ctx, PROF_BIN, false, s));
+    for (int k = 0; k < n_kf; ++k) {
+        ViewScratch &V = ctx->mv[k];
+        GSR_TRY(ensure_buf(ctx, V.pose, GSR_POSE_WORDS * sizeof(float)));
+        GSR_TRY(launch_set_pose(ctx, (float *)V.pose.p, kfs[k].pose, s));
+        GSR_TRY(run_binning(ctx, V, P, ck, (float *)V.pose.p, grow, s));
+    }
+    // per-keyframe descriptors (device pointers only; fixed once sized)
+    std::vector<BlendView> bv(n_kf);
+    std::vector<ProjView> pv(n_kf);
+    float *frames = (float *)ctx->mv_frames.p;
+    for (int k = 0; k < n_kf; ++k) {
+        float *f = frames + (size_t)k * 12 * HW;
+        gsr_render_out ro{f, f + 3 * HW, f + 4 * HW, f + 5 * HW, (int32_t *)(f + 6 * HW), nullptr};
+        bv[k] = blend_view(ctx->mv[k], &ro, f + 7 * HW, f + 10 * HW, nullptr);
+        pv[k] = ProjView{(const int32_t *)ctx->mv[k].rank_of_gid.p, (const float *)ctx->mv[k].g2d.p,
+                         (const float *)ctx->mv[k].pose.p};
+    }
+    const bool same = ctx->mv_desc_host.size() == bv.size() &&
+                      memcmp(ctx->mv_desc_host.data(), bv.data(), sizeof(BlendView) * n_kf) == 0 &&
+                      memcmp(ctx->mv_pview_host.data(), pv.data(), sizeof(ProjView) * n_kf) == 0;
+    if (!same) {
+        if (capturing) return gsr_fail(ctx, GSR_ERR_STATE, "keyframe scratch moved during capture");
+        GSR_CUDA(ctx, cudaMemcpyAsync(ctx->mv_desc.p, bv.data(), sizeof(BlendView) * n_kf, cudaMemcpyHostToDevice, s));
+        GSR_CUDA(ctx, cudaMemcpyAsync(ctx->mv_pview.p, pv.data(), sizeof(ProjView) * n_kf, cudaMemcpyHostToDevice, s));
+        GSR_CUDA(ctx, cudaStreamSynchronize(s));  // the host vectors go out of scope
+        ctx->mv_desc_host = bv;
+        ctx->mv_pview_host = pv;
+    }
+    const BlendView *dv = (const BlendView *)ctx->mv_desc.p;
+    u32 *keys[2] = {(u32 *)ctx->mv_keys[0].p, (u32 *)ctx->mv_keys[1].p};
+    u32 *items[2] = {(u32 *)ctx->mv_items[0].p, (u32 *)ctx->mv_items[1].p};
+    GSR_TRY(run_make_items(ctx, dv, n_kf, tiles, keys, items, s));
+    GSR_TRY(prof_mark(ctx, PROF_BIN, true, s));
+
+    GSR_TRY(prof_mark(ctx, PROF_FWD, false, s));
+    GSR_TRY(run_blend_multi(ctx, ck, false, dv, items[0], n_kf * tiles, (u32 *)ctx->mv_counter.p, s));
+    GSR_TRY(prof_mark(ctx, PROF_FWD, true, s));
+    GSR_TRY(prof_mark(ctx, PROF_LOSS, false, s));
+    for (int k = 0; k < n_kf; ++k) {
+        float *f = frames + (size_t)k * 12 * HW;
+        GSR_TRY(run_loss_map(ctx, ck.W, ck.H, f, f + 3 * HW, kfs[k].rgb, kfs[k].depth, o->lambda_ssim, o->w_color,
+                             o->w_depth, w[k], f + 7 * HW, f + 10 * HW, sm + SM_MAPLOSS, true, s));
+    }
+    GSR_TRY(prof_mark(ctx, PROF_LOSS, true, s));
+    GSR_TRY(prof_mark(ctx, PROF_BWD, false, s));
+    for (int k = 0; k < n_kf; ++k) GSR_TRY(zero_g2d(ctx, ctx->mv[k], s));
+    GSR_TRY(run_blend_multi(ctx, ck, true, dv, items[0], n_kf * tiles, (u32 *)ctx->mv_counter.p, s));
+    GSR_TRY(prof_mark(ctx, PROF_BWD, true, s));
+    GSR_TRY(prof_mark(ctx, PROF_PBWD, false, s));
+    GSR_TRY(run_project_backward_multi(ctx, P, ck, (const ProjView *)ctx->mv_pview.p, n_kf, &gr, s));
+    GSR_TRY(prof_mark(ctx, PROF_PBWD, true, s));
     GSR_TRY(prof_mark(ctx, PROF_ADAM, false, s));
     GSR_TRY(run_adam(ctx, g, &gr, st, &o->adam, sm + SM_MAPLOSS, s));
     GSR_TRY(prof_mark(ctx, PROF_ADAM, true, s));
@@ -634,7 +735,8 @@ extern "C" gsr_status gsr_map_step(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_
                 GSR_CUDA(ctx, cudaStreamSynchronize(s));
                 GSR_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
                 const int64_t l0 = ctx->launches;
-                gsr_status stt = map_iter(ctx, g, st, ck, kfs, n_kf, w, opt, false, cs);
+                gsr_status stt = n_kf >= 2 ? map_iter_multi(ctx, g, st, ck, kfs, n_kf, w, opt, false, cs)
+                                           : map_iter(ctx, g, st, ck, kfs, n_kf, w, opt, false, cs);
                 ctx->map_graph_kernels = ctx->launches - l0;
                 ctx->launches = l0;
                 cudaGraph_t graph = nullptr;
@@ -653,7 +755,8 @@ extern "C" gsr_status gsr_map_step(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_
             GSR_CUDA(ctx, cudaGraphLaunch(ctx->map_graph, s));
             ctx->launches += ctx->map_graph_kernels;
         } else {
-            GSR_TRY(map_iter(ctx, g, st, ck, kfs, n_kf, w, opt, grow, s));
+            if (n_kf >= 2) GSR_TRY(map_iter_multi(ctx, g, st, ck, kfs, n_kf, w, opt, grow, s));
+            else GSR_TRY(map_iter(ctx, g, st, ck, kfs, n_kf, w, opt, grow, s));
             ctx->map_sized_key = key;
         }
     }
@@ -664,5 +767,89 @@ extern "C" gsr_status gsr_map_step(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_
         out->loss_last = ((const float *)ctx->host_pinned)[20];
         out->iters = n_iters;
     }
+    return GSR_OK;
+}
+
+// --------------------------------------------------------------- autotune
+extern "C" gsr_status gsr_autotune(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam, const gsr_pose *poses,
+                                   int32_t n_poses, int32_t reps, gsr_tune_result *best, gsr_tune_result *all,
+                                   int32_t n_all, void *stream)
+{
+    if (!ctx) return GSR_ERR_INVALID_ARG;
+    GSR_TRY(check_gaussians(ctx, g));
+    if (!cam || !poses || n_poses <= 0 || reps <= 0 || !best || (n_all > 0 && !all))
+        return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "invalid autotune arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t HW = (int64_t)cam->width * cam->height;
+    FrameBufs f;
+    GSR_TRY(frame_bufs(ctx, HW, f));
+    GSR_TRY(ensure_buf(ctx, ctx->grads, sizeof(float) * 14 * (size_t)(g->n > 0 ? g->n : 1)));
+    float *G = (float *)ctx->grads.p;
+    const int64_t n = g->n;
+    gsr_gaussian_grads dg{G, G + 3 * n, G + 6 * n, G + 10 * n, G + 11 * n};
+    // dL/dpixel = 1 everywhere (the d_rgb / d_depth planes of the frame buffers)
+    {
+        std::vector<float> ones((size_t)HW * 4, 1.f);
+        GSR_CUDA(ctx, cudaMemcpy(f.d_rgb, ones.data(), sizeof(float) * 4 * HW, cudaMemcpyHostToDevice));
+    }
+    const int tiles[4][2] = {{16, 16}, {8, 8}, {16, 8}, {32, 8}};
+    const int batches[4] = {32, 64, 128, 256};
+    const gsr_options saved = ctx->opt;
+    const int saved_ppt = ctx->ppt;
+    cudaEvent_t e0, e1;
+    GSR_CUDA(ctx, cudaEventCreate(&e0));
+    GSR_CUDA(ctx, cudaEventCreate(&e1));
+    gsr_tune_result win{};
+    win.ms = 3.4e38f;
+    int idx = 0;
+    gsr_status st = GSR_OK;
+    for (int ti = 0; ti < 4 && st == GSR_OK; ++ti)
+        for (int bi = 0; bi < 4 && st == GSR_OK; ++bi)
+            for (int ppt = 1; ppt <= 2 && st == GSR_OK; ++ppt) {
+                ctx->opt.tile_w = tiles[ti][0];
+                ctx->opt.tile_h = tiles[ti][1];
+                ctx->opt.batch = batches[bi];
+                ctx->ppt = ppt;
+                if (check_camera(ctx, cam) != GSR_OK) continue;  // too many tiles for this shape
+                gsr_render_out ro{f.rgb, f.depth, f.alpha, f.T, f.last, nullptr};
+                float total = 0.f;
+                for (int r = 0; r <= reps && st == GSR_OK; ++r) {
+                    if (r == 1) st = gsr_cuda_check(ctx, cudaEventRecord(e0, s), "event");
+                    for (int k = 0; k < n_poses && st == GSR_OK; ++k) {
+                        st = gsr_render_forward(ctx, g, cam, &poses[k], &ro, stream);
+                        if (st == GSR_OK)
+                            st = gsr_render_backward(ctx, g, cam, &poses[k], &ro, f.d_rgb, f.d_depth, nullptr, &dg, nullptr,
+                                                     stream);
+                    }
+                }
+                if (st != GSR_OK) break;
+                GSR_CUDA(ctx, cudaEventRecord(e1, s));
+                GSR_CUDA(ctx, cudaEventSynchronize(e1));
+                GSR_CUDA(ctx, cudaEventElapsedTime(&total, e0, e1));
+                gsr_tune_result r{tiles[ti][0], tiles[ti][1], batches[bi], ppt, total / (float)reps};
+                if (idx < n_all) all[idx] = r;
+                ++idx;
+                if (r.ms < win.ms) win = r;
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GSR_OK) {
+        ctx->opt = saved;
+        ctx->ppt = saved_ppt;
+        return st;
+    }
+    ctx->opt = saved;
+    ctx->opt.tile_w = win.tile_w;
+    ctx->opt.tile_h = win.tile_h;
+    ctx->opt.batch = win.batch;
+    ctx->opt.pixels_per_thread = win.pixels_per_thread;
+    ctx->ppt = win.pixels_per_thread;
+    // graphs baked the old configuration
+    if (ctx->map_graph) cudaGraphExecDestroy(ctx->map_graph);
+    if (ctx->track_graph) cudaGraphExecDestroy(ctx->track_graph);
+    ctx->map_graph = ctx->track_graph = nullptr;
+    ctx->map_key = ctx->map_sized_key = ctx->track_key = 0;
+    forget_forward(ctx);
+    *best = win;
     return GSR_OK;
 }

@@ -2,214 +2,341 @@
 // Eq. (color_blending) and the depth rendering of Sec. 3.4) and its
 // back-to-front replay (backward, Sec. 3.4 adjoints).
 //
-// One CTA per pixel tile, one thread per pixel.  Gaussian records of the
-// tile's depth-ordered list are staged cooperatively in shared memory, BATCH
-// at a time; a CTA stops loading once every pixel's transmittance fell below
-// the stop threshold.  The backward walks the same list from the largest
-// last-composited index of the tile down to 0, recovering T_j = T_{j+1} /
-// (1 - alpha_j) from the saved final transmittance, and reduces the
-// per-pixel contributions of each Gaussian across the warp with shuffles
-// before one atomic add per warp and gradient component.
+// A CTA renders one pixel tile; each thread owns PPT vertically adjacent
+// pixels of one column, so a warp covers a 16 x (2 PPT) block.  Gaussian
+// records of the tile's depth-ordered list are staged cooperatively in
+// shared memory, BATCH at a time, and every staged record is evaluated for
+// all PPT pixels of a thread (one shared-memory read, PPT evaluations).  The
+// per-pixel arithmetic does not depend on PPT, so outputs are bit-identical
+// for every PPT.  A CTA stops loading once every pixel's transmittance fell
+// below the stop threshold.
+//
+// The backward walks the same list from the largest last-composited index of
+// the tile down to 0, recovering T_j = T_{j+1} / (1 - alpha_j) from the saved
+// final transmittance; each thread first sums its PPT pixels' contributions
+// to a Gaussian, then a transposed warp reduction (12 shuffles for 10
+// components) sums the warp, and one atomic add per warp and component lands
+// in the per-Gaussian accumulator.
+//
+// The same tile bodies run in two launch forms: one CTA per tile of one view,
+// and a persistent grid over (keyframe, tile) items of several views, pulled
+// from a longest-first work list through an atomic counter (no waits).
+#include <algorithm>
+
 #include "gsr_internal.cuh"
 
 namespace {
 
-template <int TW, int TH, int BATCH>
-__global__ void __launch_bounds__(TW *TH) k_blend_fwd(CamK ck, const uint2 *__restrict__ ranges,
-                                                      const u32 *__restrict__ tvals,
-                                                      const float4 *__restrict__ rec,
-                                                      float *__restrict__ out_rgb, float *__restrict__ out_depth,
-                                                      float *__restrict__ out_alpha, float *__restrict__ out_T,
-                                                      int32_t *__restrict__ out_last, int32_t *__restrict__ out_nc)
+template <int TW, int TH, int BATCH, int PPT>
+__device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
+                                         float4 *sC)
 {
-    constexpr int NT = TW * TH;
-    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
-    const int tile = blockIdx.x;
+    constexpr int NT = TW * TH / PPT;
     const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
-    const int ix = tx * TW + (int)threadIdx.x % TW, iy = ty * TH + (int)threadIdx.x / TW;
-    const bool inside = ix < ck.W && iy < ck.H;
-    const float px = (float)ix + 0.5f, py = (float)iy + 0.5f;
-    const uint2 rg = ranges[tile];
+    const int col = (int)threadIdx.x % TW, row0 = ((int)threadIdx.x / TW) * PPT;
+    const int ix = tx * TW + col;
+    const float px = (float)ix + 0.5f;
+    float py[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT], d[PPT];
+    int last[PPT], nc[PPT];
+    bool done[PPT];
+    bool tdone = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int iy = ty * TH + row0 + k;
+        py[k] = (float)iy + 0.5f;
+        done[k] = !(ix < ck.W && iy < ck.H);
+        tdone = tdone && done[k];
+        T[k] = 1.f;
+        c0[k] = c1[k] = c2[k] = d[k] = 0.f;
+        last[k] = -1;
+        nc[k] = 0;
+    }
+    const uint2 rg = vp.ranges[tile];
     const int n = (int)(rg.y - rg.x);
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, d = 0.f;
-    int last = -1, nc = 0;
-    bool done = !inside;
     for (int base = 0; base < n; base += BATCH) {
-        if (__syncthreads_count(done) == NT) break;
+        if (__syncthreads_count(tdone) == NT) break;
         for (int k = threadIdx.x; k < BATCH; k += NT) {
             const int j = base + k;
             if (j < n) {
-                const int64_t r = tvals[rg.x + j];
-                sA[k] = rec[3 * r];
-                sB[k] = rec[3 * r + 1];
-                sC[k] = rec[3 * r + 2];
+                const int64_t r = vp.tvals[rg.x + j];
+                sA[k] = vp.rec[3 * r];
+                sB[k] = vp.rec[3 * r + 1];
+                sC[k] = vp.rec[3 * r + 2];
             }
         }
         __syncthreads();
         const int cnt = min(BATCH, n - base);
-        if (!done) {
-            for (int k = 0; k < cnt; ++k) {
-                const float4 a = sA[k], b = sB[k];
-                const Eval e = eval_gaussian(px, py, a.x, a.y, a.z, a.w, b.x, b.y);
-                if (!e.use) continue;
-                const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
-                if (Tn < GSR_T_STOP) {
-                    done = true;
-                    break;
+        for (int j = 0; j < cnt && !tdone; ++j) {
+            const float4 a = sA[j], b = sB[j];
+            bool all = true;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (!done[k]) {
+                    const Eval e = eval_gaussian(px, py[k], a.x, a.y, a.z, a.w, b.x, b.y);
+                    if (e.use) {
+                        const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, e.alpha));
+                        if (Tn < GSR_T_STOP) {
+                            done[k] = true;
+                        } else {
+                            const float4 c = sC[j];
+                            const float w = e.alpha * T[k];
+                            c0[k] = fmaf(c.x, w, c0[k]);
+                            c1[k] = fmaf(c.y, w, c1[k]);
+                            c2[k] = fmaf(c.z, w, c2[k]);
+                            d[k] = fmaf(b.z, w, d[k]);
+                            T[k] = Tn;
+                            last[k] = base + j;
+                            ++nc[k];
+                        }
+                    }
                 }
-                const float4 c = sC[k];
-                const float w = e.alpha * T;
-                c0 = fmaf(c.x, w, c0);
-                c1 = fmaf(c.y, w, c1);
-                c2 = fmaf(c.z, w, c2);
-                d = fmaf(b.z, w, d);
-                T = Tn;
-                last = base + k;
-                ++nc;
+                all = all && done[k];
             }
+            tdone = all;
         }
     }
-    if (inside) {
-        const int64_t HW = (int64_t)ck.W * ck.H, p = (int64_t)iy * ck.W + ix;
-        out_rgb[p] = c0;
-        out_rgb[HW + p] = c1;
-        out_rgb[2 * HW + p] = c2;
-        out_depth[p] = d;
-        out_alpha[p] = 1.f - T;
-        out_T[p] = T;
-        out_last[p] = last;
-        if (out_nc) out_nc[p] = nc;
+    const int64_t HW = (int64_t)ck.W * ck.H;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int iy = ty * TH + row0 + k;
+        if (ix < ck.W && iy < ck.H) {
+            const int64_t p = (int64_t)iy * ck.W + ix;
+            vp.rgb[p] = c0[k];
+            vp.rgb[HW + p] = c1[k];
+            vp.rgb[2 * HW + p] = c2[k];
+            vp.depth[p] = d[k];
+            vp.alpha[p] = 1.f - T[k];
+            vp.final_T[p] = T[k];
+            vp.last_idx[p] = last[k];
+            if (vp.n_contrib) vp.n_contrib[p] = nc[k];
+        }
     }
 }
 
-template <int NV>
-__device__ __forceinline__ void warp_sum_and_add(float (&v)[NV], const int (&slot)[NV], float *dst)
+// Transposed warp reductions: every shuffle step halves the number of live
+// values per lane, so the 10 image-space gradient components of one Gaussian
+// are summed over the warp with 12 shuffles (instead of 5 per component).
+// Afterwards the lane pair (l, l^1) holds one component's total; the even
+// lane of each pair adds it to the accumulator (g2d slot).
+__device__ __forceinline__ float pick(bool hi, float a, float b) { return hi ? b : a; }
+
+__device__ __forceinline__ void warp_reduce_add10(const float (&v)[10], float *dst)
 {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-    }
+    const unsigned F = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    float mine = 0.f;
-    int s = 0;
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+    float a[6];
 #pragma unroll
-    for (int i = 0; i < NV; ++i)
-        if (lane == i) {
-            mine = v[i];
-            s = slot[i];
-        }
-    if (lane < NV && mine != 0.f) atomicAdd(dst + s, mine);
+    for (int i = 0; i < 5; ++i) a[i] = pick(h4, v[i], v[i + 5]) + __shfl_xor_sync(F, pick(h4, v[i + 5], v[i]), 16);
+    a[5] = 0.f;
+    float b[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) b[i] = pick(h3, a[i], a[i + 3]) + __shfl_xor_sync(F, pick(h3, a[i + 3], a[i]), 8);
+    b[3] = 0.f;
+    float c[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) c[i] = pick(h2, b[i], b[i + 2]) + __shfl_xor_sync(F, pick(h2, b[i + 2], b[i]), 4);
+    float d = pick(h1, c[0], c[1]) + __shfl_xor_sync(F, pick(h1, c[1], c[0]), 2);
+    d += __shfl_xor_sync(F, d, 1);
+    const int bi = (h2 ? 2 : 0) + (h1 ? 1 : 0);  // index into b (3 = padding)
+    const int ai = (h3 ? 3 : 0) + bi;            // index into a (5 = padding)
+    if (!(lane & 1) && bi < 3 && ai < 5 && d != 0.f) atomicAdd(dst + (h4 ? 5 : 0) + ai, d);
+}
+
+// pose-only variant: (u, v, conic a, b, c, z) -> slots 0..4 and 9; 8 shuffles
+__device__ __forceinline__ void warp_reduce_add6(const float (&v)[6], float *dst)
+{
+    const unsigned F = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+    float a[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a[i] = pick(h4, v[i], v[i + 3]) + __shfl_xor_sync(F, pick(h4, v[i + 3], v[i]), 16);
+    a[3] = 0.f;
+    float b[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) b[i] = pick(h3, a[i], a[i + 2]) + __shfl_xor_sync(F, pick(h3, a[i + 2], a[i]), 8);
+    float c = pick(h2, b[0], b[1]) + __shfl_xor_sync(F, pick(h2, b[1], b[0]), 4);
+    c += __shfl_xor_sync(F, c, 2);
+    c += __shfl_xor_sync(F, c, 1);
+    const int ai = (h3 ? 2 : 0) + (h2 ? 1 : 0);  // index into a (3 = padding)
+    const int comp = (h4 ? 3 : 0) + ai;          // 0..5
+    if (!(lane & 3) && ai < 3 && c != 0.f) atomicAdd(dst + (comp == 5 ? 9 : comp), c);
 }
 
 // POSE_ONLY: the tracker needs only the gradients feeding the pose
 // (u, v, conic, depth); colour and opacity gradients are skipped.
-template <int TW, int TH, int BATCH, bool POSE_ONLY>
-__global__ void __launch_bounds__(TW *TH) k_blend_bwd(CamK ck, const uint2 *__restrict__ ranges,
-                                                      const u32 *__restrict__ tvals,
-                                                      const float4 *__restrict__ rec,
-                                                      const float *__restrict__ fin_T,
-                                                      const int32_t *__restrict__ last_idx,
-                                                      const float *__restrict__ d_rgb,
-                                                      const float *__restrict__ d_depth,
-                                                      const float *__restrict__ d_alpha, float *__restrict__ g2d)
+template <int TW, int TH, int BATCH, int PPT, bool POSE_ONLY>
+__device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
+                                         float4 *sC, u32 *sR, int *s_max)
 {
-    constexpr int NT = TW * TH;
-    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
-    __shared__ u32 sR[BATCH];
-    __shared__ int s_max;
-    const int tile = blockIdx.x;
+    constexpr int NT = TW * TH / PPT;
     const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
-    const int ix = tx * TW + (int)threadIdx.x % TW, iy = ty * TH + (int)threadIdx.x / TW;
-    const bool inside = ix < ck.W && iy < ck.H;
-    const float px = (float)ix + 0.5f, py = (float)iy + 0.5f;
-    const uint2 rg = ranges[tile];
-    const int64_t HW = (int64_t)ck.W * ck.H, p = (int64_t)iy * ck.W + ix;
-    int L = -1;
-    float Tf = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, gd = 0.f, ga = 0.f;
-    if (inside) {
-        L = last_idx[p];
-        Tf = fin_T[p];
-        if (d_rgb) {
-            g0 = d_rgb[p];
-            g1 = d_rgb[HW + p];
-            g2 = d_rgb[2 * HW + p];
+    const int col = (int)threadIdx.x % TW, row0 = ((int)threadIdx.x / TW) * PPT;
+    const int ix = tx * TW + col;
+    const float px = (float)ix + 0.5f;
+    const uint2 rg = vp.ranges[tile];
+    const int64_t HW = (int64_t)ck.W * ck.H;
+    float py[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], gd[PPT], gaT[PPT], S0[PPT], S1[PPT], S2[PPT], Sd[PPT];
+    int L[PPT];
+    int lmax = -1;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int iy = ty * TH + row0 + k;
+        py[k] = (float)iy + 0.5f;
+        L[k] = -1;
+        T[k] = 1.f;
+        g0[k] = g1[k] = g2[k] = gd[k] = gaT[k] = 0.f;
+        S0[k] = S1[k] = S2[k] = Sd[k] = 0.f;
+        if (ix < ck.W && iy < ck.H) {
+            const int64_t p = (int64_t)iy * ck.W + ix;
+            L[k] = vp.last_idx[p];
+            T[k] = vp.final_T[p];
+            if (vp.d_rgb) {
+                g0[k] = vp.d_rgb[p];
+                g1[k] = vp.d_rgb[HW + p];
+                g2[k] = vp.d_rgb[2 * HW + p];
+            }
+            if (vp.d_depth) gd[k] = vp.d_depth[p];
+            if (vp.d_alpha) gaT[k] = vp.d_alpha[p] * T[k];
         }
-        if (d_depth) gd = d_depth[p];
-        if (d_alpha) ga = d_alpha[p];
+        lmax = max(lmax, L[k]);
     }
-    if (threadIdx.x == 0) s_max = -1;
+    if (threadIdx.x == 0) *s_max = -1;
     __syncthreads();
-    const int wmax = __reduce_max_sync(0xffffffffu, L);
-    if ((threadIdx.x & 31) == 0) atomicMax(&s_max, wmax);
+    const int wmax = __reduce_max_sync(0xffffffffu, lmax);
+    if ((threadIdx.x & 31) == 0) atomicMax(s_max, wmax);
     __syncthreads();
-    const int nend = min(s_max + 1, (int)(rg.y - rg.x));  // saved state never reads past the list
-    float T = Tf, S0 = 0.f, S1 = 0.f, S2 = 0.f, Sd = 0.f;
-    const float gaT = ga * Tf;
+    const int nend = min(*s_max + 1, (int)(rg.y - rg.x));  // saved state never reads past the list
     for (int bend = nend; bend > 0; bend -= BATCH) {
         const int bstart = max(0, bend - BATCH);
         const int cnt = bend - bstart;
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += NT) {
-            const u32 r = tvals[rg.x + bstart + k];
+            const u32 r = vp.tvals[rg.x + bstart + k];
             sR[k] = r;
-            sA[k] = rec[3 * (int64_t)r];
-            sB[k] = rec[3 * (int64_t)r + 1];
-            sC[k] = rec[3 * (int64_t)r + 2];
+            sA[k] = vp.rec[3 * (int64_t)r];
+            sB[k] = vp.rec[3 * (int64_t)r + 1];
+            sC[k] = vp.rec[3 * (int64_t)r + 2];
         }
         __syncthreads();
-        for (int k = cnt - 1; k >= 0; --k) {
-            const int j = bstart + k;
-            float gu = 0.f, gv = 0.f, gca = 0.f, gcb = 0.f, gcc = 0.f, gop = 0.f, gr = 0.f, gg = 0.f,
-                  gb = 0.f, gz = 0.f;
+        for (int j = cnt - 1; j >= 0; --j) {
+            const int jj = bstart + j;
+            float gu = 0.f, gv = 0.f, gca = 0.f, gcb = 0.f, gcc = 0.f, gop = 0.f, gr = 0.f, gg = 0.f, gb = 0.f,
+                  gz = 0.f;
             bool contrib = false;
-            if (j <= L) {
-                const float4 a = sA[k], b = sB[k];
-                const Eval e = eval_gaussian(px, py, a.x, a.y, a.z, a.w, b.x, b.y);
-                if (e.use) {
-                    contrib = true;
-                    const float4 c = sC[k];
-                    const float om = 1.f - e.alpha;
-                    const float iom = 1.f / om;
-                    T = T * iom;  // T_j
-                    const float w = e.alpha * T;
-                    float dLda = g0 * (c.x * T - S0 * iom) + g1 * (c.y * T - S1 * iom) + g2 * (c.z * T - S2 * iom)
-                               + gd * (b.z * T - Sd * iom) + gaT * iom;
-                    S0 = fmaf(c.x, w, S0);
-                    S1 = fmaf(c.y, w, S1);
-                    S2 = fmaf(c.z, w, S2);
-                    Sd = fmaf(b.z, w, Sd);
-                    gz = gd * w;
-                    if (!POSE_ONLY) {
-                        gr = g0 * w;
-                        gg = g1 * w;
-                        gb = g2 * w;
-                    }
-                    if (e.G <= GSR_ALPHA_MAX) {
-                        if (!POSE_ONLY) gop = dLda * e.ex;
-                        const float ds = -dLda * e.G;
-                        gu = -ds * (a.z * e.dx + a.w * e.dy);
-                        gv = -ds * (a.w * e.dx + b.x * e.dy);
-                        gca = 0.5f * ds * e.dx * e.dx;
-                        gcb = ds * e.dx * e.dy;
-                        gcc = 0.5f * ds * e.dy * e.dy;
+            const float4 a = sA[j], b = sB[j];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (jj <= L[k]) {
+                    const Eval e = eval_gaussian(px, py[k], a.x, a.y, a.z, a.w, b.x, b.y);
+                    if (e.use) {
+                        contrib = true;
+                        const float4 c = sC[j];
+                        const float iom = 1.f / (1.f - e.alpha);
+                        T[k] = T[k] * iom;  // T_j
+                        const float w = e.alpha * T[k];
+                        const float dLda = g0[k] * (c.x * T[k] - S0[k] * iom) + g1[k] * (c.y * T[k] - S1[k] * iom)
+                                         + g2[k] * (c.z * T[k] - S2[k] * iom) + gd[k] * (b.z * T[k] - Sd[k] * iom)
+                                         + gaT[k] * iom;
+                        S0[k] = fmaf(c.x, w, S0[k]);
+                        S1[k] = fmaf(c.y, w, S1[k]);
+                        S2[k] = fmaf(c.z, w, S2[k]);
+                        Sd[k] = fmaf(b.z, w, Sd[k]);
+                        gz = fmaf(gd[k], w, gz);
+                        if (!POSE_ONLY) {
+                            gr = fmaf(g0[k], w, gr);
+                            gg = fmaf(g1[k], w, gg);
+                            gb = fmaf(g2[k], w, gb);
+                        }
+                        if (e.G <= GSR_ALPHA_MAX) {
+                            if (!POSE_ONLY) gop = fmaf(dLda, e.ex, gop);
+                            const float ds = -dLda * e.G;
+                            gu = fmaf(-ds, a.z * e.dx + a.w * e.dy, gu);
+                            gv = fmaf(-ds, a.w * e.dx + b.x * e.dy, gv);
+                            gca = fmaf(0.5f * ds, e.dx * e.dx, gca);
+                            gcb = fmaf(ds, e.dx * e.dy, gcb);
+                            gcc = fmaf(0.5f * ds, e.dy * e.dy, gcc);
+                        }
                     }
                 }
             }
             if (__ballot_sync(0xffffffffu, contrib)) {
-                float *dst = g2d + 12 * (int64_t)sR[k];
+                float *dst = vp.g2d + 12 * (int64_t)sR[j];
                 if (POSE_ONLY) {
-                    float v[6] = {gu, gv, gca, gcb, gcc, gz};
-                    const int slot[6] = {0, 1, 2, 3, 4, 9};
-                    warp_sum_and_add<6>(v, slot, dst);
+                    const float v[6] = {gu, gv, gca, gcb, gcc, gz};
+                    warp_reduce_add6(v, dst);
                 } else {
-                    float v[10] = {gu, gv, gca, gcb, gcc, gop, gr, gg, gb, gz};
-                    const int slot[10] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9};
-                    warp_sum_and_add<10>(v, slot, dst);
+                    const float v[10] = {gu, gv, gca, gcb, gcc, gop, gr, gg, gb, gz};
+                    warp_reduce_add10(v, dst);
                 }
             }
         }
     }
+}
+
+template <int TW, int TH, int BATCH, int PPT>
+__global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd(CamK ck, BlendView vp)
+{
+    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
+    fwd_tile<TW, TH, BATCH, PPT>(ck, vp, blockIdx.x, sA, sB, sC);
+}
+
+template <int TW, int TH, int BATCH, int PPT, bool POSE_ONLY>
+__global__ void __launch_bounds__(TW *TH / PPT) k_blend_bwd(CamK ck, BlendView vp)
+{
+    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
+    __shared__ u32 sR[BATCH];
+    __shared__ int s_max;
+    bwd_tile<TW, TH, BATCH, PPT, POSE_ONLY>(ck, vp, blockIdx.x, sA, sB, sC, sR, &s_max);
+}
+
+// Persistent forms: items[i] = (view << 16) | tile, longest lists first.
+__device__ __forceinline__ int next_item(u32 *counter, int *s_item)
+{
+    __syncthreads();  // everyone has read the previous item
+    if (threadIdx.x == 0) *s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    return *s_item;
+}
+
+template <int TW, int TH, int BATCH, int PPT>
+__global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd_multi(CamK ck, const BlendView *__restrict__ views,
+                                                                  const u32 *__restrict__ items, int n_items,
+                                                                  u32 *counter)
+{
+    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
+    __shared__ int s_item;
+    for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
+        const u32 w = items[it];
+        fwd_tile<TW, TH, BATCH, PPT>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC);
+    }
+}
+
+template <int TW, int TH, int BATCH, int PPT>
+__global__ void __launch_bounds__(TW *TH / PPT) k_blend_bwd_multi(CamK ck, const BlendView *__restrict__ views,
+                                                                  const u32 *__restrict__ items, int n_items,
+                                                                  u32 *counter)
+{
+    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
+    __shared__ u32 sR[BATCH];
+    __shared__ int s_max, s_item;
+    for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
+        const u32 w = items[it];
+        bwd_tile<TW, TH, BATCH, PPT, false>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, &s_max);
+    }
+}
+
+__global__ void k_make_items(const BlendView *__restrict__ views, int n_views, int tiles, u32 *__restrict__ keys,
+                             u32 *__restrict__ items)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_views * tiles) return;
+    const int v = i / tiles, t = i % tiles;
+    const uint2 rg = views[v].ranges[t];
+    const u32 len = min(rg.y - rg.x, 0xffffu);
+    keys[i] = 0xffffu - len;  // ascending sort = longest first
+    items[i] = ((u32)v << 16) | (u32)t;
 }
 
 __global__ void k_zero_g2d(int64_t cap, const u32 *__restrict__ d_v, float4 *__restrict__ g2d)
@@ -219,85 +346,183 @@ __global__ void k_zero_g2d(int64_t cap, const u32 *__restrict__ d_v, float4 *__r
     if (i < n && i < cap * 3) g2d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-template <int TW, int TH, int BATCH>
-gsr_status launch_fwd(gsr_ctx *ctx, const CamK &ck, gsr_render_out *o, cudaStream_t s)
+// ------------------------------------------------------------- dispatch
+enum Kind { FWD, BWD, BWD_POSE, FWD_MULTI, BWD_MULTI };
+
+struct Launch {
+    Kind kind;
+    const CamK *ck;
+    BlendView vp;
+    const BlendView *views;
+    const u32 *items;
+    int n_items;
+    u32 *counter;
+    unsigned grid;
+};
+
+template <int TW, int TH, int BATCH, int PPT>
+gsr_status launch_cfg(gsr_ctx *ctx, const Launch &L, cudaStream_t s)
 {
-    ViewScratch &V = ctx->view;
-    const unsigned tiles = (unsigned)(ck.tiles_x * ck.tiles_y);
-    k_blend_fwd<TW, TH, BATCH><<<tiles, TW * TH, 0, s>>>(ck, (uint2 *)V.ranges.p, (u32 *)V.tvals[0].p,
-                                                        (float4 *)V.rec_sorted.p, o->rgb, o->depth, o->alpha,
-                                                        o->final_T, o->last_idx, o->n_contrib);
+    constexpr int NT = TW * TH / PPT;
+    switch (L.kind) {
+    case FWD: k_blend_fwd<TW, TH, BATCH, PPT><<<L.grid, NT, 0, s>>>(*L.ck, L.vp); break;
+    case BWD: k_blend_bwd<TW, TH, BATCH, PPT, false><<<L.grid, NT, 0, s>>>(*L.ck, L.vp); break;
+    case BWD_POSE: k_blend_bwd<TW, TH, BATCH, PPT, true><<<L.grid, NT, 0, s>>>(*L.ck, L.vp); break;
+    case FWD_MULTI:
+        k_blend_fwd_multi<TW, TH, BATCH, PPT><<<L.grid, NT, 0, s>>>(*L.ck, L.views, L.items, L.n_items, L.counter);
+        break;
+    case BWD_MULTI:
+        k_blend_bwd_multi<TW, TH, BATCH, PPT><<<L.grid, NT, 0, s>>>(*L.ck, L.views, L.items, L.n_items, L.counter);
+        break;
+    }
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     return GSR_OK;
 }
 
-template <int TW, int TH, int BATCH>
-gsr_status launch_bwd(gsr_ctx *ctx, const CamK &ck, const gsr_render_out *sv, const float *d_rgb,
-                      const float *d_depth, const float *d_alpha, bool pose_only, cudaStream_t s)
-{
-    ViewScratch &V = ctx->view;
-    const unsigned tiles = (unsigned)(ck.tiles_x * ck.tiles_y);
-    if (pose_only)
-        k_blend_bwd<TW, TH, BATCH, true><<<tiles, TW * TH, 0, s>>>(
-            ck, (uint2 *)V.ranges.p, (u32 *)V.tvals[0].p, (float4 *)V.rec_sorted.p, sv->final_T, sv->last_idx,
-            d_rgb, d_depth, d_alpha, (float *)V.g2d.p);
-    else
-        k_blend_bwd<TW, TH, BATCH, false><<<tiles, TW * TH, 0, s>>>(
-            ck, (uint2 *)V.ranges.p, (u32 *)V.tvals[0].p, (float4 *)V.rec_sorted.p, sv->final_T, sv->last_idx,
-            d_rgb, d_depth, d_alpha, (float *)V.g2d.p);
-    ctx->launches += 1;
-    GSR_LAUNCHED(ctx);
-    return GSR_OK;
-}
-
-template <int TW, int TH>
-gsr_status dispatch_batch_fwd(gsr_ctx *ctx, const CamK &ck, gsr_render_out *o, cudaStream_t s)
+template <int TW, int TH, int PPT>
+gsr_status by_batch(gsr_ctx *ctx, const Launch &L, cudaStream_t s)
 {
     switch (ctx->opt.batch) {
-    case 32: return launch_fwd<TW, TH, 32>(ctx, ck, o, s);
-    case 64: return launch_fwd<TW, TH, 64>(ctx, ck, o, s);
-    case 128: return launch_fwd<TW, TH, 128>(ctx, ck, o, s);
-    default: return launch_fwd<TW, TH, 256>(ctx, ck, o, s);
+    case 32: return launch_cfg<TW, TH, 32, PPT>(ctx, L, s);
+    case 64: return launch_cfg<TW, TH, 64, PPT>(ctx, L, s);
+    case 128: return launch_cfg<TW, TH, 128, PPT>(ctx, L, s);
+    default: return launch_cfg<TW, TH, 256, PPT>(ctx, L, s);
     }
 }
 
 template <int TW, int TH>
-gsr_status dispatch_batch_bwd(gsr_ctx *ctx, const CamK &ck, const gsr_render_out *sv, const float *a,
-                              const float *b, const float *c, bool po, cudaStream_t s)
+gsr_status by_ppt(gsr_ctx *ctx, const Launch &L, cudaStream_t s)
 {
-    switch (ctx->opt.batch) {
-    case 32: return launch_bwd<TW, TH, 32>(ctx, ck, sv, a, b, c, po, s);
-    case 64: return launch_bwd<TW, TH, 64>(ctx, ck, sv, a, b, c, po, s);
-    case 128: return launch_bwd<TW, TH, 128>(ctx, ck, sv, a, b, c, po, s);
-    default: return launch_bwd<TW, TH, 256>(ctx, ck, sv, a, b, c, po, s);
+    if (ctx->ppt == 1) return by_batch<TW, TH, 1>(ctx, L, s);
+    return by_batch<TW, TH, 2>(ctx, L, s);
+}
+
+gsr_status dispatch(gsr_ctx *ctx, const Launch &L, cudaStream_t s)
+{
+    const int tw = ctx->opt.tile_w, th = ctx->opt.tile_h;
+    if (tw == 16 && th == 16) return by_ppt<16, 16>(ctx, L, s);
+    if (tw == 8 && th == 8) return by_ppt<8, 8>(ctx, L, s);
+    if (tw == 16 && th == 8) return by_ppt<16, 8>(ctx, L, s);
+    if (tw == 32 && th == 8) return by_ppt<32, 8>(ctx, L, s);
+    return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "unsupported tile size");
+}
+
+template <int TW, int TH, int BATCH, int PPT>
+int occ_cfg(bool fwd)
+{
+    int nb = 0;
+    constexpr int NT = TW * TH / PPT;
+    cudaError_t e;
+    if (fwd) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blend_fwd_multi<TW, TH, BATCH, PPT>, NT, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blend_bwd_multi<TW, TH, BATCH, PPT>, NT, 0);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        nb = 1;
     }
+    return nb;
+}
+
+template <int TW, int TH, int PPT>
+int occ_batch(int batch, bool fwd)
+{
+    switch (batch) {
+    case 32: return occ_cfg<TW, TH, 32, PPT>(fwd);
+    case 64: return occ_cfg<TW, TH, 64, PPT>(fwd);
+    case 128: return occ_cfg<TW, TH, 128, PPT>(fwd);
+    default: return occ_cfg<TW, TH, 256, PPT>(fwd);
+    }
+}
+
+template <int TW, int TH>
+int occ_ppt(int ppt, int batch, bool fwd)
+{
+    return ppt == 1 ? occ_batch<TW, TH, 1>(batch, fwd) : occ_batch<TW, TH, 2>(batch, fwd);
 }
 
 } // namespace
 
+BlendView blend_view(const ViewScratch &V, const gsr_render_out *o, const float *d_rgb, const float *d_depth,
+                     const float *d_alpha)
+{
+    BlendView b{};
+    b.ranges = (const uint2 *)V.ranges.p;
+    b.tvals = (const u32 *)V.tvals[0].p;
+    b.rec = (const float4 *)V.rec_sorted.p;
+    b.rgb = o->rgb;
+    b.depth = o->depth;
+    b.alpha = o->alpha;
+    b.final_T = o->final_T;
+    b.last_idx = o->last_idx;
+    b.n_contrib = o->n_contrib;
+    b.d_rgb = d_rgb;
+    b.d_depth = d_depth;
+    b.d_alpha = d_alpha;
+    b.g2d = (float *)V.g2d.p;
+    return b;
+}
+
 gsr_status run_blend_forward(gsr_ctx *ctx, const Params &, const CamK &ck, gsr_render_out *o, cudaStream_t s)
 {
-    const int tw = ctx->opt.tile_w, th = ctx->opt.tile_h;
-    if (tw == 16 && th == 16) return dispatch_batch_fwd<16, 16>(ctx, ck, o, s);
-    if (tw == 8 && th == 8) return dispatch_batch_fwd<8, 8>(ctx, ck, o, s);
-    if (tw == 16 && th == 8) return dispatch_batch_fwd<16, 8>(ctx, ck, o, s);
-    if (tw == 32 && th == 8) return dispatch_batch_fwd<32, 8>(ctx, ck, o, s);
-    return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "unsupported tile size");
+    Launch L{};
+    L.kind = FWD;
+    L.ck = &ck;
+    L.vp = blend_view(ctx->view, o, nullptr, nullptr, nullptr);
+    L.grid = (unsigned)(ck.tiles_x * ck.tiles_y);
+    return dispatch(ctx, L, s);
+}
+
+gsr_status zero_g2d(gsr_ctx *ctx, ViewScratch &V, cudaStream_t s)
+{
+    k_zero_g2d<<<(unsigned)ceil_div(V.cap_n * 3, 256), 256, 0, s>>>(V.cap_n, (u32 *)V.counters.p + CNT_VISIBLE,
+                                                                    (float4 *)V.g2d.p);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
 }
 
 gsr_status run_blend_backward(gsr_ctx *ctx, const CamK &ck, const gsr_render_out *sv, const float *d_rgb,
                               const float *d_depth, const float *d_alpha, bool pose_only, cudaStream_t s)
 {
-    ViewScratch &V = ctx->view;
-    k_zero_g2d<<<(unsigned)ceil_div(V.cap_n * 3, 256), 256, 0, s>>>(V.cap_n, (u32 *)V.counters.p + CNT_VISIBLE,
-                                                                    (float4 *)V.g2d.p);
+    GSR_TRY(zero_g2d(ctx, ctx->view, s));
+    Launch L{};
+    L.kind = pose_only ? BWD_POSE : BWD;
+    L.ck = &ck;
+    L.vp = blend_view(ctx->view, sv, d_rgb, d_depth, d_alpha);
+    L.grid = (unsigned)(ck.tiles_x * ck.tiles_y);
+    return dispatch(ctx, L, s);
+}
+
+gsr_status run_blend_multi(gsr_ctx *ctx, const CamK &ck, bool backward, const BlendView *views, const u32 *items,
+                           int n_items, u32 *counter, cudaStream_t s)
+{
+    int dev_sms = 0;
+    GSR_CUDA(ctx, cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int tw = ctx->opt.tile_w, th = ctx->opt.tile_h, b = ctx->opt.batch, ppt = ctx->ppt;
+    int per_sm = 1;
+    if (tw == 16 && th == 16) per_sm = occ_ppt<16, 16>(ppt, b, !backward);
+    else if (tw == 8 && th == 8) per_sm = occ_ppt<8, 8>(ppt, b, !backward);
+    else if (tw == 16 && th == 8) per_sm = occ_ppt<16, 8>(ppt, b, !backward);
+    else if (tw == 32 && th == 8) per_sm = occ_ppt<32, 8>(ppt, b, !backward);
+    if (per_sm < 1) per_sm = 1;
+    Launch L{};
+    L.kind = backward ? BWD_MULTI : FWD_MULTI;
+    L.ck = &ck;
+    L.views = views;
+    L.items = items;
+    L.n_items = n_items;
+    L.counter = counter;
+    L.grid = (unsigned)std::min<int64_t>((int64_t)dev_sms * per_sm, n_items > 0 ? n_items : 1);
+    GSR_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(u32), s));
+    return dispatch(ctx, L, s);
+}
+
+gsr_status run_make_items(gsr_ctx *ctx, const BlendView *views, int n_views, int tiles, u32 *keys[2], u32 *items[2],
+                          cudaStream_t s)
+{
+    const int n = n_views * tiles;
+    k_make_items<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(views, n_views, tiles, keys[0], items[0]);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
-    const int tw = ctx->opt.tile_w, th = ctx->opt.tile_h;
-    if (tw == 16 && th == 16) return dispatch_batch_bwd<16, 16>(ctx, ck, sv, d_rgb, d_depth, d_alpha, pose_only, s);
-    if (tw == 8 && th == 8) return dispatch_batch_bwd<8, 8>(ctx, ck, sv, d_rgb, d_depth, d_alpha, pose_only, s);
-    if (tw == 16 && th == 8) return dispatch_batch_bwd<16, 8>(ctx, ck, sv, d_rgb, d_depth, d_alpha, pose_only, s);
-    if (tw == 32 && th == 8) return dispatch_batch_bwd<32, 8>(ctx, ck, sv, d_rgb, d_depth, d_alpha, pose_only, s);
-    return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "unsupported tile size");
+    return radix_sort_pairs(ctx, keys, items, n, nullptr, 16, s);
 }

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/gsr.h"
 
@@ -62,8 +63,25 @@ struct ViewScratch {
     uint64_t generation = 0;
 };
 
+// Pointers one blend kernel needs for one view.
+struct BlendView {
+    const uint2 *ranges;
+    const u32 *tvals;
+    const float4 *rec;
+    float *rgb, *depth, *alpha, *final_T;
+    int32_t *last_idx, *n_contrib;
+    const float *d_rgb, *d_depth, *d_alpha;
+    float *g2d;
+};
+// per-keyframe inputs of the multi-keyframe projection backward
+struct ProjView {
+    const int32_t *rank_of_gid;
+    const float *g2d;
+    const float *pose;
+};
 struct gsr_ctx {
     gsr_options opt;
+    int ppt = 2;  // pixels per thread of the blend kernels
     int device = 0;
     std::string err;
     int64_t launches = 0;
@@ -93,6 +111,11 @@ struct gsr_ctx {
     bool prof = false;
     cudaEvent_t prof_ev[2 * 8] = {};
     u32 *host_pinned = nullptr; // small pinned readback buffer
+    // batched multi-keyframe mapping: per-keyframe scratch and frames
+    std::vector<ViewScratch> mv;
+    DevBuf mv_frames, mv_desc, mv_pview, mv_keys[2], mv_items[2], mv_counter;
+    std::vector<BlendView> mv_desc_host;
+    std::vector<ProjView> mv_pview_host;
 };
 
 // -------------------------------------------------------------- host helpers
@@ -122,8 +145,8 @@ gsr_status scan_exclusive(gsr_ctx *ctx, const u32 *in, u32 *out, int64_t n_cap, 
 gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_cap, const u32 *d_n,
                             int bits, cudaStream_t s);
 
-// Grows the tile-instance capacity (and the sort scratch sized from it).
-gsr_status grow_instance_capacity(gsr_ctx *ctx, int64_t c);
+// Grows the tile-instance capacity of V (and the sort scratch sized from it).
+gsr_status grow_instance_capacity(gsr_ctx *ctx, ViewScratch &V, int64_t c);
 
 // ------------------------------------------------------------ device math
 struct CamK {
@@ -198,9 +221,17 @@ struct Params {
     int64_t n;
 };
 
+BlendView blend_view(const ViewScratch &V, const gsr_render_out *o, const float *d_rgb, const float *d_depth,
+                     const float *d_alpha);
+gsr_status zero_g2d(gsr_ctx *ctx, ViewScratch &V, cudaStream_t s);
+// persistent blend over items (view << 16 | tile) of several views
+gsr_status run_blend_multi(gsr_ctx *ctx, const CamK &ck, bool backward, const BlendView *views, const u32 *items,
+                           int n_items, u32 *counter, cudaStream_t s);
+
 gsr_status launch_set_pose(gsr_ctx *ctx, float *d_pose, const gsr_pose &p, cudaStream_t s);
-// Projection + binning into ctx->view; returns after enqueueing (no sync)
-gsr_status run_binning(gsr_ctx *ctx, const Params &P, const CamK &ck, const float *d_pose,
+// Projection + binning into V; returns after enqueueing (no sync unless
+// allow_grow, which reads the instance count back once to size V)
+gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK &ck, const float *d_pose,
                        bool allow_grow, cudaStream_t s);
 gsr_status run_blend_forward(gsr_ctx *ctx, const Params &P, const CamK &ck, gsr_render_out *out,
                              cudaStream_t s);
@@ -209,9 +240,12 @@ gsr_status run_blend_backward(gsr_ctx *ctx, const CamK &ck, const gsr_render_out
                               bool pose_only, cudaStream_t s);
 // chain image-space gradients to parameters; accumulate = add w * grad into
 // the outputs instead of overwriting them.
-gsr_status run_project_backward(gsr_ctx *ctx, const Params &P, const CamK &ck, const float *d_pose,
-                                gsr_gaussian_grads *dg, float *d_pose6, bool accumulate,
+gsr_status run_project_backward(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK &ck,
+                                const float *d_pose, gsr_gaussian_grads *dg, float *d_pose6, bool accumulate,
                                 float weight, cudaStream_t s);
+// adds the gradients of every keyframe's image-space gradients to dg (one pass)
+gsr_status run_project_backward_multi(gsr_ctx *ctx, const Params &P, const CamK &ck, const ProjView *views,
+                                      int n_views, gsr_gaussian_grads *dg, cudaStream_t s);
 gsr_status run_loss_map(gsr_ctx *ctx, int W, int H, const float *rgb, const float *depth,
                         const float *rgb_t, const float *depth_t, float lam, float wc, float wd,
                         float scale, float *d_rgb, float *d_depth, float *loss_dev, bool accumulate_loss,
@@ -232,3 +266,7 @@ gsr_status copy_tile_lists(gsr_ctx *ctx, int64_t n, int64_t n_tiles, u32 *ranges
 enum { PROF_BIN = 0, PROF_FWD = 1, PROF_LOSS = 2, PROF_BWD = 3, PROF_PBWD = 4, PROF_ADAM = 5, PROF_NSLOT = 6 };
 // records the start (end = false) or end event of a phase on `s` when profiling
 gsr_status prof_mark(gsr_ctx *ctx, int phase, bool end, cudaStream_t s);
+// work list of the persistent blend: items (view << 16 | tile) of n_views
+// views, sorted longest tile list first (stable), into items[0]
+gsr_status run_make_items(gsr_ctx *ctx, const BlendView *views, int n_views, int tiles, u32 *keys[2], u32 *items[2],
+                          cudaStream_t s);

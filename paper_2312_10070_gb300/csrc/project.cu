@@ -268,8 +268,114 @@ __global__ void k_ranges(int64_t cap_i, const u32 *__restrict__ d_n, const u32 *
 }
 
 // --------------------------------------------------------------- backward
-// K6: image-space gradients g2 = (u, v, conic a, b, c, opacity, r, g, b, z)
-// -> parameter gradients and per-Gaussian pose adjoint (left perturbation).
+// Chain of one Gaussian's image-space gradients
+//   q0 = (u, v, conic a, conic b), q1 = (conic c, opacity, r, g), q2 = (b, z, -, -)
+// back through the projection of Sec. 3.1 to its mean, log-scales, quaternion
+// and opacity logit, and (gpose != nullptr) to the left perturbation
+// xi = (rho, phi) of the pose.  Colour gradients pass through unchanged.
+__device__ __forceinline__ void chain_to_params(const CamK &ck, const PoseR &pr, const GProj &g, float4 q0, float4 q1,
+                                                float4 q2, float gm[3], float gls[3], float gq[4], float *glog,
+                                                float gpose[6])
+{
+    const float gu = q0.x, gv = q0.y, gca = q0.z, gcb = q0.w, gcc = q1.x, gop = q1.y, gz = q2.y;
+    *glog = gop * g.op * (1.f - g.op);
+    // conic Q = S^-1: G_S = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]]
+    const float idet = 1.f / g.det;
+    const float Qa = g.c * idet, Qb = -g.b * idet, Qc = g.a * idet;
+    const float hb = 0.5f * gcb;
+    const float t00 = Qa * gca + Qb * hb, t01 = Qa * hb + Qb * gcc;
+    const float t10 = Qb * gca + Qc * hb, t11 = Qb * hb + Qc * gcc;
+    const float S00 = -(t00 * Qa + t01 * Qb), S01 = -(t00 * Qb + t01 * Qc);
+    const float S11 = -(t10 * Qb + t11 * Qc);
+    // S = T T^T + eps I  ->  G_T = 2 G_S T
+    float GT[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        GT[k] = 2.f * (S00 * g.T[k] + S01 * g.T[3 + k]);
+        GT[3 + k] = 2.f * (S01 * g.T[k] + S11 * g.T[3 + k]);
+    }
+    // T = J A -> G_J = G_T A^T (only J00, J02, J11, J12 depend on p), G_A = J^T G_T
+    const float GJ00 = GT[0] * g.A[0] + GT[1] * g.A[1] + GT[2] * g.A[2];
+    const float GJ02 = GT[0] * g.A[6] + GT[1] * g.A[7] + GT[2] * g.A[8];
+    const float GJ11 = GT[3] * g.A[3] + GT[4] * g.A[4] + GT[5] * g.A[5];
+    const float GJ12 = GT[3] * g.A[6] + GT[4] * g.A[7] + GT[5] * g.A[8];
+    float GA[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        GA[k] = g.J[0] * GT[k];
+        GA[3 + k] = g.J[4] * GT[3 + k];
+        GA[6 + k] = g.J[2] * GT[k] + g.J[5] * GT[3 + k];
+    }
+    const float px = g.p[0], py = g.p[1], pz = g.p[2];
+    const float iz = 1.f / pz, iz2 = iz * iz;
+    float gp0 = gu * ck.fx * iz;
+    float gp1 = gv * ck.fy * iz;
+    float gp2 = -(gu * ck.fx * px + gv * ck.fy * py) * iz2 + gz;
+    gp2 += GJ00 * (-ck.fx * iz2) + GJ02 * (ck.fx * g.tx * iz2) + GJ11 * (-ck.fy * iz2) + GJ12 * (ck.fy * g.ty * iz2);
+    const float gtx = GJ02 * (-ck.fx * iz), gty = GJ12 * (-ck.fy * iz);
+    if (!g.clx) {
+        gp0 += gtx * iz;
+        gp2 -= gtx * px * iz2;
+    }
+    if (!g.cly) {
+        gp1 += gty * iz;
+        gp2 -= gty * py * iz2;
+    }
+    if (gpose) {
+        // rho = g_p, phi = p x g_p + vee(G_W W^T), G_W W^T = G_A A^T
+        float Y[9];
+#pragma unroll
+        for (int r2 = 0; r2 < 3; ++r2)
+#pragma unroll
+            for (int c2 = 0; c2 < 3; ++c2)
+                Y[3 * r2 + c2] = GA[3 * r2] * g.A[3 * c2] + GA[3 * r2 + 1] * g.A[3 * c2 + 1]
+                               + GA[3 * r2 + 2] * g.A[3 * c2 + 2];
+        gpose[0] = gp0;
+        gpose[1] = gp1;
+        gpose[2] = gp2;
+        gpose[3] = py * gp2 - pz * gp1 + (Y[7] - Y[5]);
+        gpose[4] = pz * gp0 - px * gp2 + (Y[2] - Y[6]);
+        gpose[5] = px * gp1 - py * gp0 + (Y[3] - Y[1]);
+    }
+    if (gm) {
+        // mean: p = W mu + t
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gm[k] = pr.R[k] * gp0 + pr.R[3 + k] * gp1 + pr.R[6 + k] * gp2;
+        // A = W M -> G_M = W^T G_A; M = R diag(s)
+        float GM[9];
+#pragma unroll
+        for (int r2 = 0; r2 < 3; ++r2)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                GM[3 * r2 + k] = pr.R[r2] * GA[k] + pr.R[3 + r2] * GA[3 + k] + pr.R[6 + r2] * GA[6 + k];
+        float GR[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float gsk = GM[k] * g.R[k] + GM[3 + k] * g.R[3 + k] + GM[6 + k] * g.R[6 + k];
+            gls[k] = gsk * g.s[k];
+            GR[k] = GM[k] * g.s[k];
+            GR[3 + k] = GM[3 + k] * g.s[k];
+            GR[6 + k] = GM[6 + k] * g.s[k];
+        }
+        const float w = g.qh[0], x = g.qh[1], y = g.qh[2], z = g.qh[3];
+        const float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+        const float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6]
+                                + w * GR[7] - 2.f * x * GR[8]);
+        const float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6]
+                                + z * GR[7] - 2.f * y * GR[8]);
+        const float gzq = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4]
+                                 + y * GR[5] + x * GR[6] + y * GR[7]);
+        const float dot = gw * w + gx * x + gy * y + gzq * z;
+        const float iq = 1.f / g.qn;
+        gq[0] = (gw - w * dot) * iq;
+        gq[1] = (gx - x * dot) * iq;
+        gq[2] = (gy - y * dot) * iq;
+        gq[3] = (gzq - z * dot) * iq;
+    }
+}
+
+// K6: image-space gradients -> parameter gradients and the pose adjoint
+// (block partial sums, reduced in a second pass).
 template <bool WANT_PARAMS>
 __global__ void __launch_bounds__(256) k_project_bwd(Params P, CamK ck, const float *__restrict__ pose,
                                                      const int32_t *__restrict__ rank_of_gid,
@@ -284,110 +390,16 @@ __global__ void __launch_bounds__(256) k_project_bwd(Params P, CamK ck, const fl
         float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
         float glog = 0.f, grgb[3] = {0.f, 0.f, 0.f};
         if (r >= 0) {
-            PoseR pr = load_pose(pose);
+            const PoseR pr = load_pose(pose);
             GProj g;
             project_core(ck, pr, P.mean, P.log_scale, P.quat, P.opacity_logit[i], i, g);
             const float4 *G4 = reinterpret_cast<const float4 *>(g2d + 12 * (int64_t)r);
-            float4 q0 = G4[0], q1 = G4[1], q2 = G4[2];
-            float gu = q0.x, gv = q0.y, gca = q0.z, gcb = q0.w, gcc = q1.x, gop = q1.y;
+            const float4 q0 = G4[0], q1 = G4[1], q2 = G4[2];
             grgb[0] = q1.z;
             grgb[1] = q1.w;
             grgb[2] = q2.x;
-            float gz = q2.y;
-            glog = gop * g.op * (1.f - g.op);
-            // conic Q = S^-1: G_S = -Q G_Q Q with G_Q = [[ga, gb/2], [gb/2, gc]]
-            float idet = 1.f / g.det;
-            float Qa = g.c * idet, Qb = -g.b * idet, Qc = g.a * idet;
-            float hb = 0.5f * gcb;
-            float t00 = Qa * gca + Qb * hb, t01 = Qa * hb + Qb * gcc;
-            float t10 = Qb * gca + Qc * hb, t11 = Qb * hb + Qc * gcc;
-            float S00 = -(t00 * Qa + t01 * Qb), S01 = -(t00 * Qb + t01 * Qc);
-            float S11 = -(t10 * Qb + t11 * Qc);
-            // S = T T^T + eps I  ->  G_T = 2 G_S T
-            float GT[6];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                GT[k] = 2.f * (S00 * g.T[k] + S01 * g.T[3 + k]);
-                GT[3 + k] = 2.f * (S01 * g.T[k] + S11 * g.T[3 + k]);
-            }
-            // T = J A -> G_J = G_T A^T (only J00, J02, J11, J12 depend on p), G_A = J^T G_T
-            float GJ00 = GT[0] * g.A[0] + GT[1] * g.A[1] + GT[2] * g.A[2];
-            float GJ02 = GT[0] * g.A[6] + GT[1] * g.A[7] + GT[2] * g.A[8];
-            float GJ11 = GT[3] * g.A[3] + GT[4] * g.A[4] + GT[5] * g.A[5];
-            float GJ12 = GT[3] * g.A[6] + GT[4] * g.A[7] + GT[5] * g.A[8];
-            float GA[9];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                GA[k] = g.J[0] * GT[k];
-                GA[3 + k] = g.J[4] * GT[3 + k];
-                GA[6 + k] = g.J[2] * GT[k] + g.J[5] * GT[3 + k];
-            }
-            float px = g.p[0], py = g.p[1], pz = g.p[2];
-            float iz = 1.f / pz, iz2 = iz * iz;
-            float gp0 = gu * ck.fx * iz;
-            float gp1 = gv * ck.fy * iz;
-            float gp2 = -(gu * ck.fx * px + gv * ck.fy * py) * iz2 + gz;
-            gp2 += GJ00 * (-ck.fx * iz2) + GJ02 * (ck.fx * g.tx * iz2) + GJ11 * (-ck.fy * iz2)
-                 + GJ12 * (ck.fy * g.ty * iz2);
-            float gtx = GJ02 * (-ck.fx * iz), gty = GJ12 * (-ck.fy * iz);
-            if (!g.clx) {
-                gp0 += gtx * iz;
-                gp2 -= gtx * px * iz2;
-            }
-            if (!g.cly) {
-                gp1 += gty * iz;
-                gp2 -= gty * py * iz2;
-            }
-            // pose: rho = g_p, phi = p x g_p + vee(G_W W^T), G_W W^T = G_A A^T
-            float Y[9];
-#pragma unroll
-            for (int r2 = 0; r2 < 3; ++r2)
-#pragma unroll
-                for (int c2 = 0; c2 < 3; ++c2)
-                    Y[3 * r2 + c2] = GA[3 * r2] * g.A[3 * c2] + GA[3 * r2 + 1] * g.A[3 * c2 + 1]
-                                   + GA[3 * r2 + 2] * g.A[3 * c2 + 2];
-            gpose[0] = gp0;
-            gpose[1] = gp1;
-            gpose[2] = gp2;
-            gpose[3] = py * gp2 - pz * gp1 + (Y[7] - Y[5]);
-            gpose[4] = pz * gp0 - px * gp2 + (Y[2] - Y[6]);
-            gpose[5] = px * gp1 - py * gp0 + (Y[3] - Y[1]);
-            if (WANT_PARAMS) {
-                PoseR W = pr;
-                // mean: p = W mu + t
-#pragma unroll
-                for (int k = 0; k < 3; ++k) gm[k] = W.R[k] * gp0 + W.R[3 + k] * gp1 + W.R[6 + k] * gp2;
-                // A = W M -> G_M = W^T G_A; M = R diag(s)
-                float GM[9];
-#pragma unroll
-                for (int r2 = 0; r2 < 3; ++r2)
-#pragma unroll
-                    for (int k = 0; k < 3; ++k)
-                        GM[3 * r2 + k] = W.R[r2] * GA[k] + W.R[3 + r2] * GA[3 + k] + W.R[6 + r2] * GA[6 + k];
-                float GR[9];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    float gsk = GM[k] * g.R[k] + GM[3 + k] * g.R[3 + k] + GM[6 + k] * g.R[6 + k];
-                    gls[k] = gsk * g.s[k];
-                    GR[k] = GM[k] * g.s[k];
-                    GR[3 + k] = GM[3 + k] * g.s[k];
-                    GR[6 + k] = GM[6 + k] * g.s[k];
-                }
-                float w = g.qh[0], x = g.qh[1], y = g.qh[2], z = g.qh[3];
-                float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
-                float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6]
-                                  + w * GR[7] - 2.f * x * GR[8]);
-                float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6]
-                                  + z * GR[7] - 2.f * y * GR[8]);
-                float gzq = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4]
-                                   + y * GR[5] + x * GR[6] + y * GR[7]);
-                float dot = gw * w + gx * x + gy * y + gzq * z;
-                float iq = 1.f / g.qn;
-                gq[0] = (gw - w * dot) * iq;
-                gq[1] = (gx - x * dot) * iq;
-                gq[2] = (gy - y * dot) * iq;
-                gq[3] = (gzq - z * dot) * iq;
-            }
+            chain_to_params(ck, pr, g, q0, q1, q2, WANT_PARAMS ? gm : nullptr, gls, gq, &glog,
+                            pose_part ? gpose : nullptr);
         }
         if (WANT_PARAMS) {
 #define GSR_PUT(ptr, idx, val) \
@@ -422,6 +434,50 @@ __global__ void __launch_bounds__(256) k_project_bwd(Params P, CamK ck, const fl
             pose_part[6 * (int64_t)blockIdx.x + threadIdx.x] = v;
         }
     }
+}
+
+// Multi-keyframe projection backward: every Gaussian's parameters are read
+// once, its image-space gradients of each keyframe in which it is visible
+// are chained through that keyframe's pose and summed in registers, and the
+// total is added to the gradient arrays (deterministic: no atomics).
+__global__ void __launch_bounds__(256) k_project_bwd_multi(Params P, CamK ck, const ProjView *__restrict__ views,
+                                                           int n_views, gsr_gaussian_grads dg)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, glog = 0.f;
+    float grgb[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < n_views; ++k) {
+        const int32_t r = views[k].rank_of_gid[i];
+        if (r < 0) continue;
+        const PoseR pr = load_pose(views[k].pose);
+        GProj g;
+        project_core(ck, pr, P.mean, P.log_scale, P.quat, P.opacity_logit[i], i, g);
+        const float4 *G4 = reinterpret_cast<const float4 *>(views[k].g2d + 12 * (int64_t)r);
+        const float4 q0 = G4[0], q1 = G4[1], q2 = G4[2];
+        float pm[3], pls[3], pq[4], plog;
+        chain_to_params(ck, pr, g, q0, q1, q2, pm, pls, pq, &plog, nullptr);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            gm[c] += pm[c];
+            gls[c] += pls[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) gq[c] += pq[c];
+        glog += plog;
+        grgb[0] += q1.z;
+        grgb[1] += q1.w;
+        grgb[2] += q2.x;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        dg.mean[3 * i + c] += gm[c];
+        dg.log_scale[3 * i + c] += gls[c];
+        dg.rgb[3 * i + c] += grgb[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dg.quat[4 * i + c] += gq[c];
+    dg.opacity_logit[i] += glog;
 }
 
 // list entries as Gaussian ids; per-id depth bits (culled: 0xffffffff)
@@ -474,10 +530,9 @@ static int bits_for(int64_t v)
     return b;
 }
 
-gsr_status run_binning(gsr_ctx *ctx, const Params &P, const CamK &ck, const float *d_pose, bool allow_grow,
-                       cudaStream_t s)
+gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK &ck, const float *d_pose,
+                       bool allow_grow, cudaStream_t s)
 {
-    ViewScratch &V = ctx->view;
     const int64_t n = P.n;
     const int64_t tiles = (int64_t)ck.tiles_x * ck.tiles_y;
     if (n > V.cap_n) {
@@ -526,7 +581,7 @@ gsr_status run_binning(gsr_ctx *ctx, const Params &P, const CamK &ck, const floa
         GSR_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, cnt + CNT_INSTANCES, sizeof(u32), cudaMemcpyDeviceToHost, s));
         GSR_CUDA(ctx, cudaStreamSynchronize(s));
         int64_t need = (int64_t)ctx->host_pinned[0];
-        if (need > V.cap_i) GSR_TRY(grow_instance_capacity(ctx, need + need / 4 + 1024));
+        if (need > V.cap_i) GSR_TRY(grow_instance_capacity(ctx, V, need + need / 4 + 1024));
     }
     if (V.cap_i <= 0) return gsr_fail(ctx, GSR_ERR_CAPACITY, "instance capacity is zero in fixed-capacity mode");
     k_emit<<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, (u32 *)V.inst_off.p, ck.tiles_x,
@@ -543,11 +598,10 @@ gsr_status run_binning(gsr_ctx *ctx, const Params &P, const CamK &ck, const floa
     return GSR_OK;
 }
 
-gsr_status run_project_backward(gsr_ctx *ctx, const Params &P, const CamK &ck, const float *d_pose,
+gsr_status run_project_backward(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK &ck, const float *d_pose,
                                 gsr_gaussian_grads *dg, float *d_pose6, bool accumulate, float weight,
                                 cudaStream_t s)
 {
-    ViewScratch &V = ctx->view;
     const int64_t n = P.n;
     const unsigned nb = (unsigned)ceil_div(n > 0 ? n : 1, 256);
     float *part = nullptr;
@@ -600,5 +654,15 @@ gsr_status copy_tile_lists(gsr_ctx *ctx, int64_t n, int64_t n_tiles, u32 *ranges
         GSR_CUDA(ctx, cudaMemcpyAsync(gids_h, V.tkeys[1].p, sizeof(u32) * ni, cudaMemcpyDeviceToHost, s));
         GSR_CUDA(ctx, cudaStreamSynchronize(s));
     }
+    return GSR_OK;
+}
+
+gsr_status run_project_backward_multi(gsr_ctx *ctx, const Params &P, const CamK &ck, const ProjView *views,
+                                      int n_views, gsr_gaussian_grads *dg, cudaStream_t s)
+{
+    const unsigned nb = (unsigned)ceil_div(P.n > 0 ? P.n : 1, 256);
+    k_project_bwd_multi<<<nb, 256, 0, s>>>(P, ck, views, n_views, *dg);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
     return GSR_OK;
 }

@@ -233,9 +233,8 @@ gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_
     return GSR_OK;
 }
 
-gsr_status grow_instance_capacity(gsr_ctx *ctx, int64_t c)
+gsr_status grow_instance_capacity(gsr_ctx *ctx, ViewScratch &V, int64_t c)
 {
-    ViewScratch &V = ctx->view;
     if (c <= V.cap_i) return GSR_OK;
     for (int k = 0; k < 2; ++k) {
         GSR_TRY(ensure_buf(ctx, V.tkeys[k], sizeof(u32) * c));

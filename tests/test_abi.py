@@ -46,6 +46,7 @@ STRUCTS = {
     "gsr_frame_stats": _lib.FrameStats, "gsr_adam_opts": _lib.AdamOpts, "gsr_adam_state": _lib.AdamState,
     "gsr_gaussians_mut": _lib.GaussiansMut, "gsr_track_opts": _lib.TrackOpts, "gsr_track_stats": _lib.TrackStats,
     "gsr_keyframe": _lib.Keyframe, "gsr_map_opts": _lib.MapOpts, "gsr_map_stats": _lib.MapStats,
+    "gsr_tune_result": _lib.TuneResult,
 }
 
 
