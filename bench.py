@@ -57,52 +57,98 @@ def fp32_peak_tflops(sm_mhz):
 
 
 class ClockSampler:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """SM clock and clock-event (throttle) reasons sampled DURING the timed
+    region: read-only NVML queries every 10 ms from a thread (the timed region
+    is far shorter than nvidia-smi's sampling period), nvidia-smi -lms 200 as
+    a fallback.  Nothing is ever set."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
+    def __init__(self, torch_device):
+        self.dev = torch_device
+        self.samples, self.reasons, self.max_mhz = [], set(), None
+        self.stop_flag = threading.Event()
+        self.thread = None
         self.proc = None
-        self.path = None
+        self.nv = None
+        self.h = None
+
+    def _nvml(self):
+        import ctypes
+        import torch
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        prop = torch.cuda.get_device_properties(self.dev)
+        bus = getattr(prop, "pci_bus_id", None)
+        ok = False
+        if bus is not None:
+            dom = getattr(prop, "pci_domain_id", 0)
+            dv = getattr(prop, "pci_device_id", 0)
+            busid = f"{dom:08x}:{bus:02x}:{dv:02x}.0".encode()
+            ok = nv.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(busid), ctypes.byref(h)) == 0
+        if not ok and nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.dev.index or 0), ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle")
+        mx = ctypes.c_uint()
+        if nv.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) == 0:
+            self.max_mhz = float(mx.value)
+        self.nv, self.h = nv, h
+
+    def _loop(self):
+        import ctypes
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop_flag.is_set():
+            if self.nv.nvmlDeviceGetClockInfo(self.h, ctypes.c_int(1), ctypes.byref(clk)) == 0:
+                self.samples.append(float(clk.value))
+            if self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h, ctypes.byref(rs)) == 0:
+                for bit, name in self.REASONS.items():
+                    if rs.value & bit:
+                        self.reasons.add(name)
+            time.sleep(0.01)
 
     def start(self):
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
-        os.close(fd)
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
-            self.proc = None
+            self._nvml()
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+        except (OSError, AttributeError):
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                              "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            except OSError:
+                self.proc = None
 
     def stop(self):
-        if self.proc is None:
-            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
-        self.proc.terminate()
-        try:
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join()
+            src = "nvml, 10 ms"
+        elif self.proc is not None:
+            self.proc.terminate()
             self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        os.unlink(self.path)
-        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(smax) if smax else None,
-                    reasons=sorted(reasons), samples=len(sm))
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                try:
+                    self.samples.append(float(f[0]))
+                    self.max_mhz = float(f[1])
+                except (ValueError, IndexError):
+                    continue
+                for nm, v in zip(names, f[2:6]):
+                    if v.lower().startswith("active"):
+                        self.reasons.add(nm)
+            os.unlink(self.path)
+            src = "nvidia-smi, 200 ms"
+        else:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no clock source"], samples=0)
+        return dict(sm_mhz=statistics.median(self.samples) if self.samples else None, sm_max_mhz=self.max_mhz,
+                    reasons=sorted(self.reasons), samples=len(self.samples), source=src)
 
 
 # ------------------------------------------------------------------ oracle
@@ -231,6 +277,8 @@ def run_gpu(args, rank, world):
     def step():
         api.map_step(ctx, g, state, cam, kf, None, 1, cfg, want_stats=False)
 
+    # tile shape, batch and pixels per thread from the autotuner (untimed)
+    tuned, _ = api.autotune(ctx, g, cam, [pose], reps=3)
     api.profile_enable(ctx, True)
     for _ in range(max(args.warmup, 3)):
         step()
@@ -241,7 +289,7 @@ def run_gpu(args, rank, world):
     e_bwd = int((probe["last_idx"].to(torch.int64) + 1).sum())
     torch.cuda.synchronize()
 
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     phase_ms = {k: [] for k in api.PHASES}
     if world > 1:
@@ -249,6 +297,7 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     launches0 = ctx.kernel_launches
     sampler.start()
+    torch.cuda.nvtx.range_push("timed")
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record()
@@ -258,6 +307,7 @@ def run_gpu(args, rank, world):
         for k, v in ph.items():
             phase_ms[k].append(v)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     launches = ctx.kernel_launches - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -317,7 +367,8 @@ def run_gpu(args, rank, world):
                     traffic=None)
     line = dict(metric=METRIC, value=value, unit="iters/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
-                data="synthetic", config=config_dict(stats, None), roofline=roof, hbm_roofline_step=hbm,
+                data="synthetic", config=dict(config_dict(stats, None), autotuned=tuned), roofline=roof,
+                hbm_roofline_step=hbm,
                 phases_ms=avg, e2e=e2e, gpu_launches=int(launches), clocks=clocks)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -70,9 +70,8 @@ typedef struct {
     int64_t max_gaussians;   /* initial scratch capacities (0 = grow on first use) */
     int64_t max_instances;   /* tile instances (Gaussian x tile pairs) */
     int64_t max_pixels;
-    int32_t pixels_per_thread; /* pixels each blend thread owns: 1 or 2 (0 = default 2);
-                                  results do not depend on it */
-    int32_t reserved;
+    int32_t ppt_fwd, ppt_bwd;  /* pixels each forward / backward blend thread owns: 1 or 2
+                                  (0 = defaults 1 and 2); results do not depend on them */
 } gsr_options;
 
 /* Pinhole camera and rasterizer constants. */
@@ -322,15 +321,17 @@ GSR_API gsr_status gsr_map_step(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_sta
 /* ------------------------------------------------------------ autotune */
 
 typedef struct {
-    int32_t tile_w, tile_h, batch, pixels_per_thread;
-    float ms;  /* mean time of one forward + backward over all given poses */
+    int32_t tile_w, tile_h, batch, ppt_fwd, ppt_bwd;
+    float ms_fwd, ms_bwd;  /* mean time of the forwards / backwards over all given poses */
+    float ms;              /* ms_fwd + ms_bwd */
 } gsr_tune_result;
 
-/* Times gsr_render_forward + gsr_render_backward (all gradients, dL/dpixel
- * = 1) of `g` at each of the n_poses poses for every configuration of tile
- * shape {16x16, 8x8, 16x8, 32x8} x batch {32, 64, 128, 256} x pixels per
- * thread {1, 2}, `reps` timed repetitions each after one warm-up, and keeps the
- * fastest on the context (its captured graphs are dropped).  The tile shape
+/* Times gsr_render_forward and gsr_render_backward (all gradients, dL/dpixel
+ * = 1) of `g` at each of the n_poses poses for every tile shape {16x16, 8x8,
+ * 16x8, 32x8} x batch {32, 64, 128, 256}, each with 1 and 2 pixels per thread
+ * for the forward and for the backward (`reps` timed repetitions after one
+ * warm-up), and keeps the fastest combination on the context (its captured
+ * graphs are dropped).  The tile shape
  * changes which Gaussians a tile lists (the rectangle rule is per tile), so a
  * context's results are reproducible for a fixed configuration; batch and
  * pixels per thread do not change results.  *best receives the winner; all

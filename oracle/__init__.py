@@ -45,7 +45,7 @@ class _Cam(ctypes.Structure):
                 ("fx", ctypes.c_double), ("fy", ctypes.c_double),
                 ("cx", ctypes.c_double), ("cy", ctypes.c_double),
                 ("z_near", ctypes.c_double), ("eps2d", ctypes.c_double),
-                ("guard", ctypes.c_double), ("amb_rel", ctypes.c_double)]
+                ("guard", ctypes.c_double), ("amb_rel", ctypes.c_double), ("guard_y", ctypes.c_double)]
 
 
 @dataclass
@@ -63,10 +63,22 @@ class Camera:
     tile_w: int = 16
     tile_h: int = 16
     amb_rel: float = 5e-4
+    guard_y: float = 0.0
 
     def c(self) -> _Cam:
         return _Cam(self.width, self.height, self.tile_w, self.tile_h, self.fx, self.fy, self.cx,
-                    self.cy, self.z_near, self.eps2d, self.guard, self.amb_rel)
+                    self.cy, self.z_near, self.eps2d, self.guard, self.amb_rel, self.guard_y)
+
+    def crop(self, tx0, ty0, tx1, ty1):
+        """Camera of the tile-aligned window of tiles [tx0, tx1] x [ty0, ty1]:
+        same projection, tiles and guard-band limits, fewer pixels."""
+        x0, y0 = tx0 * self.tile_w, ty0 * self.tile_h
+        w = min((tx1 + 1) * self.tile_w, self.width) - x0
+        h = min((ty1 + 1) * self.tile_h, self.height) - y0
+        gx = (self.guard * self.width) / w
+        gy = ((self.guard_y or self.guard) * self.height) / h
+        return Camera(w, h, self.fx, self.fy, self.cx - x0, self.cy - y0, self.z_near, self.eps2d, gx,
+                      self.tile_w, self.tile_h, self.amb_rel, gy)
 
     @property
     def tiles(self):

@@ -43,6 +43,8 @@ typedef struct {
     double eps2d;    /* low-pass dilation added to the 2D covariance (px^2) */
     double guard;    /* guard band of the J linearisation, x half-FOV tangent */
     double amb_rel;  /* relative margin under which a blend decision is flagged */
+    double guard_y;  /* guard band in y when > 0 (else `guard`); lets a crop keep
+                        the full image's linearisation limits */
 } orc_camera;
 
 #define ALPHA_MIN (1.0 / 255.0)
@@ -140,7 +142,8 @@ static void project_one(const orc_camera *c, const double Rcw[9], const double t
     matmul3(T1, Rt, o->Sc);
 
     /* J: affine approximation of the perspective projection at p */
-    double limx = c->guard * 0.5 * c->width / c->fx, limy = c->guard * 0.5 * c->height / c->fy;
+    double limx = c->guard * 0.5 * c->width / c->fx;
+    double limy = (c->guard_y > 0 ? c->guard_y : c->guard) * 0.5 * c->height / c->fy;
     double tx = px / pz, ty = py / pz;
     if (fabs(fabs(tx) - limx) <= 1e-6 * limx || fabs(fabs(ty) - limy) <= 1e-6 * limy) o->amb |= 2;
     if (tx > limx) { tx = limx; o->clamp_x = 1; }

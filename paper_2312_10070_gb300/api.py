@@ -33,7 +33,7 @@ class Context:
     """Owns a gsr_ctx (scratch, tile lists, graphs) on the current device."""
 
     def __init__(self, tile=(16, 16), batch=256, memory_saving=False, fixed_capacity=False, max_gaussians=0,
-                 max_instances=0, pixels_per_thread=0):
+                 max_instances=0, pixels_per_thread=0, ppt_fwd=0, ppt_bwd=0):
         if not torch.cuda.is_available():
             raise RuntimeError("the GB300 rasterizer needs a CUDA device; there is no CPU fallback")
         self.lib = L.load()
@@ -45,7 +45,8 @@ class Context:
         o.fixed_capacity = int(fixed_capacity)
         o.max_gaussians = max_gaussians
         o.max_instances = max_instances
-        o.pixels_per_thread = pixels_per_thread
+        o.ppt_fwd = ppt_fwd or pixels_per_thread
+        o.ppt_bwd = ppt_bwd or pixels_per_thread
         self.options = o
         h = ctypes.c_void_p()
         L.check(self.lib.gsr_create(ctypes.byref(h), ctypes.byref(o)))
@@ -347,5 +348,6 @@ def autotune(ctx: Context, g: GaussianParams, cam: L.Camera, poses, reps: int = 
     allr = (L.TuneResult * 32)()
     ctx.check(ctx.lib.gsr_autotune(ctx.handle, ctypes.byref(g.c()), ctypes.byref(cam), arr, n, int(reps),
                                    ctypes.byref(best), allr, 32, _stream()))
-    conv = lambda r: dict(tile=(r.tile_w, r.tile_h), batch=r.batch, pixels_per_thread=r.pixels_per_thread, ms=r.ms)
+    conv = lambda r: dict(tile=(r.tile_w, r.tile_h), batch=r.batch, ppt_fwd=r.ppt_fwd, ppt_bwd=r.ppt_bwd,
+                          ms_fwd=r.ms_fwd, ms_bwd=r.ms_bwd, ms=r.ms)
     return conv(best), [conv(r) for r in allr if r.batch > 0]

@@ -33,43 +33,135 @@ __device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, flo
     p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
 }
 
-__global__ void __launch_bounds__(256) k_adam(gsr_gaussians_mut g, gsr_gaussian_grads gr, gsr_adam_state st,
-                                              gsr_adam_opts o, const float *__restrict__ bc, float *__restrict__ part)
+// Flat layout: the five parameter arrays are one index space of float4
+// chunks (mean, log-scale, quaternion, opacity, colour; 14 n floats); each
+// thread updates one float4 of one array (its parameter, gradient and both
+// moments: 4 vector loads, 3 vector stores), so every access is a coalesced
+// 16-byte vector.  The isotropic regulariser needs a Gaussian's three scales
+// together: the log-scale chunks are handled as groups of 4 Gaussians
+// (3 float4), one group per thread.  Arrays whose base is not 16-byte aligned,
+// and tails, take a scalar path.
+struct FlatSeg {
+    float *p, *m, *v;
+    const float *g;
+    float lr;
+    int64_t n;  // floats
+};
+
+__device__ __forceinline__ void adam_chunk(const FlatSeg &sgm, int64_t c4, const gsr_adam_opts &o, float bc1, float bc2)
 {
-    int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    float lreg = 0.f;
-    if (i < g.n) {
-        const float bc1 = bc[0], bc2 = bc[1];
-        // isotropic regulariser on the activated scales
-        float s[3], sb = 0.f;
+    const int64_t off = 4 * c4;
+    if (off + 4 <= sgm.n) {
+        float4 p = reinterpret_cast<float4 *>(sgm.p)[c4], m = reinterpret_cast<float4 *>(sgm.m)[c4];
+        float4 v = reinterpret_cast<float4 *>(sgm.v)[c4];
+        const float4 g = reinterpret_cast<const float4 *>(sgm.g)[c4];
+        adam1(p.x, g.x, m.x, v.x, sgm.lr, o.beta1, o.beta2, o.eps, bc1, bc2);
+        adam1(p.y, g.y, m.y, v.y, sgm.lr, o.beta1, o.beta2, o.eps, bc1, bc2);
+        adam1(p.z, g.z, m.z, v.z, sgm.lr, o.beta1, o.beta2, o.eps, bc1, bc2);
+        adam1(p.w, g.w, m.w, v.w, sgm.lr, o.beta1, o.beta2, o.eps, bc1, bc2);
+        reinterpret_cast<float4 *>(sgm.p)[c4] = p;
+        reinterpret_cast<float4 *>(sgm.m)[c4] = m;
+        reinterpret_cast<float4 *>(sgm.v)[c4] = v;
+    } else {
+        for (int64_t k = off; k < sgm.n; ++k)
+            adam1(sgm.p[k], sgm.g[k], sgm.m[k], sgm.v[k], sgm.lr, o.beta1, o.beta2, o.eps, bc1, bc2);
+    }
+}
+
+// log-scales of Gaussians [i0, i0 + cnt) with the L_reg gradient; returns their L_reg terms
+__device__ __forceinline__ float adam_log_scales(const FlatSeg &sgm, int64_t i0, int cnt, float rw,
+                                                 const gsr_adam_opts &o, float bc1, float bc2)
+{
+    float lsum = 0.f;
+    for (int q = 0; q < cnt; ++q) {
+        const int64_t b = 3 * (i0 + q);
+        float sc[3], sb = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            s[k] = expf(g.log_scale[3 * i + k]);
-            sb += s[k];
+            sc[k] = expf(sgm.p[b + k]);
+            sb += sc[k];
         }
         sb *= (1.f / 3.f);
         float sg[3], ssum = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            lreg += fabsf(s[k] - sb);
-            sg[k] = sgnf(s[k] - sb);
+            lsum += fabsf(sc[k] - sb);
+            sg[k] = sgnf(sc[k] - sb);
             ssum += sg[k];
         }
-        const float rw = o.w_reg / (float)g.n;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            int64_t j = 3 * i + k;
-            adam1(g.mean[j], gr.mean[j], st.m_mean[j], st.v_mean[j], o.lr_mean, o.beta1, o.beta2, o.eps, bc1, bc2);
-            float gl = gr.log_scale[j] + rw * (sg[k] - ssum * (1.f / 3.f)) * s[k];
-            adam1(g.log_scale[j], gl, st.m_log_scale[j], st.v_log_scale[j], o.lr_log_scale, o.beta1, o.beta2, o.eps,
-                  bc1, bc2);
-            adam1(g.rgb[j], gr.rgb[j], st.m_rgb[j], st.v_rgb[j], o.lr_rgb, o.beta1, o.beta2, o.eps, bc1, bc2);
+            const float gk = sgm.g[b + k] + rw * (sg[k] - ssum * (1.f / 3.f)) * sc[k];
+            adam1(sgm.p[b + k], gk, sgm.m[b + k], sgm.v[b + k], sgm.lr, o.beta1, o.beta2, o.eps, bc1, bc2);
         }
+    }
+    return lsum;
+}
+
+// threads [0, nls) take log-scale groups of 4 Gaussians; the rest take float4
+// chunks of the other four arrays, in order
+__global__ void __launch_bounds__(256) k_adam(gsr_gaussians_mut g, gsr_gaussian_grads gr, gsr_adam_state st,
+                                              gsr_adam_opts o, const float *__restrict__ bc, float *__restrict__ part,
+                                              int64_t nls, int64_t c_mean, int64_t c_quat, int64_t c_op,
+                                              int64_t c_rgb)
+{
+    const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const float bc1 = bc[0], bc2 = bc[1];
+    float lreg = 0.f;
+    if (t < nls) {
+        const FlatSeg sg{g.log_scale, st.m_log_scale, st.v_log_scale, gr.log_scale, o.lr_log_scale, 3 * g.n};
+        const int64_t i0 = 4 * t;
+        const int cnt = (int)min((int64_t)4, g.n - i0);
+        lreg = adam_log_scales(sg, i0, cnt, o.w_reg / (float)g.n, o, bc1, bc2);
+    } else {
+        int64_t c = t - nls;
+        if (c < c_mean) {
+            adam_chunk(FlatSeg{g.mean, st.m_mean, st.v_mean, gr.mean, o.lr_mean, 3 * g.n}, c, o, bc1, bc2);
+        } else if ((c -= c_mean) < c_quat) {
+            adam_chunk(FlatSeg{g.quat, st.m_quat, st.v_quat, gr.quat, o.lr_quat, 4 * g.n}, c, o, bc1, bc2);
+        } else if ((c -= c_quat) < c_op) {
+            adam_chunk(FlatSeg{g.opacity_logit, st.m_opacity_logit, st.v_opacity_logit, gr.opacity_logit,
+                                o.lr_opacity, g.n},
+                       c, o, bc1, bc2);
+        } else if ((c -= c_op) < c_rgb) {
+            adam_chunk(FlatSeg{g.rgb, st.m_rgb, st.v_rgb, gr.rgb, o.lr_rgb, 3 * g.n}, c, o, bc1, bc2);
+        }
+    }
+    if (part) {
+        __shared__ float red[8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            int64_t j = 4 * i + k;
-            adam1(g.quat[j], gr.quat[j], st.m_quat[j], st.v_quat[j], o.lr_quat, o.beta1, o.beta2, o.eps, bc1, bc2);
+        for (int off = 16; off > 0; off >>= 1) lreg += __shfl_down_sync(0xffffffffu, lreg, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lreg;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float tt = 0.f;
+            for (int k = 0; k < 8; ++k) tt += red[k];
+            part[blockIdx.x] = tt;
         }
+    }
+}
+
+// scalar fallback for unaligned arrays: one Gaussian per thread
+__global__ void __launch_bounds__(256) k_adam_scalar(gsr_gaussians_mut g, gsr_gaussian_grads gr, gsr_adam_state st,
+                                                     gsr_adam_opts o, const float *__restrict__ bc,
+                                                     float *__restrict__ part)
+{
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const float bc1 = bc[0], bc2 = bc[1];
+    float lreg = 0.f;
+    if (i < g.n) {
+        lreg = adam_log_scales(FlatSeg{g.log_scale, st.m_log_scale, st.v_log_scale, gr.log_scale, o.lr_log_scale,
+                                       3 * g.n},
+                               i, 1, o.w_reg / (float)g.n, o, bc1, bc2);
+        for (int k = 0; k < 3; ++k) {
+            adam1(g.mean[3 * i + k], gr.mean[3 * i + k], st.m_mean[3 * i + k], st.v_mean[3 * i + k], o.lr_mean,
+                  o.beta1, o.beta2, o.eps, bc1, bc2);
+            adam1(g.rgb[3 * i + k], gr.rgb[3 * i + k], st.m_rgb[3 * i + k], st.v_rgb[3 * i + k], o.lr_rgb, o.beta1,
+                  o.beta2, o.eps, bc1, bc2);
+        }
+        for (int k = 0; k < 4; ++k)
+            adam1(g.quat[4 * i + k], gr.quat[4 * i + k], st.m_quat[4 * i + k], st.v_quat[4 * i + k], o.lr_quat,
+                  o.beta1, o.beta2, o.eps, bc1, bc2);
         adam1(g.opacity_logit[i], gr.opacity_logit[i], st.m_opacity_logit[i], st.v_opacity_logit[i], o.lr_opacity,
               o.beta1, o.beta2, o.eps, bc1, bc2);
     }
@@ -80,9 +172,9 @@ __global__ void __launch_bounds__(256) k_adam(gsr_gaussians_mut g, gsr_gaussian_
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lreg;
         __syncthreads();
         if (threadIdx.x == 0) {
-            float t = 0.f;
-            for (int k = 0; k < 8; ++k) t += red[k];
-            part[blockIdx.x] = t;
+            float tt = 0.f;
+            for (int k = 0; k < 8; ++k) tt += red[k];
+            part[blockIdx.x] = tt;
         }
     }
 }
@@ -166,7 +258,18 @@ __global__ void k_pose_adam(float *pose, const float *__restrict__ g6, float *m6
 gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads *gr, gsr_adam_state *st,
                     const gsr_adam_opts *o, float *loss_reg_dev, cudaStream_t s)
 {
-    const unsigned nb = (unsigned)ceil_div(g->n > 0 ? g->n : 1, 256);
+    // 16-byte vectors need 16-byte aligned bases for every array
+    bool vec4 = true;
+    const void *ptrs[] = {g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, gr->mean, gr->log_scale,
+                          gr->quat, gr->opacity_logit, gr->rgb, st->m_mean, st->m_log_scale, st->m_quat,
+                          st->m_opacity_logit, st->m_rgb, st->v_mean, st->v_log_scale, st->v_quat,
+                          st->v_opacity_logit, st->v_rgb};
+    for (const void *q : ptrs) vec4 = vec4 && ((uintptr_t)q % 16 == 0);
+    const int64_t n = g->n > 0 ? g->n : 1;
+    const int64_t nls = ceil_div(n, 4), c_mean = ceil_div(3 * n, 4), c_quat = n, c_op = ceil_div(n, 4),
+                  c_rgb = ceil_div(3 * n, 4);
+    const int64_t threads = vec4 ? nls + c_mean + c_quat + c_op + c_rgb : n;
+    const unsigned nb = (unsigned)ceil_div(threads, 256);
     GSR_TRY(ensure_buf(ctx, ctx->small, 256 * sizeof(float)));
     float *bc = (float *)ctx->small.p;  // [0..1] bias corrections
     float *part = nullptr;
@@ -175,7 +278,8 @@ gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads
         part = (float *)ctx->pose_part.p;
     }
     k_adam_prep<<<1, 1, 0, s>>>(st->step, o->beta1, o->beta2, bc);
-    k_adam<<<nb, 256, 0, s>>>(*g, *gr, *st, *o, bc, part);
+    if (vec4) k_adam<<<nb, 256, 0, s>>>(*g, *gr, *st, *o, bc, part, nls, c_mean, c_quat, c_op, c_rgb);
+    else k_adam_scalar<<<nb, 256, 0, s>>>(*g, *gr, *st, *o, bc, part);
     ctx->launches += 2;
     if (loss_reg_dev) {
         k_lreg_final<<<1, 1024, 0, s>>>(part, (int)nb, o->w_reg / (float)(g->n > 0 ? g->n : 1), loss_reg_dev);

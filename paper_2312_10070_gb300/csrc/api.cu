@@ -155,11 +155,12 @@ gsr_status gsr_create(gsr_ctx **out, const gsr_options *opt)
     if (!valid_tile(o.tile_w, o.tile_h)) return GSR_ERR_INVALID_ARG;
     if (o.batch != 32 && o.batch != 64 && o.batch != 128 && o.batch != 256) return GSR_ERR_INVALID_ARG;
     if (o.max_gaussians < 0 || o.max_instances < 0 || o.max_pixels < 0) return GSR_ERR_INVALID_ARG;
-    if (o.pixels_per_thread != 0 && o.pixels_per_thread != 1 && o.pixels_per_thread != 2) return GSR_ERR_INVALID_ARG;
+    if (o.ppt_fwd < 0 || o.ppt_fwd > 2 || o.ppt_bwd < 0 || o.ppt_bwd > 2) return GSR_ERR_INVALID_ARG;
     gsr_ctx *c = new (std::nothrow) gsr_ctx();
     if (!c) return GSR_ERR_OOM;
     c->opt = o;
-    c->ppt = o.pixels_per_thread ? o.pixels_per_thread : 2;
+    c->ppt_fwd = o.ppt_fwd ? o.ppt_fwd : 1;
+    c->ppt_bwd = o.ppt_bwd ? o.ppt_bwd : 2;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         (void)cudaGetLastError();
         delete c;
@@ -272,6 +273,7 @@ static gsr_status take_status(gsr_ctx *ctx, cudaStream_t s)
     if (st) GSR_CUDA(ctx, cudaMemsetAsync(cnt + CNT_STATUS, 0, sizeof(u32), s));
     if (st & GSR_FLAG_CAPACITY) return gsr_fail(ctx, GSR_ERR_CAPACITY, "tile-instance capacity exceeded");
     if (st & GSR_FLAG_NONFINITE) return gsr_fail(ctx, GSR_ERR_NONFINITE, "non-finite loss");
+    if (st & GSR_FLAG_TIMEOUT) return gsr_fail(ctx, GSR_ERR_TIMEOUT, "a bounded device wait expired");
     return GSR_OK;
 }
 
@@ -795,55 +797,66 @@ extern "C" gsr_status gsr_autotune(gsr_ctx *ctx, const gsr_gaussians *g, const g
     const int tiles[4][2] = {{16, 16}, {8, 8}, {16, 8}, {32, 8}};
     const int batches[4] = {32, 64, 128, 256};
     const gsr_options saved = ctx->opt;
-    const int saved_ppt = ctx->ppt;
-    cudaEvent_t e0, e1;
-    GSR_CUDA(ctx, cudaEventCreate(&e0));
-    GSR_CUDA(ctx, cudaEventCreate(&e1));
+    const int saved_pf = ctx->ppt_fwd, saved_pb = ctx->ppt_bwd;
+    cudaEvent_t ev[3];
+    for (int i = 0; i < 3; ++i) GSR_CUDA(ctx, cudaEventCreate(&ev[i]));
     gsr_tune_result win{};
     win.ms = 3.4e38f;
     int idx = 0;
     gsr_status st = GSR_OK;
+    gsr_render_out ro{f.rgb, f.depth, f.alpha, f.T, f.last, nullptr};
     for (int ti = 0; ti < 4 && st == GSR_OK; ++ti)
-        for (int bi = 0; bi < 4 && st == GSR_OK; ++bi)
+        for (int bi = 0; bi < 4 && st == GSR_OK; ++bi) {
+            ctx->opt.tile_w = tiles[ti][0];
+            ctx->opt.tile_h = tiles[ti][1];
+            ctx->opt.batch = batches[bi];
+            if (check_camera(ctx, cam) != GSR_OK) continue;  // too many tiles for this shape
+            float tf[3] = {0.f, 0.f, 0.f}, tb[3] = {0.f, 0.f, 0.f};
             for (int ppt = 1; ppt <= 2 && st == GSR_OK; ++ppt) {
-                ctx->opt.tile_w = tiles[ti][0];
-                ctx->opt.tile_h = tiles[ti][1];
-                ctx->opt.batch = batches[bi];
-                ctx->ppt = ppt;
-                if (check_camera(ctx, cam) != GSR_OK) continue;  // too many tiles for this shape
-                gsr_render_out ro{f.rgb, f.depth, f.alpha, f.T, f.last, nullptr};
-                float total = 0.f;
-                for (int r = 0; r <= reps && st == GSR_OK; ++r) {
-                    if (r == 1) st = gsr_cuda_check(ctx, cudaEventRecord(e0, s), "event");
+                ctx->ppt_fwd = ctx->ppt_bwd = ppt;
+                for (int r = 0; r <= reps && st == GSR_OK; ++r)
                     for (int k = 0; k < n_poses && st == GSR_OK; ++k) {
-                        st = gsr_render_forward(ctx, g, cam, &poses[k], &ro, stream);
+                        st = gsr_cuda_check(ctx, cudaEventRecord(ev[0], s), "event");
+                        if (st == GSR_OK) st = gsr_render_forward(ctx, g, cam, &poses[k], &ro, stream);
+                        if (st == GSR_OK) st = gsr_cuda_check(ctx, cudaEventRecord(ev[1], s), "event");
                         if (st == GSR_OK)
-                            st = gsr_render_backward(ctx, g, cam, &poses[k], &ro, f.d_rgb, f.d_depth, nullptr, &dg, nullptr,
-                                                     stream);
+                            st = gsr_render_backward(ctx, g, cam, &poses[k], &ro, f.d_rgb, f.d_depth, nullptr, &dg,
+                                                     nullptr, stream);
+                        if (st == GSR_OK) st = gsr_cuda_check(ctx, cudaEventRecord(ev[2], s), "event");
+                        if (st == GSR_OK) st = gsr_cuda_check(ctx, cudaEventSynchronize(ev[2]), "event");
+                        float a = 0.f, b = 0.f;
+                        if (st == GSR_OK) st = gsr_cuda_check(ctx, cudaEventElapsedTime(&a, ev[0], ev[1]), "event");
+                        if (st == GSR_OK) st = gsr_cuda_check(ctx, cudaEventElapsedTime(&b, ev[1], ev[2]), "event");
+                        if (r > 0) {  // r = 0 warms up (and sizes the scratch)
+                            tf[ppt] += a;
+                            tb[ppt] += b;
+                        }
                     }
-                }
-                if (st != GSR_OK) break;
-                GSR_CUDA(ctx, cudaEventRecord(e1, s));
-                GSR_CUDA(ctx, cudaEventSynchronize(e1));
-                GSR_CUDA(ctx, cudaEventElapsedTime(&total, e0, e1));
-                gsr_tune_result r{tiles[ti][0], tiles[ti][1], batches[bi], ppt, total / (float)reps};
-                if (idx < n_all) all[idx] = r;
-                ++idx;
-                if (r.ms < win.ms) win = r;
             }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st != GSR_OK) {
-        ctx->opt = saved;
-        ctx->ppt = saved_ppt;
-        return st;
-    }
+            if (st != GSR_OK) break;
+            gsr_tune_result res{};
+            res.tile_w = tiles[ti][0];
+            res.tile_h = tiles[ti][1];
+            res.batch = batches[bi];
+            res.ppt_fwd = tf[1] <= tf[2] ? 1 : 2;
+            res.ppt_bwd = tb[1] <= tb[2] ? 1 : 2;
+            res.ms_fwd = tf[res.ppt_fwd] / (float)reps;
+            res.ms_bwd = tb[res.ppt_bwd] / (float)reps;
+            res.ms = res.ms_fwd + res.ms_bwd;
+            if (idx < n_all) all[idx] = res;
+            ++idx;
+            if (res.ms < win.ms) win = res;
+        }
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
     ctx->opt = saved;
+    ctx->ppt_fwd = saved_pf;
+    ctx->ppt_bwd = saved_pb;
+    if (st != GSR_OK) return st;
     ctx->opt.tile_w = win.tile_w;
     ctx->opt.tile_h = win.tile_h;
     ctx->opt.batch = win.batch;
-    ctx->opt.pixels_per_thread = win.pixels_per_thread;
-    ctx->ppt = win.pixels_per_thread;
+    ctx->opt.ppt_fwd = ctx->ppt_fwd = win.ppt_fwd;
+    ctx->opt.ppt_bwd = ctx->ppt_bwd = win.ppt_bwd;
     // graphs baked the old configuration
     if (ctx->map_graph) cudaGraphExecDestroy(ctx->map_graph);
     if (ctx->track_graph) cudaGraphExecDestroy(ctx->track_graph);

@@ -233,7 +233,8 @@ __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, in
                     if (e.use) {
                         contrib = true;
                         const float4 c = sC[j];
-                        const float iom = 1.f / (1.f - e.alpha);
+                        // gradient-only use (decisions come from eval_gaussian): fast reciprocal
+                        const float iom = __fdividef(1.f, 1.f - e.alpha);
                         T[k] = T[k] * iom;  // T_j
                         const float w = e.alpha * T[k];
                         const float dLda = g0[k] * (c.x * T[k] - S0[k] * iom) + g1[k] * (c.y * T[k] - S1[k] * iom)
@@ -351,6 +352,7 @@ enum Kind { FWD, BWD, BWD_POSE, FWD_MULTI, BWD_MULTI };
 
 struct Launch {
     Kind kind;
+    int ppt;
     const CamK *ck;
     BlendView vp;
     const BlendView *views;
@@ -394,7 +396,7 @@ gsr_status by_batch(gsr_ctx *ctx, const Launch &L, cudaStream_t s)
 template <int TW, int TH>
 gsr_status by_ppt(gsr_ctx *ctx, const Launch &L, cudaStream_t s)
 {
-    if (ctx->ppt == 1) return by_batch<TW, TH, 1>(ctx, L, s);
+    if (L.ppt == 1) return by_batch<TW, TH, 1>(ctx, L, s);
     return by_batch<TW, TH, 2>(ctx, L, s);
 }
 
@@ -466,6 +468,7 @@ gsr_status run_blend_forward(gsr_ctx *ctx, const Params &, const CamK &ck, gsr_r
 {
     Launch L{};
     L.kind = FWD;
+    L.ppt = ctx->ppt_fwd;
     L.ck = &ck;
     L.vp = blend_view(ctx->view, o, nullptr, nullptr, nullptr);
     L.grid = (unsigned)(ck.tiles_x * ck.tiles_y);
@@ -487,6 +490,7 @@ gsr_status run_blend_backward(gsr_ctx *ctx, const CamK &ck, const gsr_render_out
     GSR_TRY(zero_g2d(ctx, ctx->view, s));
     Launch L{};
     L.kind = pose_only ? BWD_POSE : BWD;
+    L.ppt = ctx->ppt_bwd;
     L.ck = &ck;
     L.vp = blend_view(ctx->view, sv, d_rgb, d_depth, d_alpha);
     L.grid = (unsigned)(ck.tiles_x * ck.tiles_y);
@@ -498,7 +502,8 @@ gsr_status run_blend_multi(gsr_ctx *ctx, const CamK &ck, bool backward, const Bl
 {
     int dev_sms = 0;
     GSR_CUDA(ctx, cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    const int tw = ctx->opt.tile_w, th = ctx->opt.tile_h, b = ctx->opt.batch, ppt = ctx->ppt;
+    const int tw = ctx->opt.tile_w, th = ctx->opt.tile_h, b = ctx->opt.batch;
+    const int ppt = backward ? ctx->ppt_bwd : ctx->ppt_fwd;
     int per_sm = 1;
     if (tw == 16 && th == 16) per_sm = occ_ppt<16, 16>(ppt, b, !backward);
     else if (tw == 8 && th == 8) per_sm = occ_ppt<8, 8>(ppt, b, !backward);
@@ -507,6 +512,7 @@ gsr_status run_blend_multi(gsr_ctx *ctx, const CamK &ck, bool backward, const Bl
     if (per_sm < 1) per_sm = 1;
     Launch L{};
     L.kind = backward ? BWD_MULTI : FWD_MULTI;
+    L.ppt = ppt;
     L.ck = &ck;
     L.views = views;
     L.items = items;

@@ -22,6 +22,7 @@ typedef uint32_t u32;
 // Device status word bits.
 #define GSR_FLAG_CAPACITY 1u
 #define GSR_FLAG_NONFINITE 2u
+#define GSR_FLAG_TIMEOUT 4u
 
 // Counters block layout (u32 words in ctx->counters).
 enum {
@@ -81,7 +82,7 @@ struct ProjView {
 };
 struct gsr_ctx {
     gsr_options opt;
-    int ppt = 2;  // pixels per thread of the blend kernels
+    int ppt_fwd = 1, ppt_bwd = 2;  // pixels per thread of the blend kernels
     int device = 0;
     std::string err;
     int64_t launches = 0;

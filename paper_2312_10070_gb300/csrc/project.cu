@@ -232,28 +232,68 @@ __global__ void k_gather(int64_t cap, const u32 *__restrict__ d_v, const u32 *__
     tcount[r] = w * h;
 }
 
-// one instance (tile id, depth rank) per tile of each rectangle; the stream is
-// in depth order, so a stable sort on the tile id yields depth-ordered lists
-__global__ void k_emit(int64_t cap_v, const u32 *__restrict__ d_v, const float4 *__restrict__ rec_sorted,
-                       const u32 *__restrict__ off, int tiles_x, int64_t cap_i, u32 *__restrict__ tkeys,
-                       u32 *__restrict__ tvals, u32 *__restrict__ counters)
+// One instance (tile id, depth rank) per tile of each rectangle; the stream is
+// in depth order, so a stable sort on the tile id yields depth-ordered lists.
+// A warp handles 32 consecutive ranks: a warp scan of their rectangle areas
+// gives each rank's slot, then the lanes write the warp's instances
+// contiguously (coalesced), each lane locating the owner rank of its
+// instance with a 5-step search over the scanned slots.
+__global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restrict__ d_v,
+                                              const float4 *__restrict__ rec_sorted, const u32 *__restrict__ off,
+                                              int tiles_x, int64_t cap_i, u32 *__restrict__ tkeys,
+                                              u32 *__restrict__ tvals, u32 *__restrict__ counters)
 {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r == 0) {
         u32 total = counters[CNT_INSTANCES];
         counters[CNT_SORTN] = (int64_t)total > cap_i ? (u32)cap_i : total;
         if ((int64_t)total > cap_i) atomicOr(&counters[CNT_STATUS], GSR_FLAG_CAPACITY);
     }
-    if (r >= cap_v || r >= (int64_t)*d_v) return;
-    u32 lo = __float_as_uint(rec_sorted[3 * r + 1].w), hi = __float_as_uint(rec_sorted[3 * r + 2].w);
-    int x0 = lo & 0xffff, y0 = lo >> 16, x1 = hi & 0xffff, y1 = hi >> 16;
-    int64_t o = off[r];
-    for (int y = y0; y <= y1; ++y)
-        for (int x = x0; x <= x1; ++x, ++o)
+    const unsigned F = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t V = (int64_t)*d_v;
+    const int64_t r0 = r - lane;  // first rank of this warp
+    if (r0 >= V || r0 >= cap_v) return;  // warp-uniform
+    const bool valid = r < V && r < cap_v;
+    int x0 = 0, y0 = 0, w = 1;
+    u32 cnt = 0;
+    if (valid) {
+        const u32 lo = __float_as_uint(rec_sorted[3 * r + 1].w), hi = __float_as_uint(rec_sorted[3 * r + 2].w);
+        x0 = (int)(lo & 0xffffu);
+        y0 = (int)(lo >> 16);
+        w = (int)(hi & 0xffffu) - x0 + 1;
+        cnt = (u32)(w * ((int)(hi >> 16) - y0 + 1));
+    }
+    u32 incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(F, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const u32 excl = incl - cnt;
+    const u32 total = __shfl_sync(F, incl, 31);
+    const int64_t base = (int64_t)__shfl_sync(F, off[r0], 0);  // off[r0] is read by every lane (same address)
+    for (u32 kb = 0; kb < total; kb += 32) {
+        const u32 k = kb + lane;
+        // owner lane j: the largest j with excl_j <= k (lanes with cnt = 0 are skipped over)
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const u32 e = __shfl_sync(F, excl, j + step);
+            const u32 c = __shfl_sync(F, cnt, j + step);
+            if (j + step < 32 && c > 0 && e <= k) j += step;
+        }
+        const u32 ej = __shfl_sync(F, excl, j);
+        const int wx = __shfl_sync(F, w, j), jx = __shfl_sync(F, x0, j), jy = __shfl_sync(F, y0, j);
+        if (k < total) {
+            const int local = (int)(k - ej);
+            const int64_t o = base + k;
             if (o < cap_i) {
-                tkeys[o] = (u32)(y * tiles_x + x);
-                tvals[o] = (u32)r;
+                tkeys[o] = (u32)((jy + local / wx) * tiles_x + jx + local % wx);
+                tvals[o] = (u32)(r0 + j);
             }
+        }
+    }
 }
 
 __global__ void k_ranges(int64_t cap_i, const u32 *__restrict__ d_n, const u32 *__restrict__ tkeys,

@@ -2,6 +2,8 @@
 // (u32 key, u32 value) pairs.  Both read their element count from device
 // memory so that a whole frame can be enqueued (and graph-captured) without
 // a host round trip; grids are sized by capacity and idle blocks exit.
+#include <algorithm>
+
 #include "gsr_internal.cuh"
 
 namespace {
@@ -109,66 +111,134 @@ constexpr int RX_THREADS = RX_WARPS * 32;
 constexpr int RX_ROUNDS = 8;                         // keys per lane
 constexpr int RX_TILE = RX_THREADS * RX_ROUNDS;      // 2048 keys per block
 constexpr int RX_WARP_SPAN = 32 * RX_ROUNDS;         // 256 consecutive keys per warp
+constexpr int RX_MAX_PASSES = 4;
+constexpr u32 LB_AGG = 1u << 30, LB_INC = 2u << 30, LB_MASK = (1u << 30) - 1u;
+constexpr int LB_SPIN_LIMIT = 1 << 24;               // bounded look-back wait
 
-// Per-block digit histogram: hist[digit * nblocks + block]
-__global__ void __launch_bounds__(RX_THREADS) k_radix_hist(const u32 *__restrict__ keys, int64_t n_cap,
-                                                           const u32 *d_n, int shift, int nblocks,
-                                                           u32 *__restrict__ hist)
+// Digit totals of every pass at once: ghist[pass * RX + digit] (atomics).
+__global__ void __launch_bounds__(RX_THREADS) k_radix_global_hist(const u32 *__restrict__ keys, int64_t n_cap,
+                                                                  const u32 *d_n, int passes, u32 *__restrict__ ghist)
 {
-    __shared__ u32 cnt[RX];
-    int64_t n = eff_n(n_cap, d_n);
-    for (int d = threadIdx.x; d < RX; d += RX_THREADS) cnt[d] = 0;
+    __shared__ u32 cnt[RX_MAX_PASSES][RX];
+    const int64_t n = eff_n(n_cap, d_n);
+    for (int d = threadIdx.x; d < RX_MAX_PASSES * RX; d += RX_THREADS) (&cnt[0][0])[d] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RX_TILE;
-    if (base < n) {
-#pragma unroll
-        for (int r = 0; r < RX_ROUNDS; ++r) {
-            int64_t i = base + r * RX_THREADS + threadIdx.x;
-            if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & (RX - 1)], 1u);
-        }
+    for (int64_t i = (int64_t)blockIdx.x * RX_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RX_THREADS) {
+        const u32 k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&cnt[p][(k >> (p * RX_BITS)) & (RX - 1)], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < RX; d += RX_THREADS) hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+    for (int d = threadIdx.x; d < passes * RX; d += RX_THREADS) {
+        const u32 c = (&cnt[0][0])[d];
+        if (c) atomicAdd(&ghist[d], c);
+    }
 }
 
-// Stable scatter.  Warp w owns keys [base + w*256, base + (w+1)*256) and walks
-// them in order, 32 at a time; equal digits inside a round are ranked with
-// __match_any_sync, so the order of equal keys is preserved.
-__global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(const u32 *__restrict__ kin,
-                                                              const u32 *__restrict__ vin,
-                                                              u32 *__restrict__ kout, u32 *__restrict__ vout,
-                                                              int64_t n_cap, const u32 *d_n, int shift,
-                                                              int nblocks, const u32 *__restrict__ hist)
+// exclusive scan of each pass's 256 digit totals (one block of RX threads per pass)
+__global__ void __launch_bounds__(RX) k_radix_digit_base(u32 *ghist)
+{
+    __shared__ u32 sc[RX];
+    u32 *h = ghist + blockIdx.x * RX;
+    const u32 v = h[threadIdx.x];
+    sc[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < RX; o <<= 1) {
+        const u32 t = threadIdx.x >= (unsigned)o ? sc[threadIdx.x - o] : 0u;
+        __syncthreads();
+        sc[threadIdx.x] += t;
+        __syncthreads();
+    }
+    h[threadIdx.x] = sc[threadIdx.x] - v;
+}
+
+// One stable pass.  Blocks take 2048-key tiles in launch order (atomic ticket,
+// so every tile a block waits for belongs to a block that already runs);
+// each warp ranks its 256 consecutive keys in order with __match_any_sync; the
+// block publishes its digit counts, looks back over the preceding tiles for
+// their running totals, stages its keys in shared memory in digit order and
+// writes them out so that equal digits land in consecutive addresses.
+__global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__restrict__ kin, const u32 *__restrict__ vin,
+                                                               u32 *__restrict__ kout, u32 *__restrict__ vout,
+                                                               int64_t n_cap, const u32 *d_n, int shift,
+                                                               const u32 *__restrict__ digit_base,
+                                                               u32 *__restrict__ lookback, u32 *ticket,
+                                                               u32 *status)
 {
     __shared__ u32 wcnt[RX_WARPS][RX];
-    int64_t n = eff_n(n_cap, d_n);
-    int64_t base = (int64_t)blockIdx.x * RX_TILE;
-    if (base >= n) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ u32 s_key[RX_TILE], s_val[RX_TILE];
+    __shared__ u32 s_lstart[RX], s_gpos[RX];
+    __shared__ int s_tile;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket, 1u);
     for (int d = threadIdx.x; d < RX_WARPS * RX; d += RX_THREADS) (&wcnt[0][0])[d] = 0;
     __syncthreads();
+    const int tile = s_tile;
+    const int64_t n = eff_n(n_cap, d_n);
+    const int64_t base = (int64_t)tile * RX_TILE;
+    if (base >= n) return;  // no key in this tile (and none in any later tile)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     u32 k[RX_ROUNDS], v[RX_ROUNDS];
     int dg[RX_ROUNDS];
     const int64_t wbase = base + (int64_t)w * RX_WARP_SPAN;
 #pragma unroll
     for (int r = 0; r < RX_ROUNDS; ++r) {
-        int64_t i = wbase + r * 32 + lane;
-        bool ok = i < n;
+        const int64_t i = wbase + r * 32 + lane;
+        const bool ok = i < n;
         k[r] = ok ? kin[i] : 0u;
         v[r] = ok ? vin[i] : 0u;
         dg[r] = ok ? (int)((k[r] >> shift) & (RX - 1)) : RX;  // RX = no key
-        u32 peers = __match_any_sync(0xffffffffu, dg[r]);
-        int leader = __ffs(peers) - 1;
-        if (ok && lane == leader) wcnt[w][dg[r]] += __popc(peers);
+        const u32 peers = __match_any_sync(0xffffffffu, dg[r]);
+        if (ok && lane == __ffs(peers) - 1) wcnt[w][dg[r]] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // per digit: block offset from the global scan, then exclusive over warps
-    for (int d = threadIdx.x; d < RX; d += RX_THREADS) {
-        u32 run = hist[(int64_t)d * nblocks + blockIdx.x];
+    // per digit (thread d): block total, publish, look back
+    const int d = threadIdx.x;
+    u32 tot = 0;
+#pragma unroll
+    for (int ww = 0; ww < RX_WARPS; ++ww) tot += wcnt[ww][d];
+    u32 *my = lookback + (int64_t)tile * RX + d;
+    if (tile == 0) {
+        __stcg(my, LB_INC | tot);
+    } else {
+        __stcg(my, LB_AGG | tot);
+    }
+    u32 prefix = 0;
+    if (tile > 0) {
+        int j = tile - 1;
+        int spins = 0;
+        while (j >= 0) {
+            const u32 x = __ldcg(lookback + (int64_t)j * RX + d);
+            if ((x & ~LB_MASK) == 0u) {
+                if (++spins > LB_SPIN_LIMIT) {  // a predecessor never published: give up, flag it
+                    atomicOr(status, GSR_FLAG_TIMEOUT);
+                    break;
+                }
+                continue;
+            }
+            prefix += x & LB_MASK;
+            if ((x & ~LB_MASK) == LB_INC) break;
+            --j;
+        }
+        __stcg(my, LB_INC | (prefix + tot));
+    }
+    // block-local digit starts (exclusive scan over digits of tot)
+    {
+        __shared__ u32 sc[RX];
+        sc[d] = tot;
+        __syncthreads();
+        for (int o = 1; o < RX; o <<= 1) {
+            const u32 t = d >= o ? sc[d - o] : 0u;
+            __syncthreads();
+            sc[d] += t;
+            __syncthreads();
+        }
+        const u32 lstart = sc[d] - tot;
+        s_lstart[d] = lstart;
+        s_gpos[d] = digit_base[d] + prefix;
+        u32 run = lstart;  // per-warp starts inside the block
 #pragma unroll
         for (int ww = 0; ww < RX_WARPS; ++ww) {
-            u32 c = wcnt[ww][d];
+            const u32 c = wcnt[ww][d];
             wcnt[ww][d] = run;
             run += c;
         }
@@ -177,17 +247,26 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(const u32 *__restr
     const u32 lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < RX_ROUNDS; ++r) {
-        u32 peers = __match_any_sync(0xffffffffu, dg[r]);
-        int leader = __ffs(peers) - 1;
+        const u32 peers = __match_any_sync(0xffffffffu, dg[r]);
+        const int leader = __ffs(peers) - 1;
         u32 pos = 0;
         if (dg[r] < RX) pos = wcnt[w][dg[r]] + __popc(peers & lt);
         __syncwarp();
         if (dg[r] < RX && lane == leader) wcnt[w][dg[r]] += __popc(peers);
         __syncwarp();
         if (dg[r] < RX) {
-            kout[pos] = k[r];
-            vout[pos] = v[r];
+            s_key[pos] = k[r];
+            s_val[pos] = v[r];
         }
+    }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)RX_TILE, n - base);
+    for (int i = threadIdx.x; i < cnt; i += RX_THREADS) {
+        const u32 key = s_key[i];
+        const int dd = (int)((key >> shift) & (RX - 1));
+        const u32 gp = s_gpos[dd] + (u32)i - s_lstart[dd];
+        kout[gp] = key;
+        vout[gp] = s_val[i];
     }
 }
 
@@ -212,20 +291,28 @@ gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_
 {
     int passes = (bits + RX_BITS - 1) / RX_BITS;
     if (passes % 2) ++passes;  // an even count leaves the result in keys[0]
-    int64_t nb = ceil_div(n_cap > 0 ? n_cap : 1, RX_TILE);
-    size_t hist_words = (size_t)nb * RX;
-    GSR_TRY(ensure_buf(ctx, ctx->radix_hist, sizeof(u32) * hist_words));
-    u32 *hist = (u32 *)ctx->radix_hist.p;
+    if (passes > RX_MAX_PASSES) passes = RX_MAX_PASSES;
+    const int64_t nb = ceil_div(n_cap > 0 ? n_cap : 1, RX_TILE);
+    // layout of radix_hist: [ghist: passes * RX][per pass: lookback nb * RX + ticket]
+    const int64_t lb_words = nb * RX + 32;
+    const size_t words = (size_t)RX_MAX_PASSES * RX + (size_t)passes * lb_words;
+    GSR_TRY(ensure_buf(ctx, ctx->radix_hist, sizeof(u32) * words));
+    u32 *ghist = (u32 *)ctx->radix_hist.p;
+    u32 *lb0 = ghist + RX_MAX_PASSES * RX;
+    GSR_CUDA(ctx, cudaMemsetAsync(ghist, 0, sizeof(u32) * words, s));
+    const unsigned hb = (unsigned)std::min<int64_t>(nb, 2 * 152);
+    k_radix_global_hist<<<hb, RX_THREADS, 0, s>>>(keys[0], n_cap, d_n, passes, ghist);
+    k_radix_digit_base<<<passes, RX, 0, s>>>(ghist);
+    ctx->launches += 2;
+    GSR_LAUNCHED(ctx);
+    GSR_TRY(ensure_buf(ctx, ctx->view.counters, sizeof(u32) * CNT_WORDS));
+    u32 *status = (u32 *)ctx->view.counters.p + CNT_STATUS;
     int src = 0;
     for (int p = 0; p < passes; ++p) {
-        int shift = p * RX_BITS;
-        if (shift >= 32) shift = 24;  // padding pass: keys already ordered, stable no-op on top digit
-        k_radix_hist<<<(unsigned)nb, RX_THREADS, 0, s>>>(keys[src], n_cap, d_n, shift, (int)nb, hist);
-        ctx->launches += 1;
-        GSR_LAUNCHED(ctx);
-        GSR_TRY(scan_exclusive(ctx, hist, hist, (int64_t)hist_words, nullptr, nullptr, s));
-        k_radix_scatter<<<(unsigned)nb, RX_THREADS, 0, s>>>(keys[src], vals[src], keys[src ^ 1], vals[src ^ 1],
-                                                           n_cap, d_n, shift, (int)nb, hist);
+        u32 *lb = lb0 + (size_t)p * lb_words;
+        k_radix_onesweep<<<(unsigned)nb, RX_THREADS, 0, s>>>(keys[src], vals[src], keys[src ^ 1], vals[src ^ 1], n_cap,
+                                                             d_n, p * RX_BITS, ghist + p * RX, lb, lb + nb * RX,
+                                                             status);
         ctx->launches += 1;
         GSR_LAUNCHED(ctx);
         src ^= 1;
@@ -242,9 +329,8 @@ gsr_status grow_instance_capacity(gsr_ctx *ctx, ViewScratch &V, int64_t c)
     }
     // everything the instance sort touches is sized here, so that a captured
     // graph never needs to grow a buffer
-    const int64_t hist_words = ceil_div(c, RX_TILE) * RX;
-    GSR_TRY(ensure_buf(ctx, ctx->radix_hist, sizeof(u32) * hist_words));
-    GSR_TRY(ensure_buf(ctx, ctx->scan_tmp, sizeof(u32) * ceil_div(hist_words, SCAN_TILE)));
+    const int64_t words = RX_MAX_PASSES * RX + RX_MAX_PASSES * (ceil_div(c, RX_TILE) * RX + 32);
+    GSR_TRY(ensure_buf(ctx, ctx->radix_hist, sizeof(u32) * words));
     V.cap_i = c;
     return GSR_OK;
 }

@@ -1,0 +1,100 @@
+"""High-resolution adjoint check: 1752x1168 RGB-D, 1.5M Gaussians with
+log-scales N(-4, 0.7) and logits N(1, 1) (deep overlap, long contributor
+lists), memory-saving mode.  The autograd-facing backward (gsr_render_backward)
+is compared with FP64 central finite differences (h = 1e-6) of the oracle on
+64 seeded Gaussians.  Each FD render is restricted to the tile-aligned window
+of the Gaussian's tiles and to the Gaussians that overlap it, which renders
+that window exactly as the full image does (pinned on the CPU)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2312_10070_gb300 import api, synth as S
+from tests.gpu_common import grad_close, ocam
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
+
+
+def _linear(sc64, q, t, cam, w_rgb, w_d):
+    r = O.render(sc64, q, t, cam)
+    return float(np.sum(w_rgb * r["rgb"]) + np.sum(w_d * r["depth"])), r
+
+
+def test_hires_memory_saving_backward_matches_central_fd():
+    sc = S.hires_scene()
+    spec = S.camera_hires()
+    q, t = S.IDENTITY_POSE
+    oc = ocam(spec)
+    sc64 = O.Scene.from_dict(sc)
+    pr = O.project(sc64, q, t, oc)
+    rng = np.random.default_rng(64)
+    # 64 visible, unambiguous Gaussians with small tile rectangles
+    rect = pr["rect"]
+    area = (rect[:, 2] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 1] + 1)
+    cand = np.nonzero((pr["visible"] == 1) & (pr["amb"] == 0) & (area <= 9))[0]
+    chosen = rng.choice(cand, 64, replace=False)
+    H, W = spec.height, spec.width
+    w_rgb = rng.standard_normal((3, H, W))
+    w_d = rng.standard_normal((H, W))
+    # per chosen Gaussian: its window, the Gaussians overlapping it, and the
+    # pixels whose decisions are ambiguous (zeroed on both sides)
+    subsets = []
+    for gid in chosen:
+        x0, y0, x1, y1 = rect[gid]
+        ov = np.nonzero((pr["visible"] == 1) & (rect[:, 0] <= x1) & (rect[:, 2] >= x0) & (rect[:, 1] <= y1)
+                        & (rect[:, 3] >= y0))[0]
+        sub = O.Scene(sc64.mean[ov], sc64.log_scale[ov], sc64.quat[ov], sc64.opacity_logit[ov], sc64.rgb[ov])
+        cam = oc.crop(x0, y0, x1, y1)
+        r = O.render(sub, q, t, cam)
+        win = (slice(y0 * 16, y0 * 16 + cam.height), slice(x0 * 16, x0 * 16 + cam.width))
+        amb = r["amb"] != 0
+        w_rgb[(slice(None),) + win][:, amb] = 0.0
+        w_d[win][amb] = 0.0
+        subsets.append((gid, int(np.nonzero(ov == gid)[0][0]), sub, cam, win))
+    w_rgb = w_rgb.astype(np.float32)
+    w_d = w_d.astype(np.float32)
+
+    ctx = api.Context(memory_saving=True)
+    g = api.GaussianParams.from_numpy(sc)
+    cam = api.camera_from_spec(spec)
+    pose = api.make_pose(q, t)
+    out = api.render_forward(ctx, g, cam, pose)
+    grads, _ = api.render_backward(ctx, g, cam, pose, out, torch.from_numpy(w_rgb).cuda(),
+                                   torch.from_numpy(w_d).cuda(), None, want_pose=False)
+    gpu = {k: getattr(grads, k).cpu().numpy() for k in NAMES}
+    # memory-saving mode equals the default mode bit for bit in the forward
+    ctx2 = api.Context()
+    out2 = api.render_forward(ctx2, g, cam, pose)
+    torch.cuda.synchronize()
+    for k in ("rgb", "depth", "final_T", "last_idx"):
+        assert torch.equal(out[k], out2[k]), k
+
+    h = 1e-6
+    fd_all, gpu_all = [], []
+    for gid, li, sub, cw, win in subsets:
+        wr, wd = w_rgb[(slice(None),) + win].astype(np.float64), w_d[win].astype(np.float64)
+        _, r0 = _linear(sub, q, t, cw, wr, wd)
+        for name in NAMES:
+            arr = getattr(sub, name).reshape(sub.n, -1)
+            for k in range(arr.shape[1]):
+                old = arr[li, k]
+                arr[li, k] = old + h
+                lp, rp = _linear(sub, q, t, cw, wr, wd)
+                arr[li, k] = old - h
+                lm, rm = _linear(sub, q, t, cw, wr, wd)
+                arr[li, k] = old
+                if not (np.array_equal(rp["n_contrib"], r0["n_contrib"])
+                        and np.array_equal(rm["n_contrib"], r0["n_contrib"])):
+                    continue  # a discrete decision flips within +-h: FD not defined
+                fd_all.append((lp - lm) / (2 * h))
+                gpu_all.append(gpu[name].reshape(sc64.n, -1)[gid, k])
+    fd_all, gpu_all = np.array(fd_all), np.array(gpu_all)
+    assert len(fd_all) >= 0.9 * 64 * 14
+    ok, worst = grad_close(gpu_all, fd_all, rel=1e-3, floor=0.1, rel_l2=1e-3)
+    assert ok, worst
+    ctx.close()
+    ctx2.close()

@@ -220,3 +220,24 @@ def test_map_step_graph_replay_and_loss_decrease():
     assert abs(res[0][2]["loss_last"] - res[1][2]["loss_last"]) <= 1e-3 * res[0][2]["loss_last"]
     assert abs(res[0][3]["loss_last"] - res[1][3]["loss_last"]) <= 2e-2 * res[0][3]["loss_last"]
     ctx.close()
+
+
+def test_autotune_picks_a_config_that_keeps_parity():
+    """The autotuner tries every tile shape x batch x pixels per thread, keeps
+    the fastest, and rendering with the chosen configuration still matches
+    the oracle at that tile shape."""
+    ctx = api.Context()
+    sc, spec, q, t = unit_inputs(51, 52)
+    g = api.GaussianParams.from_numpy(sc)
+    cam = api.camera_from_spec(spec)
+    best, allr = api.autotune(ctx, g, cam, [api.make_pose(q, t)], reps=2)
+    assert len(allr) == 16
+    assert best["ms"] == min(r["ms"] for r in allr)
+    assert best["tile"] in [(16, 16), (8, 8), (16, 8), (32, 8)] and best["batch"] in (32, 64, 128, 256)
+    out = api.render_forward(ctx, g, cam, api.make_pose(q, t), want_n_contrib=True)
+    torch.cuda.synchronize()
+    ref = O.render(O.Scene.from_dict(sc), q, t, ocam(spec, best["tile"]))
+    ok = ref["amb"] == 0
+    assert np.abs(out["rgb"].cpu().numpy()[:, ok] - ref["rgb"][:, ok]).max() <= 2e-4
+    assert np.array_equal(out["n_contrib"].cpu().numpy()[ok], ref["n_contrib"][ok])
+    ctx.close()

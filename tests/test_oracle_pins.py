@@ -478,3 +478,21 @@ def test_paper_constants_fixture():
     np.testing.assert_allclose(out["loss"], (1 - lam) * out["l1_color"] + lam * (1 - out["ssim"]), rtol=1e-12)
     assert O.loss_track.__defaults__[1] == c["inlier_median_factor"]["value"]
     assert O.loss_track.__defaults__[2] == c["alpha_mask_power"]["value"]
+
+
+def test_tile_aligned_crop_renders_the_same_window():
+    """Region-restricted rendering (used for finite differences at high
+    resolution) reproduces the full render inside the window exactly."""
+    sc = O.Scene.from_dict(S.random_scene(3000, 5))
+    cs = S.camera_unit()
+    cam = O.Camera(cs.width, cs.height, cs.fx, cs.fy, cs.cx, cs.cy)
+    q, t = S.perturbed_pose(3)
+    full = O.render(sc, q, t, cam)
+    for tiles in ((3, 2, 6, 5), (0, 0, 1, 7), (8, 6, 9, 7)):
+        cc = cam.crop(*tiles)
+        cr = O.render(sc, q, t, cc)
+        y0, x0 = tiles[1] * 16, tiles[0] * 16
+        win = (slice(y0, y0 + cc.height), slice(x0, x0 + cc.width))
+        np.testing.assert_allclose(cr["rgb"], full["rgb"][(slice(None),) + win], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(cr["depth"], full["depth"][win], rtol=0, atol=1e-12)
+        assert np.array_equal(cr["n_contrib"], full["n_contrib"][win])
