@@ -278,7 +278,7 @@ def run_gpu(args, rank, world):
         api.map_step(ctx, g, state, cam, kf, None, 1, cfg, want_stats=False)
 
     # tile shape, batch and pixels per thread from the autotuner (untimed)
-    tuned, _ = api.autotune(ctx, g, cam, [pose], reps=3)
+    tuned, _ = api.autotune(ctx, g, cam, [pose], reps=6)
     api.profile_enable(ctx, True)
     for _ in range(max(args.warmup, 3)):
         step()

@@ -27,6 +27,17 @@
 
 namespace {
 
+// Cheap pre-test: sigma (computed exactly as in eval_gaussian) above the
+// staged threshold b.w means alpha < 1/255 for certain, so the entry is
+// skipped without the exponential; decisions are unchanged.
+__device__ __forceinline__ bool quick_reject(float px, float py, const float4 &a, const float4 &b)
+{
+    const float dx = __fsub_rn(px, a.x), dy = __fsub_rn(py, a.y);
+    const float q = __fmaf_rn(a.z, __fmul_rn(dx, dx), __fmul_rn(b.x, __fmul_rn(dy, dy)));
+    const float sigma = __fmaf_rn(a.w, __fmul_rn(dx, dy), __fmul_rn(0.5f, q));
+    return sigma > b.w;
+}
+
 template <int TW, int TH, int BATCH, int PPT>
 __device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
                                          float4 *sC)
@@ -60,7 +71,9 @@ __device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, in
             if (j < n) {
                 const int64_t r = vp.tvals[rg.x + j];
                 sA[k] = vp.rec[3 * r];
-                sB[k] = vp.rec[3 * r + 1];
+                float4 b = vp.rec[3 * r + 1];
+                b.w = sigma_reject(b.y);  // replaces the rectangle bits, unused here
+                sB[k] = b;
                 sC[k] = vp.rec[3 * r + 2];
             }
         }
@@ -71,7 +84,7 @@ __device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, in
             bool all = true;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (!done[k]) {
+                if (!done[k] && !quick_reject(px, py[k], a, b)) {
                     const Eval e = eval_gaussian(px, py[k], a.x, a.y, a.z, a.w, b.x, b.y);
                     if (e.use) {
                         const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, e.alpha));
@@ -216,7 +229,9 @@ __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, in
             const u32 r = vp.tvals[rg.x + bstart + k];
             sR[k] = r;
             sA[k] = vp.rec[3 * (int64_t)r];
-            sB[k] = vp.rec[3 * (int64_t)r + 1];
+            float4 bb = vp.rec[3 * (int64_t)r + 1];
+            bb.w = sigma_reject(bb.y);
+            sB[k] = bb;
             sC[k] = vp.rec[3 * (int64_t)r + 2];
         }
         __syncthreads();
@@ -228,7 +243,7 @@ __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, in
             const float4 a = sA[j], b = sB[j];
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (jj <= L[k]) {
+                if (jj <= L[k] && !quick_reject(px, py[k], a, b)) {
                     const Eval e = eval_gaussian(px, py[k], a.x, a.y, a.z, a.w, b.x, b.y);
                     if (e.use) {
                         contrib = true;

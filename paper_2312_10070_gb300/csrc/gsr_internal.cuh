@@ -216,6 +216,11 @@ __device__ __forceinline__ Eval eval_gaussian(float px, float py, float u, float
     return e;
 }
 
+// sigma beyond which alpha = o exp(-sigma) is certainly below 1/255:
+// ln(255 o) plus a margin far above the float32 error of __logf/__expf, so a
+// reject on it never changes a skip decision of eval_gaussian.
+__device__ __forceinline__ float sigma_reject(float op) { return __logf(255.f * op) + 0.02f; }
+
 // --------------------------------------------------------------- launchers
 struct Params {
     const float *mean, *log_scale, *quat, *opacity_logit, *rgb;

@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(RX) k_radix_digit_base(u32 *ghist)
 // block publishes its digit counts, looks back over the preceding tiles for
 // their running totals, stages its keys in shared memory in digit order and
 // writes them out so that equal digits land in consecutive addresses.
+template <int ROUNDS>
 __global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__restrict__ kin, const u32 *__restrict__ vin,
                                                                u32 *__restrict__ kout, u32 *__restrict__ vout,
                                                                int64_t n_cap, const u32 *d_n, int shift,
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__rest
                                                                u32 *status)
 {
     __shared__ u32 wcnt[RX_WARPS][RX];
-    __shared__ u32 s_key[RX_TILE], s_val[RX_TILE];
+    constexpr int TILE = RX_THREADS * ROUNDS, SPAN = 32 * ROUNDS;
+    __shared__ u32 s_key[TILE], s_val[TILE];
     __shared__ u32 s_lstart[RX], s_gpos[RX];
     __shared__ int s_tile;
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket, 1u);
@@ -173,14 +175,14 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__rest
     __syncthreads();
     const int tile = s_tile;
     const int64_t n = eff_n(n_cap, d_n);
-    const int64_t base = (int64_t)tile * RX_TILE;
+    const int64_t base = (int64_t)tile * TILE;
     if (base >= n) return;  // no key in this tile (and none in any later tile)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    u32 k[RX_ROUNDS], v[RX_ROUNDS];
-    int dg[RX_ROUNDS];
-    const int64_t wbase = base + (int64_t)w * RX_WARP_SPAN;
+    u32 k[ROUNDS], v[ROUNDS];
+    int dg[ROUNDS];
+    const int64_t wbase = base + (int64_t)w * SPAN;
 #pragma unroll
-    for (int r = 0; r < RX_ROUNDS; ++r) {
+    for (int r = 0; r < ROUNDS; ++r) {
         const int64_t i = wbase + r * 32 + lane;
         const bool ok = i < n;
         k[r] = ok ? kin[i] : 0u;
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__rest
     __syncthreads();
     const u32 lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int r = 0; r < RX_ROUNDS; ++r) {
+    for (int r = 0; r < ROUNDS; ++r) {
         const u32 peers = __match_any_sync(0xffffffffu, dg[r]);
         const int leader = __ffs(peers) - 1;
         u32 pos = 0;
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__rest
         }
     }
     __syncthreads();
-    const int cnt = (int)min((int64_t)RX_TILE, n - base);
+    const int cnt = (int)min((int64_t)TILE, n - base);
     for (int i = threadIdx.x; i < cnt; i += RX_THREADS) {
         const u32 key = s_key[i];
         const int dd = (int)((key >> shift) & (RX - 1));
@@ -292,7 +294,10 @@ gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_
     int passes = (bits + RX_BITS - 1) / RX_BITS;
     if (passes % 2) ++passes;  // an even count leaves the result in keys[0]
     if (passes > RX_MAX_PASSES) passes = RX_MAX_PASSES;
-    const int64_t nb = ceil_div(n_cap > 0 ? n_cap : 1, RX_TILE);
+    // small sorts use 1024-key tiles so that every SM gets work
+    const bool small = n_cap < (int64_t)2048 * 152 * 4;
+    const int64_t tile_keys = small ? RX_THREADS * 4 : RX_TILE;
+    const int64_t nb = ceil_div(n_cap > 0 ? n_cap : 1, tile_keys);
     // layout of radix_hist: [ghist: passes * RX][per pass: lookback nb * RX + ticket]
     const int64_t lb_words = nb * RX + 32;
     const size_t words = (size_t)RX_MAX_PASSES * RX + (size_t)passes * lb_words;
@@ -310,9 +315,14 @@ gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_
     int src = 0;
     for (int p = 0; p < passes; ++p) {
         u32 *lb = lb0 + (size_t)p * lb_words;
-        k_radix_onesweep<<<(unsigned)nb, RX_THREADS, 0, s>>>(keys[src], vals[src], keys[src ^ 1], vals[src ^ 1], n_cap,
-                                                             d_n, p * RX_BITS, ghist + p * RX, lb, lb + nb * RX,
-                                                             status);
+        if (small)
+            k_radix_onesweep<4><<<(unsigned)nb, RX_THREADS, 0, s>>>(keys[src], vals[src], keys[src ^ 1], vals[src ^ 1],
+                                                                    n_cap, d_n, p * RX_BITS, ghist + p * RX, lb,
+                                                                    lb + nb * RX, status);
+        else
+            k_radix_onesweep<RX_ROUNDS><<<(unsigned)nb, RX_THREADS, 0, s>>>(keys[src], vals[src], keys[src ^ 1],
+                                                                            vals[src ^ 1], n_cap, d_n, p * RX_BITS,
+                                                                            ghist + p * RX, lb, lb + nb * RX, status);
         ctx->launches += 1;
         GSR_LAUNCHED(ctx);
         src ^= 1;
@@ -329,7 +339,7 @@ gsr_status grow_instance_capacity(gsr_ctx *ctx, ViewScratch &V, int64_t c)
     }
     // everything the instance sort touches is sized here, so that a captured
     // graph never needs to grow a buffer
-    const int64_t words = RX_MAX_PASSES * RX + RX_MAX_PASSES * (ceil_div(c, RX_TILE) * RX + 32);
+    const int64_t words = RX_MAX_PASSES * RX + RX_MAX_PASSES * (ceil_div(c, RX_THREADS * 4) * RX + 32);
     GSR_TRY(ensure_buf(ctx, ctx->radix_hist, sizeof(u32) * words));
     V.cap_i = c;
     return GSR_OK;
