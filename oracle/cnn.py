@@ -75,33 +75,47 @@ def _col2im(dcols, shape_in):
     return dxp[:, 1:H + 1, 1:W + 1, :]
 
 
-def forward(params, x):
-    """Returns the output [B, 6] and a cache for backward."""
+def _identity(a):
+    return a
+
+
+def forward(params, x, rnd=None):
+    """Returns the output [B, 6] and a cache for backward.
+
+    rnd (optional) is applied to every stored activation (each ReLU output):
+    a network that keeps its activations in a narrower type than it
+    accumulates in is this function with rnd = rounding to that type."""
+    rnd = rnd or _identity
     a = np.asarray(x, np.float64)
     cache = []
     for li in range(len(CONV)):
         w, b = params[f"conv{li}.w"], params[f"conv{li}.b"]
         cols, (B, Ho, Wo) = _im2col(a)
         z = cols @ w.reshape(w.shape[0], -1).T + b
-        y = np.maximum(z, 0.0).reshape(B, Ho, Wo, -1)
+        y = rnd(np.maximum(z, 0.0)).reshape(B, Ho, Wo, -1)
         cache.append((a.shape, cols, z))
         a = y
     B = a.shape[0]
     h = a.reshape(B, -1)
     z1 = h @ params["fc0.w"].T + params["fc0.b"]
-    h1 = np.maximum(z1, 0.0)
+    h1 = rnd(np.maximum(z1, 0.0))
     out = h1 @ params["fc1.w"].T + params["fc1.b"]
     return out, (cache, h, z1, h1)
 
 
-def backward(params, cache_all, d_out):
-    """Gradients of sum(d_out * out) with respect to every parameter."""
+def backward(params, cache_all, d_out, rnd=None):
+    """Gradients of sum(d_out * out) with respect to every parameter.
+
+    rnd (optional) is applied to every stored upstream gradient: d_out and
+    each gradient after a ReLU mask (the GEMM operands of the backward)."""
+    rnd = rnd or _identity
     cache, h, z1, h1 = cache_all
+    d_out = rnd(np.asarray(d_out, np.float64))
     g = {}
     g["fc1.w"] = d_out.T @ h1
     g["fc1.b"] = d_out.sum(0)
     dh1 = d_out @ params["fc1.w"]
-    dz1 = dh1 * (z1 > 0)
+    dz1 = rnd(dh1 * (z1 > 0))
     g["fc0.w"] = dz1.T @ h
     g["fc0.b"] = dz1.sum(0)
     dh = dz1 @ params["fc0.w"]
@@ -109,7 +123,7 @@ def backward(params, cache_all, d_out):
     for li in reversed(range(len(CONV))):
         shape_in, cols, z = cache[li]
         w = params[f"conv{li}.w"]
-        dz = da.reshape(z.shape) * (z > 0)
+        dz = rnd(da.reshape(z.shape) * (z > 0))
         g[f"conv{li}.w"] = (dz.T @ cols).reshape(w.shape)
         g[f"conv{li}.b"] = dz.sum(0)
         if li > 0:

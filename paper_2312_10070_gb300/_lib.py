@@ -99,7 +99,11 @@ class TuneResult(ctypes.Structure):
                 ("ms_fwd", c_f), ("ms_bwd", c_f), ("ms", c_f)]
 
 
-# name -> (restype, argtypes); every symbol include/gsr.h declares
+class WarmstartOpts(ctypes.Structure):
+    _fields_ = [("lr", c_f), ("beta1", c_f), ("beta2", c_f), ("eps", c_f), ("w", c_f * 6)]
+
+
+# name -> (restype, argtypes); every symbol include/gsr.h and include/gsr_warmstart.h declare
 PROTOTYPES = {
     "gsr_default_options": (None, [ctypes.POINTER(Options)]),
     "gsr_default_camera": (None, [ctypes.POINTER(Camera), c_i32, c_i32, c_f, c_f, c_f, c_f]),
@@ -133,6 +137,17 @@ PROTOTYPES = {
                              ctypes.POINTER(MapStats), c_vp]),
     "gsr_autotune": (c_i32, [c_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Pose), c_i32,
                              c_i32, ctypes.POINTER(TuneResult), ctypes.POINTER(TuneResult), c_i32, c_vp]),
+    "gsr_warmstart_num_params": (c_i64, []),
+    "gsr_warmstart_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, ctypes.c_uint64]),
+    "gsr_warmstart_destroy": (None, [c_vp]),
+    "gsr_warmstart_last_error": (ctypes.c_char_p, [c_vp]),
+    "gsr_warmstart_set_params": (c_i32, [c_vp, c_vp, c_vp]),
+    "gsr_warmstart_get_params": (c_i32, [c_vp, c_vp, c_vp]),
+    "gsr_warmstart_forward": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
+    "gsr_warmstart_backward": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
+    "gsr_warmstart_default_opts": (None, [ctypes.POINTER(WarmstartOpts)]),
+    "gsr_warmstart_train_step": (c_i32, [c_vp, c_vp, c_vp, c_i32, ctypes.POINTER(WarmstartOpts), c_vp, c_vp]),
+    "gsr_warmstart_make_input": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_f, c_vp, c_vp]),
 }
 
 _lib = None

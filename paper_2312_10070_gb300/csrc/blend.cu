@@ -11,6 +11,13 @@
 // for every PPT.  A CTA stops loading once every pixel's transmittance fell
 // below the stop threshold.
 //
+// While staging, each list entry is also tested against the whole tile: if
+// the minimum of sigma over the tile's pixel-centre box exceeds the skip
+// threshold by more than the float32 error bound of both evaluations, no
+// pixel of the tile can composite it and it is not staged.  Kept entries are
+// compacted in list order and carry their list position, so every per-pixel
+// decision, last_idx and n_contrib are unchanged.
+//
 // The backward walks the same list from the largest last-composited index of
 // the tile down to 0, recovering T_j = T_{j+1} / (1 - alpha_j) from the saved
 // final transmittance; each thread first sums its PPT pixels' contributions
@@ -38,9 +45,109 @@ __device__ __forceinline__ bool quick_reject(float px, float py, const float4 &a
     return sigma > b.w;
 }
 
+// Pixel-centre box of a tile (clipped to the image).
+struct TileBox {
+    float x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ TileBox tile_box(const CamK &ck, int tile, int TW, int TH)
+{
+    const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
+    TileBox b;
+    b.x0 = (float)(tx * TW) + 0.5f;
+    b.x1 = (float)min(tx * TW + TW, ck.W) - 0.5f;
+    b.y0 = (float)(ty * TH) + 0.5f;
+    b.y1 = (float)min(ty * TH + TH, ck.H) - 0.5f;
+    return b;
+}
+
+// min over y in [y0, y1] of 0.5 A x^2 + B x y + 0.5 C y^2 (C > 0, iC ~ 1/C:
+// an inexact minimiser only raises the value by a second-order amount)
+__device__ __forceinline__ float edge_min(float x, float y0, float y1, float A, float B, float C, float iC)
+{
+    const float y = fminf(fmaxf(-B * x * iC, y0), y1);
+    return 0.5f * A * x * x + B * x * y + 0.5f * C * y * y;
+}
+
+// false only if sigma exceeds the skip threshold b.w at every pixel centre
+// of the box, as the per-pixel evaluation would compute it.  With kappa the
+// conic's condition number, both the per-pixel sigma and the box minimum m
+// computed here are within 1e-6 kappa (relative) of the exact values (a few
+// float32 roundings on terms whose absolute sum is at most kappa sigma), so
+// m (1 - e) > thr (1 + e), e = 1e-6 kappa, implies a skip at every pixel.
+__device__ __forceinline__ bool tile_may_hit(const float4 &a, const float4 &b, const TileBox &box)
+{
+    const float ca = a.z, cb = a.w, cc = b.x, thr = b.w;
+    const float det = ca * cc - cb * cb;
+    if (!(ca > 0.f && cc > 0.f && det > 0.f)) return true;
+    const float hd = 0.5f * (ca - cc);
+    const float lmax = 0.5f * (ca + cc) + sqrtf(hd * hd + cb * cb);
+    const float e = 1e-6f * __fdividef(lmax * lmax, det);
+    if (!(e < 0.25f)) return true;
+    const float X0 = box.x0 - a.x, X1 = box.x1 - a.x, Y0 = box.y0 - a.y, Y1 = box.y1 - a.y;
+    float m = 0.f;
+    if (!(X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f)) {
+        const float ia = __fdividef(1.f, ca), ic = __fdividef(1.f, cc);
+        m = fminf(fminf(edge_min(X0, Y0, Y1, ca, cb, cc, ic), edge_min(X1, Y0, Y1, ca, cb, cc, ic)),
+                  fminf(edge_min(Y0, X0, X1, cc, cb, ca, ia), edge_min(Y1, X0, X1, cc, cb, ca, ia)));
+    }
+    return !(m * (1.f - e) > thr * (1.f + e));
+}
+
+// Stage list entries [lo, hi) (hi - lo <= BATCH) of a tile: entries that may
+// hit the tile are written in list order to sA/sB/sC (sB.w = skip threshold),
+// with their list position in sJ and Gaussian rank in sR.  Returns the number
+// staged (uniform over the CTA).  s_cnt holds NT/32 ints.  The caller
+// synchronises before reading the staged entries.
+template <int NT>
+__device__ __forceinline__ int stage_entries(const BlendView &vp, u32 list_base, int lo, int hi, const TileBox &box,
+                                             float4 *sA, float4 *sB, float4 *sC, u32 *sR, int *sJ, int *s_cnt)
+{
+    constexpr int NW = NT / 32;
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    int total = 0;
+    for (int c0 = lo; c0 < hi; c0 += NT) {
+        const int j = c0 + (int)threadIdx.x;
+        bool keep = false;
+        float4 a, b;
+        u32 r = 0;
+        if (j < hi) {
+            r = vp.tvals[list_base + j];
+            a = vp.rec[3 * (int64_t)r];
+            b = vp.rec[3 * (int64_t)r + 1];
+            b.w = sigma_reject(b.y);  // replaces the rectangle bits, unused here
+            keep = tile_may_hit(a, b, box);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        int off = total, sum = __popc(bal);
+        if (NW > 1) {
+            if (lane == 0) s_cnt[warp] = sum;
+            __syncthreads();
+            sum = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const int cw = s_cnt[w];
+                off += w < warp ? cw : 0;
+                sum += cw;
+            }
+        }
+        if (keep) {
+            const int pos = off + __popc(bal & ((1u << lane) - 1u));
+            sA[pos] = a;
+            sB[pos] = b;
+            sC[pos] = vp.rec[3 * (int64_t)r + 2];
+            sR[pos] = r;
+            sJ[pos] = j;
+        }
+        total += sum;
+        if (NW > 1) __syncthreads();  // s_cnt is rewritten by the next chunk
+    }
+    return total;
+}
+
 template <int TW, int TH, int BATCH, int PPT>
 __device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
-                                         float4 *sC)
+                                         float4 *sC, u32 *sR, int *sJ, int *s_cnt)
 {
     constexpr int NT = TW * TH / PPT;
     const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
@@ -64,21 +171,11 @@ __device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, in
     }
     const uint2 rg = vp.ranges[tile];
     const int n = (int)(rg.y - rg.x);
+    const TileBox box = tile_box(ck, tile, TW, TH);
     for (int base = 0; base < n; base += BATCH) {
         if (__syncthreads_count(tdone) == NT) break;
-        for (int k = threadIdx.x; k < BATCH; k += NT) {
-            const int j = base + k;
-            if (j < n) {
-                const int64_t r = vp.tvals[rg.x + j];
-                sA[k] = vp.rec[3 * r];
-                float4 b = vp.rec[3 * r + 1];
-                b.w = sigma_reject(b.y);  // replaces the rectangle bits, unused here
-                sB[k] = b;
-                sC[k] = vp.rec[3 * r + 2];
-            }
-        }
+        const int cnt = stage_entries<NT>(vp, rg.x, base, min(n, base + BATCH), box, sA, sB, sC, sR, sJ, s_cnt);
         __syncthreads();
-        const int cnt = min(BATCH, n - base);
         for (int j = 0; j < cnt && !tdone; ++j) {
             const float4 a = sA[j], b = sB[j];
             bool all = true;
@@ -98,7 +195,7 @@ __device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, in
                             c2[k] = fmaf(c.z, w, c2[k]);
                             d[k] = fmaf(b.z, w, d[k]);
                             T[k] = Tn;
-                            last[k] = base + j;
+                            last[k] = sJ[j];
                             ++nc[k];
                         }
                     }
@@ -181,7 +278,7 @@ __device__ __forceinline__ void warp_reduce_add6(const float (&v)[6], float *dst
 // (u, v, conic, depth); colour and opacity gradients are skipped.
 template <int TW, int TH, int BATCH, int PPT, bool POSE_ONLY>
 __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
-                                         float4 *sC, u32 *sR, int *s_max)
+                                         float4 *sC, u32 *sR, int *sJ, int *s_cnt, int *s_max)
 {
     constexpr int NT = TW * TH / PPT;
     const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
@@ -221,22 +318,14 @@ __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, in
     if ((threadIdx.x & 31) == 0) atomicMax(s_max, wmax);
     __syncthreads();
     const int nend = min(*s_max + 1, (int)(rg.y - rg.x));  // saved state never reads past the list
+    const TileBox box = tile_box(ck, tile, TW, TH);
     for (int bend = nend; bend > 0; bend -= BATCH) {
         const int bstart = max(0, bend - BATCH);
-        const int cnt = bend - bstart;
         __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += NT) {
-            const u32 r = vp.tvals[rg.x + bstart + k];
-            sR[k] = r;
-            sA[k] = vp.rec[3 * (int64_t)r];
-            float4 bb = vp.rec[3 * (int64_t)r + 1];
-            bb.w = sigma_reject(bb.y);
-            sB[k] = bb;
-            sC[k] = vp.rec[3 * (int64_t)r + 2];
-        }
+        const int cnt = stage_entries<NT>(vp, rg.x, bstart, bend, box, sA, sB, sC, sR, sJ, s_cnt);
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
-            const int jj = bstart + j;
+            const int jj = sJ[j];
             float gu = 0.f, gv = 0.f, gca = 0.f, gcb = 0.f, gcc = 0.f, gop = 0.f, gr = 0.f, gg = 0.f, gb = 0.f,
                   gz = 0.f;
             bool contrib = false;
@@ -295,7 +384,9 @@ template <int TW, int TH, int BATCH, int PPT>
 __global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd(CamK ck, BlendView vp)
 {
     __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
-    fwd_tile<TW, TH, BATCH, PPT>(ck, vp, blockIdx.x, sA, sB, sC);
+    __shared__ u32 sR[BATCH];
+    __shared__ int sJ[BATCH], s_cnt[TW * TH / PPT / 32];
+    fwd_tile<TW, TH, BATCH, PPT>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt);
 }
 
 template <int TW, int TH, int BATCH, int PPT, bool POSE_ONLY>
@@ -303,8 +394,9 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_bwd(CamK ck, BlendView v
 {
     __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
     __shared__ u32 sR[BATCH];
+    __shared__ int sJ[BATCH], s_cnt[TW * TH / PPT / 32];
     __shared__ int s_max;
-    bwd_tile<TW, TH, BATCH, PPT, POSE_ONLY>(ck, vp, blockIdx.x, sA, sB, sC, sR, &s_max);
+    bwd_tile<TW, TH, BATCH, PPT, POSE_ONLY>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt, &s_max);
 }
 
 // Persistent forms: items[i] = (view << 16) | tile, longest lists first.
@@ -322,10 +414,12 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd_multi(CamK ck, const
                                                                   u32 *counter)
 {
     __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
+    __shared__ u32 sR[BATCH];
+    __shared__ int sJ[BATCH], s_cnt[TW * TH / PPT / 32];
     __shared__ int s_item;
     for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
         const u32 w = items[it];
-        fwd_tile<TW, TH, BATCH, PPT>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC);
+        fwd_tile<TW, TH, BATCH, PPT>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt);
     }
 }
 
@@ -336,10 +430,12 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_bwd_multi(CamK ck, const
 {
     __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
     __shared__ u32 sR[BATCH];
+    __shared__ int sJ[BATCH], s_cnt[TW * TH / PPT / 32];
     __shared__ int s_max, s_item;
     for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
         const u32 w = items[it];
-        bwd_tile<TW, TH, BATCH, PPT, false>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, &s_max);
+        bwd_tile<TW, TH, BATCH, PPT, false>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt,
+                                            &s_max);
     }
 }
 

@@ -1,0 +1,763 @@
+// cnn.cu -- the learned tracking warm-start network on BF16 tensor cores.
+//
+// Not a step of the paper's method (its tracker starts from the
+// constant-velocity extrapolation of Sec. 3.5): a small network that predicts
+// the twist correcting that initial pose from the rendered-versus-input RGB-D
+// residual.  Sizes and layouts are given in include/gsr_warmstart.h.
+//
+// Every layer is a GEMM with FP32 accumulation:
+//   forward         Z[M,N]   = im2col(X)[M,K] . W[N,K]^T        (+ bias, ReLU, -> BF16)
+//   data gradient   dCol[M,K] = dZ[M,N] . W[N,K]                 (then col2im + ReLU mask)
+//   weight gradient dW[N,K]  = dZ^T[N,M] . im2col(X)[M,K]       (split over M, FP32 atomics)
+// with M = batch x output pixels, N = output channels, K = 9 x input channels.
+// One kernel serves all three: mma.sync m16n8k16 BF16 on 128 x 64 tiles, both
+// operands staged to shared memory K-contiguous (transposed while staging when
+// stored the other way) and fed to the tensor cores with ldmatrix.
+#include <cuda_bf16.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "../../include/gsr_warmstart.h"
+#include "gsr_internal.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int NL = 6;
+constexpr int CIN[NL] = {8, 32, 64, 128, 128, 256};
+constexpr int CINP[NL] = {16, 32, 64, 128, 128, 256};  // stored channels (the input padded to 16)
+constexpr int COUT[NL] = {32, 64, 128, 128, 256, 256};
+constexpr int HIN[NL] = {120, 60, 30, 15, 8, 4};
+constexpr int WIN[NL] = {160, 80, 40, 20, 10, 5};
+constexpr int HOUT[NL] = {60, 30, 15, 8, 4, 2};
+constexpr int WOUT[NL] = {80, 40, 20, 10, 5, 3};
+constexpr int FLAT = 2 * 3 * 256, HID = 256, NOUT = 6, NOUTP = 8;
+constexpr int NSEG = NL + 2;
+
+struct Layout {
+    int64_t w_off[NSEG], b_off[NSEG];  // flat FP32 vector
+    int64_t wb_off[NSEG + 1];          // BF16 GEMM operands [N][K] (conv 0 padded, dense 2 padded to 8 rows)
+    int64_t n_params;
+    int cin[NL], cinp[NL];             // conv input channels: true and stored
+};
+
+struct LossW {
+    float w[NOUT];
+};
+
+// ------------------------------------------------------------------ GEMM
+constexpr int BM = 128, BN = 64, BKT = 32, SROW = BKT + 8;
+enum { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_RELU_BF16 = 2, EPI_BIAS = 3 };
+
+__device__ __forceinline__ void ldsm_x4(const bf16 *p, u32 &r0, u32 &r1, u32 &r2, u32 &r3)
+{
+    const u32 a = (u32)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x2(const bf16 *p, u32 &r0, u32 &r1)
+{
+    const u32 a = (u32)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const u32 (&a)[4], u32 b0, u32 b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Stage rows [r0, r0 + ROWS) x reduction indices [k0, k0 + BKT) of an operand
+// into sm[ROWS][SROW] (reduction index contiguous).  KMAJOR: element (r, k) is
+// g[r * ld + k]; otherwise g[k * ld + r].  Elements outside R x [0, kend) are 0.
+// Vector loads need ld % 8 == 0 and a 16-byte aligned base (checked by the host).
+template <int ROWS, bool KMAJOR>
+__device__ __forceinline__ void stage(bf16 (*sm)[SROW], const bf16 *__restrict__ g, int ld, int R, int64_t kend,
+                                      int r0, int64_t k0)
+{
+    constexpr int CH = ROWS * BKT / 8;  // chunks of 8 elements
+    for (int c = threadIdx.x; c < CH; c += 256) {
+        if (KMAJOR) {
+            const int r = c / (BKT / 8), kc = (c % (BKT / 8)) * 8;
+            const int gr = r0 + r;
+            const int64_t gk = k0 + kc;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (gr < R && gk + 8 <= kend) {
+                v = *reinterpret_cast<const uint4 *>(g + (int64_t)gr * ld + gk);
+            } else if (gr < R && gk < kend) {
+                bf16 t[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) t[i] = gk + i < kend ? g[(int64_t)gr * ld + gk + i] : __float2bfloat16(0.f);
+                v = *reinterpret_cast<uint4 *>(t);
+            }
+            *reinterpret_cast<uint4 *>(&sm[r][kc]) = v;
+        } else {
+            const int k = c / (ROWS / 8), rc = (c % (ROWS / 8)) * 8;
+            const int64_t gk = k0 + k;
+            const int gr = r0 + rc;
+            bf16 t[8];
+            if (gk < kend && gr + 8 <= R) {
+                *reinterpret_cast<uint4 *>(t) = *reinterpret_cast<const uint4 *>(g + gk * ld + gr);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) t[i] = (gk < kend && gr + i < R) ? g[gk * ld + gr + i] : __float2bfloat16(0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sm[rc + i][k] = t[i];
+        }
+    }
+}
+
+// C[M,N] (op)= sum_k A(m,k) B(k,n).  A(m,k) = AK ? A[m*lda+k] : A[k*lda+m];
+// B(k,n) = BK ? B[n*ldb+k] : B[k*ldb+n].  Grid (ceil(N/64), ceil(M/128), splits):
+// split z covers reduction indices [z*kchunk, min(K, (z+1)*kchunk)).
+template <bool AK, bool BK, int EPI>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t kchunk, const bf16 *__restrict__ A,
+                                              int lda, const bf16 *__restrict__ B, int ldb, void *C, int ldc,
+                                              const float *__restrict__ bias)
+{
+    __shared__ __align__(16) bf16 sA[BM][SROW];
+    __shared__ __align__(16) bf16 sB[BN][SROW];
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int64_t kbeg = (int64_t)blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp & 3, wn = warp >> 2;  // 4 x 2 warps of 32 x 32
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BKT) {
+        stage<BM, AK>(sA, A, lda, M, kend, m0, k0);
+        stage<BN, BK>(sB, B, ldb, N, kend, n0, k0);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BKT; kk += 16) {
+            u32 a[2][4], b[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+                ldsm_x4(&sA[wm * 32 + mi * 16 + (lane & 15)][kk + (lane >> 4) * 8], a[mi][0], a[mi][1], a[mi][2],
+                        a[mi][3]);
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni)
+                ldsm_x2(&sB[wn * 32 + ni * 8 + (lane & 7)][kk + ((lane >> 3) & 1) * 8], b[ni][0], b[ni][1]);
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni][0], b[ni][1]);
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = m0 + wm * 32 + mi * 16 + g + (q >> 1) * 8;
+                const int col = n0 + wn * 32 + ni * 8 + t * 2 + (q & 1);
+                if (row >= M || col >= N) continue;
+                const float v = acc[mi][ni][q];
+                const int64_t o = (int64_t)row * ldc + col;
+                if (EPI == EPI_STORE) ((float *)C)[o] = v;
+                else if (EPI == EPI_ATOMIC) atomicAdd((float *)C + o, v);
+                else if (EPI == EPI_BIAS) ((float *)C)[o] = v + bias[col];
+                else ((bf16 *)C)[o] = __float2bfloat16(fmaxf(v + bias[col], 0.f));
+            }
+}
+
+// --------------------------------------------------------- data movement
+// x f32 [npix, 8] -> bf16 [npix, 16] (channels 8..15 zero)
+__global__ void k_input_bf16(int64_t npix, const float *__restrict__ x, bf16 *__restrict__ y)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npix) return;
+    __align__(16) bf16 v[16];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = __float2bfloat16(x[i * 8 + c]);
+#pragma unroll
+    for (int c = 8; c < 16; ++c) v[c] = __float2bfloat16(0.f);
+    uint4 *o = reinterpret_cast<uint4 *>(y + i * 16);
+    o[0] = *reinterpret_cast<const uint4 *>(v);
+    o[1] = *reinterpret_cast<const uint4 *>(v + 8);
+}
+
+// im2col of a 3x3 stride-2 padding-1 convolution: col[(b,oy,ox)][(ky,kx,c)];
+// one thread per 8 channels (C % 8 == 0)
+__global__ void k_im2col(int B, int H, int W, int C, int Ho, int Wo, const bf16 *__restrict__ x,
+                         bf16 *__restrict__ col)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c8 = C / 8;
+    if (i >= (int64_t)B * Ho * Wo * 9 * c8) return;
+    const int cc = (int)(i % c8) * 8;
+    const int64_t r = i / c8;
+    const int tap = (int)(r % 9);
+    const int64_t m = r / 9;
+    const int ky = tap / 3, kx = tap % 3;
+    const int ox = (int)(m % Wo), oy = (int)((m / Wo) % Ho), b = (int)(m / ((int64_t)Wo * Ho));
+    const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (iy >= 0 && iy < H && ix >= 0 && ix < W)
+        v = *reinterpret_cast<const uint4 *>(x + (((int64_t)b * H + iy) * W + ix) * C + cc);
+    *reinterpret_cast<uint4 *>(col + m * (9 * C) + tap * C + cc) = v;
+}
+
+// Adjoint of im2col as a gather (each input pixel receives from at most 2 x 2
+// output positions), times the mask of the ReLU that produced x.
+__global__ void k_col2im_relu(int B, int H, int W, int C, int Ho, int Wo, const float *__restrict__ dcol,
+                              const bf16 *__restrict__ x, bf16 *__restrict__ dz)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * H * W * C) return;
+    const int c = (int)(i % C);
+    const int64_t r = i / C;
+    const int ix = (int)(r % W), iy = (int)((r / W) % H), b = (int)(r / ((int64_t)W * H));
+    float s = 0.f;
+    for (int ky = 0; ky < 3; ++ky) {
+        const int ty = iy + 1 - ky;
+        if (ty < 0 || (ty & 1) || (ty >> 1) >= Ho) continue;
+        for (int kx = 0; kx < 3; ++kx) {
+            const int tx = ix + 1 - kx;
+            if (tx < 0 || (tx & 1) || (tx >> 1) >= Wo) continue;
+            const int64_t m = ((int64_t)b * Ho + (ty >> 1)) * Wo + (tx >> 1);
+            s += dcol[m * (9 * C) + (ky * 3 + kx) * C + c];
+        }
+    }
+    dz[i] = __float2bfloat16(__bfloat162float(x[i]) > 0.f ? s : 0.f);
+}
+
+// out[n] += sum over rows of z[row * ld + n] (bias gradients); block 256 = 8 row
+// lanes x 32 columns, grid (ceil(N/32), row splits)
+__global__ void k_colsum(int64_t M, int N, int ld, const bf16 *__restrict__ z, float *__restrict__ out)
+{
+    const int n = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int64_t per = (M + gridDim.y - 1) / gridDim.y;
+    const int64_t r0 = (int64_t)blockIdx.y * per, r1 = min(M, r0 + per);
+    float s = 0.f;
+    if (n < N)
+        for (int64_t r = r0 + (threadIdx.x >> 5); r < r1; r += 8) s += __bfloat162float(z[r * ld + n]);
+    __shared__ float red[8][33];
+    red[threadIdx.x >> 5][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (threadIdx.x < 32 && n < N) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+        atomicAdd(&out[n], t);
+    }
+}
+
+// weighted squared error of the 6 outputs: loss = (1/B) sum w r^2 and the BF16
+// upstream gradient dout [B, 8] = 2 w r / B (columns 6, 7 zero)
+__global__ void k_twist_loss(int B, const float *__restrict__ out, const float *__restrict__ tgt, LossW w,
+                             float *__restrict__ dout, float *__restrict__ loss)
+{
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < B * NOUTP; i += 256) {
+        const int b = i / NOUTP, c = i % NOUTP;
+        float d = 0.f;
+        if (c < NOUT) {
+            const float r = out[b * NOUTP + c] - tgt[b * NOUT + c];
+            s += w.w[c] * r * r;
+            d = 2.f * w.w[c] * r / (float)B;
+        }
+        dout[i] = d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss) *loss = red[0] / (float)B;
+}
+
+// f32 [B, 6] (row stride ld_in) -> bf16 [B, 8] (columns 6, 7 zero)
+__global__ void k_dout_bf16(int B, const float *__restrict__ d, int ld_in, bf16 *__restrict__ o)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * NOUTP) return;
+    const int b = i / NOUTP, c = i % NOUTP;
+    o[i] = __float2bfloat16(c < NOUT ? d[b * ld_in + c] : 0.f);
+}
+
+// dz = d * (h > 0) in BF16
+__global__ void k_relu_bwd(int64_t n, const float *__restrict__ d, const bf16 *__restrict__ h, bf16 *__restrict__ dz)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dz[i] = __float2bfloat16(__bfloat162float(h[i]) > 0.f ? d[i] : 0.f);
+}
+
+// conv 0 weight gradient [32][9][16] (padded) -> the flat layout [32][9][8]
+__global__ void k_unpad(int N, int cin, int cinp, const float *__restrict__ src, float *__restrict__ dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * 9 * cin) return;
+    const int c = i % cin, nt = i / cin;
+    dst[i] = src[nt * cinp + c];
+}
+
+// FP32 masters (flat layout) -> BF16 GEMM operands
+__global__ void k_pack(const float *__restrict__ master, bf16 *__restrict__ wb, Layout L)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.wb_off[NSEG]) return;
+    int s = 0;
+    while (s < NSEG - 1 && i >= L.wb_off[s + 1]) ++s;
+    const int64_t j = i - L.wb_off[s];
+    float v = 0.f;
+    if (s < NL) {
+        const int cp = L.cinp[s], ci = L.cin[s];
+        const int64_t K = 9 * (int64_t)cp;
+        const int64_t n = j / K, kk = j % K;
+        const int tap = (int)(kk / cp), c = (int)(kk % cp);
+        if (c < ci) v = master[L.w_off[s] + (n * 9 + tap) * ci + c];
+    } else if (s == NL || j < (int64_t)NOUT * HID) {
+        v = master[L.w_off[s] + j];
+    }
+    wb[i] = __float2bfloat16(v);
+}
+
+__global__ void k_adam(int64_t n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, float lr, float b1, float b2, float eps, float bc1, float bc2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// network input from a 160x120 render and a full-resolution frame (box average)
+__global__ void k_make_input(int h, int w, const float *__restrict__ rgb_r, const float *__restrict__ d_r,
+                             const float *__restrict__ rgb_i, const float *__restrict__ d_i, float inv_scale,
+                             float *__restrict__ out)
+{
+    constexpr int H = GSR_WS_IN_H, W = GSR_WS_IN_W, HW = H * W;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= HW) return;
+    const int i = p / W, j = p % W;
+    const int y0 = (int)(((int64_t)i * h) / H), y1 = (int)(((int64_t)(i + 1) * h) / H);
+    const int x0 = (int)(((int64_t)j * w) / W), x1 = (int)(((int64_t)(j + 1) * w) / W);
+    const int64_t hw = (int64_t)h * w;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, sd = 0.f;
+    int nd = 0;
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) {
+            const int64_t q = (int64_t)y * w + x;
+            s0 += rgb_i[q];
+            s1 += rgb_i[hw + q];
+            s2 += rgb_i[2 * hw + q];
+            const float d = d_i[q];
+            if (d > 0.f) {
+                sd += d;
+                ++nd;
+            }
+        }
+    const float inv = 1.f / (float)((y1 - y0) * (x1 - x0));
+    const float di = nd ? sd / (float)nd : 0.f, dr = d_r[p];
+    const float r0 = rgb_r[p], r1 = rgb_r[HW + p], r2 = rgb_r[2 * HW + p];
+    float *o = out + (int64_t)p * 8;
+    o[0] = r0;
+    o[1] = r1;
+    o[2] = r2;
+    o[3] = dr * inv_scale;
+    o[4] = s0 * inv - r0;
+    o[5] = s1 * inv - r1;
+    o[6] = s2 * inv - r2;
+    o[7] = (dr > 0.f && di > 0.f) ? (di - dr) * inv_scale : 0.f;
+}
+
+unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+void make_layout(Layout &L)
+{
+    int64_t o = 0, wo = 0;
+    for (int l = 0; l < NSEG; ++l) {
+        const int64_t nout = l < NL ? COUT[l] : (l == NL ? HID : NOUT);
+        const int64_t kin = l < NL ? 9 * (int64_t)CIN[l] : (l == NL ? FLAT : HID);
+        const int64_t kst = l < NL ? 9 * (int64_t)CINP[l] : kin;
+        const int64_t nst = l == NL + 1 ? NOUTP : nout;
+        L.w_off[l] = o;
+        o += nout * kin;
+        L.b_off[l] = o;
+        o += nout;
+        L.wb_off[l] = wo;
+        wo += nst * kst;
+    }
+    L.wb_off[NSEG] = wo;
+    L.n_params = o;
+    for (int l = 0; l < NL; ++l) {
+        L.cin[l] = CIN[l];
+        L.cinp[l] = CINP[l];
+    }
+}
+
+} // namespace
+
+// ------------------------------------------------------------------ state
+struct gsr_warmstart {
+    int max_batch = 0;
+    int last_batch = 0;  // batch of the last forward (0 = none)
+    int64_t step = 0;
+    std::string err;
+    Layout L{};
+    DevBuf master, m1, m2, grad, wb;
+    DevBuf act[NL + 2];  // act[0] input (16 ch), act[l+1] conv l output, act[NL+1] dense-1 output
+    DevBuf col[NL];      // im2col of each conv input
+    DevBuf dz, dbuf, dwb, out, dout32, dout, loss_tmp;
+};
+
+namespace {
+
+gsr_status ws_fail(gsr_warmstart *w, gsr_status s, const std::string &m)
+{
+    if (w) w->err = m;
+    return s;
+}
+
+gsr_status ws_alloc(gsr_warmstart *w, DevBuf &b, size_t bytes)
+{
+    if (cudaMalloc(&b.p, bytes ? bytes : 16) != cudaSuccess) {
+        (void)cudaGetLastError();
+        b.p = nullptr;
+        return ws_fail(w, GSR_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    b.bytes = bytes;
+    return GSR_OK;
+}
+
+gsr_status launched(gsr_warmstart *w)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ws_fail(w, GSR_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+    return GSR_OK;
+}
+
+#define WS_TRY(e)                    \
+    do {                             \
+        gsr_status _s = (e);         \
+        if (_s != GSR_OK) return _s; \
+    } while (0)
+
+// Number of reduction splits for a GEMM with the given output tiles: enough
+// CTAs to cover the 152 SMs about twice, each split at least 8 k-tiles long.
+int64_t split_count(int M, int N, int64_t K)
+{
+    const int64_t tiles = (int64_t)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    int64_t s = std::max<int64_t>(1, 304 / tiles);
+    s = std::min<int64_t>(s, std::max<int64_t>(1, K / (8 * BKT)));
+    return std::min<int64_t>(s, 65535);
+}
+
+template <bool AK, bool BK, int EPI>
+gsr_status gemm(gsr_warmstart *w, int M, int N, int64_t K, const bf16 *A, int lda, const bf16 *B, int ldb, void *C,
+                int ldc, const float *bias, cudaStream_t s)
+{
+    if ((lda % 8) || (ldb % 8) || (((uintptr_t)A) & 15) || (((uintptr_t)B) & 15))
+        return ws_fail(w, GSR_ERR_INVALID_ARG, "GEMM operand not 16-byte aligned");
+    int64_t splits = 1;
+    if (EPI == EPI_ATOMIC) splits = split_count(M, N, K);
+    int64_t kchunk = (K + splits - 1) / splits;
+    kchunk = (kchunk + BKT - 1) / BKT * BKT;
+    splits = (K + kchunk - 1) / kchunk;
+    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)std::max<int64_t>(1, splits));
+    k_gemm<AK, BK, EPI><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, lda, B, ldb, C, ldc, bias);
+    return launched(w);
+}
+
+gsr_status pack(gsr_warmstart *w, cudaStream_t s)
+{
+    k_pack<<<blocks(w->L.wb_off[NSEG]), 256, 0, s>>>((const float *)w->master.p, (bf16 *)w->wb.p, w->L);
+    return launched(w);
+}
+
+gsr_status backward_impl(gsr_warmstart *w, const bf16 *dout, int batch, cudaStream_t s)
+{
+    const int64_t B = batch;
+    const Layout &L = w->L;
+    const bf16 *wb = (const bf16 *)w->wb.p;
+    float *grad = (float *)w->grad.p;
+    float *dbuf = (float *)w->dbuf.p;
+    bf16 *dz = (bf16 *)w->dz.p;
+    if (cudaMemsetAsync(grad, 0, sizeof(float) * L.n_params, s) != cudaSuccess)
+        return ws_fail(w, GSR_ERR_CUDA, "memset failed");
+    // dense 2: dW = dout^T h1, db = column sums of dout, dh1 = dout W
+    WS_TRY((gemm<false, false, EPI_ATOMIC>(w, NOUT, HID, B, dout, NOUTP, (const bf16 *)w->act[NL + 1].p, HID,
+                                           grad + L.w_off[NL + 1], HID, nullptr, s)));
+    k_colsum<<<dim3(1, 4), 256, 0, s>>>(B, NOUT, NOUTP, dout, grad + L.b_off[NL + 1]);
+    WS_TRY(launched(w));
+    WS_TRY((gemm<true, false, EPI_STORE>(w, batch, HID, NOUTP, dout, NOUTP, wb + L.wb_off[NL + 1], HID, dbuf, HID,
+                                         nullptr, s)));
+    k_relu_bwd<<<blocks(B * HID), 256, 0, s>>>(B * HID, dbuf, (const bf16 *)w->act[NL + 1].p, dz);
+    WS_TRY(launched(w));
+    // dense 1: dW = dz^T h0, db, dh0 = dz W, then the mask of conv 5's ReLU
+    WS_TRY((gemm<false, false, EPI_ATOMIC>(w, HID, FLAT, B, dz, HID, (const bf16 *)w->act[NL].p, FLAT,
+                                           grad + L.w_off[NL], FLAT, nullptr, s)));
+    k_colsum<<<dim3(HID / 32, 4), 256, 0, s>>>(B, HID, HID, dz, grad + L.b_off[NL]);
+    WS_TRY(launched(w));
+    WS_TRY((gemm<true, false, EPI_STORE>(w, batch, FLAT, HID, dz, HID, wb + L.wb_off[NL], FLAT, dbuf, FLAT, nullptr,
+                                         s)));
+    k_relu_bwd<<<blocks(B * FLAT), 256, 0, s>>>(B * FLAT, dbuf, (const bf16 *)w->act[NL].p, dz);
+    WS_TRY(launched(w));
+    for (int l = NL - 1; l >= 0; --l) {
+        const int64_t M = B * HOUT[l] * WOUT[l];
+        const int K = 9 * CINP[l], N = COUT[l];
+        // weight gradient, split over the M rows
+        float *dw = l == 0 ? (float *)w->dwb.p : grad + L.w_off[l];
+        if (l == 0 && cudaMemsetAsync(dw, 0, sizeof(float) * N * K, s) != cudaSuccess)
+            return ws_fail(w, GSR_ERR_CUDA, "memset failed");
+        WS_TRY((gemm<false, false, EPI_ATOMIC>(w, N, K, M, dz, N, (const bf16 *)w->col[l].p, K, dw, K, nullptr, s)));
+        const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, M / 512), 256);
+        k_colsum<<<dim3((N + 31) / 32, gy), 256, 0, s>>>(M, N, N, dz, grad + L.b_off[l]);
+        WS_TRY(launched(w));
+        if (l == 0) {
+            k_unpad<<<blocks(N * 9 * CIN[0]), 256, 0, s>>>(N, CIN[0], CINP[0], dw, grad + L.w_off[0]);
+            WS_TRY(launched(w));
+            break;
+        }
+        // data gradient of the columns, then col2im and the previous ReLU's mask
+        WS_TRY((gemm<true, false, EPI_STORE>(w, (int)M, K, N, dz, N, wb + L.wb_off[l], K, dbuf, K, nullptr, s)));
+        const int64_t nin = B * HIN[l] * WIN[l] * CINP[l];
+        k_col2im_relu<<<blocks(nin), 256, 0, s>>>(batch, HIN[l], WIN[l], CINP[l], HOUT[l], WOUT[l], dbuf,
+                                                  (const bf16 *)w->act[l].p, dz);
+        WS_TRY(launched(w));
+    }
+    return GSR_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int64_t gsr_warmstart_num_params(void)
+{
+    Layout L;
+    make_layout(L);
+    return L.n_params;
+}
+
+void gsr_warmstart_default_opts(gsr_warmstart_opts *o)
+{
+    if (!o) return;
+    o->lr = 1e-3f;
+    o->beta1 = 0.9f;
+    o->beta2 = 0.999f;
+    o->eps = 1e-8f;
+    for (int i = 0; i < 6; ++i) o->w[i] = 1.f;
+}
+
+void gsr_warmstart_destroy(gsr_warmstart *w)
+{
+    if (!w) return;
+    cudaDeviceSynchronize();
+    DevBuf *bufs[] = {&w->master, &w->m1, &w->m2, &w->grad, &w->wb, &w->dz, &w->dbuf, &w->dwb,
+                      &w->out, &w->dout32, &w->dout, &w->loss_tmp};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    for (int l = 0; l < NL + 2; ++l)
+        if (w->act[l].p) cudaFree(w->act[l].p);
+    for (int l = 0; l < NL; ++l)
+        if (w->col[l].p) cudaFree(w->col[l].p);
+    delete w;
+}
+
+gsr_status gsr_warmstart_create(gsr_warmstart **out, int32_t max_batch, uint64_t seed)
+{
+    if (!out || max_batch <= 0 || max_batch > 1024) return GSR_ERR_INVALID_ARG;  // grid.y of the first GEMM
+    *out = nullptr;
+    gsr_warmstart *w = new (std::nothrow) gsr_warmstart();
+    if (!w) return GSR_ERR_OOM;
+    w->max_batch = max_batch;
+    make_layout(w->L);
+    const Layout &L = w->L;
+    const int64_t P = L.n_params, B = max_batch;
+    int64_t max_dz = B * FLAT, max_dbuf = B * FLAT;
+    for (int l = 0; l < NL; ++l) {
+        const int64_t M = B * HOUT[l] * WOUT[l];
+        max_dz = std::max(max_dz, M * COUT[l]);
+        max_dz = std::max(max_dz, B * HIN[l] * WIN[l] * CINP[l]);
+        if (l > 0) max_dbuf = std::max(max_dbuf, M * 9 * CINP[l]);
+    }
+    gsr_status st = GSR_OK;
+    auto A = [&](DevBuf &b, size_t bytes) {
+        if (st == GSR_OK) st = ws_alloc(w, b, bytes);
+    };
+    A(w->master, sizeof(float) * P);
+    A(w->m1, sizeof(float) * P);
+    A(w->m2, sizeof(float) * P);
+    A(w->grad, sizeof(float) * P);
+    A(w->wb, sizeof(bf16) * L.wb_off[NSEG]);
+    A(w->act[0], sizeof(bf16) * B * HIN[0] * WIN[0] * CINP[0]);
+    for (int l = 0; l < NL; ++l) {
+        const int64_t M = B * HOUT[l] * WOUT[l];
+        A(w->act[l + 1], sizeof(bf16) * M * COUT[l]);
+        A(w->col[l], sizeof(bf16) * M * 9 * CINP[l]);
+    }
+    A(w->act[NL + 1], sizeof(bf16) * B * HID);
+    A(w->dz, sizeof(bf16) * max_dz);
+    A(w->dbuf, sizeof(float) * max_dbuf);
+    A(w->dwb, sizeof(float) * COUT[0] * 9 * CINP[0]);
+    A(w->out, sizeof(float) * B * NOUTP);
+    A(w->dout32, sizeof(float) * B * NOUTP);
+    A(w->dout, sizeof(bf16) * B * NOUTP);
+    A(w->loss_tmp, sizeof(float) * 4);
+    if (st != GSR_OK) {
+        gsr_warmstart_destroy(w);
+        return st;
+    }
+    // He-normal weights from the seed (output layer x 0.01), zero biases
+    std::vector<float> h((size_t)P, 0.f);
+    std::mt19937_64 rng(seed);
+    auto fill = [&](int64_t off, int64_t n, int64_t fan_in, float scale) {
+        std::normal_distribution<float> nd(0.f, scale * sqrtf(2.f / (float)fan_in));
+        for (int64_t i = 0; i < n; ++i) h[(size_t)(off + i)] = nd(rng);
+    };
+    for (int l = 0; l < NL; ++l) fill(L.w_off[l], (int64_t)COUT[l] * 9 * CIN[l], 9 * CIN[l], 1.f);
+    fill(L.w_off[NL], (int64_t)HID * FLAT, FLAT, 1.f);
+    fill(L.w_off[NL + 1], (int64_t)NOUT * HID, HID, 0.01f);
+    if (cudaMemcpy(w->master.p, h.data(), sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(w->m1.p, 0, sizeof(float) * P) != cudaSuccess ||
+        cudaMemset(w->m2.p, 0, sizeof(float) * P) != cudaSuccess || pack(w, 0) != GSR_OK ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        (void)cudaGetLastError();
+        gsr_warmstart_destroy(w);
+        return GSR_ERR_CUDA;
+    }
+    *out = w;
+    return GSR_OK;
+}
+
+const char *gsr_warmstart_last_error(const gsr_warmstart *w) { return w ? w->err.c_str() : "null network"; }
+
+gsr_status gsr_warmstart_set_params(gsr_warmstart *w, const float *params, void *stream)
+{
+    if (!w || !params) return GSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(float) * w->L.n_params;
+    if (cudaMemcpyAsync(w->master.p, params, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(w->m1.p, 0, bytes, s) != cudaSuccess || cudaMemsetAsync(w->m2.p, 0, bytes, s) != cudaSuccess)
+        return ws_fail(w, GSR_ERR_CUDA, "parameter copy failed");
+    w->step = 0;
+    return pack(w, s);
+}
+
+gsr_status gsr_warmstart_get_params(gsr_warmstart *w, float *params, void *stream)
+{
+    if (!w || !params) return GSR_ERR_INVALID_ARG;
+    if (cudaMemcpyAsync(params, w->master.p, sizeof(float) * w->L.n_params, cudaMemcpyDeviceToDevice,
+                        (cudaStream_t)stream) != cudaSuccess)
+        return ws_fail(w, GSR_ERR_CUDA, "parameter copy failed");
+    return GSR_OK;
+}
+
+gsr_status gsr_warmstart_forward(gsr_warmstart *w, const float *x, int32_t batch, float *out, void *stream)
+{
+    if (!w || !x || batch <= 0) return GSR_ERR_INVALID_ARG;
+    if (batch > w->max_batch) return ws_fail(w, GSR_ERR_CAPACITY, "batch exceeds the network's max_batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t B = batch;
+    const Layout &L = w->L;
+    const bf16 *wb = (const bf16 *)w->wb.p;
+    const float *master = (const float *)w->master.p;
+    w->last_batch = 0;
+    const int64_t npix = B * HIN[0] * WIN[0];
+    k_input_bf16<<<blocks(npix), 256, 0, s>>>(npix, x, (bf16 *)w->act[0].p);
+    WS_TRY(launched(w));
+    for (int l = 0; l < NL; ++l) {
+        const int64_t M = B * HOUT[l] * WOUT[l];
+        const int K = 9 * CINP[l];
+        k_im2col<<<blocks(M * 9 * (CINP[l] / 8)), 256, 0, s>>>(batch, HIN[l], WIN[l], CINP[l], HOUT[l], WOUT[l],
+                                                               (const bf16 *)w->act[l].p, (bf16 *)w->col[l].p);
+        WS_TRY(launched(w));
+        WS_TRY((gemm<true, true, EPI_BIAS_RELU_BF16>(w, (int)M, COUT[l], K, (const bf16 *)w->col[l].p, K,
+                                                     wb + L.wb_off[l], K, w->act[l + 1].p, COUT[l],
+                                                     master + L.b_off[l], s)));
+    }
+    WS_TRY((gemm<true, true, EPI_BIAS_RELU_BF16>(w, batch, HID, FLAT, (const bf16 *)w->act[NL].p, FLAT,
+                                                 wb + L.wb_off[NL], FLAT, w->act[NL + 1].p, HID, master + L.b_off[NL],
+                                                 s)));
+    WS_TRY((gemm<true, true, EPI_BIAS>(w, batch, NOUT, HID, (const bf16 *)w->act[NL + 1].p, HID,
+                                       wb + L.wb_off[NL + 1], HID, w->out.p, NOUTP, master + L.b_off[NL + 1], s)));
+    if (out && cudaMemcpy2DAsync(out, sizeof(float) * NOUT, w->out.p, sizeof(float) * NOUTP, sizeof(float) * NOUT,
+                                 (size_t)B, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return ws_fail(w, GSR_ERR_CUDA, "output copy failed");
+    w->last_batch = batch;
+    return GSR_OK;
+}
+
+gsr_status gsr_warmstart_backward(gsr_warmstart *w, const float *d_out, int32_t batch, float *grad, void *stream)
+{
+    if (!w || !d_out || batch <= 0) return GSR_ERR_INVALID_ARG;
+    if (batch != w->last_batch) return ws_fail(w, GSR_ERR_STATE, "backward needs a forward of the same batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    k_dout_bf16<<<blocks((int64_t)batch * NOUTP), 256, 0, s>>>(batch, d_out, NOUT, (bf16 *)w->dout.p);
+    WS_TRY(launched(w));
+    WS_TRY(backward_impl(w, (const bf16 *)w->dout.p, batch, s));
+    if (grad && cudaMemcpyAsync(grad, w->grad.p, sizeof(float) * w->L.n_params, cudaMemcpyDeviceToDevice, s) !=
+                    cudaSuccess)
+        return ws_fail(w, GSR_ERR_CUDA, "gradient copy failed");
+    return GSR_OK;
+}
+
+gsr_status gsr_warmstart_train_step(gsr_warmstart *w, const float *x, const float *target, int32_t batch,
+                                    const gsr_warmstart_opts *opts, float *loss, void *stream)
+{
+    if (!w || !x || !target || batch <= 0) return GSR_ERR_INVALID_ARG;
+    gsr_warmstart_opts o;
+    gsr_warmstart_default_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.lr >= 0.f) || !(o.beta1 >= 0.f && o.beta1 < 1.f) || !(o.beta2 >= 0.f && o.beta2 < 1.f) || !(o.eps > 0.f))
+        return ws_fail(w, GSR_ERR_INVALID_ARG, "invalid Adam options");
+    cudaStream_t s = (cudaStream_t)stream;
+    WS_TRY(gsr_warmstart_forward(w, x, batch, nullptr, stream));
+    LossW lw;
+    for (int i = 0; i < NOUT; ++i) lw.w[i] = o.w[i];
+    k_twist_loss<<<1, 256, 0, s>>>(batch, (const float *)w->out.p, target, lw, (float *)w->dout32.p,
+                                   loss ? loss : (float *)w->loss_tmp.p);
+    WS_TRY(launched(w));
+    k_dout_bf16<<<blocks((int64_t)batch * NOUTP), 256, 0, s>>>(batch, (const float *)w->dout32.p, NOUTP,
+                                                               (bf16 *)w->dout.p);
+    WS_TRY(launched(w));
+    WS_TRY(backward_impl(w, (const bf16 *)w->dout.p, batch, s));
+    w->step += 1;
+    const float bc1 = 1.f - powf(o.beta1, (float)w->step), bc2 = 1.f - powf(o.beta2, (float)w->step);
+    k_adam<<<blocks(w->L.n_params), 256, 0, s>>>(w->L.n_params, (float *)w->master.p, (const float *)w->grad.p,
+                                                 (float *)w->m1.p, (float *)w->m2.p, o.lr, o.beta1, o.beta2, o.eps,
+                                                 bc1, bc2);
+    WS_TRY(launched(w));
+    return pack(w, s);
+}
+
+gsr_status gsr_warmstart_make_input(const float *rgb_r, const float *depth_r, const float *rgb_i,
+                                    const float *depth_i, int32_t h, int32_t w, float depth_scale, float *out,
+                                    void *stream)
+{
+    if (!rgb_r || !depth_r || !rgb_i || !depth_i || !out || h < GSR_WS_IN_H || w < GSR_WS_IN_W ||
+        !(depth_scale > 0.f))
+        return GSR_ERR_INVALID_ARG;
+    k_make_input<<<blocks(GSR_WS_IN_H * GSR_WS_IN_W), 256, 0, (cudaStream_t)stream>>>(
+        h, w, rgb_r, depth_r, rgb_i, depth_i, 1.f / depth_scale, out);
+    return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+} // extern "C"

@@ -3,6 +3,7 @@ symbol include/gsr.h declares, and the ctypes mirror matches the header's
 struct layouts (checked against gcc's own sizeof/offsetof).  No compute call
 is made here."""
 import ctypes
+import glob
 import os
 import re
 import subprocess
@@ -13,11 +14,14 @@ from paper_2312_10070_gb300 import _build, _lib
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "gsr.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_functions():
-    txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^GSR_API\s+[\w\s\*]+?\b(gsr_\w+)\s*\(", txt, flags=re.M)))
+    names = set()
+    for h in HEADERS:
+        names |= set(re.findall(r"^GSR_API\s+[\w\s\*]+?\b(gsr_\w+)\s*\(", open(h).read(), flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -35,8 +39,9 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_library_has_sm103a_code_and_no_torch_types():
-    txt = open(HEADER).read()
-    assert "torch" not in txt.lower().replace("pytorch type", "")
+    for h in HEADERS:
+        txt = open(h).read()
+        assert "torch" not in txt.lower().replace("pytorch type", ""), h
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
 
 
@@ -46,12 +51,13 @@ STRUCTS = {
     "gsr_frame_stats": _lib.FrameStats, "gsr_adam_opts": _lib.AdamOpts, "gsr_adam_state": _lib.AdamState,
     "gsr_gaussians_mut": _lib.GaussiansMut, "gsr_track_opts": _lib.TrackOpts, "gsr_track_stats": _lib.TrackStats,
     "gsr_keyframe": _lib.Keyframe, "gsr_map_opts": _lib.MapOpts, "gsr_map_stats": _lib.MapStats,
-    "gsr_tune_result": _lib.TuneResult,
+    "gsr_tune_result": _lib.TuneResult, "gsr_warmstart_opts": _lib.WarmstartOpts,
 }
 
 
 def test_struct_layouts_match_header(tmp_path):
-    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
+             f'#include "{os.path.join(ROOT, "include", "gsr_warmstart.h")}"', "int main(void){"]
     for cname, py in STRUCTS.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for fname, _ in py._fields_:
@@ -92,3 +98,16 @@ def test_invalid_arguments_are_rejected_without_gpu(lib):
     o.tile_w, o.batch = 16, 100
     assert lib.gsr_create(ctypes.byref(h), ctypes.byref(o)) == -1
     assert lib.gsr_create(None, None) == -1
+
+
+def test_warmstart_layout_and_argument_checks_without_gpu(lib):
+    from oracle import cnn
+    assert lib.gsr_warmstart_num_params() == cnn.n_params()
+    o = _lib.WarmstartOpts()
+    lib.gsr_warmstart_default_opts(ctypes.byref(o))
+    assert abs(o.lr - 1e-3) < 1e-9 and list(o.w) == [1.0] * 6
+    h = ctypes.c_void_p()
+    assert lib.gsr_warmstart_create(None, 4, 0) == -1
+    assert lib.gsr_warmstart_create(ctypes.byref(h), 0, 0) == -1
+    assert lib.gsr_warmstart_create(ctypes.byref(h), 5000, 0) == -1
+    assert lib.gsr_warmstart_make_input(None, None, None, None, 120, 160, 5.0, None, None) == -1

@@ -88,3 +88,22 @@ def test_loss_gradient_and_box_downsample():
     r, dd = C.box_downsample(rgb, dep, 3, 4)
     np.testing.assert_allclose(r, rgb.reshape(3, 3, 4, 4, 4).mean(axis=(2, 4)))
     assert abs(dd[0, 0] - dep[0:4, 0:4][dep[0:4, 0:4] > 0].mean()) < 1e-12
+
+
+def test_storage_rounding_hooks():
+    """rnd = identity changes nothing; rnd = 0 leaves only the output bias and
+    zeroes every gradient (it is applied to d_out and every stored activation)."""
+    p = he_params(9)
+    x = np.random.default_rng(10).standard_normal((2, C.IN_H, C.IN_W, C.IN_C))
+    d_out = np.random.default_rng(11).standard_normal((2, 6))
+    o0, c0 = C.forward(p, x)
+    o1, c1 = C.forward(p, x, rnd=lambda a: a)
+    np.testing.assert_array_equal(o0, o1)
+    g0, g1 = C.backward(p, c0, d_out), C.backward(p, c1, d_out, rnd=lambda a: a)
+    for k in g0:
+        np.testing.assert_array_equal(g0[k], g1[k])
+    zero = lambda a: np.zeros_like(a)
+    oz, cz = C.forward(p, x, rnd=zero)
+    np.testing.assert_array_equal(oz, np.broadcast_to(p["fc1.b"], (2, 6)))
+    gz = C.backward(p, cz, d_out, rnd=zero)
+    assert all(not np.any(v) for v in gz.values())
