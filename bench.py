@@ -51,6 +51,27 @@ def peaks():
     return dict(hbm=6800.0, sm_mhz=2070.0, src="fallback")
 
 
+def kernel_sources_sha256(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2312_10070_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+    `kernel` from the committed ncu summary, or None when the kernel's sources
+    changed after that capture (or none was taken)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d or kernel_sources_sha256(d["sources"]) != d["sources_sha256"]:
+        return None
+    return d["dram_bytes_per_launch"]
+
+
 def fp32_peak_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -356,7 +377,7 @@ def run_gpu(args, rank, world):
         fl = (FLOPS_BWD_EVAL if dom == "blend_bwd" else FLOPS_FWD_EVAL) * e_bwd
         ach = fl / (avg[dom] / 1e3) / 1e12
         roof = dict(bound="alu", kernel=dom, achieved=ach, peak=peak_tf, unit="TFLOP/s", frac=ach / peak_tf,
-                    traffic=None, units=f"{e_bwd} pixel-Gaussian evaluations x "
+                    traffic=measured_traffic(dom), units=f"{e_bwd} pixel-Gaussian evaluations x "
                                        f"{FLOPS_BWD_EVAL if dom == 'blend_bwd' else FLOPS_FWD_EVAL} flops",
                     peak_note=f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_mhz']:.0f} MHz (derived)")
     else:
@@ -364,7 +385,7 @@ def run_gpu(args, rank, world):
                "adam": 392 * n}.get(dom, step_bytes)
         ach = per / (avg[dom] / 1e3) / 1e9
         roof = dict(bound="hbm", kernel=dom, achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
-                    traffic=None)
+                    traffic=measured_traffic(dom))
     line = dict(metric=METRIC, value=value, unit="iters/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
                 data="synthetic", config=dict(config_dict(stats, None), autotuned=tuned), roofline=roof,
@@ -375,6 +396,59 @@ def run_gpu(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ warm-start network
+def cnn_flops_per_sample():
+    """Algorithmic FLOPs of one training sample (forward + both backward
+    GEMMs, 2 per multiply-add, true channel counts; the first layer has no
+    data gradient)."""
+    from paper_2312_10070_gb300 import warmstart as W
+    h, w, fwd, first = W.IN_H, W.IN_W, 0, 0
+    for i, (ci, co) in enumerate(W.CONV):
+        h, w = (h - 1) // 2 + 1, (w - 1) // 2 + 1
+        f = 2 * h * w * co * 9 * ci
+        fwd += f
+        first = f if i == 0 else first
+    fwd += sum(2 * a * b for a, b in W.DENSE)
+    return fwd, 3 * fwd - first
+
+
+def run_warmstart(args):
+    """Training throughput of the warm-start CNN: Adam steps on batches of 256
+    synthetic inputs (120x160x8), inputs resident in HBM (157 MB per batch,
+    larger than L2; a different batch each step)."""
+    import torch
+    from paper_2312_10070_gb300 import warmstart as W
+    B = 256
+    nb = 4
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.rand(nb, B, W.IN_H, W.IN_W, W.IN_C, generator=gen).cuda()
+    y = (torch.rand(nb, B, 6, generator=gen) * 0.1 - 0.05).cuda()
+    net = W.WarmStartNet(max_batch=B, seed=0)
+    for i in range(max(args.warmup, 3)):
+        net.train_step(x[i % nb], y[i % nb])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        net.train_step(x[i % nb], y[i % nb])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    fwd, train = cnn_flops_per_sample()
+    tf = train * B / (ms / 1e3) / 1e12
+    d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = d.get("bf16_tflops", 1900.0)
+    line = dict(metric="warm-start CNN training samples/s (batch 256, BF16 tensor cores)", value=B / (ms / 1e3),
+                unit="samples/s", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="bf16", data="synthetic",
+                config=dict(workload="warm-start CNN train step (forward, backward, Adam), batch 256, "
+                                     "input 120x160x8", flops_per_sample=train),
+                roofline=dict(bound="tensor", kernel="warmstart_train", achieved=tf, peak=peak, unit="TFLOP/s",
+                              frac=tf / peak, traffic=measured_traffic("warmstart_train"), peak_note="measured bf16 burst" if d else "fallback"))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,7 +456,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="map", choices=["map", "warmstart"],
+                    help="map: the headline mapping iteration; warmstart: the warm-start CNN training step")
     args = ap.parse_args()
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

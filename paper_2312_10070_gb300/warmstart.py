@@ -18,6 +18,8 @@ from . import _lib as L
 from .api import _ptr, _stream
 
 IN_H, IN_W, IN_C, N_OUT = 120, 160, 8, 6
+CONV = ((8, 32), (32, 64), (64, 128), (128, 128), (128, 256), (256, 256))  # 3x3 stride-2 layers (in, out)
+DENSE = ((1536, 256), (256, 6))
 
 
 @dataclass
