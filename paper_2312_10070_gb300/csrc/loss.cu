@@ -4,10 +4,13 @@
 //   L = w_c [(1-lam) mean|I^-I| + lam (1 - SSIM)] + w_d mean_valid |D^-D|
 // SSIM uses the 11x11 Gaussian window (sigma 1.5) of Wang et al. with zero
 // padding, C1 = 0.01^2, C2 = 0.03^2, averaged over pixels and channels.  Two
-// kernels: the first forms the five window sums per channel from a 26x26
-// shared-memory tile (separable passes), the SSIM value and the adjoint maps
+// kernels: the first forms the five window sums per channel of a 32x32 output
+// tile from a 42x42 shared-memory tile, the SSIM value and the adjoint maps
 // dS/dmu_x, dS/dE[x^2], dS/dE[xy]; the second blurs the adjoint maps with the
-// same (symmetric) window and assembles dL/dI^ and dL/dD^.
+// same (symmetric) window and assembles dL/dI^ and dL/dD^.  Both separable
+// passes slide the window in registers: a thread of the horizontal pass reads
+// 18 inputs once and produces 8 outputs, a thread of the vertical pass reads
+// 14 rows once and produces 4 outputs.
 //
 // Tracking (Sec. 3.5, supplementary Sec. B):
 //   L = sum M_inlier alpha^3 (lam_c sum_ch |I^-I| + (1-lam_c)|D^-D|)
@@ -22,9 +25,13 @@
 
 namespace {
 
-constexpr int ST = 16;            // output tile
-constexpr int SHALO = 5;          // window radius
-constexpr int SW = ST + 2 * SHALO;
+constexpr int SHALO = 5;                 // window radius
+constexpr int TX = 32, TY = 32;          // output tile
+constexpr int LW = TX + 2 * SHALO;       // 42 rows / columns loaded
+constexpr int LP = LW + 1;               // padded row of the loaded tile
+constexpr int HP = TX + 1;               // padded row of the horizontal sums
+constexpr int HSEG = 8;                  // outputs per thread, horizontal pass
+constexpr int VSEG = 4;                  // outputs per thread, vertical pass
 
 __device__ __forceinline__ float sgnf(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
 
@@ -68,86 +75,142 @@ __device__ __forceinline__ void block_sum256(float (&v)[NV])
     }
 }
 
+// Horizontal pass task of thread t: segment t/32 & 3 (8 output columns) of
+// loaded row (t/128) * 32 + lane; rows beyond the tile are idle.
+__device__ __forceinline__ bool hpass_task(int &row, int &col0)
+{
+    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    row = (w >> 2) * 32 + lane;
+    col0 = (w & 3) * HSEG;
+    return row < LW;
+}
+
+// 8 horizontal window sums of f(x_i, y_i) over inputs i = col0 .. col0 + 17
+template <typename F>
+__device__ __forceinline__ void hsum8(const float (&xv)[HSEG + 10], const float (&yv)[HSEG + 10], const float (&wk)[11],
+                                      F f, float (&out)[HSEG])
+{
+#pragma unroll
+    for (int j = 0; j < HSEG; ++j) out[j] = 0.f;
+#pragma unroll
+    for (int i = 0; i < HSEG + 10; ++i) {
+        const float q = f(xv[i], yv[i]);
+#pragma unroll
+        for (int j = 0; j < HSEG; ++j)
+            if (i - j >= 0 && i - j <= 10) out[j] = fmaf(wk[i - j], q, out[j]);
+    }
+}
+
+__device__ __forceinline__ void window_regs(float (&wk)[11], const float *s_wk)
+{
+#pragma unroll
+    for (int k = 0; k < 11; ++k) wk[k] = s_wk[k];
+}
+
 __global__ void __launch_bounds__(256) k_ssim_fwd(int W, int H, const float *__restrict__ x, const float *__restrict__ y,
                                                   const float *__restrict__ dep, const float *__restrict__ dep_t,
                                                   float gscale, float *__restrict__ P, float *__restrict__ part,
                                                   u32 *__restrict__ nvalid)
 {
-    __shared__ float wk[11];
-    __shared__ float sx[SW][SW], sy[SW][SW];
-    __shared__ float hq[5][SW][ST];
-    load_window(wk);
-    const int ox = blockIdx.x * ST, oy = blockIdx.y * ST;
-    const int r = threadIdx.x / ST, c = threadIdx.x % ST;
-    const int gx = ox + c, gy = oy + r;
-    const bool inside = gx < W && gy < H;
-    const int64_t HW = (int64_t)W * H, p = (int64_t)gy * W + gx;
+    __shared__ float s_wk[11];
+    __shared__ float sx[LW][LP], sy[LW][LP];
+    __shared__ float hq[5][LW][HP];
+    load_window(s_wk);
+    float wk[11];
+    window_regs(wk, s_wk);
+    const int ox = blockIdx.x * TX, oy = blockIdx.y * TY;
+    const int c = (int)threadIdx.x & 31, r0 = ((int)threadIdx.x >> 5) * VSEG;  // vertical task
+    const int gx = ox + c;
+    const int64_t HW = (int64_t)W * H;
     const float C1 = 1e-4f, C2 = 9e-4f;
     float acc[3] = {0.f, 0.f, 0.f};  // SSIM sum, |x - y| sum, valid |D^ - D| sum
     for (int ch = 0; ch < 3; ++ch) {
-        for (int i = threadIdx.x; i < SW * SW; i += 256) {
-            int rr = i / SW, cc = i % SW;
-            int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
-            bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
-            int64_t q = (int64_t)ch * HW + (int64_t)yy * W + xx;
+        for (int i = threadIdx.x; i < LW * LW; i += 256) {
+            const int rr = i / LW, cc = i % LW;
+            const int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
+            const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
+            const int64_t q = (int64_t)ch * HW + (int64_t)yy * W + xx;
             sx[rr][cc] = ok ? x[q] : 0.f;
             sy[rr][cc] = ok ? y[q] : 0.f;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < SW * ST; i += 256) {
-            int rr = i / ST, cc = i % ST;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+        int hr, hc;
+        if (hpass_task(hr, hc)) {
+            float xv[HSEG + 10], yv[HSEG + 10], o[HSEG];
 #pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                float xv = sx[rr][cc + k], yv = sy[rr][cc + k], w = wk[k];
-                a0 = fmaf(w, xv, a0);
-                a1 = fmaf(w, yv, a1);
-                a2 = fmaf(w, xv * xv, a2);
-                a3 = fmaf(w, yv * yv, a3);
-                a4 = fmaf(w, xv * yv, a4);
+            for (int i = 0; i < HSEG + 10; ++i) {
+                xv[i] = sx[hr][hc + i];
+                yv[i] = sy[hr][hc + i];
             }
-            hq[0][rr][cc] = a0;
-            hq[1][rr][cc] = a1;
-            hq[2][rr][cc] = a2;
-            hq[3][rr][cc] = a3;
-            hq[4][rr][cc] = a4;
-        }
-        __syncthreads();
-        float m1 = 0.f, m2 = 0.f, e11 = 0.f, e22 = 0.f, e12 = 0.f;
+            hsum8(xv, yv, wk, [](float a, float) { return a; }, o);
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            float w = wk[k];
-            m1 = fmaf(w, hq[0][r + k][c], m1);
-            m2 = fmaf(w, hq[1][r + k][c], m2);
-            e11 = fmaf(w, hq[2][r + k][c], e11);
-            e22 = fmaf(w, hq[3][r + k][c], e22);
-            e12 = fmaf(w, hq[4][r + k][c], e12);
+            for (int j = 0; j < HSEG; ++j) hq[0][hr][hc + j] = o[j];
+            hsum8(xv, yv, wk, [](float, float b) { return b; }, o);
+#pragma unroll
+            for (int j = 0; j < HSEG; ++j) hq[1][hr][hc + j] = o[j];
+            hsum8(xv, yv, wk, [](float a, float) { return a * a; }, o);
+#pragma unroll
+            for (int j = 0; j < HSEG; ++j) hq[2][hr][hc + j] = o[j];
+            hsum8(xv, yv, wk, [](float, float b) { return b * b; }, o);
+#pragma unroll
+            for (int j = 0; j < HSEG; ++j) hq[3][hr][hc + j] = o[j];
+            hsum8(xv, yv, wk, [](float a, float b) { return a * b; }, o);
+#pragma unroll
+            for (int j = 0; j < HSEG; ++j) hq[4][hr][hc + j] = o[j];
         }
-        if (inside) {
-            float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * (e12 - m1 * m2) + C2;
-            float B1 = m1 * m1 + m2 * m2 + C1, B2 = (e11 - m1 * m1) + (e22 - m2 * m2) + C2;
-            float iB = 1.f / (B1 * B2);
-            float S = A1 * A2 * iB;
-            acc[0] += S;
-            float xv = sx[r + SHALO][c + SHALO], yv = sy[r + SHALO][c + SHALO];
-            acc[1] += fabsf(xv - yv);
-            P[(3 * ch + 0) * HW + p] = gscale * (2.f * m2 * (A2 - A1) * iB - 2.f * m1 * S * (1.f / B1 - 1.f / B2));
-            P[(3 * ch + 1) * HW + p] = gscale * (-S / B2);
-            P[(3 * ch + 2) * HW + p] = gscale * (2.f * A1 * iB);
+        __syncthreads();
+        float m[5][VSEG];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            float col[VSEG + 10];
+#pragma unroll
+            for (int i = 0; i < VSEG + 10; ++i) col[i] = hq[q][r0 + i][c];
+#pragma unroll
+            for (int j = 0; j < VSEG; ++j) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k < 11; ++k) a = fmaf(wk[k], col[j + k], a);
+                m[q][j] = a;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < VSEG; ++j) {
+            const int gy = oy + r0 + j;
+            if (gx < W && gy < H) {
+                const float m1 = m[0][j], m2 = m[1][j], e11 = m[2][j], e22 = m[3][j], e12 = m[4][j];
+                const float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * (e12 - m1 * m2) + C2;
+                const float B1 = m1 * m1 + m2 * m2 + C1, B2 = (e11 - m1 * m1) + (e22 - m2 * m2) + C2;
+                const float iB = 1.f / (B1 * B2);
+                const float S = A1 * A2 * iB;
+                acc[0] += S;
+                const float xv = sx[r0 + j + SHALO][c + SHALO], yv = sy[r0 + j + SHALO][c + SHALO];
+                acc[1] += fabsf(xv - yv);
+                const int64_t p = (int64_t)gy * W + gx;
+                P[(3 * ch + 0) * HW + p] = gscale * (2.f * m2 * (A2 - A1) * iB - 2.f * m1 * S * (1.f / B1 - 1.f / B2));
+                P[(3 * ch + 1) * HW + p] = gscale * (-S / B2);
+                P[(3 * ch + 2) * HW + p] = gscale * (2.f * A1 * iB);
+            }
         }
         __syncthreads();
     }
-    bool valid = false;
-    if (inside) {
-        float dt = dep_t[p];
-        valid = dt > 0.f;
-        if (valid) acc[2] = fabsf(dep[p] - dt);
+    u32 nv = 0;
+#pragma unroll
+    for (int j = 0; j < VSEG; ++j) {
+        const int gy = oy + r0 + j;
+        if (gx < W && gy < H) {
+            const int64_t p = (int64_t)gy * W + gx;
+            const float dt = dep_t[p];
+            if (dt > 0.f) {
+                acc[2] += fabsf(dep[p] - dt);
+                ++nv;
+            }
+        }
     }
-    u32 bal = __ballot_sync(0xffffffffu, valid);
-    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(nvalid, (u32)__popc(bal));
+    const u32 wsum = __reduce_add_sync(0xffffffffu, nv);
+    if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(nvalid, wsum);
     block_sum256<3>(acc);
     if (threadIdx.x == 0) {
-        int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
         part[3 * b] = acc[0];
         part[3 * b + 1] = acc[1];
         part[3 * b + 2] = acc[2];
@@ -160,58 +223,73 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(int W, int H, const float *__r
                                                   const u32 *__restrict__ nvalid, float *__restrict__ d_rgb,
                                                   float *__restrict__ d_dep)
 {
-    __shared__ float wk[11];
-    __shared__ float sp[3][SW][SW];
-    __shared__ float hq[3][SW][ST];
-    load_window(wk);
-    const int ox = blockIdx.x * ST, oy = blockIdx.y * ST;
-    const int r = threadIdx.x / ST, c = threadIdx.x % ST;
-    const int gx = ox + c, gy = oy + r;
-    const bool inside = gx < W && gy < H;
-    const int64_t HW = (int64_t)W * H, p = (int64_t)gy * W + gx;
+    __shared__ float s_wk[11];
+    __shared__ float sp[3][LW][LP];
+    __shared__ float hq[3][LW][HP];
+    load_window(s_wk);
+    float wk[11];
+    window_regs(wk, s_wk);
+    const int ox = blockIdx.x * TX, oy = blockIdx.y * TY;
+    const int c = (int)threadIdx.x & 31, r0 = ((int)threadIdx.x >> 5) * VSEG;
+    const int gx = ox + c;
+    const int64_t HW = (int64_t)W * H;
     for (int ch = 0; ch < 3; ++ch) {
-        for (int i = threadIdx.x; i < SW * SW; i += 256) {
-            int rr = i / SW, cc = i % SW;
-            int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
-            bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
-            int64_t q = (int64_t)yy * W + xx;
+        for (int i = threadIdx.x; i < LW * LW; i += 256) {
+            const int rr = i / LW, cc = i % LW;
+            const int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
+            const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
+            const int64_t q = (int64_t)yy * W + xx;
 #pragma unroll
             for (int m = 0; m < 3; ++m) sp[m][rr][cc] = ok ? P[(3 * ch + m) * HW + q] : 0.f;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < SW * ST; i += 256) {
-            int rr = i / ST, cc = i % ST;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        int hr, hc;
+        if (hpass_task(hr, hc)) {
 #pragma unroll
-            for (int k = 0; k < 11; ++k) {
-                float w = wk[k];
-                a0 = fmaf(w, sp[0][rr][cc + k], a0);
-                a1 = fmaf(w, sp[1][rr][cc + k], a1);
-                a2 = fmaf(w, sp[2][rr][cc + k], a2);
+            for (int m = 0; m < 3; ++m) {
+                float v[HSEG + 10], o[HSEG];
+#pragma unroll
+                for (int i = 0; i < HSEG + 10; ++i) v[i] = sp[m][hr][hc + i];
+                hsum8(v, v, wk, [](float a, float) { return a; }, o);
+#pragma unroll
+                for (int j = 0; j < HSEG; ++j) hq[m][hr][hc + j] = o[j];
             }
-            hq[0][rr][cc] = a0;
-            hq[1][rr][cc] = a1;
-            hq[2][rr][cc] = a2;
         }
         __syncthreads();
-        float b1 = 0.f, b2 = 0.f, b3 = 0.f;
+        float b[3][VSEG];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            float w = wk[k];
-            b1 = fmaf(w, hq[0][r + k][c], b1);
-            b2 = fmaf(w, hq[1][r + k][c], b2);
-            b3 = fmaf(w, hq[2][r + k][c], b3);
+        for (int m = 0; m < 3; ++m) {
+            float col[VSEG + 10];
+#pragma unroll
+            for (int i = 0; i < VSEG + 10; ++i) col[i] = hq[m][r0 + i][c];
+#pragma unroll
+            for (int j = 0; j < VSEG; ++j) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k < 11; ++k) a = fmaf(wk[k], col[j + k], a);
+                b[m][j] = a;
+            }
         }
-        if (inside) {
-            float xv = x[ch * HW + p], yv = y[ch * HW + p];
-            d_rgb[ch * HW + p] = l1s * sgnf(xv - yv) + b1 + 2.f * xv * b2 + yv * b3;
+#pragma unroll
+        for (int j = 0; j < VSEG; ++j) {
+            const int gy = oy + r0 + j;
+            if (gx < W && gy < H) {
+                const int64_t p = (int64_t)gy * W + gx;
+                const float xv = x[ch * HW + p], yv = y[ch * HW + p];
+                d_rgb[ch * HW + p] = l1s * sgnf(xv - yv) + b[0][j] + 2.f * xv * b[1][j] + yv * b[2][j];
+            }
         }
         __syncthreads();
     }
-    if (inside) {
-        u32 nv = *nvalid;
-        float dt = dep_t[p];
-        d_dep[p] = (dt > 0.f && nv > 0) ? dscale * sgnf(dep[p] - dt) / (float)nv : 0.f;
+    const u32 nv = *nvalid;
+#pragma unroll
+    for (int j = 0; j < VSEG; ++j) {
+        const int gy = oy + r0 + j;
+        if (gx < W && gy < H) {
+            const int64_t p = (int64_t)gy * W + gx;
+            const float dt = dep_t[p];
+            d_dep[p] = (dt > 0.f && nv > 0) ? dscale * sgnf(dep[p] - dt) / (float)nv : 0.f;
+        }
     }
 }
 
@@ -363,7 +441,7 @@ gsr_status run_loss_map(gsr_ctx *ctx, int W, int H, const float *rgb, const floa
                         float *d_depth, float *loss_dev, bool accumulate_loss, cudaStream_t s)
 {
     const int64_t HW = (int64_t)W * H;
-    dim3 grid((unsigned)ceil_div(W, ST), (unsigned)ceil_div(H, ST));
+    dim3 grid((unsigned)ceil_div(W, TX), (unsigned)ceil_div(H, TY));
     const int nb = (int)(grid.x * grid.y);
     GSR_TRY(ensure_buf(ctx, ctx->loss_maps, sizeof(float) * 9 * (size_t)HW));
     GSR_TRY(ensure_buf(ctx, ctx->loss_part, sizeof(float) * 3 * (size_t)nb));

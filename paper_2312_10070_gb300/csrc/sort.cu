@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(RX) k_radix_digit_base(u32 *ghist)
 
 // One stable pass.  Blocks take 2048-key tiles in launch order (atomic ticket,
 // so every tile a block waits for belongs to a block that already runs);
-// each warp ranks its 256 consecutive keys in order with __match_any_sync; the
+// each warp ranks its consecutive keys in order with __match_any_sync (keeping
+// each key's rank among the warp's keys of its digit); the
 // block publishes its digit counts, looks back over the preceding tiles for
 // their running totals, stages its keys in shared memory in digit order and
 // writes them out so that equal digits land in consecutive addresses.
@@ -178,9 +179,10 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__rest
     const int64_t base = (int64_t)tile * TILE;
     if (base >= n) return;  // no key in this tile (and none in any later tile)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    u32 k[ROUNDS], v[ROUNDS];
+    u32 k[ROUNDS], v[ROUNDS], rk[ROUNDS];
     int dg[ROUNDS];
     const int64_t wbase = base + (int64_t)w * SPAN;
+    const u32 lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
         const int64_t i = wbase + r * 32 + lane;
@@ -189,7 +191,11 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__rest
         v[r] = ok ? vin[i] : 0u;
         dg[r] = ok ? (int)((k[r] >> shift) & (RX - 1)) : RX;  // RX = no key
         const u32 peers = __match_any_sync(0xffffffffu, dg[r]);
-        if (ok && lane == __ffs(peers) - 1) wcnt[w][dg[r]] += __popc(peers);
+        // rank of this key among the warp's keys of its digit, in input order
+        const u32 before = ok ? wcnt[w][dg[r]] : 0u;
+        rk[r] = before + __popc(peers & lt);
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) wcnt[w][dg[r]] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -246,17 +252,10 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__rest
         }
     }
     __syncthreads();
-    const u32 lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
-        const u32 peers = __match_any_sync(0xffffffffu, dg[r]);
-        const int leader = __ffs(peers) - 1;
-        u32 pos = 0;
-        if (dg[r] < RX) pos = wcnt[w][dg[r]] + __popc(peers & lt);
-        __syncwarp();
-        if (dg[r] < RX && lane == leader) wcnt[w][dg[r]] += __popc(peers);
-        __syncwarp();
         if (dg[r] < RX) {
+            const u32 pos = wcnt[w][dg[r]] + rk[r];  // the warp's start for the digit + rank
             s_key[pos] = k[r];
             s_val[pos] = v[r];
         }
