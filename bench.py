@@ -274,8 +274,7 @@ def config_dict(stats, flops_info):
 # -------------------------------------------------------------------- GPU
 def run_gpu(args, rank, world):
     import torch
-    import torch.distributed as dist
-    from paper_2312_10070_gb300 import api, synth as S
+    from paper_2312_10070_gb300 import api, replicas, synth as S
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -313,8 +312,7 @@ def run_gpu(args, rank, world):
     sampler = ClockSampler(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     phase_ms = {k: [] for k in api.PHASES}
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.kernel_launches
     sampler.start()
@@ -332,12 +330,8 @@ def run_gpu(args, rank, world):
     clocks = sampler.stop()
     launches = ctx.kernel_launches - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        total_ms = float(tt)
+    total_ms = replicas.max_over_ranks(sum(step_ms))  # the slowest replica
+    replicas.barrier()
     value = world * args.steps / (total_ms / 1e3)
 
     # end-to-end through the public API with host buffers
@@ -351,12 +345,7 @@ def run_gpu(args, rank, world):
         depth_t.copy_(depth_h, non_blocking=True)
         api.map_step(ctx, g, state, cam, kf, None, 1, cfg, want_stats=True)  # reads the loss back
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt)
-    e2e = dict(value=world * e2e_steps / e2e_s, unit="iters/s",
+    e2e = dict(value=replicas.whole_job_rate(e2e_steps, time.perf_counter() - t0), unit="iters/s",
                h2d_bytes_per_step=int(rgb_h.numel() * 4 + depth_h.numel() * 4 + 28), d2h_bytes_per_step=8)
 
     if rank != 0:

@@ -10,9 +10,9 @@
 //   data gradient   dCol[M,K] = dZ[M,N] . W[N,K]                 (then col2im + ReLU mask)
 //   weight gradient dW[N,K]  = dZ^T[N,M] . im2col(X)[M,K]       (split over M, FP32 atomics)
 // with M = batch x output pixels, N = output channels, K = 9 x input channels.
-// One kernel serves all three: mma.sync m16n8k16 BF16 on 128 x 64 tiles, both
-// operands staged to shared memory K-contiguous (transposed while staging when
-// stored the other way) and fed to the tensor cores with ldmatrix.
+// One kernel serves all three (see the GEMM section): the im2col matrix is
+// never materialised, its tiles are gathered from the NHWC activations while
+// staging.
 #include <cuda_bf16.h>
 #include <stdio.h>
 #include <string.h>
@@ -53,13 +53,45 @@ struct LossW {
 };
 
 // ------------------------------------------------------------------ GEMM
-constexpr int BM = 128, BN = 64, BKT = 32, SROW = BKT + 8;
+// C[M,N] (op)= sum_k A(m,k) B(n,k) on 128 x 64 output tiles, 8 warps of 32 x 32,
+// BF16 mma.sync m16n8k16 with FP32 accumulation.  Operand tiles of 32
+// reduction indices are copied global -> shared by cp.async (16 bytes, zero
+// fill outside the operand) in a 3-stage ring, in the operand's own memory
+// order; fragments come from ldmatrix, transposed (.trans) for operands whose
+// row index is the contiguous one.  Operand kinds:
+//   OP_KC     element (r, k) at p[r*ld + k]            (reduction index contiguous)
+//   OP_RC     element (r, k) at p[k*ld + r]            (row index contiguous)
+//   OP_IM_KC  im2col of an NHWC tensor for a 3x3, stride-2, padding-1
+//             convolution: r = output position (b, oy, ox), k = (ky, kx, c)
+//   OP_IM_RC  the same matrix with roles swapped: r = (ky, kx, c), k = position
+// Channel counts are powers of two >= 8, so an 8-element chunk never crosses
+// a tap.
+constexpr int BM = 128, BN = 64, BKT = 32, NSTAGE = 3;
+constexpr int KC_ROW = BKT + 8;                       // shared row (elements), reduction-contiguous tiles
+constexpr int A_STAGE = BM * KC_ROW;                  // >= BKT * (BM + 8)
+constexpr int B_STAGE = BN * KC_ROW;                  // >= BKT * (BN + 8)
 enum { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_RELU_BF16 = 2, EPI_BIAS = 3 };
+enum { OP_KC = 0, OP_RC = 1, OP_IM_KC = 2, OP_IM_RC = 3 };
+
+struct Operand {
+    const bf16 *p;
+    int ld;                // OP_KC / OP_RC
+    int rows;              // staging bound on the row index (a multiple of 8 for OP_RC / OP_IM_RC)
+    int H, W, lc, Ho, Wo;  // OP_IM_*: input H x W x 2^lc channels, output Ho x Wo
+};
 
 __device__ __forceinline__ void ldsm_x4(const bf16 *p, u32 &r0, u32 &r1, u32 &r2, u32 &r3)
 {
     const u32 a = (u32)__cvta_generic_to_shared(p);
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(const bf16 *p, u32 &r0, u32 &r1, u32 &r2, u32 &r3)
+{
+    const u32 a = (u32)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                  : "r"(a));
 }
@@ -70,6 +102,12 @@ __device__ __forceinline__ void ldsm_x2(const bf16 *p, u32 &r0, u32 &r1)
     asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
 }
 
+__device__ __forceinline__ void ldsm_x2_t(const bf16 *p, u32 &r0, u32 &r1)
+{
+    const u32 a = (u32)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const u32 (&a)[4], u32 b0, u32 b1)
 {
     asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -78,61 +116,126 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const u32 (&a)[4], u32 b
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Stage rows [r0, r0 + ROWS) x reduction indices [k0, k0 + BKT) of an operand
-// into sm[ROWS][SROW] (reduction index contiguous).  KMAJOR: element (r, k) is
-// g[r * ld + k]; otherwise g[k * ld + r].  Elements outside R x [0, kend) are 0.
-// Vector loads need ld % 8 == 0 and a 16-byte aligned base (checked by the host).
-template <int ROWS, bool KMAJOR>
-__device__ __forceinline__ void stage(bf16 (*sm)[SROW], const bf16 *__restrict__ g, int ld, int R, int64_t kend,
-                                      int r0, int64_t k0)
+// 16-byte asynchronous copy; a false `valid` writes 16 zero bytes and reads nothing
+__device__ __forceinline__ void cp_async16(bf16 *smem, const bf16 *gmem, bool valid)
 {
-    constexpr int CH = ROWS * BKT / 8;  // chunks of 8 elements
-    for (int c = threadIdx.x; c < CH; c += 256) {
-        if (KMAJOR) {
-            const int r = c / (BKT / 8), kc = (c % (BKT / 8)) * 8;
-            const int gr = r0 + r;
+    const u32 sa = (u32)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copy rows [r0, r0 + ROWS) x reduction indices [k0, k0 + BKT) of an operand
+// into one stage: reduction-contiguous kinds as [ROWS][KC_ROW], row-contiguous
+// kinds as [BKT][ROWS + 8].  Elements outside rows x [0, kend) are zero.
+// rinfo (OP_IM_KC): per tile row {image offset, 2 oy - 1, 2 ox - 1, row valid}.
+template <int ROWS, int MODE>
+__device__ __forceinline__ void load_stage(bf16 *sm, const Operand &op, int64_t kend, int r0, int64_t k0,
+                                           const int4 *rinfo)
+{
+    if (MODE == OP_KC || MODE == OP_IM_KC) {
+        constexpr int CH = ROWS * (BKT / 8);
+#pragma unroll
+        for (int c = threadIdx.x; c < CH; c += 256) {
+            const int r = c >> 2, kc = (c & 3) * 8;
             const int64_t gk = k0 + kc;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (gr < R && gk + 8 <= kend) {
-                v = *reinterpret_cast<const uint4 *>(g + (int64_t)gr * ld + gk);
-            } else if (gr < R && gk < kend) {
-                bf16 t[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) t[i] = gk + i < kend ? g[(int64_t)gr * ld + gk + i] : __float2bfloat16(0.f);
-                v = *reinterpret_cast<uint4 *>(t);
-            }
-            *reinterpret_cast<uint4 *>(&sm[r][kc]) = v;
-        } else {
-            const int k = c / (ROWS / 8), rc = (c % (ROWS / 8)) * 8;
-            const int64_t gk = k0 + k;
-            const int gr = r0 + rc;
-            bf16 t[8];
-            if (gk < kend && gr + 8 <= R) {
-                *reinterpret_cast<uint4 *>(t) = *reinterpret_cast<const uint4 *>(g + gk * ld + gr);
+            const bf16 *src = op.p;
+            bool ok = gk < kend;
+            if (MODE == OP_KC) {
+                ok = ok && r0 + r < op.rows;
+                if (ok) src = op.p + (int64_t)(r0 + r) * op.ld + gk;
             } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) t[i] = (gk < kend && gr + i < R) ? g[gk * ld + gr + i] : __float2bfloat16(0.f);
+                const int4 ri = rinfo[r];
+                const int tap = (int)(gk >> op.lc), ch = (int)gk & ((1 << op.lc) - 1);
+                const int ky = tap / 3, kx = tap - 3 * ky;
+                const int iy = ri.y + ky, ix = ri.z + kx;
+                ok = ok && ri.w && iy >= 0 && iy < op.H && ix >= 0 && ix < op.W;
+                if (ok) src = op.p + ri.x + ((int64_t)(iy * op.W + ix) << op.lc) + ch;
             }
+            cp_async16(sm + r * KC_ROW + kc, src, ok);
+        }
+    } else {
+        constexpr int RCH = ROWS / 8, CH = BKT * RCH;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) sm[rc + i][k] = t[i];
+        for (int c = threadIdx.x; c < CH; c += 256) {
+            const int kr = c / RCH, rc = (c % RCH) * 8;
+            const int64_t gk = k0 + kr;
+            const int gr = r0 + rc;
+            const bf16 *src = op.p;
+            bool ok = gk < kend && gr < op.rows;
+            if (MODE == OP_RC) {
+                if (ok) src = op.p + gk * op.ld + gr;
+            } else {
+                const int hw = op.Ho * op.Wo;
+                const int m = (int)gk;
+                const int b = m / hw, rem = m - b * hw;
+                const int oy = rem / op.Wo, ox = rem - oy * op.Wo;
+                const int tap = gr >> op.lc, ch = gr & ((1 << op.lc) - 1);
+                const int ky = tap / 3, kx = tap - 3 * ky;
+                const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
+                ok = ok && iy >= 0 && iy < op.H && ix >= 0 && ix < op.W;
+                if (ok) src = op.p + (((int64_t)b * op.H * op.W + iy * op.W + ix) << op.lc) + ch;
+            }
+            cp_async16(sm + kr * (ROWS + 8) + rc, src, ok);
         }
     }
 }
 
-// C[M,N] (op)= sum_k A(m,k) B(k,n).  A(m,k) = AK ? A[m*lda+k] : A[k*lda+m];
-// B(k,n) = BK ? B[n*ldb+k] : B[k*ldb+n].  Grid (ceil(N/64), ceil(M/128), splits):
-// split z covers reduction indices [z*kchunk, min(K, (z+1)*kchunk)).
-template <bool AK, bool BK, int EPI>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t kchunk, const bf16 *__restrict__ A,
-                                              int lda, const bf16 *__restrict__ B, int ldb, void *C, int ldc,
-                                              const float *__restrict__ bias)
+// A fragment (16 x 16 at rows mb, reduction kk) of a stage
+template <int MODE>
+__device__ __forceinline__ void frag_a(const bf16 *sm, int mb, int kk, u32 (&a)[4])
 {
-    __shared__ __align__(16) bf16 sA[BM][SROW];
-    __shared__ __align__(16) bf16 sB[BN][SROW];
+    const int lane = threadIdx.x & 31;
+    if (MODE == OP_KC || MODE == OP_IM_KC) {
+        ldsm_x4(sm + (mb + (lane & 15)) * KC_ROW + kk + (lane >> 4) * 8, a[0], a[1], a[2], a[3]);
+    } else {
+        const int q = lane >> 3, r = lane & 7;  // matrix q: (k + 8 (q >> 1), m + 8 (q & 1))
+        ldsm_x4_t(sm + (kk + (q >> 1) * 8 + r) * (BM + 8) + mb + (q & 1) * 8, a[0], a[1], a[2], a[3]);
+    }
+}
+
+// B fragment (16 reduction x 8 columns at nb, kk) of a stage
+template <int MODE>
+__device__ __forceinline__ void frag_b(const bf16 *sm, int nb, int kk, u32 &b0, u32 &b1)
+{
+    const int lane = threadIdx.x & 31;
+    if (MODE == OP_KC || MODE == OP_IM_KC) {
+        ldsm_x2(sm + (nb + (lane & 7)) * KC_ROW + kk + ((lane >> 3) & 1) * 8, b0, b1);
+    } else {
+        ldsm_x2_t(sm + (kk + ((lane >> 3) & 1) * 8 + (lane & 7)) * (BN + 8) + nb, b0, b1);
+    }
+}
+
+// Grid (ceil(N/64), ceil(M/128), splits): split z reduces over
+// [z*kchunk, min(K, (z+1)*kchunk)); EPI_ATOMIC adds into C.
+template <int AMODE, int BMODE, int EPI>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t kchunk, Operand A, Operand B, void *C,
+                                              int ldc, const float *__restrict__ bias)
+{
+    __shared__ __align__(128) bf16 sA[NSTAGE][A_STAGE];
+    __shared__ __align__(128) bf16 sB[NSTAGE][B_STAGE];
+    __shared__ int4 rinfo[AMODE == OP_IM_KC ? BM : 1];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int64_t kbeg = (int64_t)blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = warp & 3, wn = warp >> 2;  // 4 x 2 warps of 32 x 32
+    const int wm = warp & 3, wn = warp >> 2;
+    if (AMODE == OP_IM_KC) {
+        if (threadIdx.x < BM) {
+            const int m = m0 + threadIdx.x;
+            const int hw = A.Ho * A.Wo;
+            const int b = m / hw, rem = m - b * hw;
+            const int oy = rem / A.Wo, ox = rem - oy * A.Wo;
+            rinfo[threadIdx.x] = make_int4((b * A.H * A.W) << A.lc, 2 * oy - 1, 2 * ox - 1, m < A.rows ? 1 : 0);
+        }
+        __syncthreads();
+    }
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -140,27 +243,39 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t k
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    for (int64_t k0 = kbeg; k0 < kend; k0 += BKT) {
-        stage<BM, AK>(sA, A, lda, M, kend, m0, k0);
-        stage<BN, BK>(sB, B, ldb, N, kend, n0, k0);
-        __syncthreads();
+    const int nk = (int)((kend - kbeg + BKT - 1) / BKT);
+#pragma unroll
+    for (int st = 0; st < NSTAGE - 1; ++st) {
+        if (st < nk) {
+            load_stage<BM, AMODE>(sA[st], A, kend, m0, kbeg + (int64_t)st * BKT, rinfo);
+            load_stage<BN, BMODE>(sB[st], B, kend, n0, kbeg + (int64_t)st * BKT, rinfo);
+        }
+        cp_async_commit();
+    }
+    for (int it = 0; it < nk; ++it) {
+        cp_async_wait<NSTAGE - 2>();
+        __syncthreads();  // stage `it` landed; every warp is done with stage it - 1
+        const int nx = it + NSTAGE - 1;
+        if (nx < nk) {
+            load_stage<BM, AMODE>(sA[nx % NSTAGE], A, kend, m0, kbeg + (int64_t)nx * BKT, rinfo);
+            load_stage<BN, BMODE>(sB[nx % NSTAGE], B, kend, n0, kbeg + (int64_t)nx * BKT, rinfo);
+        }
+        cp_async_commit();
+        const bf16 *a_s = sA[it % NSTAGE], *b_s = sB[it % NSTAGE];
 #pragma unroll
         for (int kk = 0; kk < BKT; kk += 16) {
-            u32 a[2][4], b[4][2];
+            u32 af[2][4], bfr[4][2];
 #pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-                ldsm_x4(&sA[wm * 32 + mi * 16 + (lane & 15)][kk + (lane >> 4) * 8], a[mi][0], a[mi][1], a[mi][2],
-                        a[mi][3]);
+            for (int mi = 0; mi < 2; ++mi) frag_a<AMODE>(a_s, wm * 32 + mi * 16, kk, af[mi]);
 #pragma unroll
-            for (int ni = 0; ni < 4; ++ni)
-                ldsm_x2(&sB[wn * 32 + ni * 8 + (lane & 7)][kk + ((lane >> 3) & 1) * 8], b[ni][0], b[ni][1]);
+            for (int ni = 0; ni < 4; ++ni) frag_b<BMODE>(b_s, wn * 32 + ni * 8, kk, bfr[ni][0], bfr[ni][1]);
 #pragma unroll
             for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni][0], b[ni][1]);
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni][0], bfr[ni][1]);
         }
-        __syncthreads();
     }
+    cp_async_wait<0>();
     const int g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
@@ -194,27 +309,6 @@ __global__ void k_input_bf16(int64_t npix, const float *__restrict__ x, bf16 *__
     uint4 *o = reinterpret_cast<uint4 *>(y + i * 16);
     o[0] = *reinterpret_cast<const uint4 *>(v);
     o[1] = *reinterpret_cast<const uint4 *>(v + 8);
-}
-
-// im2col of a 3x3 stride-2 padding-1 convolution: col[(b,oy,ox)][(ky,kx,c)];
-// one thread per 8 channels (C % 8 == 0)
-__global__ void k_im2col(int B, int H, int W, int C, int Ho, int Wo, const bf16 *__restrict__ x,
-                         bf16 *__restrict__ col)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c8 = C / 8;
-    if (i >= (int64_t)B * Ho * Wo * 9 * c8) return;
-    const int cc = (int)(i % c8) * 8;
-    const int64_t r = i / c8;
-    const int tap = (int)(r % 9);
-    const int64_t m = r / 9;
-    const int ky = tap / 3, kx = tap % 3;
-    const int ox = (int)(m % Wo), oy = (int)((m / Wo) % Ho), b = (int)(m / ((int64_t)Wo * Ho));
-    const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (iy >= 0 && iy < H && ix >= 0 && ix < W)
-        v = *reinterpret_cast<const uint4 *>(x + (((int64_t)b * H + iy) * W + ix) * C + cc);
-    *reinterpret_cast<uint4 *>(col + m * (9 * C) + tap * C + cc) = v;
 }
 
 // Adjoint of im2col as a gather (each input pixel receives from at most 2 x 2
@@ -423,7 +517,6 @@ struct gsr_warmstart {
     Layout L{};
     DevBuf master, m1, m2, grad, wb;
     DevBuf act[NL + 2];  // act[0] input (16 ch), act[l+1] conv l output, act[NL+1] dense-1 output
-    DevBuf col[NL];      // im2col of each conv input
     DevBuf dz, dbuf, dwb, out, dout32, dout, loss_tmp;
 };
 
@@ -469,11 +562,50 @@ int64_t split_count(int M, int N, int64_t K)
     return std::min<int64_t>(s, 65535);
 }
 
-template <bool AK, bool BK, int EPI>
-gsr_status gemm(gsr_warmstart *w, int M, int N, int64_t K, const bf16 *A, int lda, const bf16 *B, int ldb, void *C,
-                int ldc, const float *bias, cudaStream_t s)
+Operand dense(const bf16 *p, int ld, int rows)
 {
-    if ((lda % 8) || (ldb % 8) || (((uintptr_t)A) & 15) || (((uintptr_t)B) & 15))
+    Operand o{};
+    o.p = p;
+    o.ld = ld;
+    o.rows = rows;
+    return o;
+}
+
+int ilog2(int c)
+{
+    int l = 0;
+    while ((1 << l) < c) ++l;
+    return l;
+}
+
+// im2col operand of conv layer l over the stored activation x (rows = bound on
+// the row index: output positions for OP_IM_KC, 9 x channels for OP_IM_RC)
+Operand im2col(const bf16 *x, int l, int rows)
+{
+    Operand o{};
+    o.p = x;
+    o.rows = rows;
+    o.H = HIN[l];
+    o.W = WIN[l];
+    o.lc = ilog2(CINP[l]);
+    o.Ho = HOUT[l];
+    o.Wo = WOUT[l];
+    return o;
+}
+
+template <int AMODE, int BMODE, int EPI>
+gsr_status gemm(gsr_warmstart *w, int M, int N, int64_t K, const Operand &A, const Operand &B, void *C, int ldc,
+                const float *bias, cudaStream_t s)
+{
+    auto bad = [](const Operand &o, int mode) {
+        if (((uintptr_t)o.p) & 15) return true;
+        if ((mode == OP_KC || mode == OP_RC) && (o.ld % 8)) return true;
+        if ((mode == OP_RC || mode == OP_IM_RC) && (o.rows % 8)) return true;
+        return false;
+    };
+    // reduction-contiguous operands are copied in whole 8-element chunks of k
+    const bool kc = AMODE == OP_KC || AMODE == OP_IM_KC || BMODE == OP_KC || BMODE == OP_IM_KC;
+    if (bad(A, AMODE) || bad(B, BMODE) || (kc && (K % 8)))
         return ws_fail(w, GSR_ERR_INVALID_ARG, "GEMM operand not 16-byte aligned");
     int64_t splits = 1;
     if (EPI == EPI_ATOMIC) splits = split_count(M, N, K);
@@ -481,7 +613,7 @@ gsr_status gemm(gsr_warmstart *w, int M, int N, int64_t K, const bf16 *A, int ld
     kchunk = (kchunk + BKT - 1) / BKT * BKT;
     splits = (K + kchunk - 1) / kchunk;
     dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)std::max<int64_t>(1, splits));
-    k_gemm<AK, BK, EPI><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, lda, B, ldb, C, ldc, bias);
+    k_gemm<AMODE, BMODE, EPI><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, B, C, ldc, bias);
     return launched(w);
 }
 
@@ -502,21 +634,23 @@ gsr_status backward_impl(gsr_warmstart *w, const bf16 *dout, int batch, cudaStre
     if (cudaMemsetAsync(grad, 0, sizeof(float) * L.n_params, s) != cudaSuccess)
         return ws_fail(w, GSR_ERR_CUDA, "memset failed");
     // dense 2: dW = dout^T h1, db = column sums of dout, dh1 = dout W
-    WS_TRY((gemm<false, false, EPI_ATOMIC>(w, NOUT, HID, B, dout, NOUTP, (const bf16 *)w->act[NL + 1].p, HID,
-                                           grad + L.w_off[NL + 1], HID, nullptr, s)));
+    WS_TRY((gemm<OP_RC, OP_RC, EPI_ATOMIC>(w, NOUT, HID, B, dense(dout, NOUTP, NOUTP),
+                                           dense((const bf16 *)w->act[NL + 1].p, HID, HID), grad + L.w_off[NL + 1],
+                                           HID, nullptr, s)));
     k_colsum<<<dim3(1, 4), 256, 0, s>>>(B, NOUT, NOUTP, dout, grad + L.b_off[NL + 1]);
     WS_TRY(launched(w));
-    WS_TRY((gemm<true, false, EPI_STORE>(w, batch, HID, NOUTP, dout, NOUTP, wb + L.wb_off[NL + 1], HID, dbuf, HID,
-                                         nullptr, s)));
+    WS_TRY((gemm<OP_KC, OP_RC, EPI_STORE>(w, batch, HID, NOUTP, dense(dout, NOUTP, batch),
+                                          dense(wb + L.wb_off[NL + 1], HID, HID), dbuf, HID, nullptr, s)));
     k_relu_bwd<<<blocks(B * HID), 256, 0, s>>>(B * HID, dbuf, (const bf16 *)w->act[NL + 1].p, dz);
     WS_TRY(launched(w));
     // dense 1: dW = dz^T h0, db, dh0 = dz W, then the mask of conv 5's ReLU
-    WS_TRY((gemm<false, false, EPI_ATOMIC>(w, HID, FLAT, B, dz, HID, (const bf16 *)w->act[NL].p, FLAT,
-                                           grad + L.w_off[NL], FLAT, nullptr, s)));
+    WS_TRY((gemm<OP_RC, OP_RC, EPI_ATOMIC>(w, HID, FLAT, B, dense(dz, HID, HID),
+                                           dense((const bf16 *)w->act[NL].p, FLAT, FLAT), grad + L.w_off[NL], FLAT,
+                                           nullptr, s)));
     k_colsum<<<dim3(HID / 32, 4), 256, 0, s>>>(B, HID, HID, dz, grad + L.b_off[NL]);
     WS_TRY(launched(w));
-    WS_TRY((gemm<true, false, EPI_STORE>(w, batch, FLAT, HID, dz, HID, wb + L.wb_off[NL], FLAT, dbuf, FLAT, nullptr,
-                                         s)));
+    WS_TRY((gemm<OP_KC, OP_RC, EPI_STORE>(w, batch, FLAT, HID, dense(dz, HID, batch), dense(wb + L.wb_off[NL], FLAT, FLAT),
+                                          dbuf, FLAT, nullptr, s)));
     k_relu_bwd<<<blocks(B * FLAT), 256, 0, s>>>(B * FLAT, dbuf, (const bf16 *)w->act[NL].p, dz);
     WS_TRY(launched(w));
     for (int l = NL - 1; l >= 0; --l) {
@@ -526,7 +660,8 @@ gsr_status backward_impl(gsr_warmstart *w, const bf16 *dout, int batch, cudaStre
         float *dw = l == 0 ? (float *)w->dwb.p : grad + L.w_off[l];
         if (l == 0 && cudaMemsetAsync(dw, 0, sizeof(float) * N * K, s) != cudaSuccess)
             return ws_fail(w, GSR_ERR_CUDA, "memset failed");
-        WS_TRY((gemm<false, false, EPI_ATOMIC>(w, N, K, M, dz, N, (const bf16 *)w->col[l].p, K, dw, K, nullptr, s)));
+        WS_TRY((gemm<OP_RC, OP_IM_RC, EPI_ATOMIC>(w, N, K, M, dense(dz, N, N), im2col((const bf16 *)w->act[l].p, l, K),
+                                                  dw, K, nullptr, s)));
         const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, M / 512), 256);
         k_colsum<<<dim3((N + 31) / 32, gy), 256, 0, s>>>(M, N, N, dz, grad + L.b_off[l]);
         WS_TRY(launched(w));
@@ -536,7 +671,8 @@ gsr_status backward_impl(gsr_warmstart *w, const bf16 *dout, int batch, cudaStre
             break;
         }
         // data gradient of the columns, then col2im and the previous ReLU's mask
-        WS_TRY((gemm<true, false, EPI_STORE>(w, (int)M, K, N, dz, N, wb + L.wb_off[l], K, dbuf, K, nullptr, s)));
+        WS_TRY((gemm<OP_KC, OP_RC, EPI_STORE>(w, (int)M, K, N, dense(dz, N, (int)M), dense(wb + L.wb_off[l], K, K),
+                                              dbuf, K, nullptr, s)));
         const int64_t nin = B * HIN[l] * WIN[l] * CINP[l];
         k_col2im_relu<<<blocks(nin), 256, 0, s>>>(batch, HIN[l], WIN[l], CINP[l], HOUT[l], WOUT[l], dbuf,
                                                   (const bf16 *)w->act[l].p, dz);
@@ -576,8 +712,6 @@ void gsr_warmstart_destroy(gsr_warmstart *w)
         if (b->p) cudaFree(b->p);
     for (int l = 0; l < NL + 2; ++l)
         if (w->act[l].p) cudaFree(w->act[l].p);
-    for (int l = 0; l < NL; ++l)
-        if (w->col[l].p) cudaFree(w->col[l].p);
     delete w;
 }
 
@@ -611,7 +745,6 @@ gsr_status gsr_warmstart_create(gsr_warmstart **out, int32_t max_batch, uint64_t
     for (int l = 0; l < NL; ++l) {
         const int64_t M = B * HOUT[l] * WOUT[l];
         A(w->act[l + 1], sizeof(bf16) * M * COUT[l]);
-        A(w->col[l], sizeof(bf16) * M * 9 * CINP[l]);
     }
     A(w->act[NL + 1], sizeof(bf16) * B * HID);
     A(w->dz, sizeof(bf16) * max_dz);
@@ -686,18 +819,17 @@ gsr_status gsr_warmstart_forward(gsr_warmstart *w, const float *x, int32_t batch
     for (int l = 0; l < NL; ++l) {
         const int64_t M = B * HOUT[l] * WOUT[l];
         const int K = 9 * CINP[l];
-        k_im2col<<<blocks(M * 9 * (CINP[l] / 8)), 256, 0, s>>>(batch, HIN[l], WIN[l], CINP[l], HOUT[l], WOUT[l],
-                                                               (const bf16 *)w->act[l].p, (bf16 *)w->col[l].p);
-        WS_TRY(launched(w));
-        WS_TRY((gemm<true, true, EPI_BIAS_RELU_BF16>(w, (int)M, COUT[l], K, (const bf16 *)w->col[l].p, K,
-                                                     wb + L.wb_off[l], K, w->act[l + 1].p, COUT[l],
-                                                     master + L.b_off[l], s)));
+        WS_TRY((gemm<OP_IM_KC, OP_KC, EPI_BIAS_RELU_BF16>(w, (int)M, COUT[l], K,
+                                                          im2col((const bf16 *)w->act[l].p, l, (int)M),
+                                                          dense(wb + L.wb_off[l], K, COUT[l]), w->act[l + 1].p,
+                                                          COUT[l], master + L.b_off[l], s)));
     }
-    WS_TRY((gemm<true, true, EPI_BIAS_RELU_BF16>(w, batch, HID, FLAT, (const bf16 *)w->act[NL].p, FLAT,
-                                                 wb + L.wb_off[NL], FLAT, w->act[NL + 1].p, HID, master + L.b_off[NL],
-                                                 s)));
-    WS_TRY((gemm<true, true, EPI_BIAS>(w, batch, NOUT, HID, (const bf16 *)w->act[NL + 1].p, HID,
-                                       wb + L.wb_off[NL + 1], HID, w->out.p, NOUTP, master + L.b_off[NL + 1], s)));
+    WS_TRY((gemm<OP_KC, OP_KC, EPI_BIAS_RELU_BF16>(w, batch, HID, FLAT, dense((const bf16 *)w->act[NL].p, FLAT, batch),
+                                                   dense(wb + L.wb_off[NL], FLAT, HID), w->act[NL + 1].p, HID,
+                                                   master + L.b_off[NL], s)));
+    WS_TRY((gemm<OP_KC, OP_KC, EPI_BIAS>(w, batch, NOUT, HID, dense((const bf16 *)w->act[NL + 1].p, HID, batch),
+                                         dense(wb + L.wb_off[NL + 1], HID, NOUTP), w->out.p, NOUTP,
+                                         master + L.b_off[NL + 1], s)));
     if (out && cudaMemcpy2DAsync(out, sizeof(float) * NOUT, w->out.p, sizeof(float) * NOUTP, sizeof(float) * NOUT,
                                  (size_t)B, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return ws_fail(w, GSR_ERR_CUDA, "output copy failed");
