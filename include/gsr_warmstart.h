@@ -66,7 +66,8 @@ GSR_API gsr_status gsr_warmstart_set_params(gsr_warmstart *net, const float *par
 GSR_API gsr_status gsr_warmstart_get_params(gsr_warmstart *net, float *params, void *stream);
 
 /* out[B, 6] = f(x[B, 120, 160, 8]).  Keeps the activations for a following
- * gsr_warmstart_backward of the same batch.  out may be NULL. */
+ * gsr_warmstart_backward of the same batch.  out may be NULL.  x must be
+ * 16-byte aligned (GSR_ERR_INVALID_ARG otherwise). */
 GSR_API gsr_status gsr_warmstart_forward(gsr_warmstart *net, const float *x, int32_t batch, float *out,
                                          void *stream);
 

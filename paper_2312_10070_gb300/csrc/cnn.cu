@@ -7,7 +7,8 @@
 //
 // Every layer is a GEMM with FP32 accumulation:
 //   forward         Z[M,N]   = im2col(X)[M,K] . W[N,K]^T        (+ bias, ReLU, -> BF16)
-//   data gradient   dCol[M,K] = dZ[M,N] . W[N,K]                 (then col2im + ReLU mask)
+//   data gradient   dX = the adjoint of the convolution, as one GEMM per parity
+//                   class of input pixels (then the previous ReLU's mask)
 //   weight gradient dW[N,K]  = dZ^T[N,M] . im2col(X)[M,K]       (split over M, FP32 atomics)
 // with M = batch x output pixels, N = output channels, K = 9 x input channels.
 // One kernel serves all three (see the GEMM section): the im2col matrix is
@@ -32,7 +33,7 @@ namespace {
 
 constexpr int NL = 6;
 constexpr int CIN[NL] = {8, 32, 64, 128, 128, 256};
-constexpr int CINP[NL] = {16, 32, 64, 128, 128, 256};  // stored channels (the input padded to 16)
+constexpr int CINP[NL] = {8, 32, 64, 128, 128, 256};  // stored channels (equal to CIN: powers of two)
 constexpr int COUT[NL] = {32, 64, 128, 128, 256, 256};
 constexpr int HIN[NL] = {120, 60, 30, 15, 8, 4};
 constexpr int WIN[NL] = {160, 80, 40, 20, 10, 5};
@@ -43,7 +44,7 @@ constexpr int NSEG = NL + 2;
 
 struct Layout {
     int64_t w_off[NSEG], b_off[NSEG];  // flat FP32 vector
-    int64_t wb_off[NSEG + 1];          // BF16 GEMM operands [N][K] (conv 0 padded, dense 2 padded to 8 rows)
+    int64_t wb_off[NSEG + 1];          // BF16 GEMM operands [N][K] (dense 2 padded to 8 rows)
     int64_t n_params;
     int cin[NL], cinp[NL];             // conv input channels: true and stored
 };
@@ -64,21 +65,42 @@ struct LossW {
 //   OP_IM_KC  im2col of an NHWC tensor for a 3x3, stride-2, padding-1
 //             convolution: r = output position (b, oy, ox), k = (ky, kx, c)
 //   OP_IM_RC  the same matrix with roles swapped: r = (ky, kx, c), k = position
+//   OP_DT_KC  data gradient of that convolution for one parity class (py, px)
+//             of input pixels: r = input pixel (b, iy, ix) with iy = py mod 2,
+//             ix = px mod 2; k = (tap t of the class, output channel n);
+//             element dZ[b, (iy + 1 - ky) / 2, (ix + 1 - kx) / 2, n] or 0
+//   OP_WT_RC  the matching weights: r = input channel c, k = (t, n);
+//             element W[n][ky][kx][c]
+// A stride-2 3x3 kernel touches an even input row only through ky = 1 and an
+// odd one through ky = 0 and 2 (likewise columns), so the four classes have
+// 1, 2, 2 and 4 taps and the data gradient needs no column matrix.
 // Channel counts are powers of two >= 8, so an 8-element chunk never crosses
 // a tap.
 constexpr int BM = 128, BN = 64, BKT = 32, NSTAGE = 3;
 constexpr int KC_ROW = BKT + 8;                       // shared row (elements), reduction-contiguous tiles
 constexpr int A_STAGE = BM * KC_ROW;                  // >= BKT * (BM + 8)
 constexpr int B_STAGE = BN * KC_ROW;                  // >= BKT * (BN + 8)
-enum { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_RELU_BF16 = 2, EPI_BIAS = 3 };
-enum { OP_KC = 0, OP_RC = 1, OP_IM_KC = 2, OP_IM_RC = 3 };
+enum { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_RELU_BF16 = 2, EPI_BIAS = 3, EPI_MASK_BF16 = 4 };
+enum { OP_KC = 0, OP_RC = 1, OP_IM_KC = 2, OP_IM_RC = 3, OP_DT_KC = 4, OP_WT_RC = 5 };
 
 struct Operand {
     const bf16 *p;
-    int ld;                // OP_KC / OP_RC
-    int rows;              // staging bound on the row index (a multiple of 8 for OP_RC / OP_IM_RC)
-    int H, W, lc, Ho, Wo;  // OP_IM_*: input H x W x 2^lc channels, output Ho x Wo
+    int ld;                // OP_KC / OP_RC; OP_WT_RC: 9 x input channels
+    int rows;              // staging bound on the row index (a multiple of 8 for row-contiguous kinds)
+    int H, W, lc, Ho, Wo;  // OP_IM_*: input H x W x 2^lc channels, output Ho x Wo;
+                           // OP_DT_KC / OP_WT_RC: lc = log2 of the output channels n
+    int py, px, Hc, Wc;    // OP_DT_KC / OP_WT_RC: parity class and its pixel grid
+    int cin;               // OP_WT_RC: input channels
 };
+
+// taps of parity class (py, px): t -> (ky, kx)
+__device__ __forceinline__ void class_tap(int t, int py, int px, int &ky, int &kx)
+{
+    const int ntx = px ? 2 : 1;
+    const int ty = t / ntx, tx = t - ty * ntx;
+    ky = py ? (ty ? 2 : 0) : 1;
+    kx = px ? (tx ? 2 : 0) : 1;
+}
 
 __device__ __forceinline__ void ldsm_x4(const bf16 *p, u32 &r0, u32 &r1, u32 &r2, u32 &r3)
 {
@@ -140,7 +162,7 @@ template <int ROWS, int MODE>
 __device__ __forceinline__ void load_stage(bf16 *sm, const Operand &op, int64_t kend, int r0, int64_t k0,
                                            const int4 *rinfo)
 {
-    if (MODE == OP_KC || MODE == OP_IM_KC) {
+    if (MODE == OP_KC || MODE == OP_IM_KC || MODE == OP_DT_KC) {
         constexpr int CH = ROWS * (BKT / 8);
 #pragma unroll
         for (int c = threadIdx.x; c < CH; c += 256) {
@@ -151,6 +173,14 @@ __device__ __forceinline__ void load_stage(bf16 *sm, const Operand &op, int64_t 
             if (MODE == OP_KC) {
                 ok = ok && r0 + r < op.rows;
                 if (ok) src = op.p + (int64_t)(r0 + r) * op.ld + gk;
+            } else if (MODE == OP_DT_KC) {
+                const int4 ri = rinfo[r];  // {dZ image offset, iy, ix, valid}
+                const int t = (int)(gk >> op.lc), n = (int)gk & ((1 << op.lc) - 1);
+                int ky, kx;
+                class_tap(t, op.py, op.px, ky, kx);
+                const int oy = (ri.y + 1 - ky) >> 1, ox = (ri.z + 1 - kx) >> 1;
+                ok = ok && ri.w && oy < op.Ho && ox < op.Wo;
+                if (ok) src = op.p + ri.x + ((int64_t)(oy * op.Wo + ox) << op.lc) + n;
             } else {
                 const int4 ri = rinfo[r];
                 const int tap = (int)(gk >> op.lc), ch = (int)gk & ((1 << op.lc) - 1);
@@ -172,6 +202,11 @@ __device__ __forceinline__ void load_stage(bf16 *sm, const Operand &op, int64_t 
             bool ok = gk < kend && gr < op.rows;
             if (MODE == OP_RC) {
                 if (ok) src = op.p + gk * op.ld + gr;
+            } else if (MODE == OP_WT_RC) {
+                const int t = (int)(gk >> op.lc), n = (int)gk & ((1 << op.lc) - 1);
+                int ky, kx;
+                class_tap(t, op.py, op.px, ky, kx);
+                if (ok) src = op.p + (int64_t)n * op.ld + (ky * 3 + kx) * op.cin + gr;
             } else {
                 const int hw = op.Ho * op.Wo;
                 const int m = (int)gk;
@@ -193,7 +228,7 @@ template <int MODE>
 __device__ __forceinline__ void frag_a(const bf16 *sm, int mb, int kk, u32 (&a)[4])
 {
     const int lane = threadIdx.x & 31;
-    if (MODE == OP_KC || MODE == OP_IM_KC) {
+    if (MODE == OP_KC || MODE == OP_IM_KC || MODE == OP_DT_KC) {
         ldsm_x4(sm + (mb + (lane & 15)) * KC_ROW + kk + (lane >> 4) * 8, a[0], a[1], a[2], a[3]);
     } else {
         const int q = lane >> 3, r = lane & 7;  // matrix q: (k + 8 (q >> 1), m + 8 (q & 1))
@@ -201,28 +236,32 @@ __device__ __forceinline__ void frag_a(const bf16 *sm, int mb, int kk, u32 (&a)[
     }
 }
 
-// B fragment (16 reduction x 8 columns at nb, kk) of a stage
-template <int MODE>
+// B fragment (16 reduction x 8 columns at nb, kk) of a stage with TN columns
+template <int MODE, int TN>
 __device__ __forceinline__ void frag_b(const bf16 *sm, int nb, int kk, u32 &b0, u32 &b1)
 {
     const int lane = threadIdx.x & 31;
-    if (MODE == OP_KC || MODE == OP_IM_KC) {
+    if (MODE == OP_KC || MODE == OP_IM_KC || MODE == OP_DT_KC) {
         ldsm_x2(sm + (nb + (lane & 7)) * KC_ROW + kk + ((lane >> 3) & 1) * 8, b0, b1);
     } else {
-        ldsm_x2_t(sm + (kk + ((lane >> 3) & 1) * 8 + (lane & 7)) * (BN + 8) + nb, b0, b1);
+        ldsm_x2_t(sm + (kk + ((lane >> 3) & 1) * 8 + (lane & 7)) * (TN + 8) + nb, b0, b1);
     }
 }
 
-// Grid (ceil(N/64), ceil(M/128), splits): split z reduces over
+// Output tiles of 128 x TN (TN = 64, or 32 for 32-column products).
+// Grid (ceil(N/TN), ceil(M/128), splits): split z reduces over
 // [z*kchunk, min(K, (z+1)*kchunk)); EPI_ATOMIC adds into C.
-template <int AMODE, int BMODE, int EPI>
+// EPI_MASK_BF16 (with A = OP_DT_KC): C[pixel(row), col] = BF16(mask[...] > 0 ? v : 0).
+template <int AMODE, int BMODE, int EPI, int TN>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t kchunk, Operand A, Operand B, void *C,
-                                              int ldc, const float *__restrict__ bias)
+                                              int ldc, const float *__restrict__ bias, const bf16 *__restrict__ mask)
 {
     __shared__ __align__(128) bf16 sA[NSTAGE][A_STAGE];
     __shared__ __align__(128) bf16 sB[NSTAGE][B_STAGE];
-    __shared__ int4 rinfo[AMODE == OP_IM_KC ? BM : 1];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    __shared__ int4 rinfo[AMODE == OP_IM_KC || AMODE == OP_DT_KC ? BM : 1];
+    __shared__ int s_pix[AMODE == OP_DT_KC ? BM : 1];
+    constexpr int NI = TN / 16;  // n8 fragments per warp (warps: 4 x 2 of 32 x TN/2)
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * TN;
     const int64_t kbeg = (int64_t)blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = warp & 3, wn = warp >> 2;
@@ -236,11 +275,22 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t k
         }
         __syncthreads();
     }
-    float acc[2][4][4];
+    if (AMODE == OP_DT_KC) {
+        if (threadIdx.x < BM) {
+            const int m = m0 + threadIdx.x;
+            const int hw = A.Hc * A.Wc;
+            const int b = m / hw, rem = m - b * hw;
+            const int iy = 2 * (rem / A.Wc) + A.py, ix = 2 * (rem % A.Wc) + A.px;
+            rinfo[threadIdx.x] = make_int4((b * A.Ho * A.Wo) << A.lc, iy, ix, m < A.rows ? 1 : 0);
+            s_pix[threadIdx.x] = ((b * A.H + iy) * A.W + ix) * ldc;
+        }
+        __syncthreads();
+    }
+    float acc[2][NI][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < NI; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
     const int nk = (int)((kend - kbeg + BKT - 1) / BKT);
@@ -248,7 +298,7 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t k
     for (int st = 0; st < NSTAGE - 1; ++st) {
         if (st < nk) {
             load_stage<BM, AMODE>(sA[st], A, kend, m0, kbeg + (int64_t)st * BKT, rinfo);
-            load_stage<BN, BMODE>(sB[st], B, kend, n0, kbeg + (int64_t)st * BKT, rinfo);
+            load_stage<TN, BMODE>(sB[st], B, kend, n0, kbeg + (int64_t)st * BKT, rinfo);
         }
         cp_async_commit();
     }
@@ -258,21 +308,22 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t k
         const int nx = it + NSTAGE - 1;
         if (nx < nk) {
             load_stage<BM, AMODE>(sA[nx % NSTAGE], A, kend, m0, kbeg + (int64_t)nx * BKT, rinfo);
-            load_stage<BN, BMODE>(sB[nx % NSTAGE], B, kend, n0, kbeg + (int64_t)nx * BKT, rinfo);
+            load_stage<TN, BMODE>(sB[nx % NSTAGE], B, kend, n0, kbeg + (int64_t)nx * BKT, rinfo);
         }
         cp_async_commit();
         const bf16 *a_s = sA[it % NSTAGE], *b_s = sB[it % NSTAGE];
 #pragma unroll
         for (int kk = 0; kk < BKT; kk += 16) {
-            u32 af[2][4], bfr[4][2];
+            u32 af[2][4], bfr[NI][2];
 #pragma unroll
             for (int mi = 0; mi < 2; ++mi) frag_a<AMODE>(a_s, wm * 32 + mi * 16, kk, af[mi]);
 #pragma unroll
-            for (int ni = 0; ni < 4; ++ni) frag_b<BMODE>(b_s, wn * 32 + ni * 8, kk, bfr[ni][0], bfr[ni][1]);
+            for (int ni = 0; ni < NI; ++ni)
+                frag_b<BMODE, TN>(b_s, wn * (TN / 2) + ni * 8, kk, bfr[ni][0], bfr[ni][1]);
 #pragma unroll
             for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni][0], bfr[ni][1]);
+                for (int ni = 0; ni < NI; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni][0], bfr[ni][1]);
         }
     }
     cp_async_wait<0>();
@@ -280,13 +331,18 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t k
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
+        for (int ni = 0; ni < NI; ++ni)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int row = m0 + wm * 32 + mi * 16 + g + (q >> 1) * 8;
-                const int col = n0 + wn * 32 + ni * 8 + t * 2 + (q & 1);
+                const int col = n0 + wn * (TN / 2) + ni * 8 + t * 2 + (q & 1);
                 if (row >= M || col >= N) continue;
                 const float v = acc[mi][ni][q];
+                if (EPI == EPI_MASK_BF16) {
+                    const int64_t o = (int64_t)s_pix[row - m0] + col;
+                    ((bf16 *)C)[o] = __float2bfloat16(__bfloat162float(mask[o]) > 0.f ? v : 0.f);
+                    continue;
+                }
                 const int64_t o = (int64_t)row * ldc + col;
                 if (EPI == EPI_STORE) ((float *)C)[o] = v;
                 else if (EPI == EPI_ATOMIC) atomicAdd((float *)C + o, v);
@@ -296,43 +352,16 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t k
 }
 
 // --------------------------------------------------------- data movement
-// x f32 [npix, 8] -> bf16 [npix, 16] (channels 8..15 zero)
+// x f32 [npix, 8] -> bf16 [npix, 8] (16 bytes per pixel)
 __global__ void k_input_bf16(int64_t npix, const float *__restrict__ x, bf16 *__restrict__ y)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npix) return;
-    __align__(16) bf16 v[16];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = __float2bfloat16(x[i * 8 + c]);
-#pragma unroll
-    for (int c = 8; c < 16; ++c) v[c] = __float2bfloat16(0.f);
-    uint4 *o = reinterpret_cast<uint4 *>(y + i * 16);
-    o[0] = *reinterpret_cast<const uint4 *>(v);
-    o[1] = *reinterpret_cast<const uint4 *>(v + 8);
-}
-
-// Adjoint of im2col as a gather (each input pixel receives from at most 2 x 2
-// output positions), times the mask of the ReLU that produced x.
-__global__ void k_col2im_relu(int B, int H, int W, int C, int Ho, int Wo, const float *__restrict__ dcol,
-                              const bf16 *__restrict__ x, bf16 *__restrict__ dz)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)B * H * W * C) return;
-    const int c = (int)(i % C);
-    const int64_t r = i / C;
-    const int ix = (int)(r % W), iy = (int)((r / W) % H), b = (int)(r / ((int64_t)W * H));
-    float s = 0.f;
-    for (int ky = 0; ky < 3; ++ky) {
-        const int ty = iy + 1 - ky;
-        if (ty < 0 || (ty & 1) || (ty >> 1) >= Ho) continue;
-        for (int kx = 0; kx < 3; ++kx) {
-            const int tx = ix + 1 - kx;
-            if (tx < 0 || (tx & 1) || (tx >> 1) >= Wo) continue;
-            const int64_t m = ((int64_t)b * Ho + (ty >> 1)) * Wo + (tx >> 1);
-            s += dcol[m * (9 * C) + (ky * 3 + kx) * C + c];
-        }
-    }
-    dz[i] = __float2bfloat16(__bfloat162float(x[i]) > 0.f ? s : 0.f);
+    const float4 a = reinterpret_cast<const float4 *>(x)[2 * i], b = reinterpret_cast<const float4 *>(x)[2 * i + 1];
+    __align__(16) bf16 v[8] = {__float2bfloat16(a.x), __float2bfloat16(a.y), __float2bfloat16(a.z),
+                               __float2bfloat16(a.w), __float2bfloat16(b.x), __float2bfloat16(b.y),
+                               __float2bfloat16(b.z), __float2bfloat16(b.w)};
+    reinterpret_cast<uint4 *>(y)[i] = *reinterpret_cast<const uint4 *>(v);
 }
 
 // out[n] += sum over rows of z[row * ld + n] (bias gradients); block 256 = 8 row
@@ -396,15 +425,6 @@ __global__ void k_relu_bwd(int64_t n, const float *__restrict__ d, const bf16 *_
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dz[i] = __float2bfloat16(__bfloat162float(h[i]) > 0.f ? d[i] : 0.f);
-}
-
-// conv 0 weight gradient [32][9][16] (padded) -> the flat layout [32][9][8]
-__global__ void k_unpad(int N, int cin, int cinp, const float *__restrict__ src, float *__restrict__ dst)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N * 9 * cin) return;
-    const int c = i % cin, nt = i / cin;
-    dst[i] = src[nt * cinp + c];
 }
 
 // FP32 masters (flat layout) -> BF16 GEMM operands
@@ -517,7 +537,7 @@ struct gsr_warmstart {
     Layout L{};
     DevBuf master, m1, m2, grad, wb;
     DevBuf act[NL + 2];  // act[0] input (16 ch), act[l+1] conv l output, act[NL+1] dense-1 output
-    DevBuf dz, dbuf, dwb, out, dout32, dout, loss_tmp;
+    DevBuf dz, dz2, dbuf, out, dout32, dout, loss_tmp;  // dz / dz2: ping-pong upstream gradients
 };
 
 namespace {
@@ -554,9 +574,9 @@ gsr_status launched(gsr_warmstart *w)
 
 // Number of reduction splits for a GEMM with the given output tiles: enough
 // CTAs to cover the 152 SMs about twice, each split at least 8 k-tiles long.
-int64_t split_count(int M, int N, int64_t K)
+int64_t split_count(int M, int N, int64_t K, int tn)
 {
-    const int64_t tiles = (int64_t)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const int64_t tiles = (int64_t)((M + BM - 1) / BM) * ((N + tn - 1) / tn);
     int64_t s = std::max<int64_t>(1, 304 / tiles);
     s = std::min<int64_t>(s, std::max<int64_t>(1, K / (8 * BKT)));
     return std::min<int64_t>(s, 65535);
@@ -595,25 +615,30 @@ Operand im2col(const bf16 *x, int l, int rows)
 
 template <int AMODE, int BMODE, int EPI>
 gsr_status gemm(gsr_warmstart *w, int M, int N, int64_t K, const Operand &A, const Operand &B, void *C, int ldc,
-                const float *bias, cudaStream_t s)
+                const float *bias, cudaStream_t s, const bf16 *mask = nullptr)
 {
     auto bad = [](const Operand &o, int mode) {
         if (((uintptr_t)o.p) & 15) return true;
-        if ((mode == OP_KC || mode == OP_RC) && (o.ld % 8)) return true;
-        if ((mode == OP_RC || mode == OP_IM_RC) && (o.rows % 8)) return true;
+        if ((mode == OP_KC || mode == OP_RC || mode == OP_WT_RC) && (o.ld % 8)) return true;
+        if ((mode == OP_RC || mode == OP_IM_RC || mode == OP_WT_RC) && (o.rows % 8)) return true;
+        if (mode == OP_WT_RC && (o.cin % 8)) return true;
         return false;
     };
     // reduction-contiguous operands are copied in whole 8-element chunks of k
-    const bool kc = AMODE == OP_KC || AMODE == OP_IM_KC || BMODE == OP_KC || BMODE == OP_IM_KC;
+    const bool kc = AMODE == OP_KC || AMODE == OP_IM_KC || AMODE == OP_DT_KC || BMODE == OP_KC || BMODE == OP_IM_KC;
     if (bad(A, AMODE) || bad(B, BMODE) || (kc && (K % 8)))
         return ws_fail(w, GSR_ERR_INVALID_ARG, "GEMM operand not 16-byte aligned");
+    const int tn = N <= 32 ? 32 : 64;
     int64_t splits = 1;
-    if (EPI == EPI_ATOMIC) splits = split_count(M, N, K);
+    if (EPI == EPI_ATOMIC) splits = split_count(M, N, K, tn);
     int64_t kchunk = (K + splits - 1) / splits;
     kchunk = (kchunk + BKT - 1) / BKT * BKT;
     splits = (K + kchunk - 1) / kchunk;
-    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)std::max<int64_t>(1, splits));
-    k_gemm<AMODE, BMODE, EPI><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, B, C, ldc, bias);
+    dim3 grid((unsigned)((N + tn - 1) / tn), (unsigned)((M + BM - 1) / BM), (unsigned)std::max<int64_t>(1, splits));
+    if (tn == 32)
+        k_gemm<AMODE, BMODE, EPI, 32><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, B, C, ldc, bias, mask);
+    else
+        k_gemm<AMODE, BMODE, EPI, 64><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, B, C, ldc, bias, mask);
     return launched(w);
 }
 
@@ -657,26 +682,43 @@ gsr_status backward_impl(gsr_warmstart *w, const bf16 *dout, int batch, cudaStre
         const int64_t M = B * HOUT[l] * WOUT[l];
         const int K = 9 * CINP[l], N = COUT[l];
         // weight gradient, split over the M rows
-        float *dw = l == 0 ? (float *)w->dwb.p : grad + L.w_off[l];
-        if (l == 0 && cudaMemsetAsync(dw, 0, sizeof(float) * N * K, s) != cudaSuccess)
-            return ws_fail(w, GSR_ERR_CUDA, "memset failed");
         WS_TRY((gemm<OP_RC, OP_IM_RC, EPI_ATOMIC>(w, N, K, M, dense(dz, N, N), im2col((const bf16 *)w->act[l].p, l, K),
-                                                  dw, K, nullptr, s)));
+                                                  grad + L.w_off[l], K, nullptr, s)));
         const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, M / 512), 256);
         k_colsum<<<dim3((N + 31) / 32, gy), 256, 0, s>>>(M, N, N, dz, grad + L.b_off[l]);
         WS_TRY(launched(w));
-        if (l == 0) {
-            k_unpad<<<blocks(N * 9 * CIN[0]), 256, 0, s>>>(N, CIN[0], CINP[0], dw, grad + L.w_off[0]);
-            WS_TRY(launched(w));
-            break;
+        if (l == 0) break;
+        // data gradient straight into the previous layer's output gradient (ReLU
+        // mask applied), one GEMM per parity class of input pixels
+        bf16 *dz_prev = dz == (bf16 *)w->dz.p ? (bf16 *)w->dz2.p : (bf16 *)w->dz.p;
+        for (int cls = 0; cls < 4; ++cls) {
+            const int py = cls >> 1, px = cls & 1;
+            const int Hc = (HIN[l] - py + 1) >> 1, Wc = (WIN[l] - px + 1) >> 1;
+            const int rows = batch * Hc * Wc, ntap = (py ? 2 : 1) * (px ? 2 : 1);
+            if (rows == 0) continue;
+            Operand a{}, bw{};
+            a.p = dz;
+            a.rows = rows;
+            a.H = HIN[l];
+            a.W = WIN[l];
+            a.lc = ilog2(N);
+            a.Ho = HOUT[l];
+            a.Wo = WOUT[l];
+            a.py = py;
+            a.px = px;
+            a.Hc = Hc;
+            a.Wc = Wc;
+            bw.p = wb + L.wb_off[l];
+            bw.ld = K;
+            bw.rows = CINP[l];
+            bw.lc = ilog2(N);
+            bw.py = py;
+            bw.px = px;
+            bw.cin = CINP[l];
+            WS_TRY((gemm<OP_DT_KC, OP_WT_RC, EPI_MASK_BF16>(w, rows, CINP[l], (int64_t)ntap * N, a, bw, dz_prev,
+                                                             CINP[l], nullptr, s, (const bf16 *)w->act[l].p)));
         }
-        // data gradient of the columns, then col2im and the previous ReLU's mask
-        WS_TRY((gemm<OP_KC, OP_RC, EPI_STORE>(w, (int)M, K, N, dense(dz, N, (int)M), dense(wb + L.wb_off[l], K, K),
-                                              dbuf, K, nullptr, s)));
-        const int64_t nin = B * HIN[l] * WIN[l] * CINP[l];
-        k_col2im_relu<<<blocks(nin), 256, 0, s>>>(batch, HIN[l], WIN[l], CINP[l], HOUT[l], WOUT[l], dbuf,
-                                                  (const bf16 *)w->act[l].p, dz);
-        WS_TRY(launched(w));
+        dz = dz_prev;
     }
     return GSR_OK;
 }
@@ -706,7 +748,7 @@ void gsr_warmstart_destroy(gsr_warmstart *w)
 {
     if (!w) return;
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&w->master, &w->m1, &w->m2, &w->grad, &w->wb, &w->dz, &w->dbuf, &w->dwb,
+    DevBuf *bufs[] = {&w->master, &w->m1, &w->m2, &w->grad, &w->wb, &w->dz, &w->dz2, &w->dbuf,
                       &w->out, &w->dout32, &w->dout, &w->loss_tmp};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -730,7 +772,6 @@ gsr_status gsr_warmstart_create(gsr_warmstart **out, int32_t max_batch, uint64_t
         const int64_t M = B * HOUT[l] * WOUT[l];
         max_dz = std::max(max_dz, M * COUT[l]);
         max_dz = std::max(max_dz, B * HIN[l] * WIN[l] * CINP[l]);
-        if (l > 0) max_dbuf = std::max(max_dbuf, M * 9 * CINP[l]);
     }
     gsr_status st = GSR_OK;
     auto A = [&](DevBuf &b, size_t bytes) {
@@ -748,8 +789,8 @@ gsr_status gsr_warmstart_create(gsr_warmstart **out, int32_t max_batch, uint64_t
     }
     A(w->act[NL + 1], sizeof(bf16) * B * HID);
     A(w->dz, sizeof(bf16) * max_dz);
+    A(w->dz2, sizeof(bf16) * max_dz);
     A(w->dbuf, sizeof(float) * max_dbuf);
-    A(w->dwb, sizeof(float) * COUT[0] * 9 * CINP[0]);
     A(w->out, sizeof(float) * B * NOUTP);
     A(w->dout32, sizeof(float) * B * NOUTP);
     A(w->dout, sizeof(bf16) * B * NOUTP);
@@ -806,6 +847,7 @@ gsr_status gsr_warmstart_get_params(gsr_warmstart *w, float *params, void *strea
 gsr_status gsr_warmstart_forward(gsr_warmstart *w, const float *x, int32_t batch, float *out, void *stream)
 {
     if (!w || !x || batch <= 0) return GSR_ERR_INVALID_ARG;
+    if (((uintptr_t)x) & 15) return ws_fail(w, GSR_ERR_INVALID_ARG, "x must be 16-byte aligned");
     if (batch > w->max_batch) return ws_fail(w, GSR_ERR_CAPACITY, "batch exceeds the network's max_batch");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t B = batch;
