@@ -80,7 +80,7 @@ constexpr int BM = 128, BN = 64, BKT = 32, NSTAGE = 3;
 constexpr int KC_ROW = BKT + 8;                       // shared row (elements), reduction-contiguous tiles
 constexpr int A_STAGE = BM * KC_ROW;                  // >= BKT * (BM + 8)
 constexpr int B_STAGE = BN * KC_ROW;                  // >= BKT * (BN + 8)
-enum { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_RELU_BF16 = 2, EPI_BIAS = 3, EPI_MASK_BF16 = 4 };
+enum { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_BIAS_RELU_BF16 = 2, EPI_BIAS = 3, EPI_MASK_BF16 = 4, EPI_ATOMIC_T = 5 };
 enum { OP_KC = 0, OP_RC = 1, OP_IM_KC = 2, OP_IM_RC = 3, OP_DT_KC = 4, OP_WT_RC = 5 };
 
 struct Operand {
@@ -91,6 +91,7 @@ struct Operand {
                            // OP_DT_KC / OP_WT_RC: lc = log2 of the output channels n
     int py, px, Hc, Wc;    // OP_DT_KC / OP_WT_RC: parity class and its pixel grid
     int cin;               // OP_WT_RC: input channels
+    int ones_row;          // OP_IM_RC: row index holding 1 for every position (bias gradient), else -1
 };
 
 // taps of parity class (py, px): t -> (ky, kx)
@@ -200,6 +201,11 @@ __device__ __forceinline__ void load_stage(bf16 *sm, const Operand &op, int64_t 
             const int gr = r0 + rc;
             const bf16 *src = op.p;
             bool ok = gk < kend && gr < op.rows;
+            if (MODE == OP_IM_RC && gr == op.ones_row) {  // (1, 0, ..., 0) for every position
+                const uint4 one = make_uint4(ok ? 0x3F80u : 0u, 0u, 0u, 0u);  // BF16 1.0 in the low half
+                *reinterpret_cast<uint4 *>(sm + kr * (ROWS + 8) + rc) = one;
+                continue;
+            }
             if (MODE == OP_RC) {
                 if (ok) src = op.p + gk * op.ld + gr;
             } else if (MODE == OP_WT_RC) {
@@ -254,7 +260,8 @@ __device__ __forceinline__ void frag_b(const bf16 *sm, int nb, int kk, u32 &b0, 
 // EPI_MASK_BF16 (with A = OP_DT_KC): C[pixel(row), col] = BF16(mask[...] > 0 ? v : 0).
 template <int AMODE, int BMODE, int EPI, int TN>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t kchunk, Operand A, Operand B, void *C,
-                                              int ldc, const float *__restrict__ bias, const bf16 *__restrict__ mask)
+                                              int ldc, const float *__restrict__ bias, const bf16 *__restrict__ mask,
+                                              float *__restrict__ aux)
 {
     __shared__ __align__(128) bf16 sA[NSTAGE][A_STAGE];
     __shared__ __align__(128) bf16 sB[NSTAGE][B_STAGE];
@@ -341,6 +348,15 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t k
                 if (EPI == EPI_MASK_BF16) {
                     const int64_t o = (int64_t)s_pix[row - m0] + col;
                     ((bf16 *)C)[o] = __float2bfloat16(__bfloat162float(mask[o]) > 0.f ? v : 0.f);
+                    continue;
+                }
+                if (EPI == EPI_ATOMIC_T) {  // C[col][row]; the ones row of A sums into aux[col]
+                    if (row == A.ones_row) atomicAdd(aux + col, v);
+                    else atomicAdd((float *)C + (int64_t)col * ldc + row, v);
+                    continue;
+                }
+                if (EPI == EPI_ATOMIC && col == B.ones_row) {  // the ones row of B sums into aux[row]
+                    atomicAdd(aux + row, v);
                     continue;
                 }
                 const int64_t o = (int64_t)row * ldc + col;
@@ -588,6 +604,7 @@ Operand dense(const bf16 *p, int ld, int rows)
     o.p = p;
     o.ld = ld;
     o.rows = rows;
+    o.ones_row = -1;
     return o;
 }
 
@@ -610,12 +627,13 @@ Operand im2col(const bf16 *x, int l, int rows)
     o.lc = ilog2(CINP[l]);
     o.Ho = HOUT[l];
     o.Wo = WOUT[l];
+    o.ones_row = -1;
     return o;
 }
 
 template <int AMODE, int BMODE, int EPI>
 gsr_status gemm(gsr_warmstart *w, int M, int N, int64_t K, const Operand &A, const Operand &B, void *C, int ldc,
-                const float *bias, cudaStream_t s, const bf16 *mask = nullptr)
+                const float *bias, cudaStream_t s, const bf16 *mask = nullptr, float *aux = nullptr)
 {
     auto bad = [](const Operand &o, int mode) {
         if (((uintptr_t)o.p) & 15) return true;
@@ -630,15 +648,15 @@ gsr_status gemm(gsr_warmstart *w, int M, int N, int64_t K, const Operand &A, con
         return ws_fail(w, GSR_ERR_INVALID_ARG, "GEMM operand not 16-byte aligned");
     const int tn = N <= 32 ? 32 : 64;
     int64_t splits = 1;
-    if (EPI == EPI_ATOMIC) splits = split_count(M, N, K, tn);
+    if (EPI == EPI_ATOMIC || EPI == EPI_ATOMIC_T) splits = split_count(M, N, K, tn);
     int64_t kchunk = (K + splits - 1) / splits;
     kchunk = (kchunk + BKT - 1) / BKT * BKT;
     splits = (K + kchunk - 1) / kchunk;
     dim3 grid((unsigned)((N + tn - 1) / tn), (unsigned)((M + BM - 1) / BM), (unsigned)std::max<int64_t>(1, splits));
     if (tn == 32)
-        k_gemm<AMODE, BMODE, EPI, 32><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, B, C, ldc, bias, mask);
+        k_gemm<AMODE, BMODE, EPI, 32><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, B, C, ldc, bias, mask, aux);
     else
-        k_gemm<AMODE, BMODE, EPI, 64><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, B, C, ldc, bias, mask);
+        k_gemm<AMODE, BMODE, EPI, 64><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, B, C, ldc, bias, mask, aux);
     return launched(w);
 }
 
@@ -682,11 +700,18 @@ gsr_status backward_impl(gsr_warmstart *w, const bf16 *dout, int batch, cudaStre
         const int64_t M = B * HOUT[l] * WOUT[l];
         const int K = 9 * CINP[l], N = COUT[l];
         // weight gradient, split over the M rows
-        WS_TRY((gemm<OP_RC, OP_IM_RC, EPI_ATOMIC>(w, N, K, M, dense(dz, N, N), im2col((const bf16 *)w->act[l].p, l, K),
-                                                  grad + L.w_off[l], K, nullptr, s)));
-        const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, M / 512), 256);
-        k_colsum<<<dim3((N + 31) / 32, gy), 256, 0, s>>>(M, N, N, dz, grad + L.b_off[l]);
-        WS_TRY(launched(w));
+        // weight and bias gradients in one GEMM reducing over positions; the
+        // im2col operand carries an extra row of ones whose product is the bias
+        // gradient.  The larger of (N, K) takes the 128-row side of the tile.
+        Operand im = im2col((const bf16 *)w->act[l].p, l, K + 8);
+        im.ones_row = K;
+        if (K > N) {
+            WS_TRY((gemm<OP_IM_RC, OP_RC, EPI_ATOMIC_T>(w, K + 1, N, M, im, dense(dz, N, N), grad + L.w_off[l], K,
+                                                        nullptr, s, nullptr, grad + L.b_off[l])));
+        } else {
+            WS_TRY((gemm<OP_RC, OP_IM_RC, EPI_ATOMIC>(w, N, K + 1, M, dense(dz, N, N), im, grad + L.w_off[l], K,
+                                                      nullptr, s, nullptr, grad + L.b_off[l])));
+        }
         if (l == 0) break;
         // data gradient straight into the previous layer's output gradient (ReLU
         // mask applied), one GEMM per parity class of input pixels
