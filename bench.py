@@ -438,6 +438,49 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ seeding
+def run_seed(args):
+    """Sub-map seeding of one 1200x680 keyframe (first keyframe of a sub-map:
+    m_u = 100k uniform + m_c = 50k gradient candidates) against the 500k
+    Gaussians of the headline sub-map; the sub-map count is reset before
+    every step so each step appends the same Gaussians."""
+    import torch
+    from paper_2312_10070_gb300 import api, synth as S
+    spec = S.camera_room()
+    cam = api.camera_from_spec(spec)
+    scene = S.room_scene(N_GAUSS, seed=3)
+    q, t = S.submap_views()[S.HEADLINE_VIEW]
+    pose = api.make_pose(q, t)
+    ctx = api.Context()
+    g = api.GaussianParams.from_numpy(scene)
+    fr = api.render_forward(ctx, g, cam, pose)
+    rgb, depth = fr["rgb"].clone(), fr["depth"].clone()
+    sub = api.SubMap(N_GAUSS + 1200 * 680)
+    sub.append(g)
+    cfg = api.SeedConfig(first_keyframe=True, m_u=100_000, m_c=50_000)
+    st = None
+    for _ in range(max(args.warmup, 3)):
+        sub.n = N_GAUSS
+        st = api.seed_keyframe(ctx, sub, cam, pose, rgb, depth, None, cfg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for _ in range(args.steps):
+        sub.n = N_GAUSS
+        st = api.seed_keyframe(ctx, sub, cam, pose, rgb, depth, None, cfg)  # synchronises once per call
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = dict(metric="sub-map seeding keyframes/s (1200x680, 150k candidates, 500k-Gaussian sub-map)",
+                value=1e3 / ms, unit="keyframes/s", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload="gsr_seed_keyframe, first keyframe of a sub-map, room_scene seed 3 view "
+                                     f"{S.HEADLINE_VIEW}", candidates=st["n_candidates"], added=st["n_added"],
+                            wall_ms=(time.perf_counter() - t0) * 1e3 / args.steps))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,11 +488,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="map", choices=["map", "warmstart"],
-                    help="map: the headline mapping iteration; warmstart: the warm-start CNN training step")
+    ap.add_argument("--workload", default="map", choices=["map", "warmstart", "seed"],
+                    help="map: the headline mapping iteration; warmstart: the warm-start CNN training step; "
+                         "seed: sub-map seeding of one keyframe")
     args = ap.parse_args()
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "seed":
+        return run_seed(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -341,6 +341,64 @@ GSR_API gsr_status gsr_autotune(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_
                                 int32_t n_poses, int32_t reps, gsr_tune_result *best, gsr_tune_result *all,
                                 int32_t n_all, void *stream);
 
+/* ------------------------------------------------------------- seeding */
+
+/* Sub-map seeding (Sec. 3.2 densification; Sec. 4 and supplementary Sec. A
+ * for the constants).  A keyframe adds Gaussians to the active sub-map:
+ *   1. candidate pixels (valid depth > 0 only): on the first keyframe of a
+ *      sub-map (first_keyframe = 1) m_u pixels drawn uniformly without
+ *      replacement plus the m_c pixels of largest squared luminance gradient;
+ *      on later keyframes m_k pixels drawn uniformly among those whose
+ *      rendered alpha is below alpha_n.  "Drawn uniformly" = the pixels with
+ *      the smallest key (splitmix64(seed + pixel index) >> 32, ties by index);
+ *      the gradient is the central difference of Y = (R + G + B) / 3
+ *      (0 on the image border), ties by pixel index;
+ *   2. back-projection with the keyframe pose: p_c = ((x - cx) z / fx,
+ *      (y - cy) z / fy, z) at the pixel centre (x, y) = (j + 0.5, i + 0.5),
+ *      p_w = R^T (p_c - t);
+ *   3. a candidate is kept when no existing Gaussian mean lies at squared
+ *      distance < rho^2 (a hashed grid of cell size rho, 27 cells per query);
+ *   4. every kept point becomes a Gaussian appended after the n_existing ones:
+ *      mean p_w, opacity logit 0 (opacity 0.5), the pixel's RGB, identity
+ *      rotation, all three log-scales = log of its nearest-neighbour distance
+ *      among all n_existing + n_added means (exact, by a ring search on a
+ *      hashed grid), clamped to [s_min, s_max]. */
+typedef struct {
+    int32_t first_keyframe; /* 1: m_u uniform + m_c gradient; 0: m_k uniform where alpha < alpha_n */
+    int64_t m_u, m_c, m_k;  /* sample sizes (100000, 50000, 100000) */
+    float alpha_n;          /* 0.6 */
+    float rho;              /* search radius, m (0.01) */
+    float s_min, s_max;     /* scale clamp, m (1e-4, 0.1) */
+    uint64_t seed;          /* sampling key seed */
+} gsr_seed_opts;
+
+typedef struct {
+    int64_t n_candidates; /* candidate pixels after sampling */
+    int64_t n_added;      /* Gaussians appended */
+} gsr_seed_stats;
+
+GSR_API void gsr_default_seed_opts(gsr_seed_opts *o);
+
+/* rgb [3,H,W], depth [H,W] (0 = invalid) and alpha [H,W] (the sub-map's
+ * render at this pose; may be NULL when first_keyframe = 1) are device
+ * arrays of the keyframe; pose is world-to-camera.  `g` holds the sub-map in
+ * arrays of `capacity` Gaussians, the first n_existing in use (g->n is
+ * ignored); new Gaussians are written at [n_existing, n_existing + n_added).
+ * GSR_ERR_CAPACITY (nothing written) when they do not fit.  Synchronising
+ * (the count is read back once). */
+GSR_API gsr_status gsr_seed_keyframe(gsr_ctx *ctx, const gsr_camera *cam, const gsr_pose *pose, const float *rgb,
+                                     const float *depth, const float *alpha, const gsr_seed_opts *opt,
+                                     gsr_gaussians_mut *g, int64_t n_existing, int64_t capacity,
+                                     gsr_seed_stats *out, void *stream);
+
+/* The last gsr_seed_keyframe's candidates (ascending pixel index): pixel
+ * index, kept flag (1/0) and the squared distance to the nearest existing
+ * mean within the 27 searched cells (+inf if none).  Device arrays of
+ * `capacity` entries; *n receives the count (nothing is copied when it
+ * exceeds capacity: GSR_ERR_CAPACITY).  Synchronising. */
+GSR_API gsr_status gsr_seed_candidates_get(gsr_ctx *ctx, int32_t *pix, int32_t *keep, float *d2, int64_t capacity,
+                                           int64_t *n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

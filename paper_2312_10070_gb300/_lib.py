@@ -99,6 +99,15 @@ class TuneResult(ctypes.Structure):
                 ("ms_fwd", c_f), ("ms_bwd", c_f), ("ms", c_f)]
 
 
+class SeedOpts(ctypes.Structure):
+    _fields_ = [("first_keyframe", c_i32), ("m_u", c_i64), ("m_c", c_i64), ("m_k", c_i64), ("alpha_n", c_f),
+                ("rho", c_f), ("s_min", c_f), ("s_max", c_f), ("seed", ctypes.c_uint64)]
+
+
+class SeedStats(ctypes.Structure):
+    _fields_ = [("n_candidates", c_i64), ("n_added", c_i64)]
+
+
 class WarmstartOpts(ctypes.Structure):
     _fields_ = [("lr", c_f), ("beta1", c_f), ("beta2", c_f), ("eps", c_f), ("w", c_f * 6)]
 
@@ -137,6 +146,11 @@ PROTOTYPES = {
                              ctypes.POINTER(MapStats), c_vp]),
     "gsr_autotune": (c_i32, [c_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Pose), c_i32,
                              c_i32, ctypes.POINTER(TuneResult), ctypes.POINTER(TuneResult), c_i32, c_vp]),
+    "gsr_default_seed_opts": (None, [ctypes.POINTER(SeedOpts)]),
+    "gsr_seed_keyframe": (c_i32, [c_vp, ctypes.POINTER(Camera), ctypes.POINTER(Pose), c_vp, c_vp, c_vp,
+                                  ctypes.POINTER(SeedOpts), ctypes.POINTER(GaussiansMut), c_i64, c_i64,
+                                  ctypes.POINTER(SeedStats), c_vp]),
+    "gsr_seed_candidates_get": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp]),
     "gsr_warmstart_num_params": (c_i64, []),
     "gsr_warmstart_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, ctypes.c_uint64]),
     "gsr_warmstart_destroy": (None, [c_vp]),

@@ -309,6 +309,71 @@ def map_step(ctx: Context, g: GaussianParams, state: AdamMoments, cam: L.Camera,
     return dict(loss_last=st.loss_last, iters=st.iters) if want_stats else None
 
 
+# ------------------------------------------------------------- seeding
+class SubMap:
+    """Gaussian arrays of a sub-map with room for `capacity` Gaussians, the
+    first `n` in use (`params()` views them)."""
+
+    def __init__(self, capacity: int, device="cuda"):
+        self.capacity = int(capacity)
+        self.n = 0
+        z = lambda *shape: torch.zeros(shape, dtype=torch.float32, device=device)
+        self.arrays = GaussianParams(z(capacity, 3), z(capacity, 3), z(capacity, 4), z(capacity), z(capacity, 3))
+
+    def params(self) -> GaussianParams:
+        return GaussianParams(*[t[:self.n] for t in self.arrays.tensors()])
+
+    def append(self, g: GaussianParams):
+        m = g.n
+        if self.n + m > self.capacity:
+            raise ValueError("sub-map capacity exceeded")
+        for dst, src in zip(self.arrays.tensors(), g.tensors()):
+            dst[self.n:self.n + m].copy_(src)
+        self.n += m
+
+
+@dataclass
+class SeedConfig:
+    first_keyframe: bool = True
+    m_u: int = 100_000
+    m_c: int = 50_000
+    m_k: int = 100_000
+    alpha_n: float = 0.6
+    rho: float = 0.01
+    s_min: float = 1e-4
+    s_max: float = 0.1
+    seed: int = 0
+
+    def c(self) -> L.SeedOpts:
+        return L.SeedOpts(int(self.first_keyframe), self.m_u, self.m_c, self.m_k, self.alpha_n, self.rho, self.s_min,
+                          self.s_max, self.seed)
+
+
+def seed_keyframe(ctx: Context, sub: SubMap, cam: L.Camera, pose: L.Pose, rgb, depth, alpha=None,
+                  cfg: SeedConfig = None) -> dict:
+    """gsr_seed_keyframe: appends the keyframe's new Gaussians to `sub`.  Synchronising."""
+    cfg = cfg or SeedConfig()
+    st = L.SeedStats()
+    gm = sub.arrays.c_mut()
+    ctx.check(ctx.lib.gsr_seed_keyframe(ctx.handle, ctypes.byref(cam), ctypes.byref(pose), _ptr(rgb), _ptr(depth),
+                                        _ptr(alpha), ctypes.byref(cfg.c()), ctypes.byref(gm), sub.n, sub.capacity,
+                                        ctypes.byref(st), _stream()))
+    sub.n += int(st.n_added)
+    return dict(n_candidates=int(st.n_candidates), n_added=int(st.n_added))
+
+
+def seed_candidates(ctx: Context, capacity: int):
+    """The last seeding's candidates: (pixel index, kept flag, squared distance to the sub-map) tensors."""
+    n = ctypes.c_int64()
+    pix = torch.empty(capacity, dtype=torch.int32, device="cuda")
+    keep = torch.empty(capacity, dtype=torch.int32, device="cuda")
+    d2 = torch.empty(capacity, dtype=torch.float32, device="cuda")
+    ctx.check(ctx.lib.gsr_seed_candidates_get(ctx.handle, _ptr(pix), _ptr(keep), _ptr(d2), capacity,
+                                              ctypes.byref(n), _stream()))
+    k = int(n.value)
+    return pix[:k], keep[:k], d2[:k]
+
+
 # ----------------------------------------------------------- pose helpers
 def quat_mul(a, b):
     aw, ax, ay, az = a

@@ -46,6 +46,13 @@ gsr_status ensure_buf(gsr_ctx *ctx, DevBuf &b, size_t bytes)
         cudaFree(b.p);
         b.p = nullptr;
         b.bytes = 0;
+        // captured graphs may hold the old address: drop them (the next
+        // map / track step runs eagerly and captures again)
+        if (ctx->map_graph) cudaGraphExecDestroy(ctx->map_graph);
+        if (ctx->track_graph) cudaGraphExecDestroy(ctx->track_graph);
+        ctx->map_graph = ctx->track_graph = nullptr;
+        ctx->map_key = ctx->map_sized_key = ctx->track_key = 0;
+        ctx->generation += 1;
     }
     size_t want = bytes > 0 ? bytes : 16;
     cudaError_t e = cudaMalloc(&b.p, want);
@@ -216,6 +223,10 @@ void gsr_destroy(gsr_ctx *c)
     DevBuf *mb[] = {&c->mv_frames, &c->mv_desc, &c->mv_pview, &c->mv_keys[0], &c->mv_keys[1], &c->mv_items[0],
                     &c->mv_items[1], &c->mv_counter};
     for (DevBuf *b : mb) free_buf(*b);
+    SeedScratch &S = c->seed;
+    DevBuf *sb[] = {&S.flag, &S.sel, &S.off, &S.keys[0], &S.keys[1], &S.vals[0], &S.vals[1], &S.cnt, &S.cand_pix,
+                    &S.cand_pts, &S.keep, &S.keep_off, &S.d2, &S.new_cand};
+    for (DevBuf *b : sb) free_buf(*b);
     if (c->track_graph) cudaGraphExecDestroy(c->track_graph);
     if (c->map_graph) cudaGraphExecDestroy(c->map_graph);
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
@@ -487,9 +498,17 @@ extern "C" gsr_status gsr_track_step(gsr_ctx *ctx, const gsr_gaussians *g, const
         bool first = it == 0;
         if (!first && opt->use_graph) {
             // capture one iteration on the first pass, replay it afterwards
-            uint64_t key = (uint64_t)(uintptr_t)g->mean ^ ((uint64_t)g->n << 1) ^ ((uint64_t)(uintptr_t)rgb_in << 2) ^
-                           ((uint64_t)(uintptr_t)depth_in << 3) ^ ((uint64_t)cam->width << 40) ^
-                           ((uint64_t)cam->height << 52);
+            // keyed by every pointer, size, camera value and option the graph bakes in
+            uint64_t key = 1469598103934665603ull;
+            auto mix = [&key](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
+            const void *ptrs[] = {g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, rgb_in, depth_in};
+            for (const void *q : ptrs) mix((uint64_t)(uintptr_t)q);
+            mix((uint64_t)g->n);
+            mix((uint64_t)ctx->prof);
+            const unsigned char *cb = (const unsigned char *)cam;
+            for (size_t i = 0; i < sizeof(*cam); ++i) mix(cb[i]);
+            const unsigned char *ob = (const unsigned char *)opt;
+            for (size_t i = 0; i < sizeof(*opt); ++i) mix(ob[i]);
             if (!ctx->track_graph || ctx->track_key != key) {
                 if (ctx->track_graph) cudaGraphExecDestroy(ctx->track_graph);
                 ctx->track_graph = nullptr;

@@ -80,6 +80,16 @@ struct ProjView {
     const float *g2d;
     const float *pose;
 };
+// Scratch of keyframe seeding (csrc/seed.cu).
+struct SeedScratch {
+    DevBuf flag, sel, off;     // u32 per pixel: eligible, selected, exclusive scans
+    DevBuf keys[2], vals[2];   // u32 sort pairs (pixels, then grid cells)
+    DevBuf cnt;                // u32 counters: eligible, candidates, kept
+    DevBuf cand_pix, cand_pts; // per candidate: pixel index, world point (float4)
+    DevBuf keep, keep_off, d2; // per candidate: kept flag, its scan, squared distance to the sub-map
+    DevBuf new_cand;           // per kept point: candidate index
+};
+
 struct gsr_ctx {
     gsr_options opt;
     int ppt_fwd = 1, ppt_bwd = 2;  // pixels per thread of the blend kernels
@@ -117,6 +127,8 @@ struct gsr_ctx {
     DevBuf mv_frames, mv_desc, mv_pview, mv_keys[2], mv_items[2], mv_counter;
     std::vector<BlendView> mv_desc_host;
     std::vector<ProjView> mv_pview_host;
+    SeedScratch seed;
+    int64_t seed_last_candidates = 0;
 };
 
 // -------------------------------------------------------------- host helpers

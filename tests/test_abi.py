@@ -52,6 +52,7 @@ STRUCTS = {
     "gsr_gaussians_mut": _lib.GaussiansMut, "gsr_track_opts": _lib.TrackOpts, "gsr_track_stats": _lib.TrackStats,
     "gsr_keyframe": _lib.Keyframe, "gsr_map_opts": _lib.MapOpts, "gsr_map_stats": _lib.MapStats,
     "gsr_tune_result": _lib.TuneResult, "gsr_warmstart_opts": _lib.WarmstartOpts,
+    "gsr_seed_opts": _lib.SeedOpts, "gsr_seed_stats": _lib.SeedStats,
 }
 
 
