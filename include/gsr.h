@@ -399,6 +399,16 @@ GSR_API gsr_status gsr_seed_keyframe(gsr_ctx *ctx, const gsr_camera *cam, const 
 GSR_API gsr_status gsr_seed_candidates_get(gsr_ctx *ctx, int32_t *pix, int32_t *keep, float *d2, int64_t capacity,
                                            int64_t *n, void *stream);
 
+/* Pruning (supplementary Sec. A: Gaussians whose opacity falls below o_thre
+ * are removed at the middle and the end of a new keyframe's mapping).  Keeps
+ * the Gaussians with sigmoid(opacity_logit) >= min_opacity (tested as
+ * logit >= log(t / (1 - t)) in float32), compacting g's arrays -- and st's
+ * moments when st is not NULL -- in place, in their original order; entries
+ * past the kept count are left unspecified.  g->n is the count in use;
+ * *n_kept receives the new count (synchronising). */
+GSR_API gsr_status gsr_prune(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *st, float min_opacity,
+                             int64_t *n_kept, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -164,3 +164,11 @@ def seed_keyframe(rgb, depth, alpha, cam, q, t, existing_means, first: bool, m_u
     gauss = dict(mean=new, log_scale=np.repeat(np.log(s)[:, None], 3, axis=1),
                  quat=np.tile([1.0, 0.0, 0.0, 0.0], (n, 1)), opacity_logit=np.zeros(n), rgb=col)
     return dict(pix=pix, points=pts, keep=keep, d2_existing=d2_exist, nn_d2=d2, gaussians=gauss)
+
+
+def prune(params: dict, min_opacity: float):
+    """Supplementary Sec. A pruning: keep the Gaussians whose opacity
+    sigmoid(logit) is at least min_opacity, in their original order."""
+    o = 1.0 / (1.0 + np.exp(-np.asarray(params["opacity_logit"], np.float64)))
+    keep = o >= min_opacity
+    return {k: np.asarray(v)[keep] for k, v in params.items()}, keep

@@ -151,6 +151,8 @@ PROTOTYPES = {
                                   ctypes.POINTER(SeedOpts), ctypes.POINTER(GaussiansMut), c_i64, c_i64,
                                   ctypes.POINTER(SeedStats), c_vp]),
     "gsr_seed_candidates_get": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp]),
+    "gsr_prune": (c_i32, [c_vp, ctypes.POINTER(GaussiansMut), ctypes.POINTER(AdamState), c_f, ctypes.POINTER(c_i64),
+                          c_vp]),
     "gsr_warmstart_num_params": (c_i64, []),
     "gsr_warmstart_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, ctypes.c_uint64]),
     "gsr_warmstart_destroy": (None, [c_vp]),

@@ -374,6 +374,18 @@ def seed_candidates(ctx: Context, capacity: int):
     return pix[:k], keep[:k], d2[:k]
 
 
+def prune(ctx: Context, sub: SubMap, state: "AdamMoments" = None, min_opacity: float = 0.1) -> int:
+    """gsr_prune: drops sub-map Gaussians with opacity below min_opacity (and
+    their Adam moments), keeping the order.  Returns the new count."""
+    n = ctypes.c_int64()
+    gm = sub.arrays.c_mut()
+    gm.n = sub.n
+    st = ctypes.byref(state.c()) if state is not None else None
+    ctx.check(ctx.lib.gsr_prune(ctx.handle, ctypes.byref(gm), st, float(min_opacity), ctypes.byref(n), _stream()))
+    sub.n = int(n.value)
+    return sub.n
+
+
 # ----------------------------------------------------------- pose helpers
 def quat_mul(a, b):
     aw, ax, ay, az = a

@@ -225,7 +225,7 @@ void gsr_destroy(gsr_ctx *c)
     for (DevBuf *b : mb) free_buf(*b);
     SeedScratch &S = c->seed;
     DevBuf *sb[] = {&S.flag, &S.sel, &S.off, &S.keys[0], &S.keys[1], &S.vals[0], &S.vals[1], &S.cnt, &S.cand_pix,
-                    &S.cand_pts, &S.keep, &S.keep_off, &S.d2, &S.new_cand};
+                    &S.cand_pts, &S.keep, &S.keep_off, &S.d2, &S.new_cand, &S.prune_tmp};
     for (DevBuf *b : sb) free_buf(*b);
     if (c->track_graph) cudaGraphExecDestroy(c->track_graph);
     if (c->map_graph) cudaGraphExecDestroy(c->map_graph);

@@ -88,6 +88,7 @@ struct SeedScratch {
     DevBuf cand_pix, cand_pts; // per candidate: pixel index, world point (float4)
     DevBuf keep, keep_off, d2; // per candidate: kept flag, its scan, squared distance to the sub-map
     DevBuf new_cand;           // per kept point: candidate index
+    DevBuf prune_tmp;          // packed rows of the Gaussians kept by gsr_prune
 };
 
 struct gsr_ctx {

@@ -367,3 +367,93 @@ gsr_status gsr_seed_candidates_get(gsr_ctx *ctx, int32_t *pix, int32_t *keep, fl
 }
 
 } // extern "C"
+
+// ------------------------------------------------------------------ pruning
+namespace {
+
+struct PruneArrays {
+    float *p[15];  // 5 parameter arrays, then 5 first and 5 second moments (nullable)
+    int w[15];     // floats per Gaussian
+    int n_arr;
+};
+
+__global__ void k_prune_flags(int64_t n, const float *__restrict__ logit, float thr, u32 *__restrict__ keep)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keep[i] = logit[i] >= thr ? 1u : 0u;
+}
+
+// kept rows of every array -> packed scratch rows of `row` floats
+__global__ void k_prune_gather(int64_t n, const u32 *__restrict__ keep, const u32 *__restrict__ off, PruneArrays a,
+                               int row, float *__restrict__ tmp)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !keep[i]) return;
+    float *dst = tmp + (int64_t)off[i] * row;
+    int c = 0;
+    for (int k = 0; k < a.n_arr; ++k)
+        for (int j = 0; j < a.w[k]; ++j) dst[c++] = a.p[k][i * a.w[k] + j];
+}
+
+__global__ void k_prune_scatter(const u32 *__restrict__ d_kept, PruneArrays a, int row, const float *__restrict__ tmp)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)*d_kept) return;
+    const float *src = tmp + i * row;
+    int c = 0;
+    for (int k = 0; k < a.n_arr; ++k)
+        for (int j = 0; j < a.w[k]; ++j) a.p[k][i * a.w[k] + j] = src[c++];
+}
+
+} // namespace
+
+extern "C" gsr_status gsr_prune(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *st, float min_opacity,
+                                int64_t *n_kept, void *stream)
+{
+    if (!ctx || !g || !n_kept) return GSR_ERR_INVALID_ARG;
+    if (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->rgb || g->n < 0 || g->n > 0x7fffffff)
+        return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "invalid Gaussian arrays");
+    if (!(min_opacity > 0.f && min_opacity < 1.f)) return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "min_opacity not in (0, 1)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->n;
+    *n_kept = n;
+    if (n == 0) return GSR_OK;
+    PruneArrays a{};
+    float *pa[5] = {g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb};
+    const int wa[5] = {3, 3, 4, 1, 3};
+    for (int k = 0; k < 5; ++k) {
+        a.p[a.n_arr] = pa[k];
+        a.w[a.n_arr++] = wa[k];
+    }
+    if (st) {
+        float *ma[10] = {st->m_mean, st->m_log_scale, st->m_quat, st->m_opacity_logit, st->m_rgb,
+                         st->v_mean, st->v_log_scale, st->v_quat, st->v_opacity_logit, st->v_rgb};
+        for (int k = 0; k < 10; ++k) {
+            if (!ma[k]) return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "null Adam moment array");
+            a.p[a.n_arr] = ma[k];
+            a.w[a.n_arr++] = wa[k % 5];
+        }
+    }
+    int row = 0;
+    for (int k = 0; k < a.n_arr; ++k) row += a.w[k];
+    SeedScratch &S = ctx->seed;
+    GSR_TRY(ensure_buf(ctx, S.flag, sizeof(u32) * n));
+    GSR_TRY(ensure_buf(ctx, S.off, sizeof(u32) * n));
+    GSR_TRY(ensure_buf(ctx, S.cnt, sizeof(u32) * 4));
+    GSR_TRY(ensure_buf(ctx, S.prune_tmp, sizeof(float) * n * row));
+    u32 *keep = (u32 *)S.flag.p, *off = (u32 *)S.off.p, *cnt = (u32 *)S.cnt.p;
+    // sigmoid(x) >= t  <=>  x >= log(t / (1 - t))
+    const float thr = (float)log((double)min_opacity / (1.0 - (double)min_opacity));
+    k_prune_flags<<<nblk(n), 256, 0, s>>>(n, g->opacity_logit, thr, keep);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    GSR_TRY(scan_exclusive(ctx, keep, off, n, nullptr, cnt + 3, s));
+    k_prune_gather<<<nblk(n), 256, 0, s>>>(n, keep, off, a, row, (float *)S.prune_tmp.p);
+    k_prune_scatter<<<nblk(n), 256, 0, s>>>(cnt + 3, a, row, (const float *)S.prune_tmp.p);
+    ctx->launches += 2;
+    GSR_LAUNCHED(ctx);
+    GSR_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned + 44, cnt + 3, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    GSR_CUDA(ctx, cudaStreamSynchronize(s));
+    *n_kept = ctx->host_pinned[44];
+    return GSR_OK;
+}

@@ -1,0 +1,50 @@
+"""GPU pruning (gsr_prune) against the oracle's boolean selection: the kept
+Gaussians and their Adam moments, bit for bit and in order."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import seed as SD
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n", [1, 1000, 300_001])
+def test_prune_matches_oracle(n):
+    from paper_2312_10070_gb300 import api
+    rng = np.random.default_rng(n)
+    p = dict(mean=rng.standard_normal((n, 3)), log_scale=rng.standard_normal((n, 3)),
+             quat=rng.standard_normal((n, 4)), opacity_logit=rng.normal(-1.0, 2.0, n), rgb=rng.random((n, 3)))
+    p = {k: v.astype(np.float32) for k, v in p.items()}
+    # keep the test away from the float32 rounding of the threshold itself
+    thr = np.log(0.3 / 0.7)
+    p["opacity_logit"][np.abs(p["opacity_logit"] - thr) < 1e-5] += 1e-3
+    ctx = api.Context()
+    sub = api.SubMap(n + 10)
+    sub.append(api.GaussianParams.from_numpy(p))
+    mom = api.AdamMoments(sub.arrays)
+    for t in mom.m.tensors() + mom.v.tensors():
+        t.copy_(torch.randn_like(t))
+    m_before = [t[:n].cpu().numpy().copy() for t in mom.m.tensors()]
+    v_before = [t[:n].cpu().numpy().copy() for t in mom.v.tensors()]
+    kept = api.prune(ctx, sub, mom, 0.3)
+    ref, keep = SD.prune(p, 0.3)
+    assert kept == keep.sum() == sub.n
+    got = {k: t.cpu().numpy() for k, t in zip(api.GaussianParams.NAMES, sub.params().tensors())}
+    for k in api.GaussianParams.NAMES:
+        np.testing.assert_array_equal(got[k], ref[k])
+    for before, t in zip(m_before + v_before, mom.m.tensors() + mom.v.tensors()):
+        np.testing.assert_array_equal(t[:kept].cpu().numpy(), before[keep])
+
+
+def test_prune_without_moments_and_nothing_to_remove():
+    from paper_2312_10070_gb300 import api
+    rng = np.random.default_rng(1)
+    p = dict(mean=rng.standard_normal((500, 3)), log_scale=rng.standard_normal((500, 3)),
+             quat=rng.standard_normal((500, 4)), opacity_logit=np.full(500, 3.0), rgb=rng.random((500, 3)))
+    p = {k: v.astype(np.float32) for k, v in p.items()}
+    ctx = api.Context()
+    sub = api.SubMap(500)
+    sub.append(api.GaussianParams.from_numpy(p))
+    assert api.prune(ctx, sub, None, 0.5) == 500
+    np.testing.assert_array_equal(sub.params().mean.cpu().numpy(), p["mean"])
