@@ -409,6 +409,16 @@ GSR_API gsr_status gsr_seed_candidates_get(gsr_ctx *ctx, int32_t *pix, int32_t *
 GSR_API gsr_status gsr_prune(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *st, float min_opacity,
                              int64_t *n_kept, void *stream);
 
+/* Global map merge (supplementary Sec. A: the saved sub-maps are merged in
+ * sequence, each Gaussian added with the seeding rule).  Appends to `global`
+ * (arrays of `capacity`, the first n_global in use) the Gaussians of `sub`
+ * whose mean has no global mean at squared distance < rho^2, in their
+ * order, copying every parameter; other Gaussians of `sub` do not reject each
+ * other.  GSR_ERR_CAPACITY (nothing written) when they do not fit.
+ * *n_added receives the count (synchronising). */
+GSR_API gsr_status gsr_merge_submap(gsr_ctx *ctx, gsr_gaussians_mut *global, int64_t n_global, int64_t capacity,
+                                    const gsr_gaussians *sub, float rho, int64_t *n_added, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -172,3 +172,21 @@ def prune(params: dict, min_opacity: float):
     o = 1.0 / (1.0 + np.exp(-np.asarray(params["opacity_logit"], np.float64)))
     keep = o >= min_opacity
     return {k: np.asarray(v)[keep] for k, v in params.items()}, keep
+
+
+def merge(submaps, rho: float = 0.01):
+    """Supplementary Sec. A global merge: sub-maps in sequence; a Gaussian is
+    added when no Gaussian already in the global map lies at squared distance
+    < rho^2 (Gaussians of the same sub-map do not reject each other).
+    Returns the merged parameters and, per sub-map, the added mask."""
+    out = {k: [] for k in submaps[0]}
+    glob = np.zeros((0, 3))
+    masks = []
+    for sm in submaps:
+        d2 = min_dist2(np.asarray(sm["mean"], np.float64), glob)
+        add = d2 >= rho * rho
+        masks.append(add)
+        for k, v in sm.items():
+            out[k].append(np.asarray(v)[add])
+        glob = np.concatenate([glob, np.asarray(sm["mean"], np.float64)[add]])
+    return {k: np.concatenate(v) for k, v in out.items()}, masks

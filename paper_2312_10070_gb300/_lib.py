@@ -153,6 +153,8 @@ PROTOTYPES = {
     "gsr_seed_candidates_get": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp]),
     "gsr_prune": (c_i32, [c_vp, ctypes.POINTER(GaussiansMut), ctypes.POINTER(AdamState), c_f, ctypes.POINTER(c_i64),
                           c_vp]),
+    "gsr_merge_submap": (c_i32, [c_vp, ctypes.POINTER(GaussiansMut), c_i64, c_i64, ctypes.POINTER(Gaussians), c_f,
+                                 ctypes.POINTER(c_i64), c_vp]),
     "gsr_warmstart_num_params": (c_i64, []),
     "gsr_warmstart_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, ctypes.c_uint64]),
     "gsr_warmstart_destroy": (None, [c_vp]),

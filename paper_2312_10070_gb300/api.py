@@ -386,6 +386,17 @@ def prune(ctx: Context, sub: SubMap, state: "AdamMoments" = None, min_opacity: f
     return sub.n
 
 
+def merge_submap(ctx: Context, global_map: SubMap, sub: GaussianParams, rho: float = 0.01) -> int:
+    """gsr_merge_submap: appends the Gaussians of `sub` that have no global-map
+    mean within rho.  Returns the number added."""
+    n = ctypes.c_int64()
+    ctx.check(ctx.lib.gsr_merge_submap(ctx.handle, ctypes.byref(global_map.arrays.c_mut()), global_map.n,
+                                       global_map.capacity, ctypes.byref(sub.c()), float(rho), ctypes.byref(n),
+                                       _stream()))
+    global_map.n += int(n.value)
+    return int(n.value)
+
+
 # ----------------------------------------------------------- pose helpers
 def quat_mul(a, b):
     aw, ax, ay, az = a

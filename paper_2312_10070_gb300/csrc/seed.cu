@@ -457,3 +457,84 @@ extern "C" gsr_status gsr_prune(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_sta
     *n_kept = ctx->host_pinned[44];
     return GSR_OK;
 }
+
+// ------------------------------------------------------------ global merge
+namespace {
+
+__global__ void k_merge_reject(int64_t n, const float *__restrict__ q3, const float *__restrict__ means,
+                               const u32 *__restrict__ gk, const u32 *__restrict__ gv, int64_t n_grid, float inv_h,
+                               float rho2, u32 *__restrict__ keep)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float qx = q3[3 * i], qy = q3[3 * i + 1], qz = q3[3 * i + 2];
+    const int cx = cell_of(qx, inv_h), cy = cell_of(qy, inv_h), cz = cell_of(qz, inv_h);
+    float best = INFINITY;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+                best = cell_min_d2(qx, qy, qz, cx + dx, cy + dy, cz + dz, means, gk, gv, n_grid, -1, best);
+    keep[i] = best < rho2 ? 0u : 1u;
+}
+
+__global__ void k_merge_append(int64_t n, const u32 *__restrict__ keep, const u32 *__restrict__ off, gsr_gaussians src,
+                               gsr_gaussians_mut dst, int64_t base)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !keep[i]) return;
+    const int64_t o = base + off[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dst.mean[3 * o + k] = src.mean[3 * i + k];
+        dst.log_scale[3 * o + k] = src.log_scale[3 * i + k];
+        dst.rgb[3 * o + k] = src.rgb[3 * i + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst.quat[4 * o + k] = src.quat[4 * i + k];
+    dst.opacity_logit[o] = src.opacity_logit[i];
+}
+
+} // namespace
+
+extern "C" gsr_status gsr_merge_submap(gsr_ctx *ctx, gsr_gaussians_mut *global, int64_t n_global, int64_t capacity,
+                                       const gsr_gaussians *sub, float rho, int64_t *n_added, void *stream)
+{
+    if (!ctx || !global || !sub || !n_added) return GSR_ERR_INVALID_ARG;
+    if (!global->mean || !global->log_scale || !global->quat || !global->opacity_logit || !global->rgb ||
+        (sub->n > 0 && (!sub->mean || !sub->log_scale || !sub->quat || !sub->opacity_logit || !sub->rgb)))
+        return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "null Gaussian array");
+    if (n_global < 0 || capacity < n_global || capacity > 0x7fffffff || sub->n < 0 || sub->n > 0x7fffffff ||
+        !(rho > 0.f))
+        return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "invalid merge argument");
+    *n_added = 0;
+    const int64_t n = sub->n;
+    if (n == 0) return GSR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    SeedScratch &S = ctx->seed;
+    const int64_t nk = std::max<int64_t>(n_global, 1);
+    for (int k = 0; k < 2; ++k) {
+        GSR_TRY(ensure_buf(ctx, S.keys[k], sizeof(u32) * nk));
+        GSR_TRY(ensure_buf(ctx, S.vals[k], sizeof(u32) * nk));
+    }
+    GSR_TRY(ensure_buf(ctx, S.keep, sizeof(u32) * n));
+    GSR_TRY(ensure_buf(ctx, S.keep_off, sizeof(u32) * n));
+    GSR_TRY(ensure_buf(ctx, S.cnt, sizeof(u32) * 4));
+    const float inv_h = 1.f / (rho * (1.f + 1e-4f));
+    GSR_TRY(sort_cells(ctx, S, global->mean, n_global, inv_h, s));
+    k_merge_reject<<<nblk(n), 256, 0, s>>>(n, sub->mean, global->mean, (const u32 *)S.keys[0].p,
+                                           (const u32 *)S.vals[0].p, n_global, inv_h, rho * rho, (u32 *)S.keep.p);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    u32 *cnt = (u32 *)S.cnt.p;
+    GSR_TRY(scan_exclusive(ctx, (const u32 *)S.keep.p, (u32 *)S.keep_off.p, n, nullptr, cnt + 3, s));
+    GSR_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned + 44, cnt + 3, sizeof(u32), cudaMemcpyDeviceToHost, s));
+    GSR_CUDA(ctx, cudaStreamSynchronize(s));
+    const int64_t add = ctx->host_pinned[44];
+    if (n_global + add > capacity) return gsr_fail(ctx, GSR_ERR_CAPACITY, "merge would exceed the global capacity");
+    k_merge_append<<<nblk(n), 256, 0, s>>>(n, (const u32 *)S.keep.p, (const u32 *)S.keep_off.p, *sub, *global,
+                                           n_global);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    *n_added = add;
+    return GSR_OK;
+}

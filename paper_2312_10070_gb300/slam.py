@@ -1,5 +1,5 @@
 """The online Gaussian-SLAM loop (Sec. 3.2-3.5, Sec. 4, supplementary Sec. A)
-assembled from the C ABI.
+assembled from the C ABI, and the global map built from its sub-maps.
 
 Per frame: a constant-velocity initial pose (Sec. 3.5: additive on t and on
 the quaternion, which is sign-aligned and renormalised), then frame-to-model
@@ -16,7 +16,11 @@ frame is a keyframe:
      iterations on the new keyframe (Sec. 4), Gaussians with opacity below
      o_thre being pruned at the middle and the end of those iterations
      (supplementary Sec. A).
-Every numerical step runs in libgsr.so; this module only schedules.
+After the sequence, the sub-maps are merged in order into a global map with
+the seeding rule (gsr_merge_submap) and its colours are refined over every
+keyframe (supplementary Sec. A).  Sub-maps can be saved to and loaded from
+.npz files.  Every numerical step runs in libgsr.so; this module only
+schedules.
 """
 from __future__ import annotations
 
@@ -104,6 +108,7 @@ class GaussianSLAM:
         self.n_frames = 0
         self.rng = np.random.default_rng(self.cfg.schedule_seed)
         self.log = []
+        self.keyframes = []  # every keyframe of the run: (pose, rgb, depth)
 
     # -------------------------------------------------------------- mapping
     def _schedule(self, n_iters: int):
@@ -150,6 +155,7 @@ class GaussianSLAM:
             alpha = api.render_forward(self.ctx, a.sub.params(), self.cam, api.make_pose(*pose))["alpha"]
         st = api.seed_keyframe(self.ctx, a.sub, self.cam, api.make_pose(*pose), rgb, depth, alpha, scfg)
         a.keyframes.append((pose, rgb, depth))
+        self.keyframes.append((pose, rgb, depth))
         self._map(cfg.map_iters_first if first else cfg.map_iters)
         self.log.append(dict(frame=self.n_frames, new_submap=first, seeded=st["n_added"], gaussians=a.sub.n))
 
@@ -181,3 +187,58 @@ def ate_rmse(est, gt):
     """Root-mean-square camera-centre error (m) of estimated vs true world-to-camera poses."""
     e = [np.linalg.norm(camera_centre(*a) - camera_centre(*b)) for a, b in zip(est, gt)]
     return float(np.sqrt(np.mean(np.square(e))))
+
+
+# ------------------------------------------------------------ global map
+def all_submaps(s: GaussianSLAM):
+    """The finished sub-maps and the active one, as host dicts, in order."""
+    return s.submaps + ([s.active.to_host()] if s.active is not None else [])
+
+
+def save_submaps(path: str, submaps):
+    np.savez(path, **{f"{i}_{k}": v for i, sm in enumerate(submaps) for k, v in sm.items()})
+
+
+def load_submaps(path: str):
+    z = np.load(path)
+    out = {}
+    for key in z.files:
+        i, k = key.split("_", 1)
+        out.setdefault(int(i), {})[k] = z[key]
+    return [out[i] for i in sorted(out)]
+
+
+def global_map(ctx: api.Context, submaps, rho: float = 0.01) -> api.SubMap:
+    """Merge sub-maps in sequence (supplementary Sec. A): each Gaussian is
+    added when no Gaussian already in the global map lies within rho."""
+    cap = sum(len(sm["mean"]) for sm in submaps)
+    g = api.SubMap(max(cap, 1))
+    for sm in submaps:
+        api.merge_submap(ctx, g, api.GaussianParams.from_numpy(sm), rho)
+    return g
+
+
+def refine_colours(ctx: api.Context, g: api.SubMap, cam, keyframes, iters: int, lr_rgb: float = 2.5e-3,
+                   seed: int = 0):
+    """Colour refinement of the global map (supplementary Sec. A): mapping
+    iterations over randomly drawn keyframes with every learning rate but the
+    colour one at zero (and no regulariser), so only RGB changes."""
+    cfg = api.MapConfig(adam=api.AdamConfig(lr_mean=0.0, lr_log_scale=0.0, lr_quat=0.0, lr_opacity=0.0,
+                                            lr_rgb=lr_rgb, w_reg=0.0), use_graph=False)
+    moments = api.AdamMoments(g.arrays)
+    rng = np.random.default_rng(seed)
+    for _ in range(iters):
+        pose, rgb, depth = keyframes[int(rng.integers(0, len(keyframes)))]
+        api.map_step(ctx, g.params(), moments, cam, [(api.make_pose(*pose), rgb, depth)], None, 1, cfg,
+                     want_stats=False)
+    return g
+
+
+def psnr(ctx: api.Context, g: api.SubMap, cam, keyframes) -> float:
+    """Mean PSNR (dB, peak 1) of the map's renders against the keyframes' colours."""
+    vals = []
+    for pose, rgb, _ in keyframes:
+        r = api.render_forward(ctx, g.params(), cam, api.make_pose(*pose))["rgb"]
+        mse = float(torch.mean((r.clamp(0, 1) - rgb) ** 2))
+        vals.append(10.0 * math.log10(1.0 / max(mse, 1e-12)))
+    return float(np.mean(vals))

@@ -48,3 +48,45 @@ def test_prune_without_moments_and_nothing_to_remove():
     sub.append(api.GaussianParams.from_numpy(p))
     assert api.prune(ctx, sub, None, 0.5) == 500
     np.testing.assert_array_equal(sub.params().mean.cpu().numpy(), p["mean"])
+
+
+def test_merge_matches_oracle():
+    """Three overlapping sub-maps of a room merged in sequence.  Decisions
+    within 5e-3 rho^2 of the threshold are ambiguous in FP32, and so are the
+    decisions of points within 1.01 rho of an ambiguous point of an earlier
+    sub-map (its presence in the global map is uncertain)."""
+    from paper_2312_10070_gb300 import api, synth as S
+    scene = S.room_scene(60_000, seed=7)
+    rng = np.random.default_rng(8)
+    parts = []
+    for k in range(3):
+        sel = rng.random(60_000) < 0.4
+        parts.append({n: np.ascontiguousarray(v[sel]) for n, v in scene.items()})
+    ref, masks = SD.merge(parts, 0.01)
+    ctx = api.Context()
+    g = api.SubMap(sum(len(p["mean"]) for p in parts))
+    glob = np.zeros((0, 3))
+    amb_pts = np.zeros((0, 3))
+    for p, m in zip(parts, masks):
+        n0 = g.n
+        api.merge_submap(ctx, g, api.GaussianParams.from_numpy(p), 0.01)
+        got = g.arrays.mean[n0:g.n].cpu().numpy()
+        pm = p["mean"].astype(np.float64)
+        d2 = SD.min_dist2(pm, glob)
+        unsure = np.abs(d2 - 1e-4) <= 5e-3 * 1e-4
+        if len(amb_pts):
+            unsure |= SD.min_dist2(pm, amb_pts) < (1.01 * 0.01) ** 2
+        got_set = {tuple(r) for r in got.tolist()}
+        sure_keep = {tuple(r) for r in p["mean"][m & ~unsure].tolist()}
+        allowed = {tuple(r) for r in p["mean"][m | unsure].tolist()}
+        assert sure_keep <= got_set <= allowed
+        assert unsure.mean() < 0.01
+        # appended rows carry every parameter of their source Gaussian, in order
+        src = {tuple(r): i for i, r in enumerate(p["mean"].tolist())}
+        idx = np.array([src[tuple(r)] for r in got.tolist()])
+        assert np.all(np.diff(idx) > 0)
+        for k, t in zip(api.GaussianParams.NAMES, g.arrays.tensors()):
+            np.testing.assert_array_equal(t[n0:g.n].cpu().numpy(), p[k][idx])
+        glob = np.concatenate([glob, pm[m]])
+        amb_pts = np.concatenate([amb_pts, pm[unsure]])
+    assert abs(g.n - len(ref["mean"])) <= len(amb_pts)

@@ -32,7 +32,7 @@ def make_frames(scene, poses, spec, seed=0):
     return frames
 
 
-def test_online_slam_tracks_a_room_sequence():
+def test_online_slam_tracks_a_room_sequence(tmp_path):
     from paper_2312_10070_gb300 import api, slam, synth as S
     spec = S.camera_room()
     scene = S.room_scene(300_000, seed=100)
@@ -51,3 +51,23 @@ def test_online_slam_tracks_a_room_sequence():
     assert len(s.log) == 8 and all(e["seeded"] > 0 for e in s.log)
     if path > 0.6:
         assert len(s.submaps) >= 1
+    # global map: merge the sub-maps (also through a save / load round trip), refine colours
+    subs = slam.all_submaps(s)
+    path_npz = str(tmp_path / "submaps.npz")
+    slam.save_submaps(path_npz, subs)
+    loaded = slam.load_submaps(path_npz)
+    assert len(loaded) == len(subs)
+    for a, b in zip(subs, loaded):
+        for k in a:
+            np.testing.assert_array_equal(a[k], b[k])
+    g = slam.global_map(s.ctx, loaded)
+    assert len(subs[0]["mean"]) <= g.n <= sum(len(x["mean"]) for x in subs)
+    p0 = slam.psnr(s.ctx, g, s.cam, s.keyframes)
+    before = {k: t[:g.n].clone() for k, t in zip(api.GaussianParams.NAMES, g.arrays.tensors())}
+    slam.refine_colours(s.ctx, g, s.cam, s.keyframes, iters=150)
+    p1 = slam.psnr(s.ctx, g, s.cam, s.keyframes)
+    print("global map", g.n, "PSNR before / after colour refinement", p0, p1)
+    assert p1 > p0
+    for k, t in zip(api.GaussianParams.NAMES, g.arrays.tensors()):
+        if k != "rgb":
+            assert torch.equal(t[:g.n], before[k]), k

@@ -107,3 +107,23 @@ def test_distances_and_keyframe_seeding_against_kdtree():
     alpha = rng.random((H, W))
     out2 = SD.seed_keyframe(rgb, depth, alpha, cam, q, t, existing, first=False, m_k=300, rho=0.03, seed=6)
     assert out2["pix"].size == 300 and np.all(alpha.ravel()[out2["pix"]] < 0.6)
+
+
+def test_merge_rule_on_a_constructed_case():
+    rho = 0.01
+    a = dict(mean=np.array([[0.0, 0, 0], [1.0, 0, 0]]), rgb=np.array([[1.0, 0, 0], [0, 1.0, 0]]))
+    b = dict(mean=np.array([[0.005, 0, 0],      # within rho of a[0]: dropped
+                            [0.0, 0.0101, 0],   # just outside rho of a[0]: kept
+                            [2.0, 0, 0], [2.001, 0, 0]]),  # near each other only: both kept
+             rgb=np.zeros((4, 3)))
+    merged, masks = SD.merge([a, b], rho)
+    np.testing.assert_array_equal(masks[0], [True, True])
+    np.testing.assert_array_equal(masks[1], [False, True, True, True])
+    assert merged["mean"].shape == (5, 3)
+    # against scipy's k-d tree on random data
+    rng = np.random.default_rng(3)
+    s1 = dict(mean=rng.uniform(0, 0.3, (2000, 3)))
+    s2 = dict(mean=rng.uniform(0.1, 0.4, (2000, 3)))
+    _, m = SD.merge([s1, s2], 0.01)
+    d, _ = cKDTree(s1["mean"]).query(s2["mean"])
+    np.testing.assert_array_equal(m[1], d >= 0.01)
