@@ -4,13 +4,14 @@
 //   L = w_c [(1-lam) mean|I^-I| + lam (1 - SSIM)] + w_d mean_valid |D^-D|
 // SSIM uses the 11x11 Gaussian window (sigma 1.5) of Wang et al. with zero
 // padding, C1 = 0.01^2, C2 = 0.03^2, averaged over pixels and channels.  Two
-// kernels: the first forms the five window sums per channel of a 32x32 output
-// tile from a 42x42 shared-memory tile, the SSIM value and the adjoint maps
+// kernels: the first forms the five window sums per channel of a 32x48 output
+// tile from a 42x58 shared-memory tile (in two groups, so that the grid of a
+// 1200x680 frame is resident in one wave), the SSIM value and the adjoint maps
 // dS/dmu_x, dS/dE[x^2], dS/dE[xy]; the second blurs the adjoint maps with the
 // same (symmetric) window and assembles dL/dI^ and dL/dD^.  Both separable
-// passes slide the window in registers: a thread of the horizontal pass reads
-// 18 inputs once and produces 8 outputs, a thread of the vertical pass reads
-// 14 rows once and produces 4 outputs.
+// passes slide the window in registers: a horizontal task reads 14 inputs
+// once and produces 4 outputs, a thread of the vertical pass reads 16 rows
+// once and produces 6 outputs.
 //
 // Tracking (Sec. 3.5, supplementary Sec. B):
 //   L = sum M_inlier alpha^3 (lam_c sum_ch |I^-I| + (1-lam_c)|D^-D|)
@@ -26,29 +27,27 @@
 namespace {
 
 constexpr int SHALO = 5;                 // window radius
-constexpr int TX = 32, TY = 32;          // output tile
-constexpr int LW = TX + 2 * SHALO;       // 42 rows / columns loaded
+constexpr int TX = 32, TY = 48;          // output tile
+constexpr int LW = TX + 2 * SHALO;       // 42 columns loaded
+constexpr int LH = TY + 2 * SHALO;       // 58 rows loaded
 constexpr int LP = LW + 1;               // padded row of the loaded tile
 constexpr int HP = TX + 1;               // padded row of the horizontal sums
-constexpr int HSEG = 8;                  // outputs per thread, horizontal pass
-constexpr int VSEG = 4;                  // outputs per thread, vertical pass
+constexpr int HSEG = 4;                  // outputs per horizontal task (8 tasks per row)
+constexpr int VSEG = TY / 8;             // outputs per thread, vertical pass (8 warps of 32 columns)
 
 __device__ __forceinline__ float sgnf(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
 
-__device__ __forceinline__ void load_window(float *wk)
+// The 11-tap window: w_k = exp(-(k - 5)^2 / (2 * 1.5^2)) normalised to sum 1,
+// rounded to float32 (computed in double precision).  As compile-time
+// constants the taps are immediate operands of the FMAs.
+__host__ __device__ constexpr float wtap(int k)
 {
-    // 11 taps of exp(-k^2 / (2 * 1.5^2)), normalised to sum 1
-    if (threadIdx.x < 11) {
-        float k = (float)threadIdx.x - 5.f;
-        wk[threadIdx.x] = expf(-k * k / 4.5f);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int k = 0; k < 11; ++k) s += wk[k];
-        for (int k = 0; k < 11; ++k) wk[k] /= s;
-    }
-    __syncthreads();
+    return k == 0 || k == 10 ? 0.001028380123898387f
+         : k == 1 || k == 9  ? 0.0075987582094967365f
+         : k == 2 || k == 8  ? 0.036000773310661316f
+         : k == 3 || k == 7  ? 0.10936068743467331f
+         : k == 4 || k == 6  ? 0.21300554275512695f
+                             : 0.26601171493530273f;
 }
 
 // block sum of NV values over 256 threads; thread 0 gets the totals
@@ -75,19 +74,11 @@ __device__ __forceinline__ void block_sum256(float (&v)[NV])
     }
 }
 
-// Horizontal pass task of thread t: segment t/32 & 3 (8 output columns) of
-// loaded row (t/128) * 32 + lane; rows beyond the tile are idle.
-__device__ __forceinline__ bool hpass_task(int &row, int &col0)
-{
-    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
-    row = (w >> 2) * 32 + lane;
-    col0 = (w & 3) * HSEG;
-    return row < LW;
-}
-
-// 8 horizontal window sums of f(x_i, y_i) over inputs i = col0 .. col0 + 17
+// Horizontal pass tasks of a thread: segment `warp` (HSEG output columns) of
+// the loaded rows lane, lane + 32, ... (conflict-free: odd row pitches).
+// HSEG horizontal window sums of f(x_i, y_i) over inputs i = col0 .. col0 + HSEG + 9
 template <typename F>
-__device__ __forceinline__ void hsum8(const float (&xv)[HSEG + 10], const float (&yv)[HSEG + 10], const float (&wk)[11],
+__device__ __forceinline__ void hsum(const float (&xv)[HSEG + 10], const float (&yv)[HSEG + 10], const float (&wk)[11],
                                       F f, float (&out)[HSEG])
 {
 #pragma unroll
@@ -101,31 +92,49 @@ __device__ __forceinline__ void hsum8(const float (&xv)[HSEG + 10], const float 
     }
 }
 
-__device__ __forceinline__ void window_regs(float (&wk)[11], const float *s_wk)
+// Vertical window sums of NQ horizontal-sum planes, VSEG outputs per thread
+template <int NQ>
+__device__ __forceinline__ void vsum(const float (*hq)[LH][HP], int r0, int c, const float (&wk)[11],
+                                     float (&out)[NQ][VSEG])
 {
 #pragma unroll
-    for (int k = 0; k < 11; ++k) wk[k] = s_wk[k];
+    for (int q = 0; q < NQ; ++q) {
+        float col[VSEG + 10];
+#pragma unroll
+        for (int i = 0; i < VSEG + 10; ++i) col[i] = hq[q][r0 + i][c];
+#pragma unroll
+        for (int j = 0; j < VSEG; ++j) {
+            float a = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) a = fmaf(wk[k], col[j + k], a);
+            out[q][j] = a;
+        }
+    }
 }
 
-__global__ void __launch_bounds__(256) k_ssim_fwd(int W, int H, const float *__restrict__ x, const float *__restrict__ y,
+// The five window sums are formed in two groups (mu_x, mu_y, E[x^2]) and
+// (E[y^2], E[xy]) through three horizontal-sum planes, so a block needs
+// 43 KB of shared memory and the whole 1200x680 grid (570 blocks) fits in one
+// wave at four blocks per SM.
+__global__ void __launch_bounds__(256, 4) k_ssim_fwd(int W, int H, const float *__restrict__ x, const float *__restrict__ y,
                                                   const float *__restrict__ dep, const float *__restrict__ dep_t,
                                                   float gscale, float *__restrict__ P, float *__restrict__ part,
                                                   u32 *__restrict__ nvalid)
 {
-    __shared__ float s_wk[11];
-    __shared__ float sx[LW][LP], sy[LW][LP];
-    __shared__ float hq[5][LW][HP];
-    load_window(s_wk);
+    __shared__ float sx[LH][LP], sy[LH][LP];
+    __shared__ float hq[3][LH][HP];
     float wk[11];
-    window_regs(wk, s_wk);
+#pragma unroll
+    for (int k = 0; k < 11; ++k) wk[k] = wtap(k);
     const int ox = blockIdx.x * TX, oy = blockIdx.y * TY;
     const int c = (int)threadIdx.x & 31, r0 = ((int)threadIdx.x >> 5) * VSEG;  // vertical task
     const int gx = ox + c;
     const int64_t HW = (int64_t)W * H;
     const float C1 = 1e-4f, C2 = 9e-4f;
     float acc[3] = {0.f, 0.f, 0.f};  // SSIM sum, |x - y| sum, valid |D^ - D| sum
+    const int hc = ((int)threadIdx.x >> 5) * HSEG, hlane = (int)threadIdx.x & 31;
     for (int ch = 0; ch < 3; ++ch) {
-        for (int i = threadIdx.x; i < LW * LW; i += 256) {
+        for (int i = threadIdx.x; i < LH * LW; i += 256) {
             const int rr = i / LW, cc = i % LW;
             const int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
             const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
@@ -134,60 +143,61 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(int W, int H, const float *__r
             sy[rr][cc] = ok ? y[q] : 0.f;
         }
         __syncthreads();
-        int hr, hc;
-        if (hpass_task(hr, hc)) {
+        for (int hr = hlane; hr < LH; hr += 32) {
             float xv[HSEG + 10], yv[HSEG + 10], o[HSEG];
 #pragma unroll
             for (int i = 0; i < HSEG + 10; ++i) {
                 xv[i] = sx[hr][hc + i];
                 yv[i] = sy[hr][hc + i];
             }
-            hsum8(xv, yv, wk, [](float a, float) { return a; }, o);
+            hsum(xv, yv, wk, [](float a, float) { return a; }, o);
 #pragma unroll
             for (int j = 0; j < HSEG; ++j) hq[0][hr][hc + j] = o[j];
-            hsum8(xv, yv, wk, [](float, float b) { return b; }, o);
+            hsum(xv, yv, wk, [](float, float b) { return b; }, o);
 #pragma unroll
             for (int j = 0; j < HSEG; ++j) hq[1][hr][hc + j] = o[j];
-            hsum8(xv, yv, wk, [](float a, float) { return a * a; }, o);
+            hsum(xv, yv, wk, [](float a, float) { return a * a; }, o);
 #pragma unroll
             for (int j = 0; j < HSEG; ++j) hq[2][hr][hc + j] = o[j];
-            hsum8(xv, yv, wk, [](float, float b) { return b * b; }, o);
-#pragma unroll
-            for (int j = 0; j < HSEG; ++j) hq[3][hr][hc + j] = o[j];
-            hsum8(xv, yv, wk, [](float a, float b) { return a * b; }, o);
-#pragma unroll
-            for (int j = 0; j < HSEG; ++j) hq[4][hr][hc + j] = o[j];
         }
         __syncthreads();
-        float m[5][VSEG];
+        float ma[3][VSEG];
+        vsum<3>(hq, r0, c, wk, ma);
+        __syncthreads();
+        for (int hr = hlane; hr < LH; hr += 32) {
+            float xv[HSEG + 10], yv[HSEG + 10], o[HSEG];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            float col[VSEG + 10];
-#pragma unroll
-            for (int i = 0; i < VSEG + 10; ++i) col[i] = hq[q][r0 + i][c];
-#pragma unroll
-            for (int j = 0; j < VSEG; ++j) {
-                float a = 0.f;
-#pragma unroll
-                for (int k = 0; k < 11; ++k) a = fmaf(wk[k], col[j + k], a);
-                m[q][j] = a;
+            for (int i = 0; i < HSEG + 10; ++i) {
+                xv[i] = sx[hr][hc + i];
+                yv[i] = sy[hr][hc + i];
             }
+            hsum(xv, yv, wk, [](float, float b) { return b * b; }, o);
+#pragma unroll
+            for (int j = 0; j < HSEG; ++j) hq[0][hr][hc + j] = o[j];
+            hsum(xv, yv, wk, [](float a, float b) { return a * b; }, o);
+#pragma unroll
+            for (int j = 0; j < HSEG; ++j) hq[1][hr][hc + j] = o[j];
         }
+        __syncthreads();
+        float mb[2][VSEG];
+        vsum<2>(hq, r0, c, wk, mb);
 #pragma unroll
         for (int j = 0; j < VSEG; ++j) {
             const int gy = oy + r0 + j;
             if (gx < W && gy < H) {
-                const float m1 = m[0][j], m2 = m[1][j], e11 = m[2][j], e22 = m[3][j], e12 = m[4][j];
+                const float m1 = ma[0][j], m2 = ma[1][j], e11 = ma[2][j], e22 = mb[0][j], e12 = mb[1][j];
                 const float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * (e12 - m1 * m2) + C2;
                 const float B1 = m1 * m1 + m2 * m2 + C1, B2 = (e11 - m1 * m1) + (e22 - m2 * m2) + C2;
-                const float iB = 1.f / (B1 * B2);
+                // B1, B2 >= C1, C2 > 0: fast reciprocals (2 ulp) are ample here
+                const float iB1 = __fdividef(1.f, B1), iB2 = __fdividef(1.f, B2);
+                const float iB = iB1 * iB2;
                 const float S = A1 * A2 * iB;
                 acc[0] += S;
-                const float xv = sx[r0 + j + SHALO][c + SHALO], yv = sy[r0 + j + SHALO][c + SHALO];
-                acc[1] += fabsf(xv - yv);
+                const float xc = sx[r0 + j + SHALO][c + SHALO], yc = sy[r0 + j + SHALO][c + SHALO];
+                acc[1] += fabsf(xc - yc);
                 const int64_t p = (int64_t)gy * W + gx;
-                P[(3 * ch + 0) * HW + p] = gscale * (2.f * m2 * (A2 - A1) * iB - 2.f * m1 * S * (1.f / B1 - 1.f / B2));
-                P[(3 * ch + 1) * HW + p] = gscale * (-S / B2);
+                P[(3 * ch + 0) * HW + p] = gscale * (2.f * m2 * (A2 - A1) * iB - 2.f * m1 * S * (iB1 - iB2));
+                P[(3 * ch + 1) * HW + p] = gscale * (-S * iB2);
                 P[(3 * ch + 2) * HW + p] = gscale * (2.f * A1 * iB);
             }
         }
@@ -217,58 +227,49 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(int W, int H, const float *__r
     }
 }
 
+// The three adjoint maps are blurred one at a time through one loaded plane
+// and one horizontal-sum plane (18 KB of shared memory per block).
 __global__ void __launch_bounds__(256) k_ssim_bwd(int W, int H, const float *__restrict__ x, const float *__restrict__ y,
                                                   const float *__restrict__ dep, const float *__restrict__ dep_t,
                                                   const float *__restrict__ P, float l1s, float dscale,
                                                   const u32 *__restrict__ nvalid, float *__restrict__ d_rgb,
                                                   float *__restrict__ d_dep)
 {
-    __shared__ float s_wk[11];
-    __shared__ float sp[3][LW][LP];
-    __shared__ float hq[3][LW][HP];
-    load_window(s_wk);
+    __shared__ float sp[LH][LP];
+    __shared__ float hq[1][LH][HP];
     float wk[11];
-    window_regs(wk, s_wk);
+#pragma unroll
+    for (int k = 0; k < 11; ++k) wk[k] = wtap(k);
     const int ox = blockIdx.x * TX, oy = blockIdx.y * TY;
     const int c = (int)threadIdx.x & 31, r0 = ((int)threadIdx.x >> 5) * VSEG;
     const int gx = ox + c;
     const int64_t HW = (int64_t)W * H;
+    const int hc = ((int)threadIdx.x >> 5) * HSEG, hlane = (int)threadIdx.x & 31;
     for (int ch = 0; ch < 3; ++ch) {
-        for (int i = threadIdx.x; i < LW * LW; i += 256) {
-            const int rr = i / LW, cc = i % LW;
-            const int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
-            const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
-            const int64_t q = (int64_t)yy * W + xx;
-#pragma unroll
-            for (int m = 0; m < 3; ++m) sp[m][rr][cc] = ok ? P[(3 * ch + m) * HW + q] : 0.f;
-        }
-        __syncthreads();
-        int hr, hc;
-        if (hpass_task(hr, hc)) {
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                float v[HSEG + 10], o[HSEG];
-#pragma unroll
-                for (int i = 0; i < HSEG + 10; ++i) v[i] = sp[m][hr][hc + i];
-                hsum8(v, v, wk, [](float a, float) { return a; }, o);
-#pragma unroll
-                for (int j = 0; j < HSEG; ++j) hq[m][hr][hc + j] = o[j];
-            }
-        }
-        __syncthreads();
         float b[3][VSEG];
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-            float col[VSEG + 10];
-#pragma unroll
-            for (int i = 0; i < VSEG + 10; ++i) col[i] = hq[m][r0 + i][c];
-#pragma unroll
-            for (int j = 0; j < VSEG; ++j) {
-                float a = 0.f;
-#pragma unroll
-                for (int k = 0; k < 11; ++k) a = fmaf(wk[k], col[j + k], a);
-                b[m][j] = a;
+            for (int i = threadIdx.x; i < LH * LW; i += 256) {
+                const int rr = i / LW, cc = i % LW;
+                const int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
+                const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
+                sp[rr][cc] = ok ? P[(3 * ch + m) * HW + (int64_t)yy * W + xx] : 0.f;
             }
+            __syncthreads();
+            for (int hr = hlane; hr < LH; hr += 32) {
+                float v[HSEG + 10], o[HSEG];
+#pragma unroll
+                for (int i = 0; i < HSEG + 10; ++i) v[i] = sp[hr][hc + i];
+                hsum(v, v, wk, [](float a, float) { return a; }, o);
+#pragma unroll
+                for (int j = 0; j < HSEG; ++j) hq[0][hr][hc + j] = o[j];
+            }
+            __syncthreads();
+            float bm[1][VSEG];
+            vsum<1>(hq, r0, c, wk, bm);
+#pragma unroll
+            for (int j = 0; j < VSEG; ++j) b[m][j] = bm[0][j];
+            __syncthreads();
         }
 #pragma unroll
         for (int j = 0; j < VSEG; ++j) {
@@ -279,16 +280,16 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(int W, int H, const float *__r
                 d_rgb[ch * HW + p] = l1s * sgnf(xv - yv) + b[0][j] + 2.f * xv * b[1][j] + yv * b[2][j];
             }
         }
-        __syncthreads();
     }
     const u32 nv = *nvalid;
+    const float dsn = nv > 0 ? dscale / (float)nv : 0.f;
 #pragma unroll
     for (int j = 0; j < VSEG; ++j) {
         const int gy = oy + r0 + j;
         if (gx < W && gy < H) {
             const int64_t p = (int64_t)gy * W + gx;
             const float dt = dep_t[p];
-            d_dep[p] = (dt > 0.f && nv > 0) ? dscale * sgnf(dep[p] - dt) / (float)nv : 0.f;
+            d_dep[p] = dt > 0.f ? dsn * sgnf(dep[p] - dt) : 0.f;
         }
     }
 }
