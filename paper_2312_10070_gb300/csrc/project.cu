@@ -417,7 +417,7 @@ __device__ __forceinline__ void chain_to_params(const CamK &ck, const PoseR &pr,
 // K6: image-space gradients -> parameter gradients and the pose adjoint
 // (block partial sums, reduced in a second pass).
 template <bool WANT_PARAMS>
-__global__ void __launch_bounds__(256) k_project_bwd(Params P, CamK ck, const float *__restrict__ pose,
+__global__ void __launch_bounds__(256, 4) k_project_bwd(Params P, CamK ck, const float *__restrict__ pose,
                                                      const int32_t *__restrict__ rank_of_gid,
                                                      const float *__restrict__ g2d, gsr_gaussian_grads dg,
                                                      int accumulate, float weight,
