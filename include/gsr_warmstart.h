@@ -86,6 +86,20 @@ typedef struct {
 
 GSR_API void gsr_warmstart_default_opts(gsr_warmstart_opts *o);
 
+/* Kernel choice for the forward products: those with a reduction length
+ * K >= tcgen05_min_k run on the 5th-generation tensor cores (tcgen05.mma,
+ * accumulators in tensor memory), the others -- and all of them when
+ * tcgen05_min_k < 0 -- on the mma.sync kernel that also runs the backward
+ * products.  Results agree to FP32 summation order.  The default is -1: on
+ * GB300 the mma.sync kernel measured faster for every layer of this network
+ * (its products are narrow and bound by operand movement). */
+GSR_API gsr_status gsr_warmstart_set_kernels(gsr_warmstart *net, int32_t tcgen05_min_k);
+
+/* Synchronises `stream` and returns GSR_ERR_TIMEOUT (clearing it) if a
+ * tensor-core kernel's bounded wait expired since the last check; its
+ * outputs are then invalid. */
+GSR_API gsr_status gsr_warmstart_check(gsr_warmstart *net, void *stream);
+
 /* One training step on a batch: forward, loss
  *   L = (1/B) sum_b sum_c w_c (out[b,c] - target[b,c])^2,
  * backward, Adam on the FP32 masters and re-derivation of the BF16 copies.

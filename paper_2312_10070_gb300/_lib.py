@@ -164,6 +164,8 @@ PROTOTYPES = {
     "gsr_warmstart_forward": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
     "gsr_warmstart_backward": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
     "gsr_warmstart_default_opts": (None, [ctypes.POINTER(WarmstartOpts)]),
+    "gsr_warmstart_set_kernels": (c_i32, [c_vp, c_i32]),
+    "gsr_warmstart_check": (c_i32, [c_vp, c_vp]),
     "gsr_warmstart_train_step": (c_i32, [c_vp, c_vp, c_vp, c_i32, ctypes.POINTER(WarmstartOpts), c_vp, c_vp]),
     "gsr_warmstart_make_input": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_f, c_vp, c_vp]),
 }

@@ -367,6 +367,231 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t k
             }
 }
 
+// ------------------------------------------------------- tcgen05 GEMM
+// Forward products with both operands stored reduction-contiguous (OP_KC or
+// OP_IM_KC for A, OP_KC for B) on the 5th-generation tensor cores: one CTA
+// of 8 warps per 128 x TN output tile, the accumulator in tensor memory
+// (TN FP32 columns x 128 lanes), operand tiles of 32 reduction indices in a
+// 4-stage ring of shared memory filled by cp.async two steps ahead, one
+// thread issuing tcgen05.mma (M = 128, N = TN, K = 16, BF16 x BF16 -> FP32)
+// and committing each stage to an mbarrier; a stage is refilled once the
+// MMAs of two steps back have completed.  Shared-memory tiles use the
+// canonical no-swizzle K-major layout: 8-row x 16-byte core matrices, the
+// core matrix (r / 8, k / 8) at byte offset ((r / 8) * 4 + k / 8) * 128, so
+// K-adjacent core matrices are 128 bytes apart (leading byte offset) and
+// 8-row groups 512 bytes (stride byte offset).
+// Every wait is bounded: on expiry the CTA raises GSR_FLAG_TIMEOUT in *status,
+// drains its copies, frees its tensor memory and returns.
+constexpr int TC_BM = 128, TC_BK = 32, TC_STAGES = 4, TC_LAG = 2, TC_THREADS = 256;
+constexpr int TC_SPIN = 1 << 24;
+constexpr int TC_BAR_SLOTS = 8;  // mbarrier words reserved (>= TC_STAGES, even)
+static_assert(TC_BAR_SLOTS >= TC_STAGES && TC_BAR_SLOTS % 2 == 0, "mbarrier slots");
+
+__device__ __forceinline__ u32 smem_u32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc(const void *smem, u32 lbo, u32 sbo)
+{
+    return (uint64_t)((smem_u32(smem) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);  // version 1, no swizzle
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr u32 tc_idesc(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((u32)(n >> 3) << 17) | ((u32)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, u32 count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, u32 parity)
+{
+    u32 ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the completion of the phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, u32 parity)
+{
+    for (int i = 0; i < TC_SPIN; ++i)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+// Copy one stage: A rows [m0, m0 + 128) and B rows [n0, n0 + TN) x reduction
+// indices [k0, k0 + 64) into the core-matrix layout (zeros outside).
+template <int AMODE, int TN>
+__device__ __forceinline__ void tc_load_stage(bf16 *sa, bf16 *sb, const Operand &A, const Operand &B, int64_t K,
+                                              int m0, int n0, int64_t k0, const int4 *rinfo)
+{
+    constexpr int KC = TC_BK / 8;  // chunks of 8 elements per row
+    for (int c = threadIdx.x; c < (TC_BM + TN) * KC; c += TC_THREADS) {
+        const bool isa = c < TC_BM * KC;
+        const int cc = isa ? c : c - TC_BM * KC;
+        const int r = cc / KC, kc = cc % KC;
+        const int64_t gk = k0 + kc * 8;
+        bf16 *dst = (isa ? sa : sb) + ((r >> 3) * KC + kc) * 64 + (r & 7) * 8;
+        const bf16 *src = A.p;
+        bool ok = gk < K;
+        if (isa) {
+            if (AMODE == OP_KC) {
+                ok = ok && m0 + r < A.rows;
+                if (ok) src = A.p + (int64_t)(m0 + r) * A.ld + gk;
+            } else {
+                const int4 ri = rinfo[r];
+                const int tap = (int)(gk >> A.lc), ch = (int)gk & ((1 << A.lc) - 1);
+                const int ky = tap / 3, kx = tap - 3 * ky;
+                const int iy = ri.y + ky, ix = ri.z + kx;
+                ok = ok && ri.w && iy >= 0 && iy < A.H && ix >= 0 && ix < A.W;
+                if (ok) src = A.p + ri.x + ((int64_t)(iy * A.W + ix) << A.lc) + ch;
+            }
+        } else {
+            ok = ok && n0 + r < B.rows;
+            src = B.p;
+            if (ok) src = B.p + (int64_t)(n0 + r) * B.ld + gk;
+        }
+        cp_async16(dst, src, ok);
+    }
+}
+
+template <int AMODE, int EPI, int TN>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int64_t K, Operand A, Operand B, void *C, int ldc,
+                                                 const float *__restrict__ bias, u32 *status)
+{
+    constexpr int NCOLS = TN <= 32 ? 32 : (TN <= 64 ? 64 : (TN <= 128 ? 128 : 256));
+    constexpr int A_ELEMS = TC_BM * TC_BK, B_ELEMS = TN * TC_BK;
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    bf16 *sA = reinterpret_cast<bf16 *>(tc_smem);
+    bf16 *sB = sA + TC_STAGES * A_ELEMS;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sB + TC_STAGES * B_ELEMS);
+    int4 *rinfo = reinterpret_cast<int4 *>(bar + TC_BAR_SLOTS);  // 16-byte aligned: TC_BAR_SLOTS is even
+    u32 *tslot = reinterpret_cast<u32 *>(rinfo + TC_BM);
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"((u32)NCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) mbar_init(&bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (AMODE == OP_IM_KC && threadIdx.x < TC_BM) {
+        const int m = m0 + (int)threadIdx.x;
+        const int hw = A.Ho * A.Wo;
+        const int b = m / hw, rem = m - b * hw;
+        const int oy = rem / A.Wo, ox = rem - oy * A.Wo;
+        rinfo[threadIdx.x] = make_int4((b * A.H * A.W) << A.lc, 2 * oy - 1, 2 * ox - 1, m < A.rows ? 1 : 0);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const u32 tmem = *tslot;
+    const int nk = (int)((K + TC_BK - 1) / TC_BK);
+    bool failed = false;
+#pragma unroll
+    for (int st = 0; st < TC_STAGES - TC_LAG; ++st) {
+        if (st < nk) tc_load_stage<AMODE, TN>(sA + st * A_ELEMS, sB + st * B_ELEMS, A, B, K, m0, n0, (int64_t)st * TC_BK,
+                                               rinfo);
+        cp_async_commit();
+    }
+    constexpr u32 IDESC = tc_idesc(TC_BM, TN);
+    for (int it = 0; it < nk && !failed; ++it) {
+        const int buf = it % TC_STAGES;
+        cp_async_wait<TC_STAGES - TC_LAG - 1>();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                // a K step of 16 spans two core matrices along K: 256 bytes
+                const uint64_t da = tc_desc(sA + buf * A_ELEMS + kk * 128, 128, (TC_BK / 8) * 128);
+                const uint64_t db = tc_desc(sB + buf * B_ELEMS + kk * 128, 128, (TC_BK / 8) * 128);
+                const u32 acc = (it > 0 || kk > 0) ? 1u : 0u;
+                asm volatile("{\n\t.reg .pred p;\n\t"
+                             "setp.ne.b32 p, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                             "l"(da), "l"(db), "r"(IDESC), "r"(acc)
+                             : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&bar[buf]))
+                         : "memory");
+        }
+        const int nx = it + TC_STAGES - TC_LAG;
+        if (nx < nk) {
+            // the stage being refilled was read by the MMAs of step it - TC_LAG
+            if (it >= TC_LAG) {
+                const int pb = (it - TC_LAG) % TC_STAGES;
+                if (!mbar_wait(&bar[pb], (u32)(((it - TC_LAG) / TC_STAGES) & 1))) failed = true;
+            }
+            failed = __syncthreads_or(failed);
+            if (!failed)
+                tc_load_stage<AMODE, TN>(sA + (nx % TC_STAGES) * A_ELEMS, sB + (nx % TC_STAGES) * B_ELEMS, A, B, K, m0,
+                                         n0, (int64_t)nx * TC_BK, rinfo);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    if (!failed && nk > 0) {
+        const int lb = (nk - 1) % TC_STAGES;
+        if (!mbar_wait(&bar[lb], (u32)(((nk - 1) / TC_STAGES) & 1))) failed = true;
+    }
+    failed = __syncthreads_or(failed);
+    if (failed) {
+        if (threadIdx.x == 0) atomicOr(status, GSR_FLAG_TIMEOUT);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // warp w reads lane quarter w % 4 (rows) and column half w / 4
+        const int q4 = warp & 3, half = warp >> 2;
+        const int row = m0 + q4 * 32 + lane;
+#pragma unroll
+        for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 16) {
+            u32 r[16];
+            const u32 taddr = tmem + ((u32)(q4 * 32) << 16) + (u32)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                         "%15}, [%16];\n"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (row < M) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int col = n0 + c0 + q;
+                    if (col >= N) continue;
+                    const float v = __uint_as_float(r[q]);
+                    const int64_t o = (int64_t)row * ldc + col;
+                    if (EPI == EPI_BIAS) ((float *)C)[o] = v + bias[col];
+                    else ((bf16 *)C)[o] = __float2bfloat16(fmaxf(v + bias[col], 0.f));
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((u32)NCOLS) : "memory");
+}
+
+template <int TN>
+constexpr size_t tc_smem_bytes()
+{
+    return (size_t)TC_STAGES * (TC_BM + TN) * TC_BK * sizeof(bf16) + TC_BAR_SLOTS * 8 + TC_BM * 16 + 16;
+}
+
 // --------------------------------------------------------- data movement
 // x f32 [npix, 8] -> bf16 [npix, 8] (16 bytes per pixel)
 __global__ void k_input_bf16(int64_t npix, const float *__restrict__ x, bf16 *__restrict__ y)
@@ -554,6 +779,9 @@ struct gsr_warmstart {
     DevBuf master, m1, m2, grad, wb;
     DevBuf act[NL + 2];  // act[0] input (16 ch), act[l+1] conv l output, act[NL+1] dense-1 output
     DevBuf dz, dz2, dbuf, out, dout32, dout, loss_tmp;  // dz / dz2: ping-pong upstream gradients
+    DevBuf status;         // u32 device flags raised by kernels (bounded waits)
+    int tc_min_k = -1;     // forward products with K >= tc_min_k run on tcgen05 (< 0: never; the default,
+                           // as the mma.sync kernel measured faster on every layer)
 };
 
 namespace {
@@ -658,6 +886,42 @@ gsr_status gemm(gsr_warmstart *w, int M, int N, int64_t K, const Operand &A, con
     else
         k_gemm<AMODE, BMODE, EPI, 64><<<grid, 256, 0, s>>>(M, N, K, kchunk, A, B, C, ldc, bias, mask, aux);
     return launched(w);
+}
+
+template <int AMODE, int EPI, int TN>
+gsr_status gemm_tc_n(gsr_warmstart *w, int M, int N, int64_t K, const Operand &A, const Operand &B, void *C, int ldc,
+                     const float *bias, cudaStream_t s)
+{
+    constexpr size_t smem = tc_smem_bytes<TN>();
+    static bool attr_set = false;  // per process; the attribute is per function and device-independent here
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(k_gemm_tc<AMODE, EPI, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return ws_fail(w, GSR_ERR_CUDA, "tcgen05 GEMM: shared-memory attribute refused");
+        attr_set = true;
+    }
+    dim3 grid((unsigned)((N + TN - 1) / TN), (unsigned)((M + TC_BM - 1) / TC_BM));
+    k_gemm_tc<AMODE, EPI, TN><<<grid, TC_THREADS, smem, s>>>(M, N, K, A, B, C, ldc, bias, (u32 *)w->status.p);
+    return launched(w);
+}
+
+// forward product on the tensor cores (N = 256 as two 128-column tiles) when N is one of 32, 64, 128, 256 and
+// K a multiple of 8 (else the mma.sync kernel)
+template <int AMODE, int EPI>
+gsr_status gemm_fwd(gsr_warmstart *w, int M, int N, int64_t K, const Operand &A, const Operand &B, void *C, int ldc,
+                    const float *bias, cudaStream_t s)
+{
+    if (w->tc_min_k >= 0 && K >= w->tc_min_k && (K % 8) == 0 && (((uintptr_t)A.p | (uintptr_t)B.p) & 15) == 0 && (AMODE != OP_KC || A.ld % 8 == 0) &&
+        B.ld % 8 == 0) {
+        switch (N) {
+        case 32: return gemm_tc_n<AMODE, EPI, 32>(w, M, N, K, A, B, C, ldc, bias, s);
+        case 64: return gemm_tc_n<AMODE, EPI, 64>(w, M, N, K, A, B, C, ldc, bias, s);
+        case 128:
+        case 256: return gemm_tc_n<AMODE, EPI, 128>(w, M, N, K, A, B, C, ldc, bias, s);
+        default: break;
+        }
+    }
+    return gemm<AMODE, OP_KC, EPI>(w, M, N, K, A, B, C, ldc, bias, s);
 }
 
 gsr_status pack(gsr_warmstart *w, cudaStream_t s)
@@ -774,7 +1038,7 @@ void gsr_warmstart_destroy(gsr_warmstart *w)
     if (!w) return;
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&w->master, &w->m1, &w->m2, &w->grad, &w->wb, &w->dz, &w->dz2, &w->dbuf,
-                      &w->out, &w->dout32, &w->dout, &w->loss_tmp};
+                      &w->out, &w->dout32, &w->dout, &w->loss_tmp, &w->status};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     for (int l = 0; l < NL + 2; ++l)
@@ -820,6 +1084,7 @@ gsr_status gsr_warmstart_create(gsr_warmstart **out, int32_t max_batch, uint64_t
     A(w->dout32, sizeof(float) * B * NOUTP);
     A(w->dout, sizeof(bf16) * B * NOUTP);
     A(w->loss_tmp, sizeof(float) * 4);
+    A(w->status, sizeof(u32) * 4);
     if (st != GSR_OK) {
         gsr_warmstart_destroy(w);
         return st;
@@ -834,7 +1099,8 @@ gsr_status gsr_warmstart_create(gsr_warmstart **out, int32_t max_batch, uint64_t
     for (int l = 0; l < NL; ++l) fill(L.w_off[l], (int64_t)COUT[l] * 9 * CIN[l], 9 * CIN[l], 1.f);
     fill(L.w_off[NL], (int64_t)HID * FLAT, FLAT, 1.f);
     fill(L.w_off[NL + 1], (int64_t)NOUT * HID, HID, 0.01f);
-    if (cudaMemcpy(w->master.p, h.data(), sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemset(w->status.p, 0, sizeof(u32) * 4) != cudaSuccess ||
+        cudaMemcpy(w->master.p, h.data(), sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(w->m1.p, 0, sizeof(float) * P) != cudaSuccess ||
         cudaMemset(w->m2.p, 0, sizeof(float) * P) != cudaSuccess || pack(w, 0) != GSR_OK ||
         cudaDeviceSynchronize() != cudaSuccess) {
@@ -886,14 +1152,14 @@ gsr_status gsr_warmstart_forward(gsr_warmstart *w, const float *x, int32_t batch
     for (int l = 0; l < NL; ++l) {
         const int64_t M = B * HOUT[l] * WOUT[l];
         const int K = 9 * CINP[l];
-        WS_TRY((gemm<OP_IM_KC, OP_KC, EPI_BIAS_RELU_BF16>(w, (int)M, COUT[l], K,
-                                                          im2col((const bf16 *)w->act[l].p, l, (int)M),
-                                                          dense(wb + L.wb_off[l], K, COUT[l]), w->act[l + 1].p,
-                                                          COUT[l], master + L.b_off[l], s)));
+        WS_TRY((gemm_fwd<OP_IM_KC, EPI_BIAS_RELU_BF16>(w, (int)M, COUT[l], K,
+                                                       im2col((const bf16 *)w->act[l].p, l, (int)M),
+                                                       dense(wb + L.wb_off[l], K, COUT[l]), w->act[l + 1].p, COUT[l],
+                                                       master + L.b_off[l], s)));
     }
-    WS_TRY((gemm<OP_KC, OP_KC, EPI_BIAS_RELU_BF16>(w, batch, HID, FLAT, dense((const bf16 *)w->act[NL].p, FLAT, batch),
-                                                   dense(wb + L.wb_off[NL], FLAT, HID), w->act[NL + 1].p, HID,
-                                                   master + L.b_off[NL], s)));
+    WS_TRY((gemm_fwd<OP_KC, EPI_BIAS_RELU_BF16>(w, batch, HID, FLAT, dense((const bf16 *)w->act[NL].p, FLAT, batch),
+                                                dense(wb + L.wb_off[NL], FLAT, HID), w->act[NL + 1].p, HID,
+                                                master + L.b_off[NL], s)));
     WS_TRY((gemm<OP_KC, OP_KC, EPI_BIAS>(w, batch, NOUT, HID, dense((const bf16 *)w->act[NL + 1].p, HID, batch),
                                          dense(wb + L.wb_off[NL + 1], HID, NOUTP), w->out.p, NOUTP,
                                          master + L.b_off[NL + 1], s)));
@@ -945,6 +1211,28 @@ gsr_status gsr_warmstart_train_step(gsr_warmstart *w, const float *x, const floa
                                                  bc1, bc2);
     WS_TRY(launched(w));
     return pack(w, s);
+}
+
+gsr_status gsr_warmstart_set_kernels(gsr_warmstart *w, int32_t tcgen05_min_k)
+{
+    if (!w) return GSR_ERR_INVALID_ARG;
+    w->tc_min_k = tcgen05_min_k;
+    return GSR_OK;
+}
+
+gsr_status gsr_warmstart_check(gsr_warmstart *w, void *stream)
+{
+    if (!w) return GSR_ERR_INVALID_ARG;
+    u32 flags = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemcpy(&flags, w->status.p, sizeof(u32), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ws_fail(w, GSR_ERR_CUDA, "status read failed");
+    if (flags & GSR_FLAG_TIMEOUT) {
+        cudaMemset(w->status.p, 0, sizeof(u32));
+        return ws_fail(w, GSR_ERR_TIMEOUT, "a tensor-core GEMM wait expired");
+    }
+    return GSR_OK;
 }
 
 gsr_status gsr_warmstart_make_input(const float *rgb_r, const float *depth_r, const float *rgb_i,

@@ -296,15 +296,25 @@ __global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restri
     }
 }
 
+// four sorted keys per thread: a tile's range starts where its key differs
+// from the previous one and ends where it differs from the next one
 __global__ void k_ranges(int64_t cap_i, const u32 *__restrict__ d_n, const u32 *__restrict__ tkeys,
                          uint2 *__restrict__ ranges)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t n = *d_n;
-    if (i >= n || i >= cap_i) return;
-    u32 t = tkeys[i];
-    if (i == 0 || tkeys[i - 1] != t) ranges[t].x = (u32)i;
-    if (i == n - 1 || tkeys[i + 1] != t) ranges[t].y = (u32)(i + 1);
+    const int64_t i0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const int64_t n = min((int64_t)*d_n, cap_i);
+    if (i0 >= n) return;
+    u32 k[6];
+    k[0] = i0 > 0 ? tkeys[i0 - 1] : 0xffffffffu;
+#pragma unroll
+    for (int q = 1; q <= 5; ++q) k[q] = i0 + q - 1 < n ? tkeys[i0 + q - 1] : 0xffffffffu;
+#pragma unroll
+    for (int q = 1; q <= 4; ++q) {
+        const int64_t i = i0 + q - 1;
+        if (i >= n) break;
+        if (k[q - 1] != k[q]) ranges[k[q]].x = (u32)i;
+        if (k[q + 1] != k[q]) ranges[k[q]].y = (u32)(i + 1);
+    }
 }
 
 // --------------------------------------------------------------- backward
@@ -632,7 +642,8 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
     u32 *tv[2] = {(u32 *)V.tvals[0].p, (u32 *)V.tvals[1].p};
     GSR_TRY(radix_sort_pairs(ctx, tk, tv, V.cap_i, cnt + CNT_SORTN, bits_for(tiles), s));
     GSR_CUDA(ctx, cudaMemsetAsync(V.ranges.p, 0, sizeof(uint2) * tiles, s));
-    k_ranges<<<(unsigned)ceil_div(V.cap_i, 256), 256, 0, s>>>(V.cap_i, cnt + CNT_SORTN, tk[0], (uint2 *)V.ranges.p);
+    k_ranges<<<(unsigned)ceil_div(ceil_div(V.cap_i, 4), 256), 256, 0, s>>>(V.cap_i, cnt + CNT_SORTN, tk[0],
+                                                                          (uint2 *)V.ranges.p);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     return GSR_OK;

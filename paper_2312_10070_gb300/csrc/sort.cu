@@ -123,7 +123,21 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_global_hist(const u32 *__r
     const int64_t n = eff_n(n_cap, d_n);
     for (int d = threadIdx.x; d < RX_MAX_PASSES * RX; d += RX_THREADS) (&cnt[0][0])[d] = 0;
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * RX_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RX_THREADS) {
+    // four keys per thread and iteration (16-byte loads; the key arrays are
+    // allocation bases, so 16-byte aligned), the last n % 4 keys one by one
+    const int64_t n4 = n / 4;
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(keys);
+    for (int64_t i = (int64_t)blockIdx.x * RX_THREADS + threadIdx.x; i < n4; i += (int64_t)gridDim.x * RX_THREADS) {
+        const uint4 k = k4[i];
+        for (int p = 0; p < passes; ++p) {
+            const int sh = p * RX_BITS;
+            atomicAdd(&cnt[p][(k.x >> sh) & (RX - 1)], 1u);
+            atomicAdd(&cnt[p][(k.y >> sh) & (RX - 1)], 1u);
+            atomicAdd(&cnt[p][(k.z >> sh) & (RX - 1)], 1u);
+            atomicAdd(&cnt[p][(k.w >> sh) & (RX - 1)], 1u);
+        }
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * RX_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RX_THREADS) {
         const u32 k = keys[i];
         for (int p = 0; p < passes; ++p) atomicAdd(&cnt[p][(k >> (p * RX_BITS)) & (RX - 1)], 1u);
     }

@@ -71,6 +71,15 @@ class WarmStartNet:
             msg = self.lib.gsr_warmstart_last_error(self.handle).decode()
             raise L.GsrError(status, msg)
 
+    def set_kernels(self, tcgen05_min_k: int):
+        """Forward products with reduction length >= tcgen05_min_k on tcgen05,
+        the rest on the mma.sync kernel (negative: none on tcgen05)."""
+        self.check(self.lib.gsr_warmstart_set_kernels(self.handle, int(tcgen05_min_k)))
+
+    def check_status(self):
+        """Synchronise; raise if a tensor-core kernel reported an expired wait."""
+        self.check(self.lib.gsr_warmstart_check(self.handle, _stream()))
+
     def get_params(self) -> torch.Tensor:
         p = torch.empty(self.n_params, device="cuda")
         self.check(self.lib.gsr_warmstart_get_params(self.handle, _ptr(p), _stream()))

@@ -190,3 +190,21 @@ def test_invalid_calls(ws):
         net.forward(x)  # batch above max_batch
     with pytest.raises(L.GsrError):
         net.backward(torch.zeros(2, 6, device="cuda"))  # no forward of that batch yet
+
+
+@pytest.mark.parametrize("batch", [1, 5])
+def test_tcgen05_forward_matches_mma_sync(ws, batch):
+    """The tcgen05 forward products agree with the mma.sync ones (same BF16
+    operands, FP32 accumulation in a different order) on every layer."""
+    rng = np.random.default_rng(40 + batch)
+    p32 = signed_params(50 + batch)
+    x = torch.from_numpy(rng.random((batch, C.IN_H, C.IN_W, C.IN_C)).astype(np.float32)).cuda()
+    net = ws.WarmStartNet(max_batch=8, seed=0)
+    flat = C.flatten({k: v.astype(np.float64) for k, v in p32.items()}).astype(np.float32)
+    net.set_params(torch.from_numpy(flat).cuda())
+    net.set_kernels(0)      # every forward product on tcgen05
+    out_tc = net.forward(x).cpu().numpy()
+    net.check_status()
+    net.set_kernels(-1)     # none
+    out_ms = net.forward(x).cpu().numpy()
+    assert rel_l2(out_tc, out_ms) <= 2e-3, (out_tc, out_ms)
