@@ -369,23 +369,37 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int64_t K, int64_t k
 
 // ------------------------------------------------------- tcgen05 GEMM
 // Forward products with both operands stored reduction-contiguous (OP_KC or
-// OP_IM_KC for A, OP_KC for B) on the 5th-generation tensor cores: one CTA
-// of 8 warps per 128 x TN output tile, the accumulator in tensor memory
-// (TN FP32 columns x 128 lanes), operand tiles of 32 reduction indices in a
-// 4-stage ring of shared memory filled by cp.async two steps ahead, one
-// thread issuing tcgen05.mma (M = 128, N = TN, K = 16, BF16 x BF16 -> FP32)
-// and committing each stage to an mbarrier; a stage is refilled once the
-// MMAs of two steps back have completed.  Shared-memory tiles use the
-// canonical no-swizzle K-major layout: 8-row x 16-byte core matrices, the
-// core matrix (r / 8, k / 8) at byte offset ((r / 8) * 4 + k / 8) * 128, so
-// K-adjacent core matrices are 128 bytes apart (leading byte offset) and
-// 8-row groups 512 bytes (stride byte offset).
-// Every wait is bounded: on expiry the CTA raises GSR_FLAG_TIMEOUT in *status,
-// drains its copies, frees its tensor memory and returns.
-constexpr int TC_BM = 128, TC_BK = 32, TC_STAGES = 4, TC_LAG = 2, TC_THREADS = 256;
+// OP_IM_KC for A, OP_KC for B) on the 5th-generation tensor cores: a
+// persistent, warp-specialised kernel.  Each CTA (12 warps) walks output tiles
+// of 128 x TN (tile = blockIdx.x, += gridDim.x):
+//   - warps 1-7 produce: they copy operand tiles of 32 reduction indices by
+//     cp.async into a 6-stage ring of shared memory and each signals the
+//     stage's "full" mbarrier with cp.async.mbarrier.arrive (it fires when
+//     that thread's copies have landed);
+//   - one thread of warp 0 issues tcgen05.mma (M = 128, N = TN, K = 16,
+//     BF16 x BF16 -> FP32) into one of two accumulators in tensor memory
+//     (2 x TN FP32 columns x 128 lanes), commits each stage to its "empty"
+//     mbarrier (the producers refill after it) and each finished tile to the
+//     accumulator's "ready" mbarrier;
+//   - warps 8-11 drain a ready accumulator (tcgen05.ld; warp w reads lane
+//     quarter w % 4) through the epilogue and release it ("free" mbarrier),
+//     so the epilogue of one tile overlaps the MMAs of the next.
+// The ring runs across tiles; no block-wide barrier runs inside the loops.
+// Shared-memory tiles use the canonical no-swizzle K-major layout: 8-row x
+// 16-byte core matrices, the core matrix (r / 8, k / 8) at byte offset
+// ((r / 8) * 4 + k / 8) * 128, so K-adjacent core matrices are 128 bytes apart
+// (leading byte offset) and 8-row groups 512 bytes (stride byte offset).
+// Every wait is bounded: on expiry a role raises GSR_FLAG_TIMEOUT in *status
+// and stops; the CTA drains its copies, frees its tensor memory and returns.
+constexpr int TC_BM = 128, TC_BK = 32, TC_STAGES = 6;
+constexpr int TC_PRODUCER_WARPS = 7, TC_EPI_WARPS = 4;
+constexpr int TC_THREADS = 32 * (1 + TC_PRODUCER_WARPS + TC_EPI_WARPS);  // 384
+constexpr int TC_PRODUCERS = 32 * TC_PRODUCER_WARPS;
+constexpr int TC_EPI0 = 32 * (1 + TC_PRODUCER_WARPS);                    // first epilogue thread
 constexpr int TC_SPIN = 1 << 24;
-constexpr int TC_BAR_SLOTS = 8;  // mbarrier words reserved (>= TC_STAGES, even)
-static_assert(TC_BAR_SLOTS >= TC_STAGES && TC_BAR_SLOTS % 2 == 0, "mbarrier slots");
+constexpr int TC_BAR_SLOTS = 16;  // full[6], empty[6], ready[2], free[2]
+static_assert(TC_BAR_SLOTS >= 2 * TC_STAGES + 4 && TC_BAR_SLOTS % 2 == 0, "mbarrier slots");
+static_assert(TC_EPI0 % 128 == 0, "epilogue warps w % 4 = 0..3 cover the four lane quarters");
 
 __device__ __forceinline__ u32 smem_u32(const void *p) { return (u32)__cvta_generic_to_shared(p); }
 
@@ -426,14 +440,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, u32 parity)
     return false;
 }
 
-// Copy one stage: A rows [m0, m0 + 128) and B rows [n0, n0 + TN) x reduction
-// indices [k0, k0 + 64) into the core-matrix layout (zeros outside).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Producer share of one stage: A rows [m0, m0 + 128) and B rows [n0, n0 + TN)
+// x reduction indices [k0, k0 + 32) into the core-matrix layout (zeros
+// outside); producer p takes chunks p, p + TC_PRODUCERS, ...
 template <int AMODE, int TN>
-__device__ __forceinline__ void tc_load_stage(bf16 *sa, bf16 *sb, const Operand &A, const Operand &B, int64_t K,
-                                              int m0, int n0, int64_t k0, const int4 *rinfo)
+__device__ __forceinline__ void tc_load_stage(int p, bf16 *sa, bf16 *sb, const Operand &A, const Operand &B,
+                                              int64_t K, int m0, int n0, int64_t k0)
 {
     constexpr int KC = TC_BK / 8;  // chunks of 8 elements per row
-    for (int c = threadIdx.x; c < (TC_BM + TN) * KC; c += TC_THREADS) {
+    for (int c = p; c < (TC_BM + TN) * KC; c += TC_PRODUCERS) {
         const bool isa = c < TC_BM * KC;
         const int cc = isa ? c : c - TC_BM * KC;
         const int r = cc / KC, kc = cc % KC;
@@ -442,16 +469,19 @@ __device__ __forceinline__ void tc_load_stage(bf16 *sa, bf16 *sb, const Operand 
         const bf16 *src = A.p;
         bool ok = gk < K;
         if (isa) {
+            const int m = m0 + r;
+            ok = ok && m < A.rows;
             if (AMODE == OP_KC) {
-                ok = ok && m0 + r < A.rows;
-                if (ok) src = A.p + (int64_t)(m0 + r) * A.ld + gk;
-            } else {
-                const int4 ri = rinfo[r];
+                if (ok) src = A.p + (int64_t)m * A.ld + gk;
+            } else if (ok) {
+                const int hw = A.Ho * A.Wo;
+                const int b = m / hw, rem = m - b * hw;
+                const int oy = rem / A.Wo, ox = rem - oy * A.Wo;
                 const int tap = (int)(gk >> A.lc), ch = (int)gk & ((1 << A.lc) - 1);
                 const int ky = tap / 3, kx = tap - 3 * ky;
-                const int iy = ri.y + ky, ix = ri.z + kx;
-                ok = ok && ri.w && iy >= 0 && iy < A.H && ix >= 0 && ix < A.W;
-                if (ok) src = A.p + ri.x + ((int64_t)(iy * A.W + ix) << A.lc) + ch;
+                const int iy = 2 * oy - 1 + ky, ix = 2 * ox - 1 + kx;
+                ok = iy >= 0 && iy < A.H && ix >= 0 && ix < A.W;
+                if (ok) src = A.p + (((int64_t)b * A.H * A.W + iy * A.W + ix) << A.lc) + ch;
             }
         } else {
             ok = ok && n0 + r < B.rows;
@@ -464,18 +494,18 @@ __device__ __forceinline__ void tc_load_stage(bf16 *sa, bf16 *sb, const Operand 
 
 template <int AMODE, int EPI, int TN>
 __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int64_t K, Operand A, Operand B, void *C, int ldc,
-                                                 const float *__restrict__ bias, u32 *status)
+                                                        const float *__restrict__ bias, u32 *status)
 {
-    constexpr int NCOLS = TN <= 32 ? 32 : (TN <= 64 ? 64 : (TN <= 128 ? 128 : 256));
+    constexpr int NCOLS = 2 * TN <= 32 ? 32 : (2 * TN <= 64 ? 64 : (2 * TN <= 128 ? 128 : 256));
     constexpr int A_ELEMS = TC_BM * TC_BK, B_ELEMS = TN * TC_BK;
     extern __shared__ __align__(1024) uint8_t tc_smem[];
     bf16 *sA = reinterpret_cast<bf16 *>(tc_smem);
     bf16 *sB = sA + TC_STAGES * A_ELEMS;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sB + TC_STAGES * B_ELEMS);
-    int4 *rinfo = reinterpret_cast<int4 *>(bar + TC_BAR_SLOTS);  // 16-byte aligned: TC_BAR_SLOTS is even
-    u32 *tslot = reinterpret_cast<u32 *>(rinfo + TC_BM);
+    uint64_t *full = bar, *empty = bar + TC_STAGES, *ready = bar + 2 * TC_STAGES, *freeb = ready + 2;
+    u32 *tslot = reinterpret_cast<u32 *>(bar + TC_BAR_SLOTS);
     const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
-    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TN;
+    const int tiles_n = (N + TN - 1) / TN, tiles = ((M + TC_BM - 1) / TC_BM) * tiles_n;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
                      "r"((u32)NCOLS)
@@ -483,15 +513,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int64_t K,
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        for (int i = 0; i < TC_STAGES; ++i) mbar_init(&bar[i], 1);
+        for (int i = 0; i < TC_STAGES; ++i) {
+            mbar_init(&full[i], TC_PRODUCERS);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&ready[i], 1);
+            mbar_init(&freeb[i], 32 * TC_EPI_WARPS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    if (AMODE == OP_IM_KC && threadIdx.x < TC_BM) {
-        const int m = m0 + (int)threadIdx.x;
-        const int hw = A.Ho * A.Wo;
-        const int b = m / hw, rem = m - b * hw;
-        const int oy = rem / A.Wo, ox = rem - oy * A.Wo;
-        rinfo[threadIdx.x] = make_int4((b * A.H * A.W) << A.lc, 2 * oy - 1, 2 * ox - 1, m < A.rows ? 1 : 0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -499,87 +529,137 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int64_t K,
     const u32 tmem = *tslot;
     const int nk = (int)((K + TC_BK - 1) / TC_BK);
     bool failed = false;
-#pragma unroll
-    for (int st = 0; st < TC_STAGES - TC_LAG; ++st) {
-        if (st < nk) tc_load_stage<AMODE, TN>(sA + st * A_ELEMS, sB + st * B_ELEMS, A, B, K, m0, n0, (int64_t)st * TC_BK,
-                                               rinfo);
-        cp_async_commit();
-    }
-    constexpr u32 IDESC = tc_idesc(TC_BM, TN);
-    for (int it = 0; it < nk && !failed; ++it) {
-        const int buf = it % TC_STAGES;
-        cp_async_wait<TC_STAGES - TC_LAG - 1>();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-#pragma unroll
-            for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                // a K step of 16 spans two core matrices along K: 256 bytes
-                const uint64_t da = tc_desc(sA + buf * A_ELEMS + kk * 128, 128, (TC_BK / 8) * 128);
-                const uint64_t db = tc_desc(sB + buf * B_ELEMS + kk * 128, 128, (TC_BK / 8) * 128);
-                const u32 acc = (it > 0 || kk > 0) ? 1u : 0u;
-                asm volatile("{\n\t.reg .pred p;\n\t"
-                             "setp.ne.b32 p, %4, 0;\n\t"
-                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-                             "l"(da), "l"(db), "r"(IDESC), "r"(acc)
+    if (warp >= 1 && warp <= TC_PRODUCER_WARPS) {
+        // producers: one stage after another over all tiles of this CTA
+        const int p = (int)threadIdx.x - 32;
+        int64_t g = 0;  // running stage count
+        for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x) {
+            const int m0 = (t / tiles_n) * TC_BM, n0 = (t % tiles_n) * TN;
+            for (int k = 0; k < nk; ++k, ++g) {
+                const int st = (int)(g % TC_STAGES);
+                const int64_t use = g / TC_STAGES;
+                if (use > 0 && !mbar_wait(&empty[st], (u32)((use - 1) & 1))) {
+                    failed = true;
+                    break;
+                }
+                tc_load_stage<AMODE, TN>(p, sA + st * A_ELEMS, sB + st * B_ELEMS, A, B, K, m0, n0,
+                                         (int64_t)k * TC_BK);
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&full[st]))
                              : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             smem_u32(&bar[buf]))
-                         : "memory");
         }
-        const int nx = it + TC_STAGES - TC_LAG;
-        if (nx < nk) {
-            // the stage being refilled was read by the MMAs of step it - TC_LAG
-            if (it >= TC_LAG) {
-                const int pb = (it - TC_LAG) % TC_STAGES;
-                if (!mbar_wait(&bar[pb], (u32)(((it - TC_LAG) / TC_STAGES) & 1))) failed = true;
+        cp_async_wait<0>();
+    } else if (warp == 0) {
+        if (lane == 0) {
+            // MMA issue: tile i accumulates into buffer i % 2
+            constexpr u32 IDESC = tc_idesc(TC_BM, TN);
+            int64_t g = 0;
+            int i = 0;
+            for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x, ++i) {
+                const int ab = i & 1;
+                // the epilogue must have drained this accumulator (tile i - 2)
+                if (i >= 2 && !mbar_wait(&freeb[ab], (u32)(((i - 2) >> 1) & 1))) {
+                    failed = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const u32 dacc = tmem + (u32)(ab * TN);
+                for (int k = 0; k < nk; ++k, ++g) {
+                    const int st = (int)(g % TC_STAGES);
+                    if (!mbar_wait(&full[st], (u32)((g / TC_STAGES) & 1))) {
+                        failed = true;
+                        break;
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        // a K step of 16 spans two core matrices along K: 256 bytes
+                        const uint64_t da = tc_desc(sA + st * A_ELEMS + kk * 128, 128, (TC_BK / 8) * 128);
+                        const uint64_t db = tc_desc(sB + st * B_ELEMS + kk * 128, 128, (TC_BK / 8) * 128);
+                        const u32 acc = (k > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile("{\n\t.reg .pred p;\n\t"
+                                     "setp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dacc),
+                                     "l"(da), "l"(db), "r"(IDESC), "r"(acc)
+                                     : "memory");
+                    }
+                    tc_commit(&empty[st]);
+                }
+                tc_commit(&ready[ab]);
             }
-            failed = __syncthreads_or(failed);
-            if (!failed)
-                tc_load_stage<AMODE, TN>(sA + (nx % TC_STAGES) * A_ELEMS, sB + (nx % TC_STAGES) * B_ELEMS, A, B, K, m0,
-                                         n0, (int64_t)nx * TC_BK, rinfo);
         }
-        cp_async_commit();
-    }
-    cp_async_wait<0>();
-    if (!failed && nk > 0) {
-        const int lb = (nk - 1) % TC_STAGES;
-        if (!mbar_wait(&bar[lb], (u32)(((nk - 1) / TC_STAGES) & 1))) failed = true;
-    }
-    failed = __syncthreads_or(failed);
-    if (failed) {
-        if (threadIdx.x == 0) atomicOr(status, GSR_FLAG_TIMEOUT);
     } else {
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        // warp w reads lane quarter w % 4 (rows) and column half w / 4
-        const int q4 = warp & 3, half = warp >> 2;
-        const int row = m0 + q4 * 32 + lane;
+        // epilogue: warp w drains lane quarter w % 4 of each finished tile
+        const int q4 = warp & 3;
+        const bool vec = ((uintptr_t)C & 15) == 0 && ((uintptr_t)bias & 15) == 0 &&
+                         ldc % (EPI == EPI_BIAS ? 4 : 8) == 0;
+        int i = 0;
+        for (int t = blockIdx.x; t < tiles && !failed; t += gridDim.x, ++i) {
+            const int ab = i & 1;
+            if (!mbar_wait(&ready[ab], (u32)((i >> 1) & 1))) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int m0 = (t / tiles_n) * TC_BM, n0 = (t % tiles_n) * TN;
+            const int row = m0 + q4 * 32 + lane;
 #pragma unroll
-        for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 16) {
-            u32 r[16];
-            const u32 taddr = tmem + ((u32)(q4 * 32) << 16) + (u32)c0;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-                         "%15}, [%16];\n"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                           "=r"(r[14]), "=r"(r[15])
-                         : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            if (row < M) {
+            for (int c0 = 0; c0 < TN; c0 += 16) {
+                u32 r[16];
+                const u32 taddr = tmem + ((u32)(q4 * 32) << 16) + (u32)(ab * TN + c0);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                             "%14,%15}, [%16];\n"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                               "=r"(r[14]), "=r"(r[15])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                const int cb = n0 + c0;
+                if (row < M && vec && cb + 16 <= N) {
+                    // 16 consecutive outputs of this row: 16-byte stores
+                    const int64_t o = (int64_t)row * ldc + cb;
+                    if (EPI == EPI_BIAS) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int col = n0 + c0 + q;
-                    if (col >= N) continue;
-                    const float v = __uint_as_float(r[q]);
-                    const int64_t o = (int64_t)row * ldc + col;
-                    if (EPI == EPI_BIAS) ((float *)C)[o] = v + bias[col];
-                    else ((bf16 *)C)[o] = __float2bfloat16(fmaxf(v + bias[col], 0.f));
+                        for (int q = 0; q < 16; q += 4) {
+                            const float4 bq = *reinterpret_cast<const float4 *>(bias + cb + q);
+                            *reinterpret_cast<float4 *>((float *)C + o + q) =
+                                make_float4(__uint_as_float(r[q]) + bq.x, __uint_as_float(r[q + 1]) + bq.y,
+                                            __uint_as_float(r[q + 2]) + bq.z, __uint_as_float(r[q + 3]) + bq.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; q += 8) {
+                            uint4 pk;
+                            u32 *pw = reinterpret_cast<u32 *>(&pk);
+#pragma unroll
+                            for (int e = 0; e < 8; e += 2) {
+                                const __nv_bfloat162 h = __floats2bfloat162_rn(
+                                    fmaxf(__uint_as_float(r[q + e]) + bias[cb + q + e], 0.f),
+                                    fmaxf(__uint_as_float(r[q + e + 1]) + bias[cb + q + e + 1], 0.f));
+                                pw[e / 2] = *reinterpret_cast<const u32 *>(&h);
+                            }
+                            *reinterpret_cast<uint4 *>((bf16 *)C + o + q) = pk;
+                        }
+                    }
+                } else if (row < M) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int col = cb + q;
+                        if (col >= N) continue;
+                        const float v = __uint_as_float(r[q]);
+                        const int64_t o = (int64_t)row * ldc + col;
+                        if (EPI == EPI_BIAS) ((float *)C)[o] = v + bias[col];
+                        else ((bf16 *)C)[o] = __float2bfloat16(fmaxf(v + bias[col], 0.f));
+                    }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(&freeb[ab]);
         }
     }
+    failed = __syncthreads_or(failed);
+    if (failed && threadIdx.x == 0) atomicOr(status, GSR_FLAG_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -589,7 +669,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(int M, int N, int64_t K,
 template <int TN>
 constexpr size_t tc_smem_bytes()
 {
-    return (size_t)TC_STAGES * (TC_BM + TN) * TC_BK * sizeof(bf16) + TC_BAR_SLOTS * 8 + TC_BM * 16 + 16;
+    return (size_t)TC_STAGES * (TC_BM + TN) * TC_BK * sizeof(bf16) + TC_BAR_SLOTS * 8 + 16;
 }
 
 // --------------------------------------------------------- data movement
@@ -900,7 +980,10 @@ gsr_status gemm_tc_n(gsr_warmstart *w, int M, int N, int64_t K, const Operand &A
             return ws_fail(w, GSR_ERR_CUDA, "tcgen05 GEMM: shared-memory attribute refused");
         attr_set = true;
     }
-    dim3 grid((unsigned)((N + TN - 1) / TN), (unsigned)((M + TC_BM - 1) / TC_BM));
+    // persistent: as many CTAs as fit at once (shared memory and tensor memory
+    // allow two per SM), each walking tiles blockIdx.x, += gridDim.x
+    const int64_t tiles = (int64_t)((N + TN - 1) / TN) * ((M + TC_BM - 1) / TC_BM);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * 152));
     k_gemm_tc<AMODE, EPI, TN><<<grid, TC_THREADS, smem, s>>>(M, N, K, A, B, C, ldc, bias, (u32 *)w->status.p);
     return launched(w);
 }
