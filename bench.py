@@ -284,7 +284,13 @@ def run_gpu(args, rank, world):
     sc_gt = S.room_scene(N_GAUSS, seed=3)
     q, t = S.submap_views()[S.HEADLINE_VIEW]
     pose = api.make_pose(q, t)
-    ctx = api.Context()
+    if args.tuned:
+        # fixed launch configuration instead of the autotuner (for profiler
+        # runs, which must launch the same kernels as the run they explain)
+        tw, th, batch, pf, pb = (int(x) for x in args.tuned.split(","))
+        ctx = api.Context(tile=(tw, th), batch=batch, ppt_fwd=pf, ppt_bwd=pb)
+    else:
+        ctx = api.Context()
     g_gt = api.GaussianParams.from_numpy(sc_gt, dev)
     tgt = api.render_forward(ctx, g_gt, cam, pose)
     rgb_t, depth_t = tgt["rgb"].clone(), tgt["depth"].clone()
@@ -298,7 +304,11 @@ def run_gpu(args, rank, world):
         api.map_step(ctx, g, state, cam, kf, None, 1, cfg, want_stats=False)
 
     # tile shape, batch and pixels per thread from the autotuner (untimed)
-    tuned, _ = api.autotune(ctx, g, cam, [pose], reps=6)
+    if args.tuned:
+        o = ctx.options
+        tuned = dict(tile=(o.tile_w, o.tile_h), batch=o.batch, ppt_fwd=o.ppt_fwd, ppt_bwd=o.ppt_bwd, source="--tuned")
+    else:
+        tuned, _ = api.autotune(ctx, g, cam, [pose], reps=6)
     api.profile_enable(ctx, True)
     for _ in range(max(args.warmup, 3)):
         step()
@@ -488,6 +498,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuned", default="",
+                    help="tile_w,tile_h,batch,ppt_fwd,ppt_bwd: fixed blend configuration, no autotuning")
     ap.add_argument("--workload", default="map", choices=["map", "warmstart", "seed"],
                     help="map: the headline mapping iteration; warmstart: the warm-start CNN training step; "
                          "seed: sub-map seeding of one keyframe")

@@ -165,15 +165,29 @@ __global__ void __launch_bounds__(RX) k_radix_digit_base(u32 *ghist)
     h[threadIdx.x] = sc[threadIdx.x] - v;
 }
 
+// Lanes of the warp whose digit equals this lane's (digit RX marks "no key"):
+// one ballot per digit bit.
+__device__ __forceinline__ u32 digit_peers(u32 dg)
+{
+    u32 peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b <= RX_BITS; ++b) {
+        const bool bit = (dg >> b) & 1u;
+        const u32 m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+}
+
 // One stable pass.  Blocks take 2048-key tiles in launch order (atomic ticket,
 // so every tile a block waits for belongs to a block that already runs);
-// each warp ranks its consecutive keys in order with __match_any_sync (keeping
+// each warp ranks its consecutive keys in order with digit_peers (keeping
 // each key's rank among the warp's keys of its digit); the
 // block publishes its digit counts, looks back over the preceding tiles for
 // their running totals, stages its keys in shared memory in digit order and
 // writes them out so that equal digits land in consecutive addresses.
 template <int ROUNDS>
-__global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__restrict__ kin, const u32 *__restrict__ vin,
+__global__ void __launch_bounds__(RX_THREADS, 4) k_radix_onesweep(const u32 *__restrict__ kin, const u32 *__restrict__ vin,
                                                                u32 *__restrict__ kout, u32 *__restrict__ vout,
                                                                int64_t n_cap, const u32 *d_n, int shift,
                                                                const u32 *__restrict__ digit_base,
@@ -194,22 +208,24 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__rest
     if (base >= n) return;  // no key in this tile (and none in any later tile)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     u32 k[ROUNDS], v[ROUNDS], rk[ROUNDS];
-    int dg[ROUNDS];
     const int64_t wbase = base + (int64_t)w * SPAN;
     const u32 lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
         const int64_t i = wbase + r * 32 + lane;
-        const bool ok = i < n;
-        k[r] = ok ? kin[i] : 0u;
-        v[r] = ok ? vin[i] : 0u;
-        dg[r] = ok ? (int)((k[r] >> shift) & (RX - 1)) : RX;  // RX = no key
-        const u32 peers = __match_any_sync(0xffffffffu, dg[r]);
+        k[r] = i < n ? kin[i] : 0u;
+        v[r] = i < n ? vin[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const bool ok = wbase + r * 32 + lane < n;
+        const u32 dg = ok ? (k[r] >> shift) & (RX - 1) : (u32)RX;  // RX = no key
+        const u32 peers = digit_peers(dg);
         // rank of this key among the warp's keys of its digit, in input order
-        const u32 before = ok ? wcnt[w][dg[r]] : 0u;
-        rk[r] = before + __popc(peers & lt);
+        const u32 before = ok ? wcnt[w][dg] : 0u;
+        rk[r] = ok ? before + __popc(peers & lt) : ~0u;  // ~0: no key
         __syncwarp();
-        if (ok && lane == __ffs(peers) - 1) wcnt[w][dg[r]] = before + __popc(peers);
+        if (ok && lane == __ffs(peers) - 1) wcnt[w][dg] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -268,8 +284,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_onesweep(const u32 *__rest
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
-        if (dg[r] < RX) {
-            const u32 pos = wcnt[w][dg[r]] + rk[r];  // the warp's start for the digit + rank
+        if (rk[r] != ~0u) {
+            const u32 pos = wcnt[w][(k[r] >> shift) & (RX - 1)] + rk[r];  // the warp's start for the digit + rank
             s_key[pos] = k[r];
             s_val[pos] = v[r];
         }
