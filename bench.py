@@ -379,6 +379,10 @@ def run_gpu(args, rank, world):
                     traffic=measured_traffic(dom), units=f"{e_bwd} pixel-Gaussian evaluations x "
                                        f"{FLOPS_BWD_EVAL if dom == 'blend_bwd' else FLOPS_FWD_EVAL} flops",
                     peak_note=f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_mhz']:.0f} MHz (derived)")
+        # the same units measured on this device (FMA and ex2 throughput probes, after the timed region)
+        meas = api.probe_peaks()
+        roof.update(peak_measured=meas["fp32_tflops"], frac_of_measured=ach / meas["fp32_tflops"],
+                    exp_gps_measured=meas["exp_gps"])
     else:
         per = {"bin": 68 * n + 96 * V + 44 * I, "loss": 56 * P, "project_bwd": 56 * n + 152 * V,
                "adam": 392 * n}.get(dom, step_bytes)
@@ -491,6 +495,67 @@ def run_seed(args):
     print(json.dumps(line), flush=True)
 
 
+def run_map8(args):
+    """The batched sub-map mapping iteration: all 8 keyframes of the 500k
+    sub-map (1200x680) in one gsr_map_step per iteration (persistent blend
+    over a (keyframe, tile) queue, per-Gaussian gradients summed with uniform
+    weights, one Adam step), graph-captured; L2 flushed between steps."""
+    import torch
+    from paper_2312_10070_gb300 import api, synth as S
+    spec = S.camera_room()
+    cam = api.camera_from_spec(spec)
+    sc_gt = S.room_scene(N_GAUSS, seed=3)
+    ctx = api.Context()
+    g_gt = api.GaussianParams.from_numpy(sc_gt)
+    poses = [api.make_pose(q, t) for q, t in S.submap_views()]
+    kf = []
+    for p in poses:
+        r = api.render_forward(ctx, g_gt, cam, p)
+        kf.append((p, r["rgb"].clone(), r["depth"].clone()))
+    g = api.GaussianParams.from_numpy(S.noisy_copy(sc_gt, seed=3))
+    state = api.AdamMoments(g)
+    cfg = api.MapConfig()
+    tuned, _ = api.autotune(ctx, g, cam, poses, reps=3)
+    evals = 0
+    for p in poses:
+        r = api.render_forward(ctx, g, cam, p)
+        evals += int((r["last_idx"].to(torch.int64) + 1).sum())
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    api.profile_enable(ctx, True)
+    for _ in range(max(args.warmup, 3)):
+        api.map_step(ctx, g, state, cam, kf, None, 1, cfg, want_stats=False)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phase_ms = {k: [] for k in api.PHASES}
+    launches0 = ctx.kernel_launches
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        api.map_step(ctx, g, state, cam, kf, None, 1, cfg, want_stats=False)
+        ev[i][1].record()
+        for k, v in api.profile_read(ctx).items():
+            phase_ms[k].append(v)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    avg = {k: float(np.mean([x for x in v if x >= 0])) if any(x >= 0 for x in v) else None
+           for k, v in phase_ms.items()}
+    roof = None
+    if avg.get("blend_bwd"):
+        ach = FLOPS_BWD_EVAL * evals / (avg["blend_bwd"] / 1e3) / 1e12
+        pk = peaks()
+        roof = dict(bound="alu", kernel="blend_bwd", achieved=ach, peak=fp32_peak_tflops(pk["sm_mhz"]),
+                    unit="TFLOP/s", traffic=None,
+                    units=f"{evals} pixel-Gaussian evaluations over 8 keyframes x {FLOPS_BWD_EVAL} flops")
+        roof["frac"] = ach / roof["peak"]
+    line = dict(metric="batched map_step iters/s (8 keyframes at 1200x680, 500k Gaussians)", value=1e3 / ms,
+                unit="iters/s", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload="gsr_map_step over the 8 sub-map keyframes of room_scene seed 3, one Adam step "
+                                     "per iteration", keyframes=8, autotuned=tuned, l2="flushed between steps"),
+                phases_ms=avg, roofline=roof, gpu_launches=int(ctx.kernel_launches - launches0))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -500,10 +565,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuned", default="",
                     help="tile_w,tile_h,batch,ppt_fwd,ppt_bwd: fixed blend configuration, no autotuning")
-    ap.add_argument("--workload", default="map", choices=["map", "warmstart", "seed"],
-                    help="map: the headline mapping iteration; warmstart: the warm-start CNN training step; "
-                         "seed: sub-map seeding of one keyframe")
+    ap.add_argument("--workload", default="map", choices=["map", "map8", "warmstart", "seed"],
+                    help="map: the headline mapping iteration; map8: the batched 8-keyframe mapping iteration; "
+                         "warmstart: the warm-start CNN training step; seed: sub-map seeding of one keyframe")
     args = ap.parse_args()
+    if args.workload == "map8":
+        return run_map8(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
     if args.workload == "seed":

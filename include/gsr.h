@@ -419,6 +419,20 @@ GSR_API gsr_status gsr_prune(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state 
 GSR_API gsr_status gsr_merge_submap(gsr_ctx *ctx, gsr_gaussians_mut *global, int64_t n_global, int64_t capacity,
                                     const gsr_gaussians *sub, float rho, int64_t *n_added, void *stream);
 
+/* Throughput probes (no counterpart in the paper): the measured denominators
+ * of the ALU rooflines of the blend kernels.  gsr_probe_fma launches `blocks`
+ * blocks of 256 threads; each thread runs `iters` rounds of 8 independent
+ * FP32 fused multiply-adds (16 FLOP per round), so one launch performs
+ * blocks * 256 * iters * 16 FLOP.  gsr_probe_exp does the same with 8
+ * independent base-2 exponentials (ex2.approx) per round: blocks * 256 *
+ * iters * 8 exponentials.  out: caller-owned device float[blocks * 256]
+ * (a sink so the work cannot be elided; its values are meaningless).
+ * iters must be a positive multiple of 32.  Asynchronous on `stream`; time
+ * them with events on that stream.  GSR_ERR_INVALID_ARG on bad sizes,
+ * GSR_ERR_CUDA if the launch fails. */
+GSR_API gsr_status gsr_probe_fma(float *out, int32_t blocks, int32_t iters, void *stream);
+GSR_API gsr_status gsr_probe_exp(float *out, int32_t blocks, int32_t iters, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -397,6 +397,29 @@ def merge_submap(ctx: Context, global_map: SubMap, sub: GaussianParams, rho: flo
     return int(n.value)
 
 
+# ------------------------------------------------------ throughput probes
+def probe_peaks(blocks: int = 152 * 8, iters: int = 16384, reps: int = 5):
+    """Measured FP32 FMA rate (TFLOP/s) and base-2 exponential rate (G/s) of
+    the current device (gsr_probe_fma / gsr_probe_exp), best of `reps`
+    launches timed with CUDA events on the current stream."""
+    lib = L.load()
+    out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    res = {}
+    for name, fn, per in (("fp32_tflops", lib.gsr_probe_fma, 16), ("exp_gps", lib.gsr_probe_exp, 8)):
+        L.check(fn(ctypes.c_void_p(out.data_ptr()), blocks, 32, _stream()))  # warm-up
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            L.check(fn(ctypes.c_void_p(out.data_ptr()), blocks, iters, _stream()))
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        ops = blocks * 256 * iters * per
+        res[name] = ops / best / (1e12 if name == "fp32_tflops" else 1e9)
+    return res
+
+
 # ----------------------------------------------------------- pose helpers
 def quat_mul(a, b):
     aw, ax, ay, az = a

@@ -68,64 +68,96 @@ __device__ __forceinline__ void adam_chunk(const FlatSeg &sgm, int64_t c4, const
     }
 }
 
-// log-scales of Gaussians [i0, i0 + cnt) with the L_reg gradient; returns their L_reg terms
+// one Gaussian's three log-scales (in registers) with the L_reg gradient; returns its L_reg term
+__device__ __forceinline__ float adam_log_scale3(float *p, const float *g, float *m, float *v, float rw,
+                                                 const FlatSeg &sgm, const gsr_adam_opts &o, float bc1, float bc2)
+{
+    float sc[3], sb = 0.f, lsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        sc[k] = expf(p[k]);
+        sb += sc[k];
+    }
+    sb *= (1.f / 3.f);
+    float sg[3], ssum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lsum += fabsf(sc[k] - sb);
+        sg[k] = sgnf(sc[k] - sb);
+        ssum += sg[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float gk = g[k] + rw * (sg[k] - ssum * (1.f / 3.f)) * sc[k];
+        adam1(p[k], gk, m[k], v[k], sgm.lr, o.beta1, o.beta2, o.eps, bc1, bc2);
+    }
+    return lsum;
+}
+
+// log-scales of Gaussians [i0, i0 + cnt) with the L_reg gradient; returns their L_reg terms.
+// A full group of 4 Gaussians is 12 floats = 3 float4 per array, all loaded before any update.
 __device__ __forceinline__ float adam_log_scales(const FlatSeg &sgm, int64_t i0, int cnt, float rw,
                                                  const gsr_adam_opts &o, float bc1, float bc2)
 {
     float lsum = 0.f;
+    if (cnt == 4) {
+        const int64_t c4 = 3 * i0 / 4;  // i0 is a multiple of 4
+        float P[12], G[12], M[12], Vv[12];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            *reinterpret_cast<float4 *>(P + 4 * k) = reinterpret_cast<const float4 *>(sgm.p)[c4 + k];
+            *reinterpret_cast<float4 *>(G + 4 * k) = reinterpret_cast<const float4 *>(sgm.g)[c4 + k];
+            *reinterpret_cast<float4 *>(M + 4 * k) = reinterpret_cast<const float4 *>(sgm.m)[c4 + k];
+            *reinterpret_cast<float4 *>(Vv + 4 * k) = reinterpret_cast<const float4 *>(sgm.v)[c4 + k];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            lsum += adam_log_scale3(P + 3 * q, G + 3 * q, M + 3 * q, Vv + 3 * q, rw, sgm, o, bc1, bc2);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            reinterpret_cast<float4 *>(sgm.p)[c4 + k] = *reinterpret_cast<const float4 *>(P + 4 * k);
+            reinterpret_cast<float4 *>(sgm.m)[c4 + k] = *reinterpret_cast<const float4 *>(M + 4 * k);
+            reinterpret_cast<float4 *>(sgm.v)[c4 + k] = *reinterpret_cast<const float4 *>(Vv + 4 * k);
+        }
+        return lsum;
+    }
     for (int q = 0; q < cnt; ++q) {
         const int64_t b = 3 * (i0 + q);
-        float sc[3], sb = 0.f;
+        float P[3], G[3], M[3], Vv[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            sc[k] = expf(sgm.p[b + k]);
-            sb += sc[k];
+            P[k] = sgm.p[b + k];
+            G[k] = sgm.g[b + k];
+            M[k] = sgm.m[b + k];
+            Vv[k] = sgm.v[b + k];
         }
-        sb *= (1.f / 3.f);
-        float sg[3], ssum = 0.f;
+        lsum += adam_log_scale3(P, G, M, Vv, rw, sgm, o, bc1, bc2);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            lsum += fabsf(sc[k] - sb);
-            sg[k] = sgnf(sc[k] - sb);
-            ssum += sg[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float gk = sgm.g[b + k] + rw * (sg[k] - ssum * (1.f / 3.f)) * sc[k];
-            adam1(sgm.p[b + k], gk, sgm.m[b + k], sgm.v[b + k], sgm.lr, o.beta1, o.beta2, o.eps, bc1, bc2);
+            sgm.p[b + k] = P[k];
+            sgm.m[b + k] = M[k];
+            sgm.v[b + k] = Vv[k];
         }
     }
     return lsum;
 }
 
-// threads [0, nls) take log-scale groups of 4 Gaussians; the rest take float4
-// chunks of the other four arrays, in order
-__global__ void __launch_bounds__(256) k_adam(gsr_gaussians_mut g, gsr_gaussian_grads gr, gsr_adam_state st,
-                                              gsr_adam_opts o, const float *__restrict__ bc, float *__restrict__ part,
-                                              int64_t nls, int64_t c_mean, int64_t c_quat, int64_t c_op,
-                                              int64_t c_rgb)
+// Log-scales with the L_reg gradient: one group of 4 Gaussians per thread
+// (3 float4 per array, all loads issued before any update); per-block L_reg
+// partial sums in part[blockIdx.x].  A kernel of its own: its 48 live values
+// per thread would halve the occupancy of the flat kernel below.
+__global__ void __launch_bounds__(256) k_adam_log_scale(gsr_gaussians_mut g, gsr_gaussian_grads gr,
+                                                        gsr_adam_state st, gsr_adam_opts o,
+                                                        const float *__restrict__ bc, float *__restrict__ part,
+                                                        int64_t nls)
 {
     const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    const float bc1 = bc[0], bc2 = bc[1];
     float lreg = 0.f;
     if (t < nls) {
         const FlatSeg sg{g.log_scale, st.m_log_scale, st.v_log_scale, gr.log_scale, o.lr_log_scale, 3 * g.n};
         const int64_t i0 = 4 * t;
         const int cnt = (int)min((int64_t)4, g.n - i0);
-        lreg = adam_log_scales(sg, i0, cnt, o.w_reg / (float)g.n, o, bc1, bc2);
-    } else {
-        int64_t c = t - nls;
-        if (c < c_mean) {
-            adam_chunk(FlatSeg{g.mean, st.m_mean, st.v_mean, gr.mean, o.lr_mean, 3 * g.n}, c, o, bc1, bc2);
-        } else if ((c -= c_mean) < c_quat) {
-            adam_chunk(FlatSeg{g.quat, st.m_quat, st.v_quat, gr.quat, o.lr_quat, 4 * g.n}, c, o, bc1, bc2);
-        } else if ((c -= c_quat) < c_op) {
-            adam_chunk(FlatSeg{g.opacity_logit, st.m_opacity_logit, st.v_opacity_logit, gr.opacity_logit,
-                                o.lr_opacity, g.n},
-                       c, o, bc1, bc2);
-        } else if ((c -= c_op) < c_rgb) {
-            adam_chunk(FlatSeg{g.rgb, st.m_rgb, st.v_rgb, gr.rgb, o.lr_rgb, 3 * g.n}, c, o, bc1, bc2);
-        }
+        lreg = adam_log_scales(sg, i0, cnt, o.w_reg / (float)g.n, o, bc[0], bc[1]);
     }
     if (part) {
         __shared__ float red[8];
@@ -138,6 +170,26 @@ __global__ void __launch_bounds__(256) k_adam(gsr_gaussians_mut g, gsr_gaussian_
             for (int k = 0; k < 8; ++k) tt += red[k];
             part[blockIdx.x] = tt;
         }
+    }
+}
+
+// the other four arrays: float4 chunks of mean, quaternion, opacity, colour, in order
+__global__ void __launch_bounds__(256) k_adam(gsr_gaussians_mut g, gsr_gaussian_grads gr, gsr_adam_state st,
+                                              gsr_adam_opts o, const float *__restrict__ bc, int64_t c_mean,
+                                              int64_t c_quat, int64_t c_op, int64_t c_rgb)
+{
+    int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const float bc1 = bc[0], bc2 = bc[1];
+    if (c < c_mean) {
+        adam_chunk(FlatSeg{g.mean, st.m_mean, st.v_mean, gr.mean, o.lr_mean, 3 * g.n}, c, o, bc1, bc2);
+    } else if ((c -= c_mean) < c_quat) {
+        adam_chunk(FlatSeg{g.quat, st.m_quat, st.v_quat, gr.quat, o.lr_quat, 4 * g.n}, c, o, bc1, bc2);
+    } else if ((c -= c_quat) < c_op) {
+        adam_chunk(FlatSeg{g.opacity_logit, st.m_opacity_logit, st.v_opacity_logit, gr.opacity_logit, o.lr_opacity,
+                            g.n},
+                   c, o, bc1, bc2);
+    } else if ((c -= c_op) < c_rgb) {
+        adam_chunk(FlatSeg{g.rgb, st.m_rgb, st.v_rgb, gr.rgb, o.lr_rgb, 3 * g.n}, c, o, bc1, bc2);
     }
 }
 
@@ -268,8 +320,10 @@ gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads
     const int64_t n = g->n > 0 ? g->n : 1;
     const int64_t nls = ceil_div(n, 4), c_mean = ceil_div(3 * n, 4), c_quat = n, c_op = ceil_div(n, 4),
                   c_rgb = ceil_div(3 * n, 4);
-    const int64_t threads = vec4 ? nls + c_mean + c_quat + c_op + c_rgb : n;
-    const unsigned nb = (unsigned)ceil_div(threads, 256);
+    // the scalar path: one Gaussian per thread, all arrays; the vector path: log-scale
+    // groups (nb blocks, which also write the L_reg partial sums) and flat chunks
+    const unsigned nb = (unsigned)ceil_div(vec4 ? nls : n, 256);
+    const unsigned nb_flat = (unsigned)ceil_div(c_mean + c_quat + c_op + c_rgb, 256);
     GSR_TRY(ensure_buf(ctx, ctx->small, 256 * sizeof(float)));
     float *bc = (float *)ctx->small.p;  // [0..1] bias corrections
     float *part = nullptr;
@@ -278,9 +332,14 @@ gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads
         part = (float *)ctx->pose_part.p;
     }
     k_adam_prep<<<1, 1, 0, s>>>(st->step, o->beta1, o->beta2, bc);
-    if (vec4) k_adam<<<nb, 256, 0, s>>>(*g, *gr, *st, *o, bc, part, nls, c_mean, c_quat, c_op, c_rgb);
-    else k_adam_scalar<<<nb, 256, 0, s>>>(*g, *gr, *st, *o, bc, part);
-    ctx->launches += 2;
+    if (vec4) {
+        k_adam_log_scale<<<nb, 256, 0, s>>>(*g, *gr, *st, *o, bc, part, nls);
+        k_adam<<<nb_flat, 256, 0, s>>>(*g, *gr, *st, *o, bc, c_mean, c_quat, c_op, c_rgb);
+        ctx->launches += 3;
+    } else {
+        k_adam_scalar<<<nb, 256, 0, s>>>(*g, *gr, *st, *o, bc, part);
+        ctx->launches += 2;
+    }
     if (loss_reg_dev) {
         k_lreg_final<<<1, 1024, 0, s>>>(part, (int)nb, o->w_reg / (float)(g->n > 0 ? g->n : 1), loss_reg_dev);
         ctx->launches += 1;

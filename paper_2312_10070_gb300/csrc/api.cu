@@ -211,13 +211,16 @@ void gsr_destroy(gsr_ctx *c)
     ViewScratch &V = c->view;
     DevBuf *bufs[] = {&V.rec, &V.flag, &V.compact, &V.rank_of_gid, &V.dkeys[0], &V.dkeys[1], &V.dvals[0], &V.dvals[1],
                       &V.rec_sorted, &V.tcount, &V.inst_off, &V.tkeys[0], &V.tkeys[1], &V.tvals[0], &V.tvals[1],
-                      &V.ranges, &V.g2d, &V.counters, &V.pose, &c->scan_tmp, &c->radix_hist, &c->pose_part,
+                      &V.ranges, &V.g2d, &V.counters, &V.pose, &V.scan_tmp, &V.radix_hist, &V.loss_maps,
+                      &V.loss_part, &c->scan_tmp,
+                      &c->radix_hist, &c->pose_part,
                       &c->loss_part, &c->loss_maps, &c->img_tmp, &c->small, &c->grads};
     for (DevBuf *b : bufs) free_buf(*b);
     for (ViewScratch &W : c->mv) {
         DevBuf *vb[] = {&W.rec, &W.flag, &W.compact, &W.rank_of_gid, &W.dkeys[0], &W.dkeys[1], &W.dvals[0],
                         &W.dvals[1], &W.rec_sorted, &W.tcount, &W.inst_off, &W.tkeys[0], &W.tkeys[1], &W.tvals[0],
-                        &W.tvals[1], &W.ranges, &W.g2d, &W.counters, &W.pose};
+                        &W.tvals[1], &W.ranges, &W.g2d, &W.counters, &W.pose, &W.scan_tmp, &W.radix_hist,
+                        &W.loss_maps, &W.loss_part};
         for (DevBuf *b : vb) free_buf(*b);
     }
     DevBuf *mb[] = {&c->mv_frames, &c->mv_desc, &c->mv_pview, &c->mv_keys[0], &c->mv_keys[1], &c->mv_items[0],
@@ -230,6 +233,11 @@ void gsr_destroy(gsr_ctx *c)
     if (c->track_graph) cudaGraphExecDestroy(c->track_graph);
     if (c->map_graph) cudaGraphExecDestroy(c->map_graph);
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    for (int i = 0; i < gsr_ctx::N_SIDE; ++i) {
+        if (c->side[i]) cudaStreamDestroy(c->side[i]);
+        if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
+    }
     for (int i = 0; i < 2 * PROF_NSLOT; ++i)
         if (c->prof_ev[i]) cudaEventDestroy(c->prof_ev[i]);
     delete c;
@@ -638,12 +646,30 @@ static gsr_status map_iter_multi(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_st
     GSR_CUDA(ctx, cudaMemsetAsync(sm + SM_MAPLOSS, 0, sizeof(float), s));
     Params P{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, n};
 
+    // the keyframes' binning chains are independent (each has its own scratch):
+    // fork them onto side streams, keyframe k on stream k % N_SIDE, and join
+    const int ns = std::min(n_kf, gsr_ctx::N_SIDE);
+    if (!ctx->fork_ev) {
+        if (capturing) return gsr_fail(ctx, GSR_ERR_STATE, "side streams must exist before capture");
+        GSR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+        for (int i = 0; i < gsr_ctx::N_SIDE; ++i) {
+            GSR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking));
+            GSR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming));
+        }
+    }
     GSR_TRY(prof_mark(ctx, PROF_BIN, false, s));
+    GSR_CUDA(ctx, cudaEventRecord(ctx->fork_ev, s));
+    for (int i = 0; i < ns; ++i) GSR_CUDA(ctx, cudaStreamWaitEvent(ctx->side[i], ctx->fork_ev, 0));
     for (int k = 0; k < n_kf; ++k) {
         ViewScratch &V = ctx->mv[k];
+        cudaStream_t sk = ctx->side[k % ns];
         GSR_TRY(ensure_buf(ctx, V.pose, GSR_POSE_WORDS * sizeof(float)));
-        GSR_TRY(launch_set_pose(ctx, (float *)V.pose.p, kfs[k].pose, s));
-        GSR_TRY(run_binning(ctx, V, P, ck, (float *)V.pose.p, grow, s));
+        GSR_TRY(launch_set_pose(ctx, (float *)V.pose.p, kfs[k].pose, sk));
+        GSR_TRY(run_binning(ctx, V, P, ck, (float *)V.pose.p, grow, sk));
+    }
+    for (int i = 0; i < ns; ++i) {
+        GSR_CUDA(ctx, cudaEventRecord(ctx->join_ev[i], ctx->side[i]));
+        GSR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->join_ev[i], 0));
     }
     // per-keyframe descriptors (device pointers only; fixed once sized)
     std::vector<BlendView> bv(n_kf);
@@ -677,11 +703,22 @@ static gsr_status map_iter_multi(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_st
     GSR_TRY(run_blend_multi(ctx, ck, false, dv, items[0], n_kf * tiles, (u32 *)ctx->mv_counter.p, s));
     GSR_TRY(prof_mark(ctx, PROF_FWD, true, s));
     GSR_TRY(prof_mark(ctx, PROF_LOSS, false, s));
+    // per-keyframe losses on the side streams (own scratch), the scalar sums in order here
+    GSR_CUDA(ctx, cudaEventRecord(ctx->fork_ev, s));
+    for (int i = 0; i < ns; ++i) GSR_CUDA(ctx, cudaStreamWaitEvent(ctx->side[i], ctx->fork_ev, 0));
     for (int k = 0; k < n_kf; ++k) {
         float *f = frames + (size_t)k * 12 * HW;
-        GSR_TRY(run_loss_map(ctx, ck.W, ck.H, f, f + 3 * HW, kfs[k].rgb, kfs[k].depth, o->lambda_ssim, o->w_color,
-                             o->w_depth, w[k], f + 7 * HW, f + 10 * HW, sm + SM_MAPLOSS, true, s));
+        GSR_TRY(run_loss_map_kernels(ctx, &ctx->mv[k], ck.W, ck.H, f, f + 3 * HW, kfs[k].rgb, kfs[k].depth,
+                                     o->lambda_ssim, o->w_color, o->w_depth, w[k], f + 7 * HW, f + 10 * HW,
+                                     ctx->side[k % ns]));
     }
+    for (int i = 0; i < ns; ++i) {
+        GSR_CUDA(ctx, cudaEventRecord(ctx->join_ev[i], ctx->side[i]));
+        GSR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->join_ev[i], 0));
+    }
+    for (int k = 0; k < n_kf; ++k)
+        GSR_TRY(run_loss_map_final(ctx, &ctx->mv[k], ck.W, ck.H, o->lambda_ssim, o->w_color, o->w_depth, w[k],
+                                   sm + SM_MAPLOSS, true, s));
     GSR_TRY(prof_mark(ctx, PROF_LOSS, true, s));
     GSR_TRY(prof_mark(ctx, PROF_BWD, false, s));
     for (int k = 0; k < n_kf; ++k) GSR_TRY(zero_g2d(ctx, ctx->mv[k], s));

@@ -59,6 +59,10 @@ struct ViewScratch {
     DevBuf g2d;         // float x12 per rank: image-space gradients
     DevBuf counters;    // u32[CNT_WORDS]
     DevBuf pose;        // float[8]: q(4), t(3)
+    DevBuf scan_tmp;    // block sums of this view's scans
+    DevBuf radix_hist;  // digit histograms and look-back of this view's sorts
+    DevBuf loss_maps;   // SSIM adjoint maps of this view's mapping loss (batched mapping)
+    DevBuf loss_part;   // per-block partial sums of this view's mapping loss
     int64_t cap_n = 0, cap_i = 0, cap_t = 0;
     // identity of the last forward, to decide whether the saved lists are valid
     uint64_t generation = 0;
@@ -126,6 +130,11 @@ struct gsr_ctx {
     // batched multi-keyframe mapping: per-keyframe scratch and frames
     std::vector<ViewScratch> mv;
     DevBuf mv_frames, mv_desc, mv_pview, mv_keys[2], mv_items[2], mv_counter;
+    // side streams of the batched binning (one chain of binning kernels per
+    // keyframe runs on each; forked from and joined to the caller's stream)
+    static constexpr int N_SIDE = 8;
+    cudaStream_t side[N_SIDE] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[N_SIDE] = {};
     std::vector<BlendView> mv_desc_host;
     std::vector<ProjView> mv_pview_host;
     SeedScratch seed;
@@ -151,13 +160,15 @@ static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // --------------------------------------------------------- scan / radix sort
 // Device-wide exclusive scan of u32.  The element count is min(*d_n, n_cap)
 // when d_n is given, else n_cap.  The total is written to *d_total (nullable).
+// tmp: the block-sum scratch (nullptr: the context's).
 gsr_status scan_exclusive(gsr_ctx *ctx, const u32 *in, u32 *out, int64_t n_cap, const u32 *d_n,
-                          u32 *d_total, cudaStream_t s);
+                          u32 *d_total, cudaStream_t s, DevBuf *tmp = nullptr);
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits), 8 bits
 // per pass.  The element count is read on the device from *d_n (<= n_cap).
 // The sorted pairs end in keys[0]/vals[0].
+// hist: the histogram / look-back scratch (nullptr: the context's).
 gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_cap, const u32 *d_n,
-                            int bits, cudaStream_t s);
+                            int bits, cudaStream_t s, DevBuf *hist = nullptr);
 
 // Grows the tile-instance capacity of V (and the sort scratch sized from it).
 gsr_status grow_instance_capacity(gsr_ctx *ctx, ViewScratch &V, int64_t c);
@@ -265,10 +276,20 @@ gsr_status run_project_backward(gsr_ctx *ctx, ViewScratch &V, const Params &P, c
 // adds the gradients of every keyframe's image-space gradients to dg (one pass)
 gsr_status run_project_backward_multi(gsr_ctx *ctx, const Params &P, const CamK &ck, const ProjView *views,
                                       int n_views, gsr_gaussian_grads *dg, cudaStream_t s);
+// The mapping loss of one view: run_loss_map = run_loss_map_kernels (SSIM
+// forward and backward; the per-pixel adjoints) + run_loss_map_final (the
+// scalar).  V (nullable): the view whose loss scratch and counters to use,
+// so that several views' kernels may run concurrently on different streams
+// (their finals then run in order on one stream).
 gsr_status run_loss_map(gsr_ctx *ctx, int W, int H, const float *rgb, const float *depth,
                         const float *rgb_t, const float *depth_t, float lam, float wc, float wd,
                         float scale, float *d_rgb, float *d_depth, float *loss_dev, bool accumulate_loss,
                         cudaStream_t s);
+gsr_status run_loss_map_kernels(gsr_ctx *ctx, ViewScratch *V, int W, int H, const float *rgb, const float *depth,
+                                const float *rgb_t, const float *depth_t, float lam, float wc, float wd,
+                                float scale, float *d_rgb, float *d_depth, cudaStream_t s);
+gsr_status run_loss_map_final(gsr_ctx *ctx, ViewScratch *V, int W, int H, float lam, float wc, float wd,
+                              float scale, float *loss_dev, bool accumulate_loss, cudaStream_t s);
 gsr_status run_loss_track(gsr_ctx *ctx, int W, int H, const float *rgb, const float *depth,
                           const float *alpha, const float *rgb_t, const float *depth_t, float lam_c,
                           float k_med, float apow, float *d_rgb, float *d_depth, float *loss_dev,

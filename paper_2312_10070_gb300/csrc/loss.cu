@@ -437,28 +437,54 @@ __global__ void k_track_final(const float *__restrict__ part, int nb, const u32 
 
 } // namespace
 
-gsr_status run_loss_map(gsr_ctx *ctx, int W, int H, const float *rgb, const float *depth, const float *rgb_t,
-                        const float *depth_t, float lam, float wc, float wd, float scale, float *d_rgb,
-                        float *d_depth, float *loss_dev, bool accumulate_loss, cudaStream_t s)
+gsr_status run_loss_map_kernels(gsr_ctx *ctx, ViewScratch *V, int W, int H, const float *rgb, const float *depth,
+                                const float *rgb_t, const float *depth_t, float lam, float wc, float wd,
+                                float scale, float *d_rgb, float *d_depth, cudaStream_t s)
 {
     const int64_t HW = (int64_t)W * H;
     dim3 grid((unsigned)ceil_div(W, TX), (unsigned)ceil_div(H, TY));
     const int nb = (int)(grid.x * grid.y);
-    GSR_TRY(ensure_buf(ctx, ctx->loss_maps, sizeof(float) * 9 * (size_t)HW));
-    GSR_TRY(ensure_buf(ctx, ctx->loss_part, sizeof(float) * 3 * (size_t)nb));
-    GSR_TRY(ensure_buf(ctx, ctx->view.counters, sizeof(u32) * CNT_WORDS));
-    u32 *cnt = (u32 *)ctx->view.counters.p;
+    ViewScratch &cv = V ? *V : ctx->view;
+    DevBuf &maps = V ? V->loss_maps : ctx->loss_maps, &part = V ? V->loss_part : ctx->loss_part;
+    GSR_TRY(ensure_buf(ctx, maps, sizeof(float) * 9 * (size_t)HW));
+    GSR_TRY(ensure_buf(ctx, part, sizeof(float) * 3 * (size_t)nb));
+    GSR_TRY(ensure_buf(ctx, cv.counters, sizeof(u32) * CNT_WORDS));
+    u32 *cnt = (u32 *)cv.counters.p;
     GSR_CUDA(ctx, cudaMemsetAsync(cnt + CNT_NVALID, 0, sizeof(u32), s));
     const float inv3hw = 1.f / (3.f * (float)HW);
-    k_ssim_fwd<<<grid, 256, 0, s>>>(W, H, rgb, rgb_t, depth, depth_t, -scale * wc * lam * inv3hw,
-                                    (float *)ctx->loss_maps.p, (float *)ctx->loss_part.p, cnt + CNT_NVALID);
-    k_ssim_bwd<<<grid, 256, 0, s>>>(W, H, rgb, rgb_t, depth, depth_t, (float *)ctx->loss_maps.p,
+    k_ssim_fwd<<<grid, 256, 0, s>>>(W, H, rgb, rgb_t, depth, depth_t, -scale * wc * lam * inv3hw, (float *)maps.p,
+                                    (float *)part.p, cnt + CNT_NVALID);
+    k_ssim_bwd<<<grid, 256, 0, s>>>(W, H, rgb, rgb_t, depth, depth_t, (float *)maps.p,
                                     scale * wc * (1.f - lam) * inv3hw, scale * wd, cnt + CNT_NVALID, d_rgb, d_depth);
-    k_loss_map_final<<<1, 96, 0, s>>>((float *)ctx->loss_part.p, nb, cnt + CNT_NVALID, inv3hw, lam, wc, wd, scale,
-                                      loss_dev, accumulate_loss ? 1 : 0, cnt + CNT_STATUS);
-    ctx->launches += 3;
+    ctx->launches += 2;
     GSR_LAUNCHED(ctx);
     return GSR_OK;
+}
+
+gsr_status run_loss_map_final(gsr_ctx *ctx, ViewScratch *V, int W, int H, float lam, float wc, float wd,
+                              float scale, float *loss_dev, bool accumulate_loss, cudaStream_t s)
+{
+    const int64_t HW = (int64_t)W * H;
+    const int nb = (int)(ceil_div(W, TX) * ceil_div(H, TY));
+    ViewScratch &cv = V ? *V : ctx->view;
+    DevBuf &part = V ? V->loss_part : ctx->loss_part;
+    GSR_TRY(ensure_buf(ctx, ctx->view.counters, sizeof(u32) * CNT_WORDS));
+    const u32 *cnt = (const u32 *)cv.counters.p;
+    u32 *status = (u32 *)ctx->view.counters.p + CNT_STATUS;  // the context's status word
+    k_loss_map_final<<<1, 96, 0, s>>>((float *)part.p, nb, cnt + CNT_NVALID, 1.f / (3.f * (float)HW), lam, wc, wd,
+                                      scale, loss_dev, accumulate_loss ? 1 : 0, status);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+gsr_status run_loss_map(gsr_ctx *ctx, int W, int H, const float *rgb, const float *depth, const float *rgb_t,
+                        const float *depth_t, float lam, float wc, float wd, float scale, float *d_rgb,
+                        float *d_depth, float *loss_dev, bool accumulate_loss, cudaStream_t s)
+{
+    GSR_TRY(run_loss_map_kernels(ctx, nullptr, W, H, rgb, depth, rgb_t, depth_t, lam, wc, wd, scale, d_rgb, d_depth,
+                                 s));
+    return run_loss_map_final(ctx, nullptr, W, H, lam, wc, wd, scale, loss_dev, accumulate_loss, s);
 }
 
 gsr_status run_loss_track(gsr_ctx *ctx, int W, int H, const float *rgb, const float *depth, const float *alpha,

@@ -612,20 +612,21 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
     k_project<<<nb, 256, 0, s>>>(P, ck, d_pose, (float4 *)V.rec.p, (u32 *)V.flag.p, (int32_t *)V.rank_of_gid.p);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
-    GSR_TRY(scan_exclusive(ctx, (u32 *)V.flag.p, (u32 *)V.compact.p, n, nullptr, cnt + CNT_VISIBLE, s));
+    GSR_TRY(scan_exclusive(ctx, (u32 *)V.flag.p, (u32 *)V.compact.p, n, nullptr, cnt + CNT_VISIBLE, s,
+                           &V.scan_tmp));
     k_compact<<<nb, 256, 0, s>>>(n, (u32 *)V.flag.p, (u32 *)V.compact.p, (float4 *)V.rec.p, (u32 *)V.dkeys[0].p,
                                  (u32 *)V.dvals[0].p);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     u32 *dk[2] = {(u32 *)V.dkeys[0].p, (u32 *)V.dkeys[1].p};
     u32 *dv[2] = {(u32 *)V.dvals[0].p, (u32 *)V.dvals[1].p};
-    GSR_TRY(radix_sort_pairs(ctx, dk, dv, n, cnt + CNT_VISIBLE, 32, s));
+    GSR_TRY(radix_sort_pairs(ctx, dk, dv, n, cnt + CNT_VISIBLE, 32, s, &V.radix_hist));
     k_gather<<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, dv[0], (float4 *)V.rec.p, (float4 *)V.rec_sorted.p,
                                 (int32_t *)V.rank_of_gid.p, (u32 *)V.tcount.p);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     GSR_TRY(scan_exclusive(ctx, (u32 *)V.tcount.p, (u32 *)V.inst_off.p, n, cnt + CNT_VISIBLE,
-                           cnt + CNT_INSTANCES, s));
+                           cnt + CNT_INSTANCES, s, &V.scan_tmp));
     if (allow_grow) {
         // one 4-byte readback sizes the instance buffers (grow-on-demand mode)
         GSR_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, cnt + CNT_INSTANCES, sizeof(u32), cudaMemcpyDeviceToHost, s));
@@ -640,7 +641,7 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
     GSR_LAUNCHED(ctx);
     u32 *tk[2] = {(u32 *)V.tkeys[0].p, (u32 *)V.tkeys[1].p};
     u32 *tv[2] = {(u32 *)V.tvals[0].p, (u32 *)V.tvals[1].p};
-    GSR_TRY(radix_sort_pairs(ctx, tk, tv, V.cap_i, cnt + CNT_SORTN, bits_for(tiles), s));
+    GSR_TRY(radix_sort_pairs(ctx, tk, tv, V.cap_i, cnt + CNT_SORTN, bits_for(tiles), s, &V.radix_hist));
     GSR_CUDA(ctx, cudaMemsetAsync(V.ranges.p, 0, sizeof(uint2) * tiles, s));
     k_ranges<<<(unsigned)ceil_div(ceil_div(V.cap_i, 4), 256), 256, 0, s>>>(V.cap_i, cnt + CNT_SORTN, tk[0],
                                                                           (uint2 *)V.ranges.p);

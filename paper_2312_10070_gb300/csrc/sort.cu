@@ -304,11 +304,12 @@ __global__ void __launch_bounds__(RX_THREADS, 4) k_radix_onesweep(const u32 *__r
 } // namespace
 
 gsr_status scan_exclusive(gsr_ctx *ctx, const u32 *in, u32 *out, int64_t n_cap, const u32 *d_n,
-                          u32 *d_total, cudaStream_t s)
+                          u32 *d_total, cudaStream_t s, DevBuf *tmp)
 {
     int64_t nb = ceil_div(n_cap > 0 ? n_cap : 1, SCAN_TILE);
-    GSR_TRY(ensure_buf(ctx, ctx->scan_tmp, sizeof(u32) * (size_t)nb));
-    u32 *sums = (u32 *)ctx->scan_tmp.p;
+    DevBuf &sb = tmp ? *tmp : ctx->scan_tmp;
+    GSR_TRY(ensure_buf(ctx, sb, sizeof(u32) * (size_t)nb));
+    u32 *sums = (u32 *)sb.p;
     k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n_cap, d_n, sums);
     k_scan_sums<<<1, 1024, 0, s>>>(sums, (int)nb, d_total);
     k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n_cap, d_n, sums);
@@ -318,8 +319,9 @@ gsr_status scan_exclusive(gsr_ctx *ctx, const u32 *in, u32 *out, int64_t n_cap, 
 }
 
 gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_cap, const u32 *d_n,
-                            int bits, cudaStream_t s)
+                            int bits, cudaStream_t s, DevBuf *hist)
 {
+    DevBuf &hb_buf = hist ? *hist : ctx->radix_hist;
     int passes = (bits + RX_BITS - 1) / RX_BITS;
     if (passes % 2) ++passes;  // an even count leaves the result in keys[0]
     if (passes > RX_MAX_PASSES) passes = RX_MAX_PASSES;
@@ -330,8 +332,8 @@ gsr_status radix_sort_pairs(gsr_ctx *ctx, u32 *keys[2], u32 *vals[2], int64_t n_
     // layout of radix_hist: [ghist: passes * RX][per pass: lookback nb * RX + ticket]
     const int64_t lb_words = nb * RX + 32;
     const size_t words = (size_t)RX_MAX_PASSES * RX + (size_t)passes * lb_words;
-    GSR_TRY(ensure_buf(ctx, ctx->radix_hist, sizeof(u32) * words));
-    u32 *ghist = (u32 *)ctx->radix_hist.p;
+    GSR_TRY(ensure_buf(ctx, hb_buf, sizeof(u32) * words));
+    u32 *ghist = (u32 *)hb_buf.p;
     u32 *lb0 = ghist + RX_MAX_PASSES * RX;
     GSR_CUDA(ctx, cudaMemsetAsync(ghist, 0, sizeof(u32) * words, s));
     const unsigned hb = (unsigned)std::min<int64_t>(nb, 2 * 152);
@@ -369,7 +371,7 @@ gsr_status grow_instance_capacity(gsr_ctx *ctx, ViewScratch &V, int64_t c)
     // everything the instance sort touches is sized here, so that a captured
     // graph never needs to grow a buffer
     const int64_t words = RX_MAX_PASSES * RX + RX_MAX_PASSES * (ceil_div(c, RX_THREADS * 4) * RX + 32);
-    GSR_TRY(ensure_buf(ctx, ctx->radix_hist, sizeof(u32) * words));
+    GSR_TRY(ensure_buf(ctx, V.radix_hist, sizeof(u32) * words));
     V.cap_i = c;
     return GSR_OK;
 }
