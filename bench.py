@@ -59,16 +59,23 @@ def kernel_sources_sha256(files):
     return h.hexdigest()
 
 
-def measured_traffic(kernel):
+def measured_traffic(kernel, tuned=None):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
     `kernel` from the committed ncu summary, or None when the kernel's sources
-    changed after that capture (or none was taken)."""
+    changed after that capture, when the capture ran another launch
+    configuration than `tuned` (tile, batch, pixels per thread), or when none
+    was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
     if not d or kernel_sources_sha256(d["sources"]) != d["sources_sha256"]:
         return None
+    c = d.get("config")
+    if c and tuned:
+        ppt = tuned.get("ppt_bwd" if kernel == "blend_bwd" else "ppt_fwd")
+        if list(c["tile"]) != list(tuned["tile"]) or c["batch"] != tuned["batch"] or c["ppt"] != ppt:
+            return None
     return d["dram_bytes_per_launch"]
 
 
@@ -376,7 +383,7 @@ def run_gpu(args, rank, world):
         fl = (FLOPS_BWD_EVAL if dom == "blend_bwd" else FLOPS_FWD_EVAL) * e_bwd
         ach = fl / (avg[dom] / 1e3) / 1e12
         roof = dict(bound="alu", kernel=dom, achieved=ach, peak=peak_tf, unit="TFLOP/s", frac=ach / peak_tf,
-                    traffic=measured_traffic(dom), units=f"{e_bwd} pixel-Gaussian evaluations x "
+                    traffic=measured_traffic(dom, tuned), units=f"{e_bwd} pixel-Gaussian evaluations x "
                                        f"{FLOPS_BWD_EVAL if dom == 'blend_bwd' else FLOPS_FWD_EVAL} flops",
                     peak_note=f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_mhz']:.0f} MHz (derived)")
         # the same units measured on this device (FMA and ex2 throughput probes, after the timed region)
