@@ -99,6 +99,13 @@ def test_invalid_arguments_are_rejected_without_gpu(lib):
     o.tile_w, o.batch = 16, 100
     assert lib.gsr_create(ctypes.byref(h), ctypes.byref(o)) == -1
     assert lib.gsr_create(None, None) == -1
+    # throughput probes: sizes are checked before any launch
+    assert lib.gsr_probe_fma(None, 1, 32, None) == -1
+    assert lib.gsr_probe_exp(None, 1, 32, None) == -1
+    buf = ctypes.c_void_p(16)  # never dereferenced: the checks below fail first
+    assert lib.gsr_probe_fma(buf, 0, 32, None) == -1
+    assert lib.gsr_probe_fma(buf, 1, 33, None) == -1
+    assert lib.gsr_probe_exp(buf, 1, 0, None) == -1
 
 
 def test_warmstart_layout_and_argument_checks_without_gpu(lib):

@@ -168,14 +168,18 @@ def test_memory_saving_mode_is_bit_identical():
         assert ok, (k, worst)
 
 
-def test_full_size_room_view_matches_oracle(ctx):
-    """1200x680, 500k-Gaussian sub-map, the headline view (the bench's launch)."""
+@pytest.mark.parametrize("tile,batch,ppt", [((16, 16), 256, 0), ((8, 8), 128, 1)])
+def test_full_size_room_view_matches_oracle(tile, batch, ppt):
+    """1200x680, 500k-Gaussian sub-map, the headline view, in the default
+    launch configuration and in the one the benchmark's autotuner picks
+    (8x8 tiles, staging batch 128, one pixel per thread)."""
+    ctx = api.Context(tile=tile, batch=batch, pixels_per_thread=ppt)
     sc = S.room_scene(500_000, seed=3)
     spec = S.camera_room()
     q, t = S.submap_views()[S.HEADLINE_VIEW]
     g, cam, pose, out, saved = run_forward(ctx, sc, spec, q, t)
     sc64 = O.Scene.from_dict(sc)
-    ref = O.render(sc64, q, t, ocam(spec))
+    ref = O.render(sc64, q, t, ocam(spec, tile))
     check_forward(out, ref, max_amb=0.1)
     st = api.frame_stats(ctx)
     pr = O.project(sc64, q, t, ocam(spec))
@@ -188,12 +192,13 @@ def test_full_size_room_view_matches_oracle(ctx):
     d_dep = (rng.standard_normal((H, W)) * mask).astype(np.float32)
     grads, pose6 = api.render_backward(ctx, g, cam, pose, saved, torch.from_numpy(d_rgb).cuda(),
                                        torch.from_numpy(d_dep).cuda(), None)
-    refb = O.render_backward(sc64, q, t, ocam(spec), d_rgb, d_dep, None)
+    refb = O.render_backward(sc64, q, t, ocam(spec, tile), d_rgb, d_dep, None)
     for k in api.GaussianParams.NAMES:
         ok, worst = grad_close(getattr(grads, k).cpu().numpy(), refb[k])
         assert ok, (k, worst)
     ok, worst = grad_close(pose6.cpu().numpy(), refb["pose"])
     assert ok, ("pose", worst)
+    ctx.close()
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
