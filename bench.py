@@ -265,6 +265,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def rect_list_counts(api, g, cam, poses, tile):
+    """(walked evaluations, tile instances) of the method's rectangle lists
+    at `poses`: E = sum over pixels of (last composited list position + 1)
+    in the depth-ordered list of every Gaussian whose rectangle covers the
+    pixel's tile.  The unit of the blend rooflines; the kernels' own culled
+    lists skip part of it."""
+    import torch
+    c = api.Context(tile=tuple(tile), rect_lists=True)
+    e = inst = 0
+    for p in poses:
+        r = api.render_forward(c, g, cam, p)
+        e += int((r["last_idx"].to(torch.int64) + 1).sum())
+        inst += int(api.frame_stats(c)["n_instances"])
+    c.close()
+    return e, inst
+
+
 def config_dict(stats, flops_info):
     from paper_2312_10070_gb300 import synth as S
     c = dict(workload=f"sub-map mapping iteration, 1 keyframe: 1200x680 RGB-D, {N_GAUSS} Gaussians "
@@ -275,6 +292,8 @@ def config_dict(stats, flops_info):
              l2="flushed between timed steps (256 MB write)", parallelism="replicas")
     if stats:
         c.update(visible=int(stats["n_visible"]), instances=int(stats["n_instances"]))
+        if "n_instances_rect" in stats:
+            c["instances_rect_lists"] = int(stats["n_instances_rect"])
     return c
 
 
@@ -321,9 +340,10 @@ def run_gpu(args, rank, world):
         step()
     torch.cuda.synchronize()
     # counters of the current parameters (outside the timed region)
-    probe = api.render_forward(ctx, g, cam, pose)
+    api.render_forward(ctx, g, cam, pose)
     stats = api.frame_stats(ctx)
-    e_bwd = int((probe["last_idx"].to(torch.int64) + 1).sum())
+    e_bwd, inst_rect = rect_list_counts(api, g, cam, [pose], tuned["tile"])
+    stats["n_instances_rect"] = inst_rect
     torch.cuda.synchronize()
 
     sampler = ClockSampler(dev)
@@ -371,7 +391,8 @@ def run_gpu(args, rank, world):
     avg = {k: float(np.mean([x for x in v if x >= 0])) if any(x >= 0 for x in v) else None
            for k, v in phase_ms.items()}
     dom = max((k for k in avg if avg[k] is not None), key=lambda k: avg[k])
-    n, V, I, P = N_GAUSS, stats["n_visible"], stats["n_instances"], 1200 * 680
+    # the byte model counts the method's tile instances (rectangle lists)
+    n, V, I, P = N_GAUSS, stats["n_visible"], stats.get("n_instances_rect", stats["n_instances"]), 1200 * 680
     step_bytes = 68 * n + 388 * V + 52 * I + 132 * P + 392 * n
     ms_per_step = total_ms / args.steps
     hbm = dict(bound="hbm", achieved=step_bytes / (ms_per_step / 1e3) / 1e9, peak=pk["hbm"], unit="GB/s",
@@ -523,10 +544,7 @@ def run_map8(args):
     state = api.AdamMoments(g)
     cfg = api.MapConfig()
     tuned, _ = api.autotune(ctx, g, cam, poses, reps=3)
-    evals = 0
-    for p in poses:
-        r = api.render_forward(ctx, g, cam, p)
-        evals += int((r["last_idx"].to(torch.int64) + 1).sum())
+    evals, _ = rect_list_counts(api, g, cam, poses, tuned["tile"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     api.profile_enable(ctx, True)
     for _ in range(max(args.warmup, 3)):

@@ -72,6 +72,13 @@ typedef struct {
     int64_t max_pixels;
     int32_t ppt_fwd, ppt_bwd;  /* pixels each forward / backward blend thread owns: 1 or 2
                                   (0 = defaults 1 and 2); results do not depend on them */
+    int32_t rect_lists;        /* 0 (default): a tile's list holds the Gaussians whose rectangle
+                                  covers it AND that may composite at one of its pixel centres
+                                  (minimum of sigma over the tile's pixel-centre box below the
+                                  skip threshold, with the float32 error margin); 1: every
+                                  Gaussian whose rectangle covers the tile (Sec. 3.1's tiling as
+                                  the prior art defines it).  Images, n_contrib and gradients are
+                                  the same either way; last_idx indexes the list in use. */
 } gsr_options;
 
 /* Pinhole camera and rasterizer constants. */

@@ -27,7 +27,7 @@ STATUS = {0: "GSR_OK", -1: "GSR_ERR_INVALID_ARG", -2: "GSR_ERR_CUDA", -3: "GSR_E
 class Options(ctypes.Structure):
     _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("batch", c_i32), ("memory_saving", c_i32),
                 ("fixed_capacity", c_i32), ("max_gaussians", c_i64), ("max_instances", c_i64),
-                ("max_pixels", c_i64), ("ppt_fwd", c_i32), ("ppt_bwd", c_i32)]
+                ("max_pixels", c_i64), ("ppt_fwd", c_i32), ("ppt_bwd", c_i32), ("rect_lists", c_i32)]
 
 
 class Camera(ctypes.Structure):

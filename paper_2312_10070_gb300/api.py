@@ -33,7 +33,7 @@ class Context:
     """Owns a gsr_ctx (scratch, tile lists, graphs) on the current device."""
 
     def __init__(self, tile=(16, 16), batch=256, memory_saving=False, fixed_capacity=False, max_gaussians=0,
-                 max_instances=0, pixels_per_thread=0, ppt_fwd=0, ppt_bwd=0):
+                 max_instances=0, pixels_per_thread=0, ppt_fwd=0, ppt_bwd=0, rect_lists=False):
         if not torch.cuda.is_available():
             raise RuntimeError("the GB300 rasterizer needs a CUDA device; there is no CPU fallback")
         self.lib = L.load()
@@ -47,6 +47,7 @@ class Context:
         o.max_instances = max_instances
         o.ppt_fwd = ppt_fwd or pixels_per_thread
         o.ppt_bwd = ppt_bwd or pixels_per_thread
+        o.rect_lists = int(rect_lists)
         self.options = o
         h = ctypes.c_void_p()
         L.check(self.lib.gsr_create(ctypes.byref(h), ctypes.byref(o)))

@@ -163,6 +163,7 @@ gsr_status gsr_create(gsr_ctx **out, const gsr_options *opt)
     if (o.batch != 32 && o.batch != 64 && o.batch != 128 && o.batch != 256) return GSR_ERR_INVALID_ARG;
     if (o.max_gaussians < 0 || o.max_instances < 0 || o.max_pixels < 0) return GSR_ERR_INVALID_ARG;
     if (o.ppt_fwd < 0 || o.ppt_fwd > 2 || o.ppt_bwd < 0 || o.ppt_bwd > 2) return GSR_ERR_INVALID_ARG;
+    if (o.rect_lists != 0 && o.rect_lists != 1) return GSR_ERR_INVALID_ARG;
     gsr_ctx *c = new (std::nothrow) gsr_ctx();
     if (!c) return GSR_ERR_OOM;
     c->opt = o;

@@ -45,55 +45,6 @@ __device__ __forceinline__ bool quick_reject(float px, float py, const float4 &a
     return sigma > b.w;
 }
 
-// Pixel-centre box of a tile (clipped to the image).
-struct TileBox {
-    float x0, x1, y0, y1;
-};
-
-__device__ __forceinline__ TileBox tile_box(const CamK &ck, int tile, int TW, int TH)
-{
-    const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
-    TileBox b;
-    b.x0 = (float)(tx * TW) + 0.5f;
-    b.x1 = (float)min(tx * TW + TW, ck.W) - 0.5f;
-    b.y0 = (float)(ty * TH) + 0.5f;
-    b.y1 = (float)min(ty * TH + TH, ck.H) - 0.5f;
-    return b;
-}
-
-// min over y in [y0, y1] of 0.5 A x^2 + B x y + 0.5 C y^2 (C > 0, iC ~ 1/C:
-// an inexact minimiser only raises the value by a second-order amount)
-__device__ __forceinline__ float edge_min(float x, float y0, float y1, float A, float B, float C, float iC)
-{
-    const float y = fminf(fmaxf(-B * x * iC, y0), y1);
-    return 0.5f * A * x * x + B * x * y + 0.5f * C * y * y;
-}
-
-// false only if sigma exceeds the skip threshold b.w at every pixel centre
-// of the box, as the per-pixel evaluation would compute it.  With kappa the
-// conic's condition number, both the per-pixel sigma and the box minimum m
-// computed here are within 1e-6 kappa (relative) of the exact values (a few
-// float32 roundings on terms whose absolute sum is at most kappa sigma), so
-// m (1 - e) > thr (1 + e), e = 1e-6 kappa, implies a skip at every pixel.
-__device__ __forceinline__ bool tile_may_hit(const float4 &a, const float4 &b, const TileBox &box)
-{
-    const float ca = a.z, cb = a.w, cc = b.x, thr = b.w;
-    const float det = ca * cc - cb * cb;
-    if (!(ca > 0.f && cc > 0.f && det > 0.f)) return true;
-    const float hd = 0.5f * (ca - cc);
-    const float lmax = 0.5f * (ca + cc) + sqrtf(hd * hd + cb * cb);
-    const float e = 1e-6f * __fdividef(lmax * lmax, det);
-    if (!(e < 0.25f)) return true;
-    const float X0 = box.x0 - a.x, X1 = box.x1 - a.x, Y0 = box.y0 - a.y, Y1 = box.y1 - a.y;
-    float m = 0.f;
-    if (!(X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f)) {
-        const float ia = __fdividef(1.f, ca), ic = __fdividef(1.f, cc);
-        m = fminf(fminf(edge_min(X0, Y0, Y1, ca, cb, cc, ic), edge_min(X1, Y0, Y1, ca, cb, cc, ic)),
-                  fminf(edge_min(Y0, X0, X1, cc, cb, ca, ia), edge_min(Y1, X0, X1, cc, cb, ca, ia)));
-    }
-    return !(m * (1.f - e) > thr * (1.f + e));
-}
-
 // Stage list entries [lo, hi) (hi - lo <= BATCH) of a tile: entries that may
 // hit the tile are written in list order to sA/sB/sC (sB.w = skip threshold),
 // with their list position in sJ and Gaussian rank in sR.  Returns the number
@@ -116,7 +67,7 @@ __device__ __forceinline__ int stage_entries(const BlendView &vp, u32 list_base,
             a = vp.rec[3 * (int64_t)r];
             b = vp.rec[3 * (int64_t)r + 1];
             b.w = sigma_reject(b.y);  // replaces the rectangle bits, unused here
-            keep = tile_may_hit(a, b, box);
+            keep = vp.culled || tile_may_hit(a, b, box);  // culled lists: tested when built
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         int off = total, sum = __popc(bal);
@@ -572,6 +523,7 @@ BlendView blend_view(const ViewScratch &V, const gsr_render_out *o, const float 
     b.d_depth = d_depth;
     b.d_alpha = d_alpha;
     b.g2d = (float *)V.g2d.p;
+    b.culled = V.culled ? 1 : 0;
     return b;
 }
 

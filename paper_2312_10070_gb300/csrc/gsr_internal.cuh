@@ -51,7 +51,7 @@ struct ViewScratch {
     DevBuf dkeys[2];    // u32 depth keys (ping-pong)
     DevBuf dvals[2];    // u32 Gaussian ids
     DevBuf rec_sorted;  // float4 x3 per depth rank
-    DevBuf tcount;      // u32 tiles touched per rank
+    DevBuf tcount;      // u32 tile instances per warp of 32 depth ranks
     DevBuf inst_off;    // u32 exclusive scan of tcount
     DevBuf tkeys[2];    // u32 tile id per instance
     DevBuf tvals[2];    // u32 depth rank per instance
@@ -64,6 +64,7 @@ struct ViewScratch {
     DevBuf loss_maps;   // SSIM adjoint maps of this view's mapping loss (batched mapping)
     DevBuf loss_part;   // per-block partial sums of this view's mapping loss
     int64_t cap_n = 0, cap_i = 0, cap_t = 0;
+    bool culled = false;  // the lists hold only entries that pass the tile test
     // identity of the last forward, to decide whether the saved lists are valid
     uint64_t generation = 0;
 };
@@ -77,6 +78,8 @@ struct BlendView {
     int32_t *last_idx, *n_contrib;
     const float *d_rgb, *d_depth, *d_alpha;
     float *g2d;
+    int culled;    // 1: every list entry passed the tile test when the lists were built
+    int reserved;  // explicit padding (descriptors are compared bytewise)
 };
 // per-keyframe inputs of the multi-keyframe projection backward
 struct ProjView {
@@ -244,6 +247,55 @@ __device__ __forceinline__ Eval eval_gaussian(float px, float py, float u, float
 // ln(255 o) plus a margin far above the float32 error of __logf/__expf, so a
 // reject on it never changes a skip decision of eval_gaussian.
 __device__ __forceinline__ float sigma_reject(float op) { return __logf(255.f * op) + 0.02f; }
+
+// Pixel-centre box of a tile (clipped to the image).
+struct TileBox {
+    float x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ TileBox tile_box(const CamK &ck, int tile, int TW, int TH)
+{
+    const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
+    TileBox b;
+    b.x0 = (float)(tx * TW) + 0.5f;
+    b.x1 = (float)min(tx * TW + TW, ck.W) - 0.5f;
+    b.y0 = (float)(ty * TH) + 0.5f;
+    b.y1 = (float)min(ty * TH + TH, ck.H) - 0.5f;
+    return b;
+}
+
+// min over y in [y0, y1] of 0.5 A x^2 + B x y + 0.5 C y^2 (C > 0, iC ~ 1/C:
+// an inexact minimiser only raises the value by a second-order amount)
+__device__ __forceinline__ float edge_min(float x, float y0, float y1, float A, float B, float C, float iC)
+{
+    const float y = fminf(fmaxf(-B * x * iC, y0), y1);
+    return 0.5f * A * x * x + B * x * y + 0.5f * C * y * y;
+}
+
+// false only if sigma exceeds the skip threshold b.w at every pixel centre
+// of the box, as the per-pixel evaluation would compute it.  With kappa the
+// conic's condition number, both the per-pixel sigma and the box minimum m
+// computed here are within 1e-6 kappa (relative) of the exact values (a few
+// float32 roundings on terms whose absolute sum is at most kappa sigma), so
+// m (1 - e) > thr (1 + e), e = 1e-6 kappa, implies a skip at every pixel.
+__device__ __forceinline__ bool tile_may_hit(const float4 &a, const float4 &b, const TileBox &box)
+{
+    const float ca = a.z, cb = a.w, cc = b.x, thr = b.w;
+    const float det = ca * cc - cb * cb;
+    if (!(ca > 0.f && cc > 0.f && det > 0.f)) return true;
+    const float hd = 0.5f * (ca - cc);
+    const float lmax = 0.5f * (ca + cc) + sqrtf(hd * hd + cb * cb);
+    const float e = 1e-6f * __fdividef(lmax * lmax, det);
+    if (!(e < 0.25f)) return true;
+    const float X0 = box.x0 - a.x, X1 = box.x1 - a.x, Y0 = box.y0 - a.y, Y1 = box.y1 - a.y;
+    float m = 0.f;
+    if (!(X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f)) {
+        const float ia = __fdividef(1.f, ca), ic = __fdividef(1.f, cc);
+        m = fminf(fminf(edge_min(X0, Y0, Y1, ca, cb, cc, ic), edge_min(X1, Y0, Y1, ca, cb, cc, ic)),
+                  fminf(edge_min(Y0, X0, X1, cc, cb, ca, ia), edge_min(Y1, X0, X1, cc, cb, ca, ia)));
+    }
+    return !(m * (1.f - e) > thr * (1.f + e));
+}
 
 // --------------------------------------------------------------- launchers
 struct Params {

@@ -214,10 +214,10 @@ __global__ void k_compact(int64_t n, const u32 *__restrict__ flag, const u32 *__
     vals[o] = (u32)i;
 }
 
-// records in depth order; tiles touched per rank
+// records in depth order
 __global__ void k_gather(int64_t cap, const u32 *__restrict__ d_v, const u32 *__restrict__ vals,
                          const float4 *__restrict__ rec, float4 *__restrict__ rec_sorted,
-                         int32_t *__restrict__ rank_of_gid, u32 *__restrict__ tcount)
+                         int32_t *__restrict__ rank_of_gid)
 {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= cap || r >= (int64_t)*d_v) return;
@@ -227,20 +227,165 @@ __global__ void k_gather(int64_t cap, const u32 *__restrict__ d_v, const u32 *__
     rec_sorted[3 * r + 1] = b;
     rec_sorted[3 * r + 2] = c;
     rank_of_gid[gid] = (int32_t)r;
-    u32 lo = __float_as_uint(b.w), hi = __float_as_uint(c.w);
-    u32 w = (hi & 0xffffu) - (lo & 0xffffu) + 1u, h = (hi >> 16) - (lo >> 16) + 1u;
-    tcount[r] = w * h;
 }
 
-// One instance (tile id, depth rank) per tile of each rectangle; the stream is
-// in depth order, so a stable sort on the tile id yields depth-ordered lists.
-// A warp handles 32 consecutive ranks: a warp scan of their rectangle areas
-// gives each rank's slot, then the lanes write the warp's instances
-// contiguously (coalesced), each lane locating the owner rank of its
-// instance with a 5-step search over the scanned slots.
+// Candidate instances of one warp: the tiles of the rectangles of its 32
+// consecutive depth ranks, in rank order and row-major within a rectangle,
+// taken 32 at a time (candidate k = kb + lane).  With CULL a candidate is
+// kept only if its Gaussian may composite somewhere in the tile
+// (tile_may_hit, the test the blend kernels' staging applies), so the tile
+// lists hold only such entries; every per-pixel decision is unchanged.
+struct WarpRects {
+    int x0 = 0, y0 = 0, w = 1;
+    float iw = 1.f;  // 1 / w
+    u32 cnt = 0, excl = 0, total = 0;
+    // the lane's Gaussian for the tile test: centre, conic, the reciprocals of
+    // its diagonal, and the threshold the box minimum of sigma is compared with
+    float u = 0.f, v = 0.f, ca = 1.f, cb = 0.f, cc = 1.f, ia = 1.f, ic = 1.f, thr = 0.f;
+};
+
+// The tile test of tile_may_hit with its per-Gaussian part hoisted: the box
+// minimum m of sigma is compared with thr (1 + e) / (1 - e) (e = 1e-6 kappa),
+// which tile_may_hit's m (1 - e) > thr (1 + e) rearranges to; the extra
+// relative 1e-6 absorbs the rounding of the rearrangement, so the test stays
+// conservative.  Degenerate conics keep every tile (threshold +inf).
+__device__ __forceinline__ void tile_test_setup(const float4 &a, const float4 &b, float thr0, WarpRects &q)
+{
+    q.u = a.x;
+    q.v = a.y;
+    q.ca = a.z;
+    q.cb = a.w;
+    q.cc = b.x;
+    const float det = q.ca * q.cc - q.cb * q.cb;
+    q.thr = __int_as_float(0x7f800000);  // +inf: keep
+    if (!(q.ca > 0.f && q.cc > 0.f && det > 0.f)) return;
+    const float hd = 0.5f * (q.ca - q.cc);
+    const float lmax = 0.5f * (q.ca + q.cc) + sqrtf(hd * hd + q.cb * q.cb);
+    const float e = 1e-6f * __fdividef(lmax * lmax, det);
+    if (!(e < 0.25f)) return;
+    q.ia = __fdividef(1.f, q.ca);
+    q.ic = __fdividef(1.f, q.cc);
+    const float t = thr0 * __fdividef(1.f + e, 1.f - e);
+    q.thr = t + 1e-6f * fabsf(t);
+}
+
+__device__ __forceinline__ WarpRects warp_rects(const float4 *__restrict__ rec_sorted, int64_t r, bool valid, bool cull)
+{
+    const unsigned F = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    WarpRects q;
+    if (valid) {
+        const float4 b = rec_sorted[3 * r + 1];
+        const u32 lo = __float_as_uint(b.w), hi = __float_as_uint(rec_sorted[3 * r + 2].w);
+        q.x0 = (int)(lo & 0xffffu);
+        q.y0 = (int)(lo >> 16);
+        q.w = (int)(hi & 0xffffu) - q.x0 + 1;
+        q.iw = __fdividef(1.f, (float)q.w);
+        q.cnt = (u32)(q.w * ((int)(hi >> 16) - q.y0 + 1));
+        if (cull) tile_test_setup(rec_sorted[3 * r], b, sigma_reject(b.y), q);
+    }
+    u32 incl = q.cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(F, incl, o);
+        if (lane >= o) incl += t;
+    }
+    q.excl = incl - q.cnt;
+    q.total = __shfl_sync(F, incl, 31);
+    return q;
+}
+
+// candidate k (< q.total for a real one): its owner lane j and tile id; *keep
+// = the tile test when CULL (else true)
+template <bool CULL>
+__device__ __forceinline__ u32 candidate(const CamK &ck, const WarpRects &q, u32 k, int *owner, bool *keep)
+{
+    const unsigned F = 0xffffffffu;
+    // owner lane j: the largest j with excl_j <= k (lanes with cnt = 0 are skipped over)
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const u32 e = __shfl_sync(F, q.excl, j + step);
+        const u32 c = __shfl_sync(F, q.cnt, j + step);
+        if (j + step < 32 && c > 0 && e <= k) j += step;
+    }
+    const u32 ej = __shfl_sync(F, q.excl, j);
+    const int wx = __shfl_sync(F, q.w, j), jx = __shfl_sync(F, q.x0, j), jy = __shfl_sync(F, q.y0, j);
+    const float iwx = __shfl_sync(F, q.iw, j);
+    const int local = (int)(k - ej);
+    // row = local / wx without an integer division: local < 2^24 and the
+    // rounding of (local + 0.5) / wx stays far inside the half-step margin
+    int row = (int)(((float)local + 0.5f) * iwx);
+    int col = local - row * wx;
+    if (col < 0) {  // never taken at image sizes (local < 2^20); keeps the split exact regardless
+        --row;
+        col += wx;
+    } else if (col >= wx) {
+        ++row;
+        col -= wx;
+    }
+    const int tx = jx + col, ty = jy + row;
+    const u32 tile = (u32)(ty * ck.tiles_x + tx);
+    *owner = j;
+    *keep = true;
+    if (CULL) {
+        const float u = __shfl_sync(F, q.u, j), v = __shfl_sync(F, q.v, j);
+        const float ca = __shfl_sync(F, q.ca, j), cb = __shfl_sync(F, q.cb, j), cc = __shfl_sync(F, q.cc, j);
+        const float ia = __shfl_sync(F, q.ia, j), ic = __shfl_sync(F, q.ic, j), thr = __shfl_sync(F, q.thr, j);
+        if (k < q.total) {
+            const float X0 = (float)(tx * ck.tw) + 0.5f - u, X1 = (float)min(tx * ck.tw + ck.tw, ck.W) - 0.5f - u;
+            const float Y0 = (float)(ty * ck.th) + 0.5f - v, Y1 = (float)min(ty * ck.th + ck.th, ck.H) - 0.5f - v;
+            float m = 0.f;
+            if (!(X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f))
+                m = fminf(fminf(edge_min(X0, Y0, Y1, ca, cb, cc, ic), edge_min(X1, Y0, Y1, ca, cb, cc, ic)),
+                          fminf(edge_min(Y0, X0, X1, cc, cb, ca, ia), edge_min(Y1, X0, X1, cc, cb, ca, ia)));
+            *keep = !(m > thr);
+        }
+    }
+    return tile;
+}
+
+// Instances per warp of 32 consecutive ranks (wcount[warp]; 0 past the
+// visible count), the input of the scan that places each warp's instances.
+template <bool CULL>
+__global__ void __launch_bounds__(256) k_count_instances(int64_t cap_v, const u32 *__restrict__ d_v,
+                                                         const float4 *__restrict__ rec_sorted, CamK ck,
+                                                         u32 *__restrict__ wcount)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t r0 = r - lane, gw = r >> 5;
+    if (r0 >= cap_v) return;  // warp-uniform; the grid has ceil(cap_v / 32) warps below cap_v
+    const int64_t V = (int64_t)*d_v;
+    if (r0 >= V) {
+        if (lane == 0) wcount[gw] = 0u;
+        return;
+    }
+    const WarpRects q = warp_rects(rec_sorted, r, r < V && r < cap_v, CULL);
+    if (!CULL) {
+        if (lane == 0) wcount[gw] = q.total;
+        return;
+    }
+    u32 kept = 0;
+    for (u32 kb = 0; kb < q.total; kb += 32) {
+        int j;
+        bool keep;
+        const u32 k = kb + lane;
+        candidate<CULL>(ck, q, k, &j, &keep);
+        kept += __popc(__ballot_sync(0xffffffffu, keep && k < q.total));
+    }
+    if (lane == 0) wcount[gw] = kept;
+}
+
+// One instance (tile id, depth rank) per kept candidate; the stream is in
+// depth order, so a stable sort on the tile id yields depth-ordered lists.  A
+// warp writes its instances contiguously from woff[warp] (the exclusive scan
+// of k_count_instances), compacting kept candidates with a ballot, each lane
+// locating the owner rank of its candidate with a 5-step search.
+template <bool CULL>
 __global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restrict__ d_v,
-                                              const float4 *__restrict__ rec_sorted, const u32 *__restrict__ off,
-                                              int tiles_x, int64_t cap_i, u32 *__restrict__ tkeys,
+                                              const float4 *__restrict__ rec_sorted, const u32 *__restrict__ woff,
+                                              CamK ck, int64_t cap_i, u32 *__restrict__ tkeys,
                                               u32 *__restrict__ tvals, u32 *__restrict__ counters)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,45 +399,24 @@ __global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restri
     const int64_t V = (int64_t)*d_v;
     const int64_t r0 = r - lane;  // first rank of this warp
     if (r0 >= V || r0 >= cap_v) return;  // warp-uniform
-    const bool valid = r < V && r < cap_v;
-    int x0 = 0, y0 = 0, w = 1;
-    u32 cnt = 0;
-    if (valid) {
-        const u32 lo = __float_as_uint(rec_sorted[3 * r + 1].w), hi = __float_as_uint(rec_sorted[3 * r + 2].w);
-        x0 = (int)(lo & 0xffffu);
-        y0 = (int)(lo >> 16);
-        w = (int)(hi & 0xffffu) - x0 + 1;
-        cnt = (u32)(w * ((int)(hi >> 16) - y0 + 1));
-    }
-    u32 incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const u32 t = __shfl_up_sync(F, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const u32 excl = incl - cnt;
-    const u32 total = __shfl_sync(F, incl, 31);
-    const int64_t base = (int64_t)__shfl_sync(F, off[r0], 0);  // off[r0] is read by every lane (same address)
-    for (u32 kb = 0; kb < total; kb += 32) {
+    const WarpRects q = warp_rects(rec_sorted, r, r < V && r < cap_v, CULL);
+    const int64_t base = (int64_t)woff[r >> 5];
+    u32 run = 0;
+    for (u32 kb = 0; kb < q.total; kb += 32) {
         const u32 k = kb + lane;
-        // owner lane j: the largest j with excl_j <= k (lanes with cnt = 0 are skipped over)
-        int j = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const u32 e = __shfl_sync(F, excl, j + step);
-            const u32 c = __shfl_sync(F, cnt, j + step);
-            if (j + step < 32 && c > 0 && e <= k) j += step;
-        }
-        const u32 ej = __shfl_sync(F, excl, j);
-        const int wx = __shfl_sync(F, w, j), jx = __shfl_sync(F, x0, j), jy = __shfl_sync(F, y0, j);
-        if (k < total) {
-            const int local = (int)(k - ej);
-            const int64_t o = base + k;
+        int j;
+        bool keep;
+        const u32 tile = candidate<CULL>(ck, q, k, &j, &keep);
+        keep = keep && k < q.total;
+        const u32 bal = __ballot_sync(F, keep);
+        if (keep) {
+            const int64_t o = base + run + __popc(bal & ((1u << lane) - 1u));
             if (o < cap_i) {
-                tkeys[o] = (u32)((jy + local / wx) * tiles_x + jx + local % wx);
+                tkeys[o] = tile;
                 tvals[o] = (u32)(r0 + j);
             }
         }
+        run += __popc(bal);
     }
 }
 
@@ -622,11 +746,21 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
     u32 *dv[2] = {(u32 *)V.dvals[0].p, (u32 *)V.dvals[1].p};
     GSR_TRY(radix_sort_pairs(ctx, dk, dv, n, cnt + CNT_VISIBLE, 32, s, &V.radix_hist));
     k_gather<<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, dv[0], (float4 *)V.rec.p, (float4 *)V.rec_sorted.p,
-                                (int32_t *)V.rank_of_gid.p, (u32 *)V.tcount.p);
-    ctx->launches += 1;
+                                (int32_t *)V.rank_of_gid.p);
+    // instances per warp of 32 ranks, then their placement (tcount / inst_off
+    // hold one entry per warp)
+    const bool cull = !ctx->opt.rect_lists;
+    if (cull)
+        k_count_instances<true><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, ck,
+                                                   (u32 *)V.tcount.p);
+    else
+        k_count_instances<false><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, ck,
+                                                    (u32 *)V.tcount.p);
+    ctx->launches += 2;
     GSR_LAUNCHED(ctx);
-    GSR_TRY(scan_exclusive(ctx, (u32 *)V.tcount.p, (u32 *)V.inst_off.p, n, cnt + CNT_VISIBLE,
+    GSR_TRY(scan_exclusive(ctx, (u32 *)V.tcount.p, (u32 *)V.inst_off.p, ceil_div(n, 32), nullptr,
                            cnt + CNT_INSTANCES, s, &V.scan_tmp));
+    V.culled = cull;
     if (allow_grow) {
         // one 4-byte readback sizes the instance buffers (grow-on-demand mode)
         GSR_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, cnt + CNT_INSTANCES, sizeof(u32), cudaMemcpyDeviceToHost, s));
@@ -635,8 +769,12 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
         if (need > V.cap_i) GSR_TRY(grow_instance_capacity(ctx, V, need + need / 4 + 1024));
     }
     if (V.cap_i <= 0) return gsr_fail(ctx, GSR_ERR_CAPACITY, "instance capacity is zero in fixed-capacity mode");
-    k_emit<<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, (u32 *)V.inst_off.p, ck.tiles_x,
-                              V.cap_i, (u32 *)V.tkeys[0].p, (u32 *)V.tvals[0].p, cnt);
+    if (cull)
+        k_emit<true><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, (u32 *)V.inst_off.p, ck,
+                                        V.cap_i, (u32 *)V.tkeys[0].p, (u32 *)V.tvals[0].p, cnt);
+    else
+        k_emit<false><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, (u32 *)V.inst_off.p, ck,
+                                         V.cap_i, (u32 *)V.tkeys[0].p, (u32 *)V.tvals[0].p, cnt);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     u32 *tk[2] = {(u32 *)V.tkeys[0].p, (u32 *)V.tkeys[1].p};

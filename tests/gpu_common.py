@@ -64,3 +64,36 @@ def unit_inputs(seed=1, pose_seed=2):
     sc = S.random_scene(5000, seed)
     q, t = S.perturbed_pose(pose_seed)
     return sc, S.camera_unit(), q, t
+
+
+def last_gids(last_idx, starts, gids, tile, width):
+    """Gaussian id of each pixel's last composited list entry (-1 if none):
+    last_idx indexes the list of the pixel's tile, which starts at
+    starts[tile] in gids."""
+    last_idx = np.asarray(last_idx, np.int64)
+    H, W = last_idx.shape
+    ys, xs = np.mgrid[0:H, 0:W]
+    tx = (width + tile[0] - 1) // tile[0]
+    t = (ys // tile[1]) * tx + xs // tile[0]
+    pos = np.asarray(starts, np.int64)[t] + last_idx
+    if len(gids) == 0:
+        return np.full_like(last_idx, -1)
+    g = np.asarray(gids)[np.clip(pos, 0, len(gids) - 1)]
+    return np.where(last_idx >= 0, g, -1)
+
+
+def box_min_sigma(u, v, ca, cb, cc, x0, x1, y0, y1):
+    """Exact (FP64) minimum over the box [x0, x1] x [y0, y1] of
+    sigma = 0.5 ca dx^2 + cb dx dy + 0.5 cc dy^2, dx = x - u, dy = y - v
+    (a convex quadratic: 0 if (u, v) is inside, else the least of the four
+    edge minima, each at the clamped one-dimensional minimiser)."""
+    X0, X1, Y0, Y1 = x0 - u, x1 - u, y0 - v, y1 - v
+
+    def edge(X, lo, hi, a, b, c):
+        y = np.clip(-b * X / c, lo, hi)
+        return 0.5 * a * X * X + b * X * y + 0.5 * c * y * y
+    m = np.minimum.reduce([edge(X0, Y0, Y1, ca, cb, cc), edge(X1, Y0, Y1, ca, cb, cc),
+                           edge(Y0, X0, X1, cc, cb, ca), edge(Y1, X0, X1, cc, cb, ca)])
+    inside = (X0 <= 0) & (X1 >= 0) & (Y0 <= 0) & (Y1 >= 0)
+    return np.where(inside, 0.0, m)
+

@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 
 import oracle as O
 from paper_2312_10070_gb300 import api, synth as S
-from tests.gpu_common import grad_close, ocam, tile_sequences_match, unit_inputs
+from tests.gpu_common import box_min_sigma, grad_close, last_gids, ocam, tile_sequences_match, unit_inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +37,10 @@ def run_forward(ctx, sc, spec, q, t, tile=(16, 16)):
     return g, cam, pose, {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}, out
 
 
-def check_forward(out, ref, max_amb=0.08):
+def check_forward(out, ref, max_amb=0.08, lists=None):
+    """lists = (ctx, scene64, q, t, oracle camera): the context's tile lists
+    are culled, so last_idx (a position in the list in use) is compared as the
+    Gaussian it names, against the oracle's rectangle lists."""
     ok = ref["amb"] == 0
     assert ok.mean() >= 1 - max_amb, ok.mean()
     for k in ("depth", "alpha", "final_T"):
@@ -46,20 +49,32 @@ def check_forward(out, ref, max_amb=0.08):
     err = np.abs(out["rgb"][:, ok] - ref["rgb"][:, ok]).max()
     assert err <= 2e-4, ("rgb", err)
     assert np.array_equal(out["n_contrib"][ok], ref["n_contrib"][ok])
-    assert np.array_equal(out["last_idx"][ok], ref["last_idx"][ok])
+    if lists is None:
+        assert np.array_equal(out["last_idx"][ok], ref["last_idx"][ok])
+        return
+    c, sc64, q, t, oc = lists
+    tx, ty = oc.tiles
+    ranges, gids, _ = api.tile_lists(c, tx * ty, sc64.n)
+    bins = O.bin_tiles(sc64, q, t, oc)
+    tile = (oc.tile_w, oc.tile_h)
+    g_gpu = last_gids(out["last_idx"], ranges[:, 0], gids, tile, oc.width)
+    g_ref = last_gids(ref["last_idx"], bins["start"][:-1], bins["gid"], tile, oc.width)
+    assert np.array_equal(g_gpu[ok], g_ref[ok])
 
 
 @pytest.mark.parametrize("seed,pose_seed", [(1, 2), (7, 8)])
 def test_forward_unit_matches_oracle(ctx, seed, pose_seed):
     sc, spec, q, t = unit_inputs(seed, pose_seed)
     _, _, _, out, _ = run_forward(ctx, sc, spec, q, t)
-    ref = O.render(O.Scene.from_dict(sc), q, t, ocam(spec))
-    check_forward(out, ref)
+    sc64 = O.Scene.from_dict(sc)
+    ref = O.render(sc64, q, t, ocam(spec))
+    check_forward(out, ref, lists=(ctx, sc64, q, t, ocam(spec)))
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8), (32, 8)])
 def test_tile_lists_bit_exact(tile):
-    c = api.Context(tile=tile)
+    """Rectangle lists (rect_lists=1): the prior art's tiling, bit for bit."""
+    c = api.Context(tile=tile, rect_lists=True)
     sc, spec, q, t = unit_inputs(3, 4)
     g, cam, pose, out, _ = run_forward(c, sc, spec, q, t)
     oc = ocam(spec, tile)
@@ -145,7 +160,9 @@ def test_edge_cases(ctx):
     # ragged image against the oracle
     sc = S.random_scene(400, 4, box=((-0.6, 0.6), (-0.45, 0.45), (1, 3)), log_scale=(-3.0, 0.4))
     _, _, _, out, _ = run_forward(ctx, sc, spec, *S.IDENTITY_POSE)
-    check_forward(out, O.render(O.Scene.from_dict(sc), *S.IDENTITY_POSE, ocam(spec)))
+    sc64 = O.Scene.from_dict(sc)
+    check_forward(out, O.render(sc64, *S.IDENTITY_POSE, ocam(spec)),
+                  lists=(ctx, sc64, *S.IDENTITY_POSE, ocam(spec)))
 
 
 def test_memory_saving_mode_is_bit_identical():
@@ -180,7 +197,7 @@ def test_full_size_room_view_matches_oracle(tile, batch, ppt):
     g, cam, pose, out, saved = run_forward(ctx, sc, spec, q, t)
     sc64 = O.Scene.from_dict(sc)
     ref = O.render(sc64, q, t, ocam(spec, tile))
-    check_forward(out, ref, max_amb=0.1)
+    check_forward(out, ref, max_amb=0.1, lists=(ctx, sc64, q, t, ocam(spec, tile)))
     st = api.frame_stats(ctx)
     pr = O.project(sc64, q, t, ocam(spec))
     assert abs(st["n_visible"] - pr["visible"].sum()) <= (pr["amb"] & 1).sum()
@@ -222,3 +239,91 @@ def test_pixels_per_thread_is_bit_identical(tile):
         assert ok, (k, worst)
     ok, worst = grad_close(res[0][2], res[1][2])
     assert ok, worst
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_culled_lists_keep_exactly_what_can_composite(tile):
+    """Default lists (rect_lists=0): each tile's list is its rectangle list
+    with entries removed that cannot composite at any pixel centre of the
+    tile.  Checked against FP64: an entry whose exact minimum of sigma over
+    the tile's pixel centres is below the skip threshold ln(255 o) by a
+    relative 1e-4 is kept; one whose exact minimum over the tile's
+    pixel-centre box exceeds the kernels' skip test (ln(255 o) + 0.02, a
+    margin above the float32 error of the exponential) by a relative 1e-3 is
+    dropped; the order is the
+    rectangle list's (the same GPU lists with rect_lists=1, filtered)."""
+    sc, spec, q, t = unit_inputs(3, 4)
+    oc = ocam(spec, tile)
+    sc64 = O.Scene.from_dict(sc)
+    tx, ty = oc.tiles
+    lists = {}
+    for rect in (False, True):
+        c = api.Context(tile=tile, rect_lists=rect)
+        run_forward(c, sc, spec, q, t)
+        lists[rect] = api.tile_lists(c, tx * ty, sc64.n)
+        c.close()
+    pr = O.project(sc64, q, t, oc)
+    skip = (pr["amb"] & 1).astype(bool)
+    u, v = pr["uv"][:, 0], pr["uv"][:, 1]
+    ca, cb, cc = pr["conic"].T
+    thr = np.log(255.0 * pr["opacity"])
+    (rc, gc, _), (rr, gr, _) = lists[False], lists[True]
+    n_rect = n_cull = 0
+    for tl in range(tx * ty):
+        full = gr[rr[tl, 0]:rr[tl, 1]]
+        kept = gc[rc[tl, 0]:rc[tl, 1]]
+        n_rect += len(full)
+        n_cull += len(kept)
+        assert list(kept) == [g for g in full if g in set(kept.tolist())], tl
+        if len(full) == 0:
+            continue
+        X, Y = tl % tx, tl // tx
+        x0, y0 = X * tile[0] + 0.5, Y * tile[1] + 0.5
+        x1, y1 = min(X * tile[0] + tile[0], spec.width) - 0.5, min(Y * tile[1] + tile[1], spec.height) - 0.5
+        f = full.astype(np.int64)
+        px, py = np.meshgrid(np.arange(x0, x1 + 0.5), np.arange(y0, y1 + 0.5))
+        dx = px.ravel()[None, :] - u[f][:, None]
+        dy = py.ravel()[None, :] - v[f][:, None]
+        sig = (0.5 * ca[f][:, None] * dx * dx + cb[f][:, None] * dx * dy + 0.5 * cc[f][:, None] * dy * dy).min(1)
+        boxm = box_min_sigma(u[f], v[f], ca[f], cb[f], cc[f], x0, x1, y0, y1)
+        must_keep = (sig < thr[f] - 1e-4 * np.abs(thr[f])) & ~skip[f]
+        # the kernels' test keeps a margin e = 1e-6 kappa (kappa = the conic's
+        # condition number) on both sides, and keeps everything when e >= 0.25
+        thr_k = thr[f] + 0.02
+        hd = 0.5 * (ca[f] - cc[f])
+        lmax = 0.5 * (ca[f] + cc[f]) + np.sqrt(hd * hd + cb[f] ** 2)
+        e = 1e-6 * lmax ** 2 / np.maximum(ca[f] * cc[f] - cb[f] ** 2, 1e-300)
+        must_drop = ((boxm * (1 - e) > thr_k * (1 + e) + 1e-3 * np.abs(thr_k)) & (e < 0.2) & ~skip[f])
+        ks = set(kept.tolist())
+        assert all(g in ks for g in f[must_keep]), tl
+        assert not any(g in ks for g in f[must_drop]), tl
+    assert n_cull < n_rect
+    print("instances: rectangle lists", n_rect, "culled lists", n_cull)
+
+
+def test_culled_and_rect_lists_render_identically():
+    """Culling changes the lists, not the result: images, contributor counts
+    and the last composited Gaussian of every pixel are bit-identical, and
+    the gradients agree (float atomics may sum in another order)."""
+    sc, spec, q, t = unit_inputs(5, 6)
+    res = []
+    for rect in (False, True):
+        c = api.Context(tile=(8, 8), batch=128, pixels_per_thread=1, rect_lists=rect)
+        g, cam, pose, out, saved = run_forward(c, sc, spec, q, t)
+        tx, ty = ocam(spec, (8, 8)).tiles
+        ranges, gids, _ = api.tile_lists(c, tx * ty, len(sc["mean"]))
+        d = torch.ones((3, spec.height, spec.width), device="cuda")
+        grads, pose6 = api.render_backward(c, g, cam, pose, saved, d, d[0] * 0.5, d[0] * -0.25)
+        torch.cuda.synchronize()
+        res.append((out, last_gids(out["last_idx"], ranges[:, 0], gids, (8, 8), spec.width), grads,
+                    pose6.cpu().numpy()))
+        c.close()
+    for k in ("rgb", "depth", "alpha", "final_T", "n_contrib"):
+        assert np.array_equal(res[0][0][k], res[1][0][k]), k
+    assert np.array_equal(res[0][1], res[1][1])
+    for k in api.GaussianParams.NAMES:
+        ok, worst = grad_close(getattr(res[0][2], k).cpu().numpy(), getattr(res[1][2], k).cpu().numpy())
+        assert ok, (k, worst)
+    ok, worst = grad_close(res[0][3], res[1][3])
+    assert ok, worst
+
