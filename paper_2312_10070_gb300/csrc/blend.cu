@@ -238,7 +238,9 @@ __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, in
     const float px = (float)ix + 0.5f;
     const uint2 rg = vp.ranges[tile];
     const int64_t HW = (int64_t)ck.W * ck.H;
-    float py[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], gd[PPT], gaT[PPT], S0[PPT], S1[PPT], S2[PPT], Sd[PPT];
+    // Q = sum over the entries behind the current one of (dL/dC . c_u + dL/dD z_u) alpha_u T_u:
+    // the four suffix sums of the colour / depth adjoints folded into one dot product
+    float py[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], gd[PPT], gaT[PPT], Q[PPT];
     int L[PPT];
     int lmax = -1;
 #pragma unroll
@@ -248,7 +250,7 @@ __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, in
         L[k] = -1;
         T[k] = 1.f;
         g0[k] = g1[k] = g2[k] = gd[k] = gaT[k] = 0.f;
-        S0[k] = S1[k] = S2[k] = Sd[k] = 0.f;
+        Q[k] = 0.f;
         if (ix < ck.W && iy < ck.H) {
             const int64_t p = (int64_t)iy * ck.W + ix;
             L[k] = vp.last_idx[p];
@@ -292,13 +294,11 @@ __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, in
                         const float iom = __fdividef(1.f, 1.f - e.alpha);
                         T[k] = T[k] * iom;  // T_j
                         const float w = e.alpha * T[k];
-                        const float dLda = g0[k] * (c.x * T[k] - S0[k] * iom) + g1[k] * (c.y * T[k] - S1[k] * iom)
-                                         + g2[k] * (c.z * T[k] - S2[k] * iom) + gd[k] * (b.z * T[k] - Sd[k] * iom)
-                                         + gaT[k] * iom;
-                        S0[k] = fmaf(c.x, w, S0[k]);
-                        S1[k] = fmaf(c.y, w, S1[k]);
-                        S2[k] = fmaf(c.z, w, S2[k]);
-                        Sd[k] = fmaf(b.z, w, Sd[k]);
+                        // dL/dalpha_j = sum_c g_c (c_j T_j - S_c / (1 - alpha_j)) + gaT / (1 - alpha_j)
+                        //             = T_j P - (Q - gaT) / (1 - alpha_j),  P = g . (c_j, z_j)
+                        const float P = fmaf(g0[k], c.x, fmaf(g1[k], c.y, fmaf(g2[k], c.z, gd[k] * b.z)));
+                        const float dLda = fmaf(T[k], P, -(Q[k] - gaT[k]) * iom);
+                        Q[k] = fmaf(P, w, Q[k]);
                         gz = fmaf(gd[k], w, gz);
                         if (!POSE_ONLY) {
                             gr = fmaf(g0[k], w, gr);
