@@ -585,7 +585,9 @@ static gsr_status map_iter(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *s
     float *sm = (float *)ctx->small.p;
     FrameBufs f;
     GSR_TRY(frame_bufs(ctx, HW, f));
-    GSR_CUDA(ctx, cudaMemsetAsync(G, 0, sizeof(float) * 14 * n, s));
+    // one keyframe: the projection backward writes every gradient (no zeroing,
+    // no read-modify-write); several: they accumulate into zeroed arrays
+    if (n_kf > 1) GSR_CUDA(ctx, cudaMemsetAsync(G, 0, sizeof(float) * 14 * n, s));
     GSR_CUDA(ctx, cudaMemsetAsync(sm + SM_MAPLOSS, 0, sizeof(float), s));
     Params P{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, n};
     float *d_pose = (float *)ctx->view.pose.p;
@@ -606,7 +608,7 @@ static gsr_status map_iter(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *s
         GSR_TRY(run_blend_backward(ctx, ck, &ro, f.d_rgb, f.d_depth, nullptr, false, s));
         GSR_TRY(prof_mark(ctx, PROF_BWD, true, s));
         GSR_TRY(prof_mark(ctx, PROF_PBWD, false, s));
-        GSR_TRY(run_project_backward(ctx, ctx->view, P, ck, d_pose, &gr, nullptr, true, 1.f, s));
+        GSR_TRY(run_project_backward(ctx, ctx->view, P, ck, d_pose, &gr, nullptr, n_kf > 1, 1.f, s));
         GSR_TRY(prof_mark(ctx, PROF_PBWD, true, s));
     }
     GSR_TRY(prof_mark(ctx, PROF_ADAM, false, s));

@@ -560,6 +560,11 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd(Params P, CamK ck, const
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float gpose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (i < P.n) {
+        // start the parameter loads while the rank (which decides whether they are needed) arrives
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.mean + 3 * i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.log_scale + 3 * i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.quat + 4 * i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.opacity_logit + i));
         int32_t r = rank_of_gid[i];
         float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
         float glog = 0.f, grgb[3] = {0.f, 0.f, 0.f};
