@@ -26,6 +26,14 @@
 
 namespace {
 
+// 4-byte asynchronous global -> shared copy; ok = false writes 0 (src-size 0)
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 constexpr int SHALO = 5;                 // window radius
 constexpr int TX = 32, TY = 48;          // output tile
 constexpr int LW = TX + 2 * SHALO;       // 42 columns loaded
@@ -133,15 +141,22 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(int W, int H, const float *
     const float C1 = 1e-4f, C2 = 9e-4f;
     float acc[3] = {0.f, 0.f, 0.f};  // SSIM sum, |x - y| sum, valid |D^ - D| sum
     const int hc = ((int)threadIdx.x >> 5) * HSEG, hlane = (int)threadIdx.x & 31;
-    for (int ch = 0; ch < 3; ++ch) {
+    // channel ch + 1's halo is copied into sx / sy asynchronously while channel
+    // ch's vertical sums and outputs are computed (its planes are read out by then)
+    auto load_channel = [&](int ch) {
+#pragma unroll 1
         for (int i = threadIdx.x; i < LH * LW; i += 256) {
             const int rr = i / LW, cc = i % LW;
             const int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
             const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
-            const int64_t q = (int64_t)ch * HW + (int64_t)yy * W + xx;
-            sx[rr][cc] = ok ? x[q] : 0.f;
-            sy[rr][cc] = ok ? y[q] : 0.f;
+            const int64_t q = ok ? (int64_t)ch * HW + (int64_t)yy * W + xx : 0;
+            cp_async4(&sx[rr][cc], x + q, ok);
+            cp_async4(&sy[rr][cc], y + q, ok);
         }
+    };
+    load_channel(0);
+    for (int ch = 0; ch < 3; ++ch) {
+        cp_async_wait_all();
         __syncthreads();
         for (int hr = hlane; hr < LH; hr += 32) {
             float xv[HSEG + 10], yv[HSEG + 10], o[HSEG];
@@ -178,7 +193,13 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(int W, int H, const float *
 #pragma unroll
             for (int j = 0; j < HSEG; ++j) hq[1][hr][hc + j] = o[j];
         }
+        float l1 = 0.f;  // this thread's |x - y| of the channel, read before sx / sy are refilled
+#pragma unroll
+        for (int j = 0; j < VSEG; ++j)
+            if (gx < W && oy + r0 + j < H) l1 += fabsf(sx[r0 + j + SHALO][c + SHALO] - sy[r0 + j + SHALO][c + SHALO]);
+        acc[1] += l1;
         __syncthreads();
+        if (ch < 2) load_channel(ch + 1);
         float mb[2][VSEG];
         vsum<2>(hq, r0, c, wk, mb);
 #pragma unroll
@@ -193,8 +214,6 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(int W, int H, const float *
                 const float iB = iB1 * iB2;
                 const float S = A1 * A2 * iB;
                 acc[0] += S;
-                const float xc = sx[r0 + j + SHALO][c + SHALO], yc = sy[r0 + j + SHALO][c + SHALO];
-                acc[1] += fabsf(xc - yc);
                 const int64_t p = (int64_t)gy * W + gx;
                 P[(3 * ch + 0) * HW + p] = gscale * (2.f * m2 * (A2 - A1) * iB - 2.f * m1 * S * (iB1 - iB2));
                 P[(3 * ch + 1) * HW + p] = gscale * (-S * iB2);
