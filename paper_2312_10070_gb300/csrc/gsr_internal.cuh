@@ -51,7 +51,7 @@ struct ViewScratch {
     DevBuf dkeys[2];    // u32 depth keys (ping-pong)
     DevBuf dvals[2];    // u32 Gaussian ids
     DevBuf rec_sorted;  // float4 x3 per depth rank
-    DevBuf tcount;      // u32 tile instances per warp of 32 depth ranks
+    DevBuf tcount;      // u32 kept tile instances per depth rank
     DevBuf inst_off;    // u32 exclusive scan of tcount
     DevBuf tkeys[2];    // u32 tile id per instance
     DevBuf tvals[2];    // u32 depth rank per instance

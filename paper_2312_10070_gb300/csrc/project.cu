@@ -214,10 +214,102 @@ __global__ void k_compact(int64_t n, const u32 *__restrict__ flag, const u32 *__
     vals[o] = (u32)i;
 }
 
-// records in depth order
+// Tile culling by rows.  A tile of the rectangle is kept when its Gaussian may
+// composite at one of its pixel centres: when the minimum of sigma over the
+// tile's pixel-centre box is at most the skip threshold T (ln(255 o) + 0.02,
+// widened by the float32 error margin of tile_may_hit: T (1 + e) / (1 - e),
+// e = 1e-6 kappa).  sigma is convex, so within one tile row (the band
+// dy in [Y0, Y1]) the x offsets where min over the band of sigma <= T form one
+// interval [L, R]: the x-extent of the ellipse sigma <= T cut by the band.
+// The ellipse's extreme points are at dy = -/+ (b / c) x_max, x_max =
+// sqrt(2 c T / det), and its boundary at dy is dx = (-b dy +/- sqrt(2 a T -
+// det dy^2)) / a, so R (L) is that boundary at the extreme point's dy clamped
+// to the band (cut to the ellipse's dy-extent sqrt(2 a T / det)).  The kept
+// tiles of the row are one run of columns; [L, R] is widened by 2e-4 px plus
+// a relative 2e-6 so that float32 rounding never drops a tile the exact test
+// keeps.  The box test of tile_may_hit decides the same tiles up to that
+// widening.
+struct RowCull {
+    float u = 0.f, v = 0.f, a = 1.f, b = 0.f, det = 1.f, ia = 1.f, t2a = 0.f, ymax = 0.f, kx = 0.f;
+    int mode = 0;  // 0: by rows, 1: every tile of the rectangle, 2: none
+};
+
+// Both the counting and the emitting kernel evaluate these two functions; every
+// operation is an explicitly rounded intrinsic, so no contraction can make the
+// two kernels decide a tile differently (the emitter writes exactly the counted
+// instances).
+__device__ __forceinline__ RowCull row_cull_setup(const float4 &A, const float4 &B, float thr0, bool cull)
+{
+    RowCull q;
+    q.mode = 1;
+    if (!cull) return q;
+    const float a = A.z, b = A.w, c = B.x;
+    const float det = __fsub_rn(__fmul_rn(a, c), __fmul_rn(b, b));
+    if (!(a > 0.f && c > 0.f && det > 0.f)) return q;
+    const float hd = __fmul_rn(0.5f, __fsub_rn(a, c));
+    const float lmax = __fadd_rn(__fmul_rn(0.5f, __fadd_rn(a, c)),
+                                 __fsqrt_rn(__fadd_rn(__fmul_rn(hd, hd), __fmul_rn(b, b))));
+    const float e = __fmul_rn(1e-6f, __fdiv_rn(__fmul_rn(lmax, lmax), det));
+    if (!(e < 0.25f)) return q;
+    float T = __fmul_rn(thr0, __fdiv_rn(__fadd_rn(1.f, e), __fsub_rn(1.f, e)));
+    T = __fadd_rn(T, __fmul_rn(1e-6f, fabsf(T)));
+    if (!(T >= 0.f)) {
+        q.mode = 2;
+        return q;
+    }
+    q.mode = 0;
+    q.u = A.x;
+    q.v = A.y;
+    q.a = a;
+    q.b = b;
+    q.det = det;
+    q.ia = __frcp_rn(a);
+    q.t2a = __fmul_rn(__fmul_rn(2.f, a), T);
+    q.ymax = __fsqrt_rn(__fdiv_rn(q.t2a, det));
+    q.kx = __fmul_rn(__fdiv_rn(b, c), __fsqrt_rn(__fdiv_rn(__fmul_rn(__fmul_rn(2.f, c), T), det)));
+    return q;
+}
+
+// kept tile columns [*lo, *hi] of tile row ty (within [rx0, rx1]; *lo > *hi: none)
+__device__ __forceinline__ void row_cols(const RowCull &q, const CamK &ck, int ty, int rx0, int rx1, int *lo, int *hi)
+{
+    *lo = rx0;
+    *hi = rx1;
+    if (q.mode == 1) return;
+    if (q.mode == 2) {
+        *hi = rx0 - 1;
+        return;
+    }
+    const float Y0 = __fsub_rn(__fadd_rn((float)(ty * ck.th), 0.5f), q.v);
+    const float Y1 = __fsub_rn(__fsub_rn((float)min(ty * ck.th + ck.th, ck.H), 0.5f), q.v);
+    float ylo = fmaxf(Y0, -q.ymax), yhi = fminf(Y1, q.ymax);
+    if (ylo > __fadd_rn(yhi, 2e-4f)) {
+        *hi = rx0 - 1;
+        return;
+    }
+    yhi = fmaxf(yhi, ylo);
+    const float dR = fminf(fmaxf(-q.kx, ylo), yhi), dL = fminf(fmaxf(q.kx, ylo), yhi);
+    const float sR = __fsqrt_rn(fmaxf(0.f, __fsub_rn(q.t2a, __fmul_rn(q.det, __fmul_rn(dR, dR)))));
+    const float sL = __fsqrt_rn(fmaxf(0.f, __fsub_rn(q.t2a, __fmul_rn(q.det, __fmul_rn(dL, dL)))));
+    float R = __fmul_rn(__fadd_rn(__fmul_rn(-q.b, dR), sR), q.ia);
+    float L = __fmul_rn(__fsub_rn(__fmul_rn(-q.b, dL), sL), q.ia);
+    const float d = __fadd_rn(2e-4f, __fmul_rn(2e-6f, __fadd_rn(fabsf(L), fabsf(R))));
+    L = __fsub_rn(L, d);
+    R = __fadd_rn(R, d);
+    // column tx's box spans x offsets [tx tw + 0.5 - u, tx tw + tw - 0.5 - u] (the
+    // last column unclipped: conservative); clamp before converting to int
+    const float tw = (float)ck.tw;
+    const float flo = fmaxf(ceilf(__fsub_rn(__fdiv_rn(__fadd_rn(__fadd_rn(L, q.u), 0.5f), tw), 1.f)), (float)rx0);
+    const float fhi = fminf(floorf(__fdiv_rn(__fsub_rn(__fadd_rn(R, q.u), 0.5f), tw)), (float)rx1);
+    *lo = (int)flo;
+    *hi = fhi < flo ? *lo - 1 : (int)fhi;
+}
+
+// records in depth order; kept tile instances per rank
+template <bool CULL>
 __global__ void k_gather(int64_t cap, const u32 *__restrict__ d_v, const u32 *__restrict__ vals,
                          const float4 *__restrict__ rec, float4 *__restrict__ rec_sorted,
-                         int32_t *__restrict__ rank_of_gid)
+                         int32_t *__restrict__ rank_of_gid, CamK ck, u32 *__restrict__ tcount)
 {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= cap || r >= (int64_t)*d_v) return;
@@ -227,166 +319,33 @@ __global__ void k_gather(int64_t cap, const u32 *__restrict__ d_v, const u32 *__
     rec_sorted[3 * r + 1] = b;
     rec_sorted[3 * r + 2] = c;
     rank_of_gid[gid] = (int32_t)r;
-}
-
-// Candidate instances of one warp: the tiles of the rectangles of its 32
-// consecutive depth ranks, in rank order and row-major within a rectangle,
-// taken 32 at a time (candidate k = kb + lane).  With CULL a candidate is
-// kept only if its Gaussian may composite somewhere in the tile
-// (tile_may_hit, the test the blend kernels' staging applies), so the tile
-// lists hold only such entries; every per-pixel decision is unchanged.
-struct WarpRects {
-    int x0 = 0, y0 = 0, w = 1;
-    float iw = 1.f;  // 1 / w
-    u32 cnt = 0, excl = 0, total = 0;
-    // the lane's Gaussian for the tile test: centre, conic, the reciprocals of
-    // its diagonal, and the threshold the box minimum of sigma is compared with
-    float u = 0.f, v = 0.f, ca = 1.f, cb = 0.f, cc = 1.f, ia = 1.f, ic = 1.f, thr = 0.f;
-};
-
-// The tile test of tile_may_hit with its per-Gaussian part hoisted: the box
-// minimum m of sigma is compared with thr (1 + e) / (1 - e) (e = 1e-6 kappa),
-// which tile_may_hit's m (1 - e) > thr (1 + e) rearranges to; the extra
-// relative 1e-6 absorbs the rounding of the rearrangement, so the test stays
-// conservative.  Degenerate conics keep every tile (threshold +inf).
-__device__ __forceinline__ void tile_test_setup(const float4 &a, const float4 &b, float thr0, WarpRects &q)
-{
-    q.u = a.x;
-    q.v = a.y;
-    q.ca = a.z;
-    q.cb = a.w;
-    q.cc = b.x;
-    const float det = q.ca * q.cc - q.cb * q.cb;
-    q.thr = __int_as_float(0x7f800000);  // +inf: keep
-    if (!(q.ca > 0.f && q.cc > 0.f && det > 0.f)) return;
-    const float hd = 0.5f * (q.ca - q.cc);
-    const float lmax = 0.5f * (q.ca + q.cc) + sqrtf(hd * hd + q.cb * q.cb);
-    const float e = 1e-6f * __fdividef(lmax * lmax, det);
-    if (!(e < 0.25f)) return;
-    q.ia = __fdividef(1.f, q.ca);
-    q.ic = __fdividef(1.f, q.cc);
-    const float t = thr0 * __fdividef(1.f + e, 1.f - e);
-    q.thr = t + 1e-6f * fabsf(t);
-}
-
-__device__ __forceinline__ WarpRects warp_rects(const float4 *__restrict__ rec_sorted, int64_t r, bool valid, bool cull)
-{
-    const unsigned F = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    WarpRects q;
-    if (valid) {
-        const float4 b = rec_sorted[3 * r + 1];
-        const u32 lo = __float_as_uint(b.w), hi = __float_as_uint(rec_sorted[3 * r + 2].w);
-        q.x0 = (int)(lo & 0xffffu);
-        q.y0 = (int)(lo >> 16);
-        q.w = (int)(hi & 0xffffu) - q.x0 + 1;
-        q.iw = __fdividef(1.f, (float)q.w);
-        q.cnt = (u32)(q.w * ((int)(hi >> 16) - q.y0 + 1));
-        if (cull) tile_test_setup(rec_sorted[3 * r], b, sigma_reject(b.y), q);
-    }
-    u32 incl = q.cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const u32 t = __shfl_up_sync(F, incl, o);
-        if (lane >= o) incl += t;
-    }
-    q.excl = incl - q.cnt;
-    q.total = __shfl_sync(F, incl, 31);
-    return q;
-}
-
-// candidate k (< q.total for a real one): its owner lane j and tile id; *keep
-// = the tile test when CULL (else true)
-template <bool CULL>
-__device__ __forceinline__ u32 candidate(const CamK &ck, const WarpRects &q, u32 k, int *owner, bool *keep)
-{
-    const unsigned F = 0xffffffffu;
-    // owner lane j: the largest j with excl_j <= k (lanes with cnt = 0 are skipped over)
-    int j = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const u32 e = __shfl_sync(F, q.excl, j + step);
-        const u32 c = __shfl_sync(F, q.cnt, j + step);
-        if (j + step < 32 && c > 0 && e <= k) j += step;
-    }
-    const u32 ej = __shfl_sync(F, q.excl, j);
-    const int wx = __shfl_sync(F, q.w, j), jx = __shfl_sync(F, q.x0, j), jy = __shfl_sync(F, q.y0, j);
-    const float iwx = __shfl_sync(F, q.iw, j);
-    const int local = (int)(k - ej);
-    // row = local / wx without an integer division: local < 2^24 and the
-    // rounding of (local + 0.5) / wx stays far inside the half-step margin
-    int row = (int)(((float)local + 0.5f) * iwx);
-    int col = local - row * wx;
-    if (col < 0) {  // never taken at image sizes (local < 2^20); keeps the split exact regardless
-        --row;
-        col += wx;
-    } else if (col >= wx) {
-        ++row;
-        col -= wx;
-    }
-    const int tx = jx + col, ty = jy + row;
-    const u32 tile = (u32)(ty * ck.tiles_x + tx);
-    *owner = j;
-    *keep = true;
-    if (CULL) {
-        const float u = __shfl_sync(F, q.u, j), v = __shfl_sync(F, q.v, j);
-        const float ca = __shfl_sync(F, q.ca, j), cb = __shfl_sync(F, q.cb, j), cc = __shfl_sync(F, q.cc, j);
-        const float ia = __shfl_sync(F, q.ia, j), ic = __shfl_sync(F, q.ic, j), thr = __shfl_sync(F, q.thr, j);
-        if (k < q.total) {
-            const float X0 = (float)(tx * ck.tw) + 0.5f - u, X1 = (float)min(tx * ck.tw + ck.tw, ck.W) - 0.5f - u;
-            const float Y0 = (float)(ty * ck.th) + 0.5f - v, Y1 = (float)min(ty * ck.th + ck.th, ck.H) - 0.5f - v;
-            float m = 0.f;
-            if (!(X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f))
-                m = fminf(fminf(edge_min(X0, Y0, Y1, ca, cb, cc, ic), edge_min(X1, Y0, Y1, ca, cb, cc, ic)),
-                          fminf(edge_min(Y0, X0, X1, cc, cb, ca, ia), edge_min(Y1, X0, X1, cc, cb, ca, ia)));
-            *keep = !(m > thr);
-        }
-    }
-    return tile;
-}
-
-// Instances per warp of 32 consecutive ranks (wcount[warp]; 0 past the
-// visible count), the input of the scan that places each warp's instances.
-template <bool CULL>
-__global__ void __launch_bounds__(256) k_count_instances(int64_t cap_v, const u32 *__restrict__ d_v,
-                                                         const float4 *__restrict__ rec_sorted, CamK ck,
-                                                         u32 *__restrict__ wcount)
-{
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const int64_t r0 = r - lane, gw = r >> 5;
-    if (r0 >= cap_v) return;  // warp-uniform; the grid has ceil(cap_v / 32) warps below cap_v
-    const int64_t V = (int64_t)*d_v;
-    if (r0 >= V) {
-        if (lane == 0) wcount[gw] = 0u;
-        return;
-    }
-    const WarpRects q = warp_rects(rec_sorted, r, r < V && r < cap_v, CULL);
+    const u32 lo = __float_as_uint(b.w), hi = __float_as_uint(c.w);
+    const int x0 = (int)(lo & 0xffffu), y0 = (int)(lo >> 16), x1 = (int)(hi & 0xffffu), y1 = (int)(hi >> 16);
     if (!CULL) {
-        if (lane == 0) wcount[gw] = q.total;
+        tcount[r] = (u32)((x1 - x0 + 1) * (y1 - y0 + 1));
         return;
     }
-    u32 kept = 0;
-    for (u32 kb = 0; kb < q.total; kb += 32) {
-        int j;
-        bool keep;
-        const u32 k = kb + lane;
-        candidate<CULL>(ck, q, k, &j, &keep);
-        kept += __popc(__ballot_sync(0xffffffffu, keep && k < q.total));
+    const RowCull q = row_cull_setup(a, b, sigma_reject(b.y), true);
+    u32 n = 0;
+    for (int ty = y0; ty <= y1; ++ty) {
+        int l, h;
+        row_cols(q, ck, ty, x0, x1, &l, &h);
+        n += (u32)max(0, h - l + 1);
     }
-    if (lane == 0) wcount[gw] = kept;
+    tcount[r] = n;
 }
 
-// One instance (tile id, depth rank) per kept candidate; the stream is in
-// depth order, so a stable sort on the tile id yields depth-ordered lists.  A
-// warp writes its instances contiguously from woff[warp] (the exclusive scan
-// of k_count_instances), compacting kept candidates with a ballot, each lane
-// locating the owner rank of its candidate with a 5-step search.
+// One instance (tile id, depth rank) per kept tile, written from off[rank]
+// (the exclusive scan of the counts); the stream is in depth order, so a
+// stable sort on the tile id yields depth-ordered lists.  A rank with at most
+// 64 instances is written by its own thread, row by row; larger ones are
+// written by their whole warp, one at a time, the lanes sharing each row's run.
 template <bool CULL>
 __global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restrict__ d_v,
-                                              const float4 *__restrict__ rec_sorted, const u32 *__restrict__ woff,
-                                              CamK ck, int64_t cap_i, u32 *__restrict__ tkeys,
-                                              u32 *__restrict__ tvals, u32 *__restrict__ counters)
+                                              const float4 *__restrict__ rec_sorted, const u32 *__restrict__ tcount,
+                                              const u32 *__restrict__ off, CamK ck, int64_t cap_i,
+                                              u32 *__restrict__ tkeys, u32 *__restrict__ tvals,
+                                              u32 *__restrict__ counters)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r == 0) {
@@ -397,26 +356,66 @@ __global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restri
     const unsigned F = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t V = (int64_t)*d_v;
-    const int64_t r0 = r - lane;  // first rank of this warp
-    if (r0 >= V || r0 >= cap_v) return;  // warp-uniform
-    const WarpRects q = warp_rects(rec_sorted, r, r < V && r < cap_v, CULL);
-    const int64_t base = (int64_t)woff[r >> 5];
-    u32 run = 0;
-    for (u32 kb = 0; kb < q.total; kb += 32) {
-        const u32 k = kb + lane;
-        int j;
-        bool keep;
-        const u32 tile = candidate<CULL>(ck, q, k, &j, &keep);
-        keep = keep && k < q.total;
-        const u32 bal = __ballot_sync(F, keep);
-        if (keep) {
-            const int64_t o = base + run + __popc(bal & ((1u << lane) - 1u));
-            if (o < cap_i) {
-                tkeys[o] = tile;
-                tvals[o] = (u32)(r0 + j);
-            }
+    if (r - lane >= V || r - lane >= cap_v) return;  // warp-uniform
+    const bool valid = r < V && r < cap_v;
+    int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
+    u32 cnt = 0, base = 0;
+    RowCull q;
+    if (valid) {
+        const float4 a = rec_sorted[3 * r], b = rec_sorted[3 * r + 1];
+        const u32 lo = __float_as_uint(b.w), hi = __float_as_uint(rec_sorted[3 * r + 2].w);
+        x0 = (int)(lo & 0xffffu);
+        y0 = (int)(lo >> 16);
+        x1 = (int)(hi & 0xffffu);
+        y1 = (int)(hi >> 16);
+        q = row_cull_setup(a, b, sigma_reject(b.y), CULL);
+        cnt = tcount[r];
+        base = off[r];
+    }
+    const bool big = cnt > 64u;
+    if (valid && !big && cnt > 0u) {
+        const int64_t end = (int64_t)base + cnt;  // never past the counted instances
+        int64_t o = base;
+        for (int ty = y0; ty <= y1; ++ty) {
+            int l, h;
+            row_cols(q, ck, ty, x0, x1, &l, &h);
+            for (int tx = l; tx <= h && o < end; ++tx, ++o)
+                if (o < cap_i) {
+                    tkeys[o] = (u32)(ty * ck.tiles_x + tx);
+                    tvals[o] = (u32)r;
+                }
         }
-        run += __popc(bal);
+    }
+    u32 bm = __ballot_sync(F, valid && big);
+    while (bm) {
+        const int j = __ffs(bm) - 1;
+        bm &= bm - 1;
+        RowCull qj;
+        qj.u = __shfl_sync(F, q.u, j);
+        qj.v = __shfl_sync(F, q.v, j);
+        qj.a = __shfl_sync(F, q.a, j);
+        qj.b = __shfl_sync(F, q.b, j);
+        qj.det = __shfl_sync(F, q.det, j);
+        qj.ia = __shfl_sync(F, q.ia, j);
+        qj.t2a = __shfl_sync(F, q.t2a, j);
+        qj.ymax = __shfl_sync(F, q.ymax, j);
+        qj.kx = __shfl_sync(F, q.kx, j);
+        qj.mode = __shfl_sync(F, q.mode, j);
+        const int jx0 = __shfl_sync(F, x0, j), jy0 = __shfl_sync(F, y0, j);
+        const int jx1 = __shfl_sync(F, x1, j), jy1 = __shfl_sync(F, y1, j);
+        int64_t o = __shfl_sync(F, base, j);
+        const int64_t end = o + __shfl_sync(F, cnt, j);  // never past the counted instances
+        const u32 rj = (u32)(r - lane + j);
+        for (int ty = jy0; ty <= jy1; ++ty) {
+            int l, h;
+            row_cols(qj, ck, ty, jx0, jx1, &l, &h);
+            for (int k = lane; k <= h - l; k += 32)
+                if (o + k < cap_i && o + k < end) {
+                    tkeys[o + k] = (u32)(ty * ck.tiles_x + l + k);
+                    tvals[o + k] = rj;
+                }
+            o += max(0, h - l + 1);
+        }
     }
 }
 
@@ -750,20 +749,16 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
     u32 *dk[2] = {(u32 *)V.dkeys[0].p, (u32 *)V.dkeys[1].p};
     u32 *dv[2] = {(u32 *)V.dvals[0].p, (u32 *)V.dvals[1].p};
     GSR_TRY(radix_sort_pairs(ctx, dk, dv, n, cnt + CNT_VISIBLE, 32, s, &V.radix_hist));
-    k_gather<<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, dv[0], (float4 *)V.rec.p, (float4 *)V.rec_sorted.p,
-                                (int32_t *)V.rank_of_gid.p);
-    // instances per warp of 32 ranks, then their placement (tcount / inst_off
-    // hold one entry per warp)
     const bool cull = !ctx->opt.rect_lists;
     if (cull)
-        k_count_instances<true><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, ck,
-                                                   (u32 *)V.tcount.p);
+        k_gather<true><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, dv[0], (float4 *)V.rec.p, (float4 *)V.rec_sorted.p,
+                                          (int32_t *)V.rank_of_gid.p, ck, (u32 *)V.tcount.p);
     else
-        k_count_instances<false><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, ck,
-                                                    (u32 *)V.tcount.p);
-    ctx->launches += 2;
+        k_gather<false><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, dv[0], (float4 *)V.rec.p, (float4 *)V.rec_sorted.p,
+                                           (int32_t *)V.rank_of_gid.p, ck, (u32 *)V.tcount.p);
+    ctx->launches += 1;
     GSR_LAUNCHED(ctx);
-    GSR_TRY(scan_exclusive(ctx, (u32 *)V.tcount.p, (u32 *)V.inst_off.p, ceil_div(n, 32), nullptr,
+    GSR_TRY(scan_exclusive(ctx, (u32 *)V.tcount.p, (u32 *)V.inst_off.p, n, cnt + CNT_VISIBLE,
                            cnt + CNT_INSTANCES, s, &V.scan_tmp));
     V.culled = cull;
     if (allow_grow) {
@@ -775,11 +770,13 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
     }
     if (V.cap_i <= 0) return gsr_fail(ctx, GSR_ERR_CAPACITY, "instance capacity is zero in fixed-capacity mode");
     if (cull)
-        k_emit<true><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, (u32 *)V.inst_off.p, ck,
-                                        V.cap_i, (u32 *)V.tkeys[0].p, (u32 *)V.tvals[0].p, cnt);
+        k_emit<true><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, (u32 *)V.tcount.p,
+                                        (u32 *)V.inst_off.p, ck, V.cap_i, (u32 *)V.tkeys[0].p, (u32 *)V.tvals[0].p,
+                                        cnt);
     else
-        k_emit<false><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, (u32 *)V.inst_off.p, ck,
-                                         V.cap_i, (u32 *)V.tkeys[0].p, (u32 *)V.tvals[0].p, cnt);
+        k_emit<false><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, (float4 *)V.rec_sorted.p, (u32 *)V.tcount.p,
+                                         (u32 *)V.inst_off.p, ck, V.cap_i, (u32 *)V.tkeys[0].p, (u32 *)V.tvals[0].p,
+                                         cnt);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     u32 *tk[2] = {(u32 *)V.tkeys[0].p, (u32 *)V.tkeys[1].p};
