@@ -241,8 +241,15 @@ def test_pixels_per_thread_is_bit_identical(tile):
     assert ok, worst
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
-def test_culled_lists_keep_exactly_what_can_composite(tile):
+def room_inputs():
+    """Thin, oriented surfels: a 320x180 view of a 60k-Gaussian room."""
+    spec = S.scale_camera(S.camera_room(), 320, 180)
+    q, t = S.submap_views()[2]
+    return S.room_scene(60_000, seed=7), spec, q, t
+
+
+@pytest.mark.parametrize("tile,scene", [((16, 16), "unit"), ((8, 8), "unit"), ((8, 8), "room"), ((16, 8), "room")])
+def test_culled_lists_keep_exactly_what_can_composite(tile, scene):
     """Default lists (rect_lists=0): each tile's list is its rectangle list
     with entries removed that cannot composite at any pixel centre of the
     tile.  Checked against FP64: an entry whose exact minimum of sigma over
@@ -252,7 +259,7 @@ def test_culled_lists_keep_exactly_what_can_composite(tile):
     margin above the float32 error of the exponential) by a relative 1e-3 is
     dropped; the order is the
     rectangle list's (the same GPU lists with rect_lists=1, filtered)."""
-    sc, spec, q, t = unit_inputs(3, 4)
+    sc, spec, q, t = unit_inputs(3, 4) if scene == "unit" else room_inputs()
     oc = ocam(spec, tile)
     sc64 = O.Scene.from_dict(sc)
     tx, ty = oc.tiles
