@@ -581,6 +581,70 @@ def run_map8(args):
     print(json.dumps(line), flush=True)
 
 
+def run_hires(args):
+    """The high-resolution configuration, 1752x1168 with 1.5M Gaussians
+    (hires_scene seed 4, identity pose; target = render of the scene,
+    optimised copy = scene + noise): the mapping iteration (gsr_map_step), and
+    the autograd-facing render forward + backward pair (gsr_render_forward,
+    gsr_render_backward with unit image gradients) in the default mode (the
+    backward reuses the forward's tile lists) and in the memory-saving mode
+    (the backward re-projects and re-bins).  L2 flushed between steps."""
+    import torch
+    from paper_2312_10070_gb300 import api, synth as S
+    spec = S.camera_hires()
+    cam = api.camera_from_spec(spec)
+    sc = S.hires_scene()
+    pose = api.make_pose(*S.IDENTITY_POSE)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record()
+            fn()
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    out = {}
+    ctx = api.Context(tile=(8, 8), batch=128, pixels_per_thread=1)
+    g_gt = api.GaussianParams.from_numpy(sc)
+    r = api.render_forward(ctx, g_gt, cam, pose)
+    kf = [(pose, r["rgb"].clone(), r["depth"].clone())]
+    del g_gt, r
+    g = api.GaussianParams.from_numpy(S.noisy_copy(sc, seed=4))
+    state = api.AdamMoments(g)
+    cfg = api.MapConfig()
+    ms = timed(lambda: api.map_step(ctx, g, state, cam, kf, None, 1, cfg, want_stats=False))
+    st = api.frame_stats(ctx)
+    out["map_step"] = dict(iters_per_s=1e3 / ms, ms_per_step=ms, visible=int(st["n_visible"]),
+                           instances=int(st["n_instances"]))
+    ctx.close()
+    d_rgb = torch.ones((3, spec.height, spec.width), device="cuda")
+    d_dep = torch.ones((spec.height, spec.width), device="cuda")
+    grads = g.zeros_like()
+    for mode in ("default", "memory_saving"):
+        c = api.Context(tile=(8, 8), batch=128, pixels_per_thread=1, memory_saving=(mode == "memory_saving"))
+
+        def fwd_bwd():
+            o = api.render_forward(c, g, cam, pose)
+            api.render_backward(c, g, cam, pose, o, d_rgb, d_dep, None, out=grads)
+        ms = timed(fwd_bwd)
+        out["render_fwd_bwd_" + mode] = dict(iters_per_s=1e3 / ms, ms_per_step=ms)
+        c.close()
+    line = dict(metric="mapping iters/s at 1752x1168, 1.5M Gaussians", value=out["map_step"]["iters_per_s"],
+                unit="iters/s", n_gpus=1, steps=args.steps, warmup=args.warmup,
+                ms_per_step=out["map_step"]["ms_per_step"], higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(workload="hires_scene(1.5M, seed 4), identity pose, tile 8x8 / batch 128 / one pixel per "
+                                     "thread", results=out, l2="flushed between steps (256 MB write)"))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -590,12 +654,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuned", default="",
                     help="tile_w,tile_h,batch,ppt_fwd,ppt_bwd: fixed blend configuration, no autotuning")
-    ap.add_argument("--workload", default="map", choices=["map", "map8", "warmstart", "seed"],
+    ap.add_argument("--workload", default="map", choices=["map", "map8", "hires", "warmstart", "seed"],
                     help="map: the headline mapping iteration; map8: the batched 8-keyframe mapping iteration; "
+                         "hires: 1752x1168 / 1.5M Gaussians in the default and the memory-saving mode; "
                          "warmstart: the warm-start CNN training step; seed: sub-map seeding of one keyframe")
     args = ap.parse_args()
     if args.workload == "map8":
         return run_map8(args)
+    if args.workload == "hires":
+        return run_hires(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
     if args.workload == "seed":

@@ -337,9 +337,15 @@ __global__ void k_gather(int64_t cap, const u32 *__restrict__ d_v, const u32 *__
 
 // One instance (tile id, depth rank) per kept tile, written from off[rank]
 // (the exclusive scan of the counts); the stream is in depth order, so a
-// stable sort on the tile id yields depth-ordered lists.  A rank with at most
-// 64 instances is written by its own thread, row by row; larger ones are
-// written by their whole warp, one at a time, the lanes sharing each row's run.
+// stable sort on the tile id yields depth-ordered lists.  The 32 ranks of a
+// warp own one contiguous output range.  Each lane lists its rank's row runs
+// (output offset, tile row, first column) in a per-warp table in shared
+// memory, in output order; then the lanes write the warp's range position by
+// position, each finding its run by binary search, so consecutive lanes store
+// to consecutive addresses.  A warp whose rows exceed the table writes
+// rank by rank from each lane instead.
+constexpr int EMIT_RUNS = 512;  // row runs per warp
+
 template <bool CULL>
 __global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restrict__ d_v,
                                               const float4 *__restrict__ rec_sorted, const u32 *__restrict__ tcount,
@@ -347,6 +353,9 @@ __global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restri
                                               u32 *__restrict__ tkeys, u32 *__restrict__ tvals,
                                               u32 *__restrict__ counters)
 {
+    __shared__ u32 s_start[8][EMIT_RUNS];  // run's first output offset, relative to the warp's range
+    __shared__ u32 s_cell[8][EMIT_RUNS];   // (tile row << 16) | first column
+    __shared__ uint8_t s_lane[8][EMIT_RUNS];
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r == 0) {
         u32 total = counters[CNT_INSTANCES];
@@ -354,9 +363,9 @@ __global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restri
         if ((int64_t)total > cap_i) atomicOr(&counters[CNT_STATUS], GSR_FLAG_CAPACITY);
     }
     const unsigned F = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int64_t V = (int64_t)*d_v;
-    if (r - lane >= V || r - lane >= cap_v) return;  // warp-uniform
+    const int lane = threadIdx.x & 31, w = (int)threadIdx.x >> 5;
+    const int64_t V = (int64_t)*d_v, r0 = r - lane;
+    if (r0 >= V || r0 >= cap_v) return;  // warp-uniform
     const bool valid = r < V && r < cap_v;
     int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
     u32 cnt = 0, base = 0;
@@ -372,8 +381,49 @@ __global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restri
         cnt = tcount[r];
         base = off[r];
     }
-    const bool big = cnt > 64u;
-    if (valid && !big && cnt > 0u) {
+    const u32 wbase = __shfl_sync(F, base, 0);  // lane 0's rank is valid (r0 < V)
+    const u32 wend = __reduce_max_sync(F, valid ? base + cnt : 0u);
+    // table slots: one per row of each rank with instances (empty rows included)
+    const u32 nrow = (valid && cnt > 0u) ? (u32)(y1 - y0 + 1) : 0u;
+    u32 incl = nrow;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(F, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const u32 nruns = __shfl_sync(F, incl, 31);
+    if (nruns <= (u32)EMIT_RUNS) {
+        u32 slot = incl - nrow, rel = base - wbase;
+        for (u32 k = 0; k < nrow; ++k, ++slot) {
+            const int ty = y0 + (int)k;
+            int l, h;
+            row_cols(q, ck, ty, x0, x1, &l, &h);
+            s_start[w][slot] = rel;
+            s_cell[w][slot] = ((u32)ty << 16) | (u32)l;
+            s_lane[w][slot] = (uint8_t)lane;
+            rel += (u32)max(0, h - l + 1);
+        }
+        __syncwarp();
+        const u32 total = wend - wbase;
+        for (u32 p = lane; p < total; p += 32) {
+            // the last run starting at or before p (empty runs share the next run's start)
+            int lo = 0, hi = (int)nruns - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_start[w][mid] <= p) lo = mid;
+                else hi = mid - 1;
+            }
+            const u32 cell = s_cell[w][lo];
+            const int64_t o = (int64_t)wbase + p;
+            if (o < cap_i) {
+                tkeys[o] = (cell >> 16) * (u32)ck.tiles_x + (cell & 0xffffu) + (p - s_start[w][lo]);
+                tvals[o] = (u32)(r0 + s_lane[w][lo]);
+            }
+        }
+        return;
+    }
+    // too many rows for the table: each lane writes its own rank
+    if (valid && cnt > 0u) {
         const int64_t end = (int64_t)base + cnt;  // never past the counted instances
         int64_t o = base;
         for (int ty = y0; ty <= y1; ++ty) {
@@ -384,37 +434,6 @@ __global__ void __launch_bounds__(256) k_emit(int64_t cap_v, const u32 *__restri
                     tkeys[o] = (u32)(ty * ck.tiles_x + tx);
                     tvals[o] = (u32)r;
                 }
-        }
-    }
-    u32 bm = __ballot_sync(F, valid && big);
-    while (bm) {
-        const int j = __ffs(bm) - 1;
-        bm &= bm - 1;
-        RowCull qj;
-        qj.u = __shfl_sync(F, q.u, j);
-        qj.v = __shfl_sync(F, q.v, j);
-        qj.a = __shfl_sync(F, q.a, j);
-        qj.b = __shfl_sync(F, q.b, j);
-        qj.det = __shfl_sync(F, q.det, j);
-        qj.ia = __shfl_sync(F, q.ia, j);
-        qj.t2a = __shfl_sync(F, q.t2a, j);
-        qj.ymax = __shfl_sync(F, q.ymax, j);
-        qj.kx = __shfl_sync(F, q.kx, j);
-        qj.mode = __shfl_sync(F, q.mode, j);
-        const int jx0 = __shfl_sync(F, x0, j), jy0 = __shfl_sync(F, y0, j);
-        const int jx1 = __shfl_sync(F, x1, j), jy1 = __shfl_sync(F, y1, j);
-        int64_t o = __shfl_sync(F, base, j);
-        const int64_t end = o + __shfl_sync(F, cnt, j);  // never past the counted instances
-        const u32 rj = (u32)(r - lane + j);
-        for (int ty = jy0; ty <= jy1; ++ty) {
-            int l, h;
-            row_cols(qj, ck, ty, jx0, jx1, &l, &h);
-            for (int k = lane; k <= h - l; k += 32)
-                if (o + k < cap_i && o + k < end) {
-                    tkeys[o + k] = (u32)(ty * ck.tiles_x + l + k);
-                    tvals[o + k] = rj;
-                }
-            o += max(0, h - l + 1);
         }
     }
 }
