@@ -110,7 +110,6 @@ constexpr int RX_WARPS = 8;
 constexpr int RX_THREADS = RX_WARPS * 32;
 constexpr int RX_ROUNDS = 8;                         // keys per lane
 constexpr int RX_TILE = RX_THREADS * RX_ROUNDS;      // 2048 keys per block
-constexpr int RX_WARP_SPAN = 32 * RX_ROUNDS;         // 256 consecutive keys per warp
 constexpr int RX_MAX_PASSES = 4;
 constexpr u32 LB_AGG = 1u << 30, LB_INC = 2u << 30, LB_MASK = (1u << 30) - 1u;
 constexpr int LB_SPIN_LIMIT = 1 << 24;               // bounded look-back wait
@@ -165,13 +164,14 @@ __global__ void __launch_bounds__(RX) k_radix_digit_base(u32 *ghist)
     h[threadIdx.x] = sc[threadIdx.x] - v;
 }
 
-// Lanes of the warp whose digit equals this lane's (digit RX marks "no key"):
-// one ballot per digit bit.
+// Lanes of the warp whose digit equals this lane's: one ballot per digit bit
+// (BITS = RX_BITS + 1 when digit RX marks "no key" in a partial tile).
+template <int BITS>
 __device__ __forceinline__ u32 digit_peers(u32 dg)
 {
     u32 peers = 0xffffffffu;
 #pragma unroll
-    for (int b = 0; b <= RX_BITS; ++b) {
+    for (int b = 0; b < BITS; ++b) {
         const bool bit = (dg >> b) & 1u;
         const u32 m = __ballot_sync(0xffffffffu, bit);
         peers &= bit ? m : ~m;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(RX_THREADS, 4) k_radix_onesweep(const u32 *__r
     __shared__ u32 wcnt[RX_WARPS][RX];
     constexpr int TILE = RX_THREADS * ROUNDS, SPAN = 32 * ROUNDS;
     __shared__ u32 s_key[TILE], s_val[TILE];
-    __shared__ u32 s_lstart[RX], s_gpos[RX];
+    __shared__ u32 s_gpos[RX];
     __shared__ int s_tile;
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket, 1u);
     for (int d = threadIdx.x; d < RX_WARPS * RX; d += RX_THREADS) (&wcnt[0][0])[d] = 0;
@@ -216,11 +216,12 @@ __global__ void __launch_bounds__(RX_THREADS, 4) k_radix_onesweep(const u32 *__r
         k[r] = i < n ? kin[i] : 0u;
         v[r] = i < n ? vin[i] : 0u;
     }
+    const bool full = base + TILE <= n;  // every lane holds a key in every round
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
         const bool ok = wbase + r * 32 + lane < n;
         const u32 dg = ok ? (k[r] >> shift) & (RX - 1) : (u32)RX;  // RX = no key
-        const u32 peers = digit_peers(dg);
+        const u32 peers = full ? digit_peers<RX_BITS>(dg) : digit_peers<RX_BITS + 1>(dg);
         // rank of this key among the warp's keys of its digit, in input order
         const u32 before = ok ? wcnt[w][dg] : 0u;
         rk[r] = ok ? before + __popc(peers & lt) : ~0u;  // ~0: no key
@@ -271,8 +272,7 @@ __global__ void __launch_bounds__(RX_THREADS, 4) k_radix_onesweep(const u32 *__r
             __syncthreads();
         }
         const u32 lstart = sc[d] - tot;
-        s_lstart[d] = lstart;
-        s_gpos[d] = digit_base[d] + prefix;
+        s_gpos[d] = digit_base[d] + prefix - lstart;  // global slot of local position i: s_gpos + i
         u32 run = lstart;  // per-warp starts inside the block
 #pragma unroll
         for (int ww = 0; ww < RX_WARPS; ++ww) {
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(RX_THREADS, 4) k_radix_onesweep(const u32 *__r
     for (int i = threadIdx.x; i < cnt; i += RX_THREADS) {
         const u32 key = s_key[i];
         const int dd = (int)((key >> shift) & (RX - 1));
-        const u32 gp = s_gpos[dd] + (u32)i - s_lstart[dd];
+        const u32 gp = s_gpos[dd] + (u32)i;
         kout[gp] = key;
         vout[gp] = s_val[i];
     }
