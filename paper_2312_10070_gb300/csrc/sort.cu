@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(RX_THREADS, 4) k_radix_onesweep(const u32 *__r
                     atomicOr(status, GSR_FLAG_TIMEOUT);
                     break;
                 }
+                if (spins > 4) __nanosleep(32);  // leave the issue slots to the warps still ranking
                 continue;
             }
             prefix += x & LB_MASK;
