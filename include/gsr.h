@@ -325,6 +325,14 @@ GSR_API gsr_status gsr_map_step(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_sta
                         const float *kf_weights, int32_t n_iters, const gsr_map_opts *opt,
                         gsr_map_stats *out, void *stream);
 
+/* Stream-ordered read of the mapping loss (no synchronisation): enqueues on
+ * `stream` a copy of the weighted loss (+ w_reg L_reg) of the last iteration
+ * of the last gsr_map_step on this context into *loss_dev (caller-owned
+ * device float), so a caller can read every step's loss back without
+ * stalling the next step.  Call it on the stream of that gsr_map_step
+ * (before any map step it copies 0).  GSR_ERR_INVALID_ARG on NULL arguments. */
+GSR_API gsr_status gsr_map_loss(gsr_ctx *ctx, float *loss_dev, void *stream);
+
 /* ------------------------------------------------------------ autotune */
 
 typedef struct {

@@ -155,6 +155,7 @@ PROTOTYPES = {
                           c_vp]),
     "gsr_merge_submap": (c_i32, [c_vp, ctypes.POINTER(GaussiansMut), c_i64, c_i64, ctypes.POINTER(Gaussians), c_f,
                                  ctypes.POINTER(c_i64), c_vp]),
+    "gsr_map_loss": (c_i32, [c_vp, c_vp, c_vp]),
     "gsr_probe_fma": (c_i32, [c_vp, c_i32, c_i32, c_vp]),
     "gsr_probe_exp": (c_i32, [c_vp, c_i32, c_i32, c_vp]),
     "gsr_warmstart_num_params": (c_i64, []),

@@ -310,6 +310,14 @@ def map_step(ctx: Context, g: GaussianParams, state: AdamMoments, cam: L.Camera,
     return dict(loss_last=st.loss_last, iters=st.iters) if want_stats else None
 
 
+def map_loss(ctx: Context, out: torch.Tensor = None) -> torch.Tensor:
+    """gsr_map_loss: the last map step's loss, copied on the current stream
+    into a device scalar (no synchronisation)."""
+    out = out if out is not None else torch.empty((), dtype=torch.float32, device="cuda")
+    ctx.check(ctx.lib.gsr_map_loss(ctx.handle, ctypes.c_void_p(out.data_ptr()), _stream()))
+    return out
+
+
 # ------------------------------------------------------------- seeding
 class SubMap:
     """Gaussian arrays of a sub-map with room for `capacity` Gaussians, the

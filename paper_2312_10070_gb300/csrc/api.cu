@@ -736,6 +736,14 @@ static gsr_status map_iter_multi(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_st
     return GSR_OK;
 }
 
+extern "C" gsr_status gsr_map_loss(gsr_ctx *ctx, float *loss_dev, void *stream)
+{
+    if (!ctx || !loss_dev) return GSR_ERR_INVALID_ARG;
+    GSR_CUDA(ctx, cudaMemcpyAsync(loss_dev, (const float *)ctx->small.p + SM_MAPLOSS, sizeof(float),
+                                  cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return GSR_OK;
+}
+
 extern "C" gsr_status gsr_map_step(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *st, const gsr_camera *cam,
                                    const gsr_keyframe *kfs, int32_t n_kf, const float *kf_weights, int32_t n_iters,
                                    const gsr_map_opts *opt, gsr_map_stats *out, void *stream)

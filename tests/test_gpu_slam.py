@@ -210,6 +210,8 @@ def test_map_step_graph_replay_and_loss_decrease():
         s1 = api.map_step(ctx, g, st, cam, kfs, None, 2, cfg)
         g2 = g.clone()
         s2 = api.map_step(ctx, g, st, cam, kfs, None, 30, cfg)
+        # the stream-ordered readout gives the same loss as the synchronising stats
+        assert float(api.map_loss(ctx).cpu()) == s2["loss_last"]
         res.append((g2, s0, s1, s2))
         assert s2["loss_last"] < 0.8 * s0["loss_last"], (s0, s2)
     for k in api.GaussianParams.NAMES:
