@@ -15,7 +15,6 @@
 
 namespace {
 
-__device__ __forceinline__ float sgnf(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
 
 __global__ void k_adam_prep(int32_t *step, float b1, float b2, float *bc)
 {
@@ -28,9 +27,7 @@ __global__ void k_adam_prep(int32_t *step, float b1, float b2, float *bc)
 __device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, float lr, float b1, float b2, float eps,
                                       float bc1, float bc2)
 {
-    m = b1 * m + (1.f - b1) * g;
-    v = b2 * v + (1.f - b2) * g * g;
-    p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+    adam_update(p, g, m, v, lr, b1, b2, eps, bc1, bc2);
 }
 
 // Flat layout: the five parameter arrays are one index space of float4
@@ -72,26 +69,7 @@ __device__ __forceinline__ void adam_chunk(const FlatSeg &sgm, int64_t c4, const
 __device__ __forceinline__ float adam_log_scale3(float *p, const float *g, float *m, float *v, float rw,
                                                  const FlatSeg &sgm, const gsr_adam_opts &o, float bc1, float bc2)
 {
-    float sc[3], sb = 0.f, lsum = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        sc[k] = expf(p[k]);
-        sb += sc[k];
-    }
-    sb *= (1.f / 3.f);
-    float sg[3], ssum = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        lsum += fabsf(sc[k] - sb);
-        sg[k] = sgnf(sc[k] - sb);
-        ssum += sg[k];
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float gk = g[k] + rw * (sg[k] - ssum * (1.f / 3.f)) * sc[k];
-        adam1(p[k], gk, m[k], v[k], sgm.lr, o.beta1, o.beta2, o.eps, bc1, bc2);
-    }
-    return lsum;
+    return adam_log_scales3(p, g, m, v, rw, sgm.lr, o, bc1, bc2);
 }
 
 // log-scales of Gaussians [i0, i0 + cnt) with the L_reg gradient; returns their L_reg terms.
@@ -344,6 +322,24 @@ gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads
         k_lreg_final<<<1, 1024, 0, s>>>(part, (int)nb, o->w_reg / (float)(g->n > 0 ? g->n : 1), loss_reg_dev);
         ctx->launches += 1;
     }
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+gsr_status adam_prep(gsr_ctx *ctx, gsr_adam_state *st, const gsr_adam_opts *o, float **bc, cudaStream_t s)
+{
+    GSR_TRY(ensure_buf(ctx, ctx->small, 256 * sizeof(float)));
+    *bc = (float *)ctx->small.p;  // [0..1] bias corrections
+    k_adam_prep<<<1, 1, 0, s>>>(st->step, o->beta1, o->beta2, *bc);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+gsr_status adam_lreg_final(gsr_ctx *ctx, const float *part, int nb, float scale, float *loss_reg_dev, cudaStream_t s)
+{
+    k_lreg_final<<<1, 1024, 0, s>>>(part, nb, scale, loss_reg_dev);
+    ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     return GSR_OK;
 }

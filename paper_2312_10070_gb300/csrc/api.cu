@@ -608,7 +608,18 @@ static gsr_status map_iter(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *s
         GSR_TRY(run_blend_backward(ctx, ck, &ro, f.d_rgb, f.d_depth, nullptr, false, s));
         GSR_TRY(prof_mark(ctx, PROF_BWD, true, s));
         GSR_TRY(prof_mark(ctx, PROF_PBWD, false, s));
-        GSR_TRY(run_project_backward(ctx, ctx->view, P, ck, d_pose, &gr, nullptr, n_kf > 1, 1.f, s));
+        if (n_kf == 1) {
+            // projection backward fused with Adam (the "adam" phase holds only the L_reg sum)
+            GSR_TRY(run_project_backward_adam(ctx, ctx->view, g, st, &o->adam, ck, d_pose, nullptr, s));
+            GSR_TRY(prof_mark(ctx, PROF_PBWD, true, s));
+            GSR_TRY(prof_mark(ctx, PROF_ADAM, false, s));
+            const unsigned nb = (unsigned)ceil_div(n > 0 ? n : 1, 256);
+            GSR_TRY(adam_lreg_final(ctx, (const float *)ctx->pose_part.p, (int)nb,
+                                    o->adam.w_reg / (float)(n > 0 ? n : 1), sm + SM_MAPLOSS, s));
+            GSR_TRY(prof_mark(ctx, PROF_ADAM, true, s));
+            return GSR_OK;
+        }
+        GSR_TRY(run_project_backward(ctx, ctx->view, P, ck, d_pose, &gr, nullptr, true, 1.f, s));
         GSR_TRY(prof_mark(ctx, PROF_PBWD, true, s));
     }
     GSR_TRY(prof_mark(ctx, PROF_ADAM, false, s));

@@ -248,6 +248,47 @@ __device__ __forceinline__ Eval eval_gaussian(float px, float py, float u, float
 // reject on it never changes a skip decision of eval_gaussian.
 __device__ __forceinline__ float sigma_reject(float op) { return __logf(255.f * op) + 0.02f; }
 
+// ------------------------------------------------------------- Adam
+// One bias-corrected Adam update of one parameter (shared by the optimiser
+// kernels and the fused projection backward + Adam of the one-keyframe step).
+__device__ __forceinline__ void adam_update(float &p, float g, float &m, float &v, float lr, float b1, float b2,
+                                            float eps, float bc1, float bc2)
+{
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+}
+
+__device__ __forceinline__ float sign_of(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
+
+// One Gaussian's three log-scales p (in registers) with gradient g plus the
+// gradient of rw * |s - mean(s)|_1 (s = exp(p), Sec. 3.4 L_reg); returns the
+// unweighted L_reg term.
+__device__ __forceinline__ float adam_log_scales3(float *p, const float *g, float *m, float *v, float rw, float lr,
+                                                  const gsr_adam_opts &o, float bc1, float bc2)
+{
+    float sc[3], sb = 0.f, lsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        sc[k] = expf(p[k]);
+        sb += sc[k];
+    }
+    sb *= (1.f / 3.f);
+    float sg[3], ssum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lsum += fabsf(sc[k] - sb);
+        sg[k] = sign_of(sc[k] - sb);
+        ssum += sg[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float gk = g[k] + rw * (sg[k] - ssum * (1.f / 3.f)) * sc[k];
+        adam_update(p[k], gk, m[k], v[k], lr, o.beta1, o.beta2, o.eps, bc1, bc2);
+    }
+    return lsum;
+}
+
 // Pixel-centre box of a tile (clipped to the image).
 struct TileBox {
     float x0, x1, y0, y1;
@@ -346,6 +387,15 @@ gsr_status run_loss_track(gsr_ctx *ctx, int W, int H, const float *rgb, const fl
                           const float *alpha, const float *rgb_t, const float *depth_t, float lam_c,
                           float k_med, float apow, float *d_rgb, float *d_depth, float *loss_dev,
                           float *median_dev, cudaStream_t s);
+// step counter advance + bias corrections (device float[2], returned in *bc),
+// and the final L_reg reduction into *loss_reg_dev (part: nb block partial sums)
+gsr_status adam_prep(gsr_ctx *ctx, gsr_adam_state *st, const gsr_adam_opts *o, float **bc, cudaStream_t s);
+gsr_status adam_lreg_final(gsr_ctx *ctx, const float *part, int nb, float scale, float *loss_reg_dev, cudaStream_t s);
+// one-keyframe step: projection backward of every Gaussian fused with its Adam
+// update and L_reg (the gradients never reach memory)
+gsr_status run_project_backward_adam(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians_mut *g, gsr_adam_state *st,
+                                     const gsr_adam_opts *o, const CamK &ck, const float *d_pose,
+                                     float *loss_reg_dev, cudaStream_t s);
 gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads *gr,
                     gsr_adam_state *st, const gsr_adam_opts *o, float *loss_reg_dev, cudaStream_t s);
 gsr_status run_pose_adam(gsr_ctx *ctx, float *d_pose, const float *d_grad6, float *m6, float *v6,

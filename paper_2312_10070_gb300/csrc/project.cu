@@ -633,6 +633,96 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd(Params P, CamK ck, const
     }
 }
 
+// One-keyframe mapping step: the projection backward of Gaussian i (as in
+// k_project_bwd) followed at once by its Adam update with L_reg, so its 14
+// gradients stay in registers: the parameters are read once, the moments
+// read and written once, and no gradient array is written or read back.
+// Gaussians outside the view have zero gradients and still take their Adam
+// step.  Per-block sums of the L_reg terms go to lreg_part.
+__global__ void __launch_bounds__(256, 4) k_project_bwd_adam(Params P, gsr_gaussians_mut gw, CamK ck,
+                                                          const float *__restrict__ pose,
+                                                          const int32_t *__restrict__ rank_of_gid,
+                                                          const float *__restrict__ g2d, gsr_adam_state st,
+                                                          gsr_adam_opts o, const float *__restrict__ bc,
+                                                          float *__restrict__ lreg_part)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float lreg = 0.f;
+    if (i < P.n) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.mean + 3 * i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.log_scale + 3 * i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.quat + 4 * i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.opacity_logit + i));
+        const int32_t r = rank_of_gid[i];
+        float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+        float glog = 0.f, grgb[3] = {0.f, 0.f, 0.f};
+        if (r >= 0) {
+            const PoseR pr = load_pose(pose);
+            GProj g;
+            project_core(ck, pr, P.mean, P.log_scale, P.quat, P.opacity_logit[i], i, g);
+            const float4 *G4 = reinterpret_cast<const float4 *>(g2d + 12 * (int64_t)r);
+            const float4 q0 = G4[0], q1 = G4[1], q2 = G4[2];
+            grgb[0] = q1.z;
+            grgb[1] = q1.w;
+            grgb[2] = q2.x;
+            chain_to_params(ck, pr, g, q0, q1, q2, gm, gls, gq, &glog, nullptr);
+        }
+        const float bc1 = bc[0], bc2 = bc[1];
+        float p[4], m[4], v[4];
+        // log-scales with L_reg
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            p[k] = gw.log_scale[3 * i + k];
+            m[k] = st.m_log_scale[3 * i + k];
+            v[k] = st.v_log_scale[3 * i + k];
+        }
+        lreg = adam_log_scales3(p, gls, m, v, o.w_reg / (float)P.n, o.lr_log_scale, o, bc1, bc2);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gw.log_scale[3 * i + k] = p[k];
+            st.m_log_scale[3 * i + k] = m[k];
+            st.v_log_scale[3 * i + k] = v[k];
+        }
+        // means, colours, quaternion, opacity
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float pm = gw.mean[3 * i + k], mm = st.m_mean[3 * i + k], vm = st.v_mean[3 * i + k];
+            adam_update(pm, gm[k], mm, vm, o.lr_mean, o.beta1, o.beta2, o.eps, bc1, bc2);
+            gw.mean[3 * i + k] = pm;
+            st.m_mean[3 * i + k] = mm;
+            st.v_mean[3 * i + k] = vm;
+            float pc = gw.rgb[3 * i + k], mc = st.m_rgb[3 * i + k], vc = st.v_rgb[3 * i + k];
+            adam_update(pc, grgb[k], mc, vc, o.lr_rgb, o.beta1, o.beta2, o.eps, bc1, bc2);
+            gw.rgb[3 * i + k] = pc;
+            st.m_rgb[3 * i + k] = mc;
+            st.v_rgb[3 * i + k] = vc;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float pq = gw.quat[4 * i + k], mq = st.m_quat[4 * i + k], vq = st.v_quat[4 * i + k];
+            adam_update(pq, gq[k], mq, vq, o.lr_quat, o.beta1, o.beta2, o.eps, bc1, bc2);
+            gw.quat[4 * i + k] = pq;
+            st.m_quat[4 * i + k] = mq;
+            st.v_quat[4 * i + k] = vq;
+        }
+        float po = gw.opacity_logit[i], mo = st.m_opacity_logit[i], vo = st.v_opacity_logit[i];
+        adam_update(po, glog, mo, vo, o.lr_opacity, o.beta1, o.beta2, o.eps, bc1, bc2);
+        gw.opacity_logit[i] = po;
+        st.m_opacity_logit[i] = mo;
+        st.v_opacity_logit[i] = vo;
+    }
+    __shared__ float red[8];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lreg += __shfl_down_sync(0xffffffffu, lreg, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lreg;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += red[k];
+        lreg_part[blockIdx.x] = t;
+    }
+}
+
 // Multi-keyframe projection backward: every Gaussian's parameters are read
 // once, its image-space gradients of each keyframe in which it is visible
 // are chained through that keyframe's pose and summed in registers, and the
@@ -836,6 +926,25 @@ gsr_status run_project_backward(gsr_ctx *ctx, ViewScratch &V, const Params &P, c
         ctx->launches += 1;
         GSR_LAUNCHED(ctx);
     }
+    return GSR_OK;
+}
+
+gsr_status run_project_backward_adam(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians_mut *g, gsr_adam_state *st,
+                                     const gsr_adam_opts *o, const CamK &ck, const float *d_pose,
+                                     float *loss_reg_dev, cudaStream_t s)
+{
+    const int64_t n = g->n;
+    const unsigned nb = (unsigned)ceil_div(n > 0 ? n : 1, 256);
+    GSR_TRY(ensure_buf(ctx, ctx->pose_part, sizeof(float) * 6 * nb));
+    float *part = (float *)ctx->pose_part.p;
+    float *bc = nullptr;
+    GSR_TRY(adam_prep(ctx, st, o, &bc, s));
+    const Params P{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, n};
+    k_project_bwd_adam<<<nb, 256, 0, s>>>(P, *g, ck, d_pose, (const int32_t *)V.rank_of_gid.p, (const float *)V.g2d.p,
+                                          *st, *o, bc, part);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    if (loss_reg_dev) GSR_TRY(adam_lreg_final(ctx, part, (int)nb, o->w_reg / (float)(n > 0 ? n : 1), loss_reg_dev, s));
     return GSR_OK;
 }
 
