@@ -860,6 +860,11 @@ struct gsr_warmstart {
     DevBuf act[NL + 2];  // act[0] input (16 ch), act[l+1] conv l output, act[NL+1] dense-1 output
     DevBuf dz, dz2, dbuf, out, dout32, dout, loss_tmp;  // dz / dz2: ping-pong upstream gradients
     DevBuf status;         // u32 device flags raised by kernels (bounded waits)
+    // side streams of the backward: per convolution layer the weight gradient
+    // runs on side[0] while the four parity-class data-gradient GEMMs run on
+    // the caller's stream and side[1..3] (forked and joined with events)
+    cudaStream_t side[4] = {};
+    cudaEvent_t ev_fork = nullptr, ev_part[4] = {}, ev_wgrad[NL] = {};
     int tc_min_k = -1;     // forward products with K >= tc_min_k run on tcgen05 (< 0: never; the default,
                            // as the mma.sync kernel measured faster on every layer)
 };
@@ -1043,27 +1048,39 @@ gsr_status backward_impl(gsr_warmstart *w, const bf16 *dout, int batch, cudaStre
                                           dbuf, FLAT, nullptr, s)));
     k_relu_bwd<<<blocks(B * FLAT), 256, 0, s>>>(B * FLAT, dbuf, (const bf16 *)w->act[NL].p, dz);
     WS_TRY(launched(w));
+    auto ev = [&](cudaError_t e) { return e == cudaSuccess ? GSR_OK : ws_fail(w, GSR_ERR_CUDA, "stream event failed"); };
     for (int l = NL - 1; l >= 0; --l) {
         const int64_t M = B * HOUT[l] * WOUT[l];
         const int K = 9 * CINP[l], N = COUT[l];
-        // weight gradient, split over the M rows
-        // weight and bias gradients in one GEMM reducing over positions; the
-        // im2col operand carries an extra row of ones whose product is the bias
-        // gradient.  The larger of (N, K) takes the 128-row side of the tile.
+        // dz of this layer is complete on s: fork
+        WS_TRY(ev(cudaEventRecord(w->ev_fork, s)));
+        for (int i = 0; i < 4; ++i) WS_TRY(ev(cudaStreamWaitEvent(w->side[i], w->ev_fork, 0)));
+        // weight and bias gradients in one GEMM reducing over positions (on
+        // side[0]); the im2col operand carries an extra row of ones whose
+        // product is the bias gradient.  The larger of (N, K) takes the 128-row
+        // side of the tile.
         Operand im = im2col((const bf16 *)w->act[l].p, l, K + 8);
         im.ones_row = K;
         if (K > N) {
             WS_TRY((gemm<OP_IM_RC, OP_RC, EPI_ATOMIC_T>(w, K + 1, N, M, im, dense(dz, N, N), grad + L.w_off[l], K,
-                                                        nullptr, s, nullptr, grad + L.b_off[l])));
+                                                        nullptr, w->side[0], nullptr, grad + L.b_off[l])));
         } else {
             WS_TRY((gemm<OP_RC, OP_IM_RC, EPI_ATOMIC>(w, N, K + 1, M, dense(dz, N, N), im, grad + L.w_off[l], K,
-                                                      nullptr, s, nullptr, grad + L.b_off[l])));
+                                                      nullptr, w->side[0], nullptr, grad + L.b_off[l])));
         }
+        WS_TRY(ev(cudaEventRecord(w->ev_wgrad[l], w->side[0])));
         if (l == 0) break;
         // data gradient straight into the previous layer's output gradient (ReLU
         // mask applied), one GEMM per parity class of input pixels
         bf16 *dz_prev = dz == (bf16 *)w->dz.p ? (bf16 *)w->dz2.p : (bf16 *)w->dz.p;
+        // dz_prev is the buffer the weight gradient of layer l + 1 reads
+        if (l + 1 < NL)
+            for (int i = 0; i < 4; ++i) {
+                cudaStream_t sc = i == 0 ? s : w->side[i];
+                WS_TRY(ev(cudaStreamWaitEvent(sc, w->ev_wgrad[l + 1], 0)));
+            }
         for (int cls = 0; cls < 4; ++cls) {
+            cudaStream_t sc = cls == 0 ? s : w->side[cls];
             const int py = cls >> 1, px = cls & 1;
             const int Hc = (HIN[l] - py + 1) >> 1, Wc = (WIN[l] - px + 1) >> 1;
             const int rows = batch * Hc * Wc, ntap = (py ? 2 : 1) * (px ? 2 : 1);
@@ -1088,10 +1105,17 @@ gsr_status backward_impl(gsr_warmstart *w, const bf16 *dout, int batch, cudaStre
             bw.px = px;
             bw.cin = CINP[l];
             WS_TRY((gemm<OP_DT_KC, OP_WT_RC, EPI_MASK_BF16>(w, rows, CINP[l], (int64_t)ntap * N, a, bw, dz_prev,
-                                                             CINP[l], nullptr, s, (const bf16 *)w->act[l].p)));
+                                                             CINP[l], nullptr, sc, (const bf16 *)w->act[l].p)));
+        }
+        // join the parity classes: the next layer reads all of dz_prev
+        for (int i = 1; i < 4; ++i) {
+            WS_TRY(ev(cudaEventRecord(w->ev_part[i], w->side[i])));
+            WS_TRY(ev(cudaStreamWaitEvent(s, w->ev_part[i], 0)));
         }
         dz = dz_prev;
     }
+    // every weight gradient is in before the caller's stream goes on (Adam)
+    for (int l = 0; l < NL; ++l) WS_TRY(ev(cudaStreamWaitEvent(s, w->ev_wgrad[l], 0)));
     return GSR_OK;
 }
 
@@ -1126,6 +1150,13 @@ void gsr_warmstart_destroy(gsr_warmstart *w)
         if (b->p) cudaFree(b->p);
     for (int l = 0; l < NL + 2; ++l)
         if (w->act[l].p) cudaFree(w->act[l].p);
+    for (int i = 0; i < 4; ++i) {
+        if (w->side[i]) cudaStreamDestroy(w->side[i]);
+        if (w->ev_part[i]) cudaEventDestroy(w->ev_part[i]);
+    }
+    for (int l = 0; l < NL; ++l)
+        if (w->ev_wgrad[l]) cudaEventDestroy(w->ev_wgrad[l]);
+    if (w->ev_fork) cudaEventDestroy(w->ev_fork);
     delete w;
 }
 
@@ -1168,6 +1199,15 @@ gsr_status gsr_warmstart_create(gsr_warmstart **out, int32_t max_batch, uint64_t
     A(w->dout, sizeof(bf16) * B * NOUTP);
     A(w->loss_tmp, sizeof(float) * 4);
     A(w->status, sizeof(u32) * 4);
+    for (int i = 0; i < 4 && st == GSR_OK; ++i)
+        if (cudaStreamCreateWithFlags(&w->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&w->ev_part[i], cudaEventDisableTiming) != cudaSuccess)
+            st = ws_fail(w, GSR_ERR_CUDA, "stream / event creation failed");
+    for (int l = 0; l < NL && st == GSR_OK; ++l)
+        if (cudaEventCreateWithFlags(&w->ev_wgrad[l], cudaEventDisableTiming) != cudaSuccess)
+            st = ws_fail(w, GSR_ERR_CUDA, "event creation failed");
+    if (st == GSR_OK && cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        st = ws_fail(w, GSR_ERR_CUDA, "event creation failed");
     if (st != GSR_OK) {
         gsr_warmstart_destroy(w);
         return st;
