@@ -38,9 +38,13 @@ METRIC = "fwd+bwd render iters/s at 1200×680, 500k Gaussians; % HBM roofline"
 N_GAUSS = 500_000
 BAND_FRACTION = 8  # the CPU sample is 1/8 of the frame (85 rows)
 
-# algorithmic FP32 flops per pixel-Gaussian evaluation (FMA = 2), see the design doc
-FLOPS_FWD_EVAL = 22
-FLOPS_BWD_EVAL = 61
+# FP32 flops per walked pixel-Gaussian evaluation (every list entry a pixel
+# visits up to its last composited one; FMA = 2): the unit costs of the
+# method's cost model, about 20 forward and 50 backward.  A visited entry that
+# composites costs more (22 forward; 61 backward: recompute 11, adjoints 50),
+# one the sigma pre-test rejects about 9.
+FLOPS_FWD_EVAL = 20
+FLOPS_BWD_EVAL = 50
 
 
 def peaks():

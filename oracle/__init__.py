@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "gsr_oracle.c")
 _SO = os.path.join(_HERE, "libgsr_oracle.so")
 _lib = None
 
-# Fixed readings of points the paper leaves open (listed in the design doc).
+# Fixed readings of points the paper leaves open.
 ALPHA_MIN = 1.0 / 255.0
 ALPHA_MAX = 0.99
 T_STOP = 1e-4
