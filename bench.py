@@ -618,6 +618,66 @@ def run_map8(args):
     print(json.dumps(line), flush=True)
 
 
+def run_track(args):
+    """Frame-to-model tracking at 1200x680 against 300k Gaussians
+    (room_scene seed 100): each step tracks one frame of a smooth room
+    trajectory (room_trajectory seed 100, ~1.5 cm / <= 1 degree apart) with
+    100 pose-only iterations (render, L_tracking with the alpha and inlier
+    masks, pose backward, pose Adam + retraction) from the constant-velocity
+    initial pose, through gsr_track_step.  Targets are renders at the true
+    pose plus N(0, 0.01) colour noise and 1 % depth noise, depth invalid where
+    alpha < 0.5.  L2 is flushed before every frame; the 100 iterations of a
+    frame run back to back, as in tracking."""
+    import torch
+    from paper_2312_10070_gb300 import api, synth as S
+    from paper_2312_10070_gb300.warmstart import pose_error
+    iters = 100
+    spec = S.camera_room()
+    cam = api.camera_from_spec(spec)
+    ctx = api.Context()
+    g = api.GaussianParams.from_numpy(S.room_scene(300_000, seed=100))
+    n_frames = max(args.warmup, 3) + args.steps
+    qs, ts = S.room_trajectory(100, n_frames=n_frames + 2)
+    frames = []
+    for k in range(2, n_frames + 2):
+        r = api.render_forward(ctx, g, cam, api.make_pose(qs[k], ts[k]))
+        rgb, dep = S.add_sensor_noise(r["rgb"].cpu().numpy(), r["depth"].cpu().numpy(), r["alpha"].cpu().numpy(),
+                                      seed=k)
+        # constant-velocity initial pose on (q, t), q sign-aligned and renormalised
+        q1, q2 = np.asarray(qs[k - 1], np.float64), np.asarray(qs[k - 2], np.float64)
+        q2 = -q2 if np.dot(q1, q2) < 0 else q2
+        qi = 2 * q1 - q2
+        ti = 2 * np.asarray(ts[k - 1], np.float64) - np.asarray(ts[k - 2], np.float64)
+        frames.append((torch.from_numpy(rgb).cuda(), torch.from_numpy(dep).cuda(), qi / np.linalg.norm(qi), ti, k))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    ms, errs, launches = [], [], 0
+    for i, (rgb, dep, qi, ti, k) in enumerate(frames):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ctx.kernel_launches
+        e0.record()
+        p, st = api.track_step(ctx, g, cam, rgb, dep, api.make_pose(qi, ti), iters, api.TrackConfig())
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= len(frames) - args.steps:  # the first frames are warm-up (graph capture, scratch growth)
+            ms.append(e0.elapsed_time(e1))
+            launches += ctx.kernel_launches - l0
+            errs.append(pose_error(np.array(p.q[:], np.float64), np.array(p.t[:], np.float64), qs[k], ts[k]))
+    errs = np.array(errs)
+    ms_frame = float(np.mean(ms))
+    line = dict(metric="tracking iters/s (pose-only fwd+bwd at 1200x680, 300k Gaussians)",
+                value=iters / (ms_frame / 1e3), unit="iters/s", n_gpus=1, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms_frame, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+                data="synthetic",
+                config=dict(workload="gsr_track_step, 100 iterations per frame from the constant-velocity pose, "
+                                     "room_scene(300k, seed 100), room_trajectory seed 100", iters_per_frame=iters,
+                            l2="flushed before every frame", ms_per_frame=ms_frame,
+                            pose_error_max_cm=float(errs[:, 0].max() * 100), pose_error_max_deg=float(errs[:, 1].max())),
+                gpu_launches=int(launches))
+    print(json.dumps(line), flush=True)
+
+
 def run_hires(args):
     """The high-resolution configuration, 1752x1168 with 1.5M Gaussians
     (hires_scene seed 4, identity pose; target = render of the scene,
@@ -691,10 +751,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuned", default="",
                     help="tile_w,tile_h,batch,ppt_fwd,ppt_bwd: fixed blend configuration, no autotuning")
-    ap.add_argument("--workload", default="map", choices=["map", "map8", "hires", "warmstart", "seed"],
+    ap.add_argument("--workload", default="map", choices=["map", "map8", "hires", "warmstart", "seed", "track"],
                     help="map: the headline mapping iteration; map8: the batched 8-keyframe mapping iteration; "
                          "hires: 1752x1168 / 1.5M Gaussians in the default and the memory-saving mode; "
-                         "warmstart: the warm-start CNN training step; seed: sub-map seeding of one keyframe")
+                         "warmstart: the warm-start CNN training step; seed: sub-map seeding of one keyframe; "
+                         "track: 100-iteration frame-to-model tracking of 1200x680 frames, 300k Gaussians")
     args = ap.parse_args()
     if args.workload == "map8":
         return run_map8(args)
@@ -704,6 +765,8 @@ def main():
         return run_warmstart(args)
     if args.workload == "seed":
         return run_seed(args)
+    if args.workload == "track":
+        return run_track(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -1,7 +1,9 @@
 """The learned warm-start, trained on the GPU on synthetic rooms, reduces the
 error of a perturbed initial pose on held-out rooms, and the warm-started
 tracker (falling back to the plain initial pose when the network's pose has
-the larger tracking loss) needs no more iterations than the plain one.
+the larger tracking loss) needs no more iterations than the plain one; the
+wall-clock ms per frame of both trackers, network and fallback test
+included, are printed.
 
 Training rooms: room_scene(200k Gaussians), seeds 1000-1063, 24 frames each
 (trajectories with about 4 cm / 3 degrees between frames), 32 initial poses
@@ -9,6 +11,8 @@ per frame (49152 samples, 30 GB of inputs on the device); initial pose = true
 pose moved by a random twist of up to 5 cm / 3 degrees; 4000 Adam steps of
 256.  Held-out rooms: seeds 2000-2002, 16 frames x 4 initial poses.
 """
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -60,22 +64,49 @@ def test_warm_start_reduces_held_out_pose_error(trained):
     assert m1[0] < 0.85 * m0[0] and m1[1] < 0.85 * m0[1], (m0, m1)
 
 
+def _wall_ms(fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, (time.perf_counter() - t0) * 1e3
+
+
 def test_warm_started_tracker_with_fallback(trained):
+    """Iterations and wall-clock ms per frame to reach 1 cm / 0.5 degrees,
+    plain against warm-started.  The warm-started frame pays for the network
+    (160 x 120 render, input builder, batch-1 forward, twist read back), for
+    the fallback test (tracking loss at both start poses, one tracker
+    iteration each) and for its own tracker iterations; the plain frame for
+    its tracker iterations only.  Every frame's graphs are captured before the
+    timed calls (the convergence search runs first on the same frame)."""
     W, net = trained["W"], trained["net"]
     ctx_f, ctx_l, spec = trained["ctx_f"], trained["ctx_l"], trained["spec"]
     g, ev = trained["evals"][0]
     budgets = (10, 20, 40, 80, 160)
-    plain, warm, fallbacks = [], [], 0
+    cap = 2 * budgets[-1]
+    plain, warm, fallbacks, plain_ms, warm_ms = [], [], 0, [], []
     for k in range(0, 24, 3):
         fr = ev.frames[ev.frame[k]]
         q0, t0 = ev.init[k]
         n0, loss0, _ = W.iterations_to_converge(ctx_f, g, spec, fr, q0, t0, budgets)
         qw, tw = W.warm_start_pose(net, ctx_l, g, spec, fr, q0, t0)
         n1, loss1, _ = W.iterations_to_converge(ctx_f, g, spec, fr, qw, tw, budgets)
-        if loss1 > loss0:  # fallback: keep the plain initial pose
+        use_warm = loss1 <= loss0
+        if not use_warm:  # fallback: keep the plain initial pose
             n1, fallbacks = n0, fallbacks + 1
-        cap = 2 * budgets[-1]
         plain.append(n0 if n0 is not None else cap)
         warm.append(n1 if n1 is not None else cap)
+        # wall clock of each path for this frame
+        _, ms0 = _wall_ms(lambda: W.track_from(ctx_f, g, spec, fr, q0, t0, plain[-1]))
+        (qw2, tw2), ms_net = _wall_ms(lambda: W.warm_start_pose(net, ctx_l, g, spec, fr, q0, t0))
+        _, ms_check = _wall_ms(lambda: (W.track_from(ctx_f, g, spec, fr, qw2, tw2, 1),
+                                        W.track_from(ctx_f, g, spec, fr, q0, t0, 1)))
+        qs, ts = (qw2, tw2) if use_warm else (q0, t0)
+        _, ms1 = _wall_ms(lambda: W.track_from(ctx_f, g, spec, fr, qs, ts, warm[-1]))
+        plain_ms.append(ms0)
+        warm_ms.append(ms_net + ms_check + ms1)
     print("iterations plain", plain, "warm", warm, "fallbacks", fallbacks)
+    print("ms per frame plain %.2f warm-started %.2f (per frame: plain %s, warm %s)"
+          % (np.mean(plain_ms), np.mean(warm_ms), np.round(plain_ms, 2).tolist(), np.round(warm_ms, 2).tolist()))
     assert np.mean(warm) <= np.mean(plain)
