@@ -160,8 +160,24 @@ GSR_API gsr_status gsr_profile_read(gsr_ctx *ctx, float *ms, int32_t n, void *st
 GSR_API gsr_status gsr_render_forward(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
                               const gsr_pose *pose, gsr_render_out *out, void *stream);
 
-/* Counters of the last forward (synchronises `stream`). */
+/* Counters of the last forward (synchronises `stream`).  Also returns, and
+ * clears, a device-side condition latched since the last synchronising call
+ * (GSR_ERR_CAPACITY: a fixed-capacity forward had more tile instances than
+ * room, so its lists were truncated; GSR_ERR_NONFINITE; GSR_ERR_TIMEOUT);
+ * `st` is filled in either case. */
 GSR_API gsr_status gsr_frame_stats_get(gsr_ctx *ctx, gsr_frame_stats *st, void *stream);
+
+/* Failure-detection check (the paper has no counterpart).  Runs, in one warp,
+ * the bounded wait that the radix sort's decoupled look-back uses, on a word
+ * of the context's counter block that no kernel publishes, so the wait gives
+ * up after `polls` polls (1 .. 1000000: microseconds to about a second),
+ * latches GSR_ERR_TIMEOUT in the context's status word and the kernel
+ * returns.  The call synchronises `stream` and returns the latched status
+ * (GSR_ERR_TIMEOUT, or an earlier latched condition first), clearing it, so
+ * the context stays usable.  It exercises the error path of a wait that
+ * expires without faulting or hanging the GPU.  GSR_ERR_INVALID_ARG for a
+ * NULL context or `polls` out of range (no launch). */
+GSR_API gsr_status gsr_check_wait_timeout(gsr_ctx *ctx, int32_t polls, void *stream);
 
 /* Copies the tile lists of the last forward to HOST memory (synchronises;
  * for tests and debugging).  ranges: host uint32[2 * n_tiles] = [start, end)

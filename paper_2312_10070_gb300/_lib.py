@@ -126,6 +126,7 @@ PROTOTYPES = {
     "gsr_render_forward": (c_i32, [c_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Pose),
                                    ctypes.POINTER(RenderOut), c_vp]),
     "gsr_frame_stats_get": (c_i32, [c_vp, ctypes.POINTER(FrameStats), c_vp]),
+    "gsr_check_wait_timeout": (c_i32, [c_vp, c_i32, c_vp]),
     "gsr_tile_lists_get": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, ctypes.POINTER(c_i64), c_vp]),
     "gsr_render_backward": (c_i32, [c_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Pose),
                                     ctypes.POINTER(RenderOut), c_vp, c_vp, c_vp, ctypes.POINTER(GaussianGrads),

@@ -160,6 +160,12 @@ def frame_stats(ctx: Context) -> dict:
                 capacity_instances=st.capacity_instances)
 
 
+def check_wait_timeout(ctx: Context, polls: int = 4096):
+    """gsr_check_wait_timeout: a bounded device wait on a word nothing
+    publishes; raises GsrError(GSR_ERR_TIMEOUT) once it has expired."""
+    ctx.check(ctx.lib.gsr_check_wait_timeout(ctx.handle, int(polls), _stream()))
+
+
 def tile_lists(ctx: Context, n_tiles: int, n_gaussians: int, capacity: int = None):
     """gsr_tile_lists_get: (ranges uint32 [n_tiles, 2], gids int32 [I], depth bits uint32 [n])."""
     st = frame_stats(ctx)

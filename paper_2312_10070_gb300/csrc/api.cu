@@ -362,7 +362,25 @@ extern "C" gsr_status gsr_frame_stats_get(gsr_ctx *ctx, gsr_frame_stats *st, voi
                                         ceil_div(ctx->fwd_cam.height, ctx->opt.tile_h)
                                   : 0;
     st->capacity_instances = ctx->view.cap_i;
-    return GSR_OK;
+    return take_status(ctx, s);  // the counters are filled either way
+}
+
+// Defined in sort.cu: one warp runs the radix sort's bounded look-back wait
+// on `word`, giving up after `polls` polls with GSR_FLAG_TIMEOUT in *status.
+gsr_status lookback_wait_check(gsr_ctx *ctx, const u32 *word, int32_t polls, u32 *status, cudaStream_t s);
+
+extern "C" gsr_status gsr_check_wait_timeout(gsr_ctx *ctx, int32_t polls, void *stream)
+{
+    if (!ctx) return GSR_ERR_INVALID_ARG;
+    if (polls < 1 || polls > 1000000) return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "polls must lie in [1, 1000000]");
+    cudaStream_t s = (cudaStream_t)stream;
+    GSR_TRY(ensure_buf(ctx, ctx->view.counters, sizeof(u32) * CNT_WORDS));
+    u32 *cnt = (u32 *)ctx->view.counters.p;
+    // the last word of the counter block is written by no kernel: zero it, then wait on it
+    u32 *word = cnt + (CNT_WORDS - 1);
+    GSR_CUDA(ctx, cudaMemsetAsync(word, 0, sizeof(u32), s));
+    GSR_TRY(lookback_wait_check(ctx, word, polls, cnt + CNT_STATUS, s));
+    return take_status(ctx, s);
 }
 
 extern "C" gsr_status gsr_tile_lists_get(gsr_ctx *ctx, uint32_t *ranges, int32_t *gids, int64_t capacity,

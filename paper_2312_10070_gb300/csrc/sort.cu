@@ -114,6 +114,25 @@ constexpr int RX_MAX_PASSES = 4;
 constexpr u32 LB_AGG = 1u << 30, LB_INC = 2u << 30, LB_MASK = (1u << 30) - 1u;
 constexpr int LB_SPIN_LIMIT = 1 << 24;               // bounded look-back wait
 
+// Bounded wait for a look-back word: polls *p (through L2) until one of the
+// `ready` bits is set, at most `limit` polls, sleeping briefly between polls
+// after the first few so that the blocks still ranking get the issue slots.
+// Returns the word, or 0 once the limit is reached, after latching
+// GSR_FLAG_TIMEOUT in *status (the caller goes on without the value rather
+// than waiting forever).
+__device__ __forceinline__ u32 wait_published(const u32 *p, u32 ready, int limit, u32 *status)
+{
+    for (int spins = 0;; ++spins) {
+        const u32 x = __ldcg(p);
+        if (x & ready) return x;
+        if (spins >= limit) {
+            atomicOr(status, GSR_FLAG_TIMEOUT);
+            return 0u;
+        }
+        if (spins >= 4) __nanosleep(32);
+    }
+}
+
 // Digit totals of every pass at once: ghist[pass * RX + digit] (atomics).
 __global__ void __launch_bounds__(RX_THREADS) k_radix_global_hist(const u32 *__restrict__ keys, int64_t n_cap,
                                                                   const u32 *d_n, int passes, u32 *__restrict__ ghist)
@@ -244,17 +263,9 @@ __global__ void __launch_bounds__(RX_THREADS, 4) k_radix_onesweep(const u32 *__r
     u32 prefix = 0;
     if (tile > 0) {
         int j = tile - 1;
-        int spins = 0;
         while (j >= 0) {
-            const u32 x = __ldcg(lookback + (int64_t)j * RX + d);
-            if ((x & ~LB_MASK) == 0u) {
-                if (++spins > LB_SPIN_LIMIT) {  // a predecessor never published: give up, flag it
-                    atomicOr(status, GSR_FLAG_TIMEOUT);
-                    break;
-                }
-                if (spins > 4) __nanosleep(32);  // leave the issue slots to the warps still ranking
-                continue;
-            }
+            const u32 x = wait_published(lookback + (int64_t)j * RX + d, ~LB_MASK, LB_SPIN_LIMIT, status);
+            if (x == 0u) break;  // a predecessor never published: flagged, give up
             prefix += x & LB_MASK;
             if ((x & ~LB_MASK) == LB_INC) break;
             --j;
@@ -302,7 +313,22 @@ __global__ void __launch_bounds__(RX_THREADS, 4) k_radix_onesweep(const u32 *__r
     }
 }
 
+// Failure-detection check: one warp runs the look-back's bounded wait on a
+// word that nothing publishes, so the wait expires and latches the timeout.
+__global__ void k_wait_unpublished(const u32 *word, int limit, u32 *status)
+{
+    wait_published(word, ~LB_MASK, limit, status);
+}
+
 } // namespace
+
+gsr_status lookback_wait_check(gsr_ctx *ctx, const u32 *word, int32_t polls, u32 *status, cudaStream_t s)
+{
+    k_wait_unpublished<<<1, 32, 0, s>>>(word, polls, status);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
 
 gsr_status scan_exclusive(gsr_ctx *ctx, const u32 *in, u32 *out, int64_t n_cap, const u32 *d_n,
                           u32 *d_total, cudaStream_t s, DevBuf *tmp)

@@ -101,6 +101,8 @@ def test_invalid_arguments_are_rejected_without_gpu(lib):
     assert lib.gsr_create(None, None) == -1
     # stream-ordered loss readout: NULL arguments are rejected before any CUDA call
     assert lib.gsr_map_loss(None, None, None) == -1
+    # bounded-wait check: a NULL context is rejected before any launch
+    assert lib.gsr_check_wait_timeout(None, 100, None) == -1
     # throughput probes: sizes are checked before any launch
     assert lib.gsr_probe_fma(None, 1, 32, None) == -1
     assert lib.gsr_probe_exp(None, 1, 32, None) == -1
