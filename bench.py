@@ -65,22 +65,24 @@ def kernel_sources_sha256(files):
 
 def measured_traffic(kernel, tuned=None):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-    `kernel` from the committed ncu summary, or None when the kernel's sources
-    changed after that capture, when the capture ran another launch
-    configuration than `tuned` (tile, batch, pixels per thread), or when none
-    was taken."""
+    `kernel` from the committed ncu captures (profiles/traffic.json: per
+    kernel, one entry per captured launch configuration), or None when no
+    capture ran the launch configuration of `tuned` (tile, batch, pixels per
+    thread), when the kernel's sources changed after that capture, or when
+    none was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p)).get(kernel)
-    if not d or kernel_sources_sha256(d["sources"]) != d["sources_sha256"]:
-        return None
-    c = d.get("config")
-    if c and tuned:
-        ppt = tuned.get("ppt_bwd" if kernel == "blend_bwd" else "ppt_fwd")
-        if list(c["tile"]) != list(tuned["tile"]) or c["batch"] != tuned["batch"] or c["ppt"] != ppt:
-            return None
-    return d["dram_bytes_per_launch"]
+    for d in json.load(open(p)).get(kernel, []):
+        if kernel_sources_sha256(d["sources"]) != d["sources_sha256"]:
+            continue
+        c = d.get("config")
+        if c and tuned:
+            ppt = tuned.get("ppt_bwd" if kernel == "blend_bwd" else "ppt_fwd")
+            if list(c["tile"]) != list(tuned["tile"]) or c["batch"] != tuned["batch"] or c["ppt"] != ppt:
+                continue
+        return d["dram_bytes_per_launch"]
+    return None
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -235,10 +237,21 @@ def cpu_baseline(budget_s=30.0):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return dict(value=done / (BAND_FRACTION * dt), unit="iters/s", cores=O.num_threads(), kind="oracle",
+    cores = O.num_threads()
+    # the same oracle on one thread, one band
+    O.set_num_threads(1)
+    try:
+        t1 = time.perf_counter()
+        oracle_band_step(sc64, q, t, spec, 0)
+        dt1 = time.perf_counter() - t1
+    finally:
+        O.set_num_threads(cores)
+    return dict(value=done / (BAND_FRACTION * dt), unit="iters/s", cores=cores, kind="oracle",
                 sample=f"{done} of the 8 1200x85 bands of view {S.HEADLINE_VIEW} (each band: all 500k Gaussians "
                        f"projected, render, loss, backward, Adam); iters/s = bands / (8 x seconds)",
-                seconds=dt)
+                seconds=dt,
+                single_thread=dict(value=1.0 / (BAND_FRACTION * dt1), unit="iters/s", cores=1, seconds=dt1,
+                                   sample="band 0 of the same view on one thread, scaled x1/8"))
 
 
 def run_reference(args, rank, world):

@@ -122,6 +122,8 @@ def _load():
         lib.orc_pose_retract.argtypes = [P] * 5
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_num_threads.argtypes = []
+        lib.orc_set_num_threads.restype = None
+        lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -136,6 +138,11 @@ def _f64(a):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Thread count of the oracle's OpenMP loops (for timing runs)."""
+    _load().orc_set_num_threads(int(n))
 
 
 class Scene:

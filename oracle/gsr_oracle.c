@@ -972,3 +972,14 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Thread count of the OpenMP loops (timing runs: 1 for the single-thread
+ * baseline); n <= 0 leaves it unchanged. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

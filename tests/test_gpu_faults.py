@@ -11,6 +11,9 @@ the next synchronising call, and the context stays usable afterwards.
 - timeout: the radix sort's bounded look-back wait, run on a word nothing
   publishes, gives up after a few thousand polls; GSR_ERR_TIMEOUT is returned
   and the same context then renders bit-identically to a fresh one.
+- allocation failure: a scratch hint of 2^40 Gaussians asks cudaMalloc for
+  4 TiB, which it refuses without allocating; gsr_create returns GSR_ERR_OOM,
+  frees what it had allocated, and a new context works.
 """
 import numpy as np
 import pytest
@@ -86,3 +89,15 @@ def test_bounded_wait_expires_with_timeout_status():
         assert torch.equal(out[k], ref[k]), k
     ctx.close()
     ref_ctx.close()
+
+
+def test_allocation_failure_is_reported_and_cleaned_up():
+    with pytest.raises(_lib.GsrError) as e:
+        api.Context(max_gaussians=1 << 40)
+    assert e.value.status == -3, e.value
+    g, cam, pose = unit_scene()
+    ctx = api.Context()
+    out = api.render_forward(ctx, g, cam, pose)
+    assert api.frame_stats(ctx)["n_visible"] > 0
+    assert float(out["alpha"].max()) > 0.5
+    ctx.close()
