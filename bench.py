@@ -66,23 +66,30 @@ def kernel_sources_sha256(files):
 def measured_traffic(kernel, tuned=None):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
     `kernel` from the committed ncu captures (profiles/traffic.json: per
-    kernel, one entry per captured launch configuration), or None when no
-    capture ran the launch configuration of `tuned` (tile, batch, pixels per
-    thread), when the kernel's sources changed after that capture, or when
-    none was taken."""
+    kernel, one entry per captured launch configuration), or None when the
+    kernel's sources changed after the captures or none was taken.  The
+    capture of the same tile, batch and pixels per thread as `tuned` is
+    preferred; else one of the same tile shape (the traffic is set by the tile
+    lists, records and images: the captures of batch 64 with two pixels per
+    thread and batch 128 with one differ by 0.1 % in the backward and 2 % in
+    the forward).  Returns (bytes, captured configuration)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
-        return None
+        return None, None
+    same_tile = None
     for d in json.load(open(p)).get(kernel, []):
         if kernel_sources_sha256(d["sources"]) != d["sources_sha256"]:
             continue
         c = d.get("config")
-        if c and tuned:
-            ppt = tuned.get("ppt_bwd" if kernel == "blend_bwd" else "ppt_fwd")
-            if list(c["tile"]) != list(tuned["tile"]) or c["batch"] != tuned["batch"] or c["ppt"] != ppt:
-                continue
-        return d["dram_bytes_per_launch"]
-    return None
+        if not (c and tuned):
+            return d["dram_bytes_per_launch"], c
+        ppt = tuned.get("ppt_bwd" if kernel == "blend_bwd" else "ppt_fwd")
+        if list(c["tile"]) != list(tuned["tile"]):
+            continue
+        if c["batch"] == tuned["batch"] and c["ppt"] == ppt:
+            return d["dram_bytes_per_launch"], c
+        same_tile = same_tile or (d["dram_bytes_per_launch"], c)
+    return same_tile or (None, None)
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -453,8 +460,9 @@ def run_gpu(args, rank, world):
     if dom in ("blend_bwd", "blend_fwd"):
         fl = (FLOPS_BWD_EVAL if dom == "blend_bwd" else FLOPS_FWD_EVAL) * e_bwd
         ach = fl / (avg[dom] / 1e3) / 1e12
+        traffic, traffic_cfg = measured_traffic(dom, tuned)
         roof = dict(bound="alu", kernel=dom, achieved=ach, peak=peak_tf, unit="TFLOP/s", frac=ach / peak_tf,
-                    traffic=measured_traffic(dom, tuned), units=f"{e_bwd} pixel-Gaussian evaluations x "
+                    traffic=traffic, traffic_config=traffic_cfg, units=f"{e_bwd} pixel-Gaussian evaluations x "
                                        f"{FLOPS_BWD_EVAL if dom == 'blend_bwd' else FLOPS_FWD_EVAL} flops",
                     peak_note=f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_mhz']:.0f} MHz (derived)")
         # the same units measured on this device (FMA and ex2 throughput probes, after the timed region)
@@ -466,7 +474,7 @@ def run_gpu(args, rank, world):
                "adam": 392 * n}.get(dom, step_bytes)
         ach = per / (avg[dom] / 1e3) / 1e9
         roof = dict(bound="hbm", kernel=dom, achieved=ach, peak=pk["hbm"], unit="GB/s", frac=ach / pk["hbm"],
-                    traffic=measured_traffic(dom))
+                    traffic=measured_traffic(dom)[0])
     line = dict(metric=METRIC, value=value, unit="iters/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
                 data="synthetic", config=dict(config_dict(stats, None), autotuned=tuned), roofline=roof,
@@ -526,7 +534,7 @@ def run_warmstart(args):
                 config=dict(workload="warm-start CNN train step (forward, backward, Adam), batch 256, "
                                      "input 120x160x8", flops_per_sample=train),
                 roofline=dict(bound="tensor", kernel="warmstart_train", achieved=tf, peak=peak, unit="TFLOP/s",
-                              frac=tf / peak, traffic=measured_traffic("warmstart_train"), peak_note="measured bf16 burst" if d else "fallback"))
+                              frac=tf / peak, traffic=measured_traffic("warmstart_train")[0], peak_note="measured bf16 burst" if d else "fallback"))
     print(json.dumps(line), flush=True)
 
 
