@@ -197,16 +197,27 @@ _BAND_TARGETS = {}
 _ADAM = {}
 
 
-def oracle_band_step(sc64, q, t, spec, band_index=0):
-    """One step of the FP64 oracle on a horizontal band (1/8) of the frame:
-    render, mapping loss against the band of a target, backward, Adam.  The
-    target is a perturbed render of the band, made once per band."""
+def band_camera(spec, band_index):
     import oracle as O
     h = spec.height // BAND_FRACTION
-    cam = O.Camera(spec.width, h, spec.fx, spec.fy, spec.cx, spec.cy - band_index * h)
-    if band_index not in _BAND_TARGETS:
-        tr = O.render(sc64, q, t, cam)
-        _BAND_TARGETS[band_index] = (np.clip(tr["rgb"] * 0.97 + 0.01, 0, 1), tr["depth"] * 1.01)
+    return O.Camera(spec.width, h, spec.fx, spec.fy, spec.cx, spec.cy - band_index * h)
+
+
+def make_band_targets(sc64, q, t, spec):
+    """The target of every band (a perturbed render of it): inputs of the
+    oracle steps, made before any timing."""
+    import oracle as O
+    for b in range(BAND_FRACTION):
+        tr = O.render(sc64, q, t, band_camera(spec, b))
+        _BAND_TARGETS[b] = (np.clip(tr["rgb"] * 0.97 + 0.01, 0, 1), tr["depth"] * 1.01)
+
+
+def oracle_band_step(sc64, q, t, spec, band_index=0):
+    """One step of the FP64 oracle on a horizontal band (1/8) of the frame:
+    render, mapping loss against the band's target (make_band_targets),
+    backward, Adam."""
+    import oracle as O
+    cam = band_camera(spec, band_index)
     rgb_t, depth_t = _BAND_TARGETS[band_index]
     r = O.render(sc64, q, t, cam)
     lm = O.loss_map(r["rgb"], r["depth"], rgb_t, depth_t)
@@ -231,11 +242,7 @@ def cpu_baseline(budget_s=30.0):
     sc64 = O.Scene.from_dict(S.room_scene(N_GAUSS, seed=3))
     q, t = S.submap_views()[S.HEADLINE_VIEW]
     spec = S.camera_room()
-    for b in range(BAND_FRACTION):  # targets are inputs, made outside the timing
-        h = spec.height // BAND_FRACTION
-        cam = O.Camera(spec.width, h, spec.fx, spec.fy, spec.cx, spec.cy - b * h)
-        tr = O.render(sc64, q, t, cam)
-        _BAND_TARGETS[b] = (np.clip(tr["rgb"] * 0.97 + 0.01, 0, 1), tr["depth"] * 1.01)
+    make_band_targets(sc64, q, t, spec)  # inputs, made outside the timing
     t0 = time.perf_counter()
     done = 0
     for b in range(BAND_FRACTION):
@@ -270,6 +277,7 @@ def run_reference(args, rank, world):
     sc64 = O.Scene.from_dict(S.room_scene(N_GAUSS, seed=3))
     q, t = S.submap_views()[S.HEADLINE_VIEW]
     spec = S.camera_room()
+    make_band_targets(sc64, q, t, spec)  # inputs, made outside the timing
     for i in range(args.warmup):
         oracle_band_step(sc64, q, t, spec, i % BAND_FRACTION)
     t0 = time.perf_counter()
