@@ -110,6 +110,18 @@ class GaussianParams:
     rgb: torch.Tensor
 
     NAMES = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
+    ROW_SHAPES = ((3,), (3,), (4,), (), (3,))
+
+    def check(self):
+        """Raises ValueError unless every array is float32 with the layout
+        gsr_gaussians documents ([n,3], [n,3], [n,4], [n], [n,3]): the C ABI
+        reads them as such and cannot tell."""
+        n = self.n
+        for k, row in zip(self.NAMES, self.ROW_SHAPES):
+            t = getattr(self, k)
+            if t.dtype != torch.float32 or tuple(t.shape) != (n,) + row:
+                raise ValueError(f"{k}: expected float32 {[n, *row]}, got {t.dtype} {list(t.shape)}")
+        return self
 
     @classmethod
     def from_numpy(cls, d: dict, device="cuda"):
@@ -130,13 +142,13 @@ class GaussianParams:
         return GaussianParams(*[torch.zeros_like(t) for t in self.tensors()])
 
     def c(self) -> L.Gaussians:
-        return L.Gaussians(*[_ptr(t) for t in self.tensors()], self.n)
+        return L.Gaussians(*[_ptr(t) for t in self.check().tensors()], self.n)
 
     def c_mut(self) -> L.GaussiansMut:
-        return L.GaussiansMut(*[_ptr(t) for t in self.tensors()], self.n)
+        return L.GaussiansMut(*[_ptr(t) for t in self.check().tensors()], self.n)
 
     def c_grads(self) -> L.GaussianGrads:
-        return L.GaussianGrads(*[_ptr(t) for t in self.tensors()])
+        return L.GaussianGrads(*[_ptr(t) for t in self.check().tensors()])
 
 
 def render_forward(ctx: Context, g: GaussianParams, cam: L.Camera, pose: L.Pose, want_n_contrib=False) -> dict:
