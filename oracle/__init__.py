@@ -94,7 +94,9 @@ _I64 = ctypes.POINTER(ctypes.c_int64)
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        # GSR_ORACLE_LIB names another build of gsr_oracle.c to load instead:
+        # the mutation tests load copies with one planted mistake each
+        lib = ctypes.CDLL(os.environ.get("GSR_ORACLE_LIB") or build())
         P = ctypes.c_void_p
         lib.orc_project.restype = ctypes.c_int64
         lib.orc_project.argtypes = [ctypes.c_int64] + [P] * 6 + [ctypes.POINTER(_Cam)] + [P] * 9
