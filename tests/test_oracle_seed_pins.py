@@ -25,11 +25,24 @@ def test_splitmix64_published_outputs_and_bijectivity():
     assert np.all(np.abs(bits - 0.5) < 0.005)                # every output bit balanced
 
 
+def test_sampling_keys_are_the_published_generator_outputs():
+    """The key of pixel 0 under seed k * gamma is the k-th published output of
+    SplitMix64 seeded with 0, high 32 bits."""
+    gold = json.load(open(os.path.join(HERE, "golden", "splitmix64.json")))
+    for k, h in enumerate(gold["outputs_hex"]):
+        assert int(SD.uniform_keys(1, (k * GOLD) % (1 << 64))[0]) == int(h, 16) >> 32
+
+
 def test_uniform_sample_is_an_exact_nested_uniform_subset():
     rng = np.random.default_rng(0)
     elig = rng.random(4000) < 0.6
     a = SD.sample_uniform(elig, 500, seed=7)
     b = SD.sample_uniform(elig, 900, seed=7)
+    # the sample is the m eligible pixels of smallest key: no unselected
+    # eligible pixel has a smaller key than a selected one
+    keys = SD.uniform_keys(4000, 7).astype(np.int64)
+    rest = np.setdiff1d(np.nonzero(elig)[0], a)
+    assert keys[a].max() <= keys[rest].min()
     assert a.size == 500 and b.size == 900 and np.all(elig[a])
     assert np.all(np.diff(a) > 0) and set(a) <= set(b)       # ascending, nested
     np.testing.assert_array_equal(SD.sample_uniform(elig, 10 ** 6, 3), np.nonzero(elig)[0])
