@@ -48,6 +48,20 @@ MUTATIONS = [
     ("L_reg: scale mean over two axes", "sb /= 3.0;", "sb /= 2.0;"),
     ("Adam: second-moment bias correction dropped", "double mh = m1[i] / bc1, vh = m2[i] / bc2;",
      "double mh = m1[i] / bc1, vh = m2[i];"),
+    ("tile rectangle: right edge one tile short", "o->x1 = imin(tiles_x - 1, (int)floor(ex[1] / c->tile_w));",
+     "o->x1 = imin(tiles_x - 1, (int)floor(ex[1] / c->tile_w) - 1);"),
+    ("sort: depth order reversed", "if (da < db) return -1;\n    if (da > db) return 1;",
+     "if (da < db) return 1;\n    if (da > db) return -1;"),
+    ("log-scale chain: ds/dlog s = s dropped", "g_ls[k] = gs * o->s[k];", "g_ls[k] = gs;"),
+    ("quaternion: normalisation's projection dropped",
+     "for (int k = 0; k < 4; ++k) g_quat[k] = (gqh[k] - o->qhat[k] * dot) / o->qnorm;",
+     "for (int k = 0; k < 4; ++k) g_quat[k] = gqh[k] / o->qnorm;"),
+    ("SE(3) retraction: V's second-order term dropped", "V[i] = I + B * K[i] + Cc * K2[i];",
+     "V[i] = I + B * K[i];"),
+    ("tracking: colour residual weighted by 1 - lambda_c",
+     "L += w * (lam_c * lc + (1 - lam_c) * ed);", "L += w * ((1 - lam_c) * lc + (1 - lam_c) * ed);"),
+    ("tracking: alpha mask with exponent 1", "double w = in ? pow(alpha[p], apow) : 0.0;",
+     "double w = in ? alpha[p] : 0.0;"),
 ]
 
 

@@ -397,6 +397,11 @@ def test_loss_track_brute_force_and_fd():
     w = inl * al ** 3
     ref = np.sum(w * (0.5 * np.abs(a - b).sum(0) + 0.5 * e))
     np.testing.assert_allclose(out["loss"], ref, rtol=1e-12)
+    # Sec. 3.5 weighs colour by lambda_c and depth by 1 - lambda_c for any lambda_c
+    # (0.5 above hides a swap) and masks by alpha to any power
+    o2 = O.loss_track(a, d, al, b, dt, 0.3, 50.0, 2.0)
+    ref2 = np.sum(inl * al ** 2 * (0.3 * np.abs(a - b).sum(0) + 0.7 * e))
+    np.testing.assert_allclose(o2["loss"], ref2, rtol=1e-12)
     h = 1e-7
     for ch, y, x in [(0, 3, 3), (2, 9, 12), (1, 5, 6)]:
         ap, am = a.copy(), a.copy()
