@@ -1,6 +1,8 @@
-"""Host-side argument checks of the Python binding (no GPU): Gaussian arrays
-must be float32 with the documented layout before their pointers cross the
-C ABI, and tensors must be contiguous CUDA tensors."""
+"""Host-side code of the Python package, on the CPU: argument checks of the
+binding (Gaussian arrays must be float32 with the documented layout before
+their pointers cross the C ABI; tensors must be contiguous CUDA tensors),
+and the host pose arithmetic (SE(3) retraction against the oracle's, pose
+errors against scipy, twist sampling ranges)."""
 import pytest
 import torch
 
@@ -37,3 +39,44 @@ def test_wrong_dtype_or_shape_is_rejected_before_the_abi(name, bad):
 def test_host_tensors_are_rejected():
     with pytest.raises(ValueError, match="CUDA"):
         params().c()
+
+
+def test_host_pose_retraction_matches_the_oracle():
+    """api.pose_exp_left (product host code: the autograd wrapper's and the
+    warm start's pose update) against the oracle's SE(3) retraction, which is
+    pinned to the matrix exponential; small, large and zero rotations."""
+    import numpy as np
+    import oracle as O
+    rng = np.random.default_rng(3)
+    for k in range(20):
+        q = rng.standard_normal(4)
+        q /= np.linalg.norm(q)
+        t = rng.standard_normal(3)
+        xi = rng.standard_normal(6) * (0.5 if k % 2 else 1e-3)
+        if k == 0:
+            xi[3:] = 0.0
+        qa, ta = api.pose_exp_left(q, t, xi)
+        qo, to = O.pose_retract(q, t, xi)
+        qo = qo if qo[0] >= 0 else -qo
+        np.testing.assert_allclose(qa, qo, atol=1e-12)
+        np.testing.assert_allclose(ta, to, atol=1e-12)
+
+
+def test_pose_error_and_twist_sampling():
+    """warmstart.pose_error against scipy rotations; random_twist stays in
+    its ball and angle range."""
+    import numpy as np
+    from scipy.spatial.transform import Rotation
+    from paper_2312_10070_gb300 import warmstart as W
+    rng = np.random.default_rng(5)
+    for _ in range(10):
+        q, qg = rng.standard_normal(4), rng.standard_normal(4)
+        t, tg = rng.standard_normal(3), rng.standard_normal(3)
+        R = Rotation.from_quat(np.roll(q / np.linalg.norm(q), -1)).as_matrix()
+        Rg = Rotation.from_quat(np.roll(qg / np.linalg.norm(qg), -1)).as_matrix()
+        d, ang = W.pose_error(q, t, qg, tg)
+        assert abs(d - np.linalg.norm(-R.T @ t + Rg.T @ tg)) < 1e-12
+        assert abs(ang - np.degrees(Rotation.from_matrix(R @ Rg.T).magnitude())) < 1e-9
+    for _ in range(200):
+        xi = W.random_twist(rng, 0.05, 3.0)
+        assert np.linalg.norm(xi[:3]) <= 0.05 + 1e-15 and np.linalg.norm(xi[3:]) <= np.deg2rad(3.0) + 1e-15
