@@ -341,7 +341,8 @@ GSR_API gsr_status gsr_map_step(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_sta
                         const float *kf_weights, int32_t n_iters, const gsr_map_opts *opt,
                         gsr_map_stats *out, void *stream);
 
-/* Stream-ordered read of the mapping loss (no synchronisation): enqueues on
+/* Stream-ordered read of the mapping loss of Eq. (joint_loss), Sec. 3.2/3.4
+ * (no synchronisation): enqueues on
  * `stream` a copy of the weighted loss (+ w_reg L_reg) of the last iteration
  * of the last gsr_map_step on this context into *loss_dev (caller-owned
  * device float), so a caller can read every step's loss back without
@@ -357,7 +358,10 @@ typedef struct {
     float ms;              /* ms_fwd + ms_bwd */
 } gsr_tune_result;
 
-/* Times gsr_render_forward and gsr_render_backward (all gradients, dL/dpixel
+/* Launch-configuration autotuner (no counterpart in the paper: tile shape,
+ * Gaussians per shared-memory batch and pixels per thread are parameters of
+ * this implementation of Sec. 3.1's tile-based rasterisation).
+ * Times gsr_render_forward and gsr_render_backward (all gradients, dL/dpixel
  * = 1) of `g` at each of the n_poses poses for every tile shape {16x16, 8x8,
  * 16x8, 32x8} x batch {32, 64, 128, 256}, each with 1 and 2 pixels per thread
  * for the forward and for the backward (`reps` timed repetitions after one
