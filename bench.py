@@ -488,7 +488,7 @@ def run_gpu(args, rank, world):
                 data="synthetic", config=dict(config_dict(stats, None), autotuned=tuned), roofline=roof,
                 hbm_roofline_step=hbm,
                 phases_ms=avg, e2e=e2e, gpu_launches=int(launches), clocks=clocks)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the oracle is timed in single-GPU runs only
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
 
