@@ -328,6 +328,51 @@ def test_render_backward_matches_central_fd():
         assert abs(g["pose"][k] - fd) <= 1e-6 * (abs(fd) + 1.0), (k, g["pose"][k], fd)
 
 
+def test_guard_band_clamp_gradient_matches_central_fd():
+    """Gaussians whose centres lie beyond the guard band (|p_x/p_z| > 1.3 x the
+    half-FOV tangent, likewise y) but whose footprints reach into the image:
+    J is evaluated at the clamped coordinate, which passes no gradient.  The
+    analytic gradient of every parameter and of the pose against FP64 central
+    differences of the same clamped forward."""
+    cam = O.Camera(48, 32, 45.0, 45.0, 24.0, 16.0, tile_w=16, tile_h=16)
+    limx, limy = 1.3 * 24.0 / 45.0, 1.3 * 16.0 / 45.0
+    means = [[1.0, 0.05, 1.2], [-0.1, -0.72, 1.4], [0.15, 0.1, 2.0]]
+    sc = one_gaussian_scene(means, [0.35, 0.3, 0.05], [0.7, 0.6, 0.8], [[0.9, 0.2, 0.1], [0.1, 0.8, 0.3],
+                                                                           [0.3, 0.3, 0.9]])
+    sc.quat = np.array([[0.9, 0.1, -0.2, 0.3], [0.8, -0.3, 0.1, 0.2], [1.0, 0.0, 0.0, 0.0]])
+    sc.log_scale = sc.log_scale + np.array([[0.0, -0.4, -1.5], [-0.3, 0.0, -1.2], [0.0, 0.0, 0.0]])
+    m = np.array(means)
+    assert abs(m[0, 0] / m[0, 2]) > limx and abs(m[1, 1] / m[1, 2]) > limy   # both clamps active
+    rng = np.random.default_rng(11)
+    w = (rng.standard_normal((3, 32, 48)), rng.standard_normal((32, 48)), rng.standard_normal((32, 48)))
+    L0, r0 = _linear_loss(sc, ID_Q, ID_T, cam, w)
+    assert r0["alpha"][:, 40:].max() > 0.05 and r0["alpha"][:4, :].max() > 0.05  # the clamped ones are seen
+    g = O.render_backward(sc, ID_Q, ID_T, cam, *w)
+    h = 1e-6
+    for name, shape in (("mean", 3), ("log_scale", 3), ("quat", 4), ("opacity_logit", 1)):
+        flat = getattr(sc, name).reshape(sc.n, -1)
+        garr = g[name].reshape(sc.n, -1)
+        for i in range(2):
+            for k in range(shape):
+                old = flat[i, k]
+                flat[i, k] = old + h
+                Lp, rp = _linear_loss(sc, ID_Q, ID_T, cam, w)
+                flat[i, k] = old - h
+                Lm, rm = _linear_loss(sc, ID_Q, ID_T, cam, w)
+                flat[i, k] = old
+                assert np.array_equal(rp["n_contrib"], r0["n_contrib"]) and np.array_equal(rm["n_contrib"],
+                                                                                          r0["n_contrib"])
+                fd = (Lp - Lm) / (2 * h)
+                assert abs(garr[i, k] - fd) <= 1e-6 * (abs(fd) + 1.0), (name, i, k, garr[i, k], fd)
+    for k in range(6):
+        xi = np.zeros(6)
+        xi[k] = h
+        Lp, _ = _linear_loss(sc, *O.pose_retract(ID_Q, ID_T, xi), cam, w)
+        Lm, _ = _linear_loss(sc, *O.pose_retract(ID_Q, ID_T, -xi), cam, w)
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(g["pose"][k] - fd) <= 1e-6 * (abs(fd) + 1.0), (k, g["pose"][k], fd)
+
+
 def test_loss_map_gradient_fd_and_ssim_library():
     rng = np.random.default_rng(9)
     H, W = 14, 17
