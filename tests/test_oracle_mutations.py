@@ -62,6 +62,8 @@ MUTATIONS = [
      "L += w * (lam_c * lc + (1 - lam_c) * ed);", "L += w * ((1 - lam_c) * lc + (1 - lam_c) * ed);"),
     ("tracking: alpha mask with exponent 1", "double w = in ? pow(alpha[p], apow) : 0.0;",
      "double w = in ? alpha[p] : 0.0;"),
+    ("near plane at the camera centre", "if (pz <= c->z_near && !z_amb) return;",
+     "if (pz <= 0.0 && !z_amb) return;"),
     ("guard band: gradient through the clamped coordinate",
      "if (!o->clamp_x) { gp[0] += gtx / pz; gp[2] += -gtx * px / (pz * pz); }",
      "{ gp[0] += gtx / pz; gp[2] += -gtx * px / (pz * pz); }"),

@@ -54,6 +54,18 @@ def test_single_isotropic_gaussian_footprint():
     assert (r["n_contrib"] == (a > 0)).all()
 
 
+def test_near_plane_cull():
+    """Gaussians at camera depth p_z <= z_near (0.2 m) are culled; just beyond
+    it they render (Sec. 3.1's projection with the near plane read as z_near)."""
+    cam = O.Camera(64, 48, 100.0, 100.0, 32.0, 24.0)
+    for z, seen in ((0.15, False), (0.19, False), (0.21, True), (0.25, True)):
+        sc = one_gaussian_scene([[0, 0, z]], [0.02 * z], [0.8], [[0.2, 0.5, 0.9]])
+        pr = O.project(sc, ID_Q, ID_T, cam)
+        r = O.render(sc, ID_Q, ID_T, cam)
+        assert pr["visible"][0] == int(seen) and pr["amb"][0] == 0, z
+        assert (r["alpha"].max() > 0.5) == seen and (r["alpha"].max() == 0.0) == (not seen), z
+
+
 def test_off_axis_cov2d_closed_form():
     """Isotropic Sigma = s^2 I is rotation invariant, so Sigma^I = s^2 J J^T + eps I
     with the pinhole Jacobian J at p (Zwicker et al. EWA, Sec. 3.1)."""
