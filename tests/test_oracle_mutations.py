@@ -15,7 +15,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "gsr_oracle.c")
 
-# (what the mistake is, text in gsr_oracle.c, its replacement)
+# (what the mistake is, text in gsr_oracle.c, its replacement); a mistake that
+# spans several sites gives tuples of texts and replacements
 MUTATIONS = [
     ("pose adjoint: sign of the rotation term from Sigma_cam",
      "g_pose[3] += 2.0 * (Y[7] - Y[5]);", "g_pose[3] += 2.0 * (Y[5] - Y[7]);"),
@@ -62,8 +63,9 @@ MUTATIONS = [
      "L += w * (lam_c * lc + (1 - lam_c) * ed);", "L += w * ((1 - lam_c) * lc + (1 - lam_c) * ed);"),
     ("tracking: alpha mask with exponent 1", "double w = in ? pow(alpha[p], apow) : 0.0;",
      "double w = in ? alpha[p] : 0.0;"),
-    ("near plane at the camera centre", "if (pz <= c->z_near && !z_amb) return;",
-     "if (pz <= 0.0 && !z_amb) return;"),
+    ("near plane at the camera centre",
+     ("if (pz <= c->z_near && !z_amb) return;", "if (empty || pz <= c->z_near) return;"),
+     ("if (pz <= 0.0 && !z_amb) return;", "if (empty || pz <= 0.0) return;")),
     ("guard band: gradient through the clamped coordinate",
      "if (!o->clamp_x) { gp[0] += gtx / pz; gp[2] += -gtx * px / (pz * pz); }",
      "{ gp[0] += gtx / pz; gp[2] += -gtx * px / (pz * pz); }"),
@@ -92,8 +94,12 @@ def results(tmp_path_factory):
     src = open(SRC).read()
     texts = [("unmodified", src)]
     for name, old, new in MUTATIONS:
-        assert src.count(old) == 1, f"mutation site not unique or missing: {name}"
-        texts.append((name, src.replace(old, new)))
+        olds, news = (old, new) if isinstance(old, tuple) else ((old,), (new,))
+        text = src
+        for o, n in zip(olds, news):  # a mistake may span several sites
+            assert text.count(o) == 1, f"mutation site not unique or missing: {name}"
+            text = text.replace(o, n)
+        texts.append((name, text))
     libs = [build(t, os.path.join(d, f"m{i}.so")) for i, (_, t) in enumerate(texts)]
     with ThreadPoolExecutor(max_workers=4) as ex:
         out = list(ex.map(run_pins, libs))
