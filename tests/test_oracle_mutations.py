@@ -63,6 +63,18 @@ MUTATIONS = [
      "L += w * (lam_c * lc + (1 - lam_c) * ed);", "L += w * ((1 - lam_c) * lc + (1 - lam_c) * ed);"),
     ("tracking: alpha mask with exponent 1", "double w = in ? pow(alpha[p], apow) : 0.0;",
      "double w = in ? alpha[p] : 0.0;"),
+    ("alpha skip threshold 1/128", "#define ALPHA_MIN (1.0 / 255.0)", "#define ALPHA_MIN (1.0 / 128.0)"),
+    ("transmittance stop threshold 1e-3", "#define T_STOP 1e-4", "#define T_STOP 1e-3"),
+    ("SSIM window sigma 2", "exp(-((k - 5) * (k - 5)) / (2.0 * 1.5 * 1.5))",
+     "exp(-((k - 5) * (k - 5)) / (2.0 * 2.0 * 2.0))"),
+    ("depth L1 over invalid pixels too",
+     ("if (depth_t[p] > 0) { ++nvalid; l1d += fabs(depth[p] - depth_t[p]); }",
+      "d_depth[p] = (depth_t[p] > 0 && nvalid > 0)"),
+     ("if (depth_t[p] >= 0) { ++nvalid; l1d += fabs(depth[p] - depth_t[p]); }",
+      "d_depth[p] = (depth_t[p] >= 0 && nvalid > 0)")),
+    ("opacity: sigmoid of -logit", "o->opacity = 1.0 / (1.0 + exp(-logit));", "o->opacity = 1.0 / (1.0 + exp(logit));"),
+    ("quaternion: sign of w z in R[0][1]", "R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);",
+     "R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y + w * z);"),
     ("near plane at the camera centre",
      ("if (pz <= c->z_near && !z_amb) return;", "if (empty || pz <= c->z_near) return;"),
      ("if (pz <= 0.0 && !z_amb) return;", "if (empty || pz <= 0.0) return;")),
