@@ -68,6 +68,15 @@ def relative_motion(qa, ta, qb, tb):
     return float(np.linalg.norm(camera_centre(qa, ta) - camera_centre(qb, tb))), float(np.degrees(np.arccos(cos)))
 
 
+def needs_new_submap(pose, first_pose, cfg: SLAMConfig) -> bool:
+    """Sub-map switching rule (Sec. 3.2, thresholds of Sec. 4): a keyframe
+    starts a new sub-map when its camera centre lies more than d_thre from
+    that of the active sub-map's first keyframe, or its orientation differs
+    by more than theta_thre_deg."""
+    d, ang = relative_motion(*pose, *first_pose)
+    return d > cfg.d_thre or ang > cfg.theta_thre_deg
+
+
 def constant_velocity(q1, t1, q2, t2):
     """Initial pose of frame i from frames i-1 (q1, t1) and i-2 (q2, t2):
     T_i = T_{i-1} + (T_{i-1} - T_{i-2}) on t and on the sign-aligned
@@ -140,11 +149,9 @@ class GaussianSLAM:
     def _keyframe(self, pose, rgb, depth):
         cfg = self.cfg
         first = self.active is None
-        if not first:
-            d, ang = relative_motion(*pose, *self.active.first_pose)
-            if d > cfg.d_thre or ang > cfg.theta_thre_deg:
-                self.submaps.append(self.active.to_host())
-                first = True
+        if not first and needs_new_submap(pose, self.active.first_pose, cfg):
+            self.submaps.append(self.active.to_host())
+            first = True
         if first:
             self.active = ActiveSubMap(cfg.capacity, pose)
         a = self.active

@@ -42,3 +42,28 @@ def test_schedule_gives_the_new_keyframe_at_least_40_percent():
     assert len(sched) == 100 and sched.count(5) >= 40 and max(sched) == 5 and min(sched) >= 0
     s.active.keyframes = [None]
     assert s._schedule(7) == [0] * 7
+
+
+def test_submap_switch_at_half_a_metre_or_fifty_degrees():
+    cfg = slam.SLAMConfig()
+    q0, t0 = _quat([0, 0, 1], 0.0), np.zeros(3)
+    # world-to-camera t = -R c: with R = I the camera centre is -t
+    assert not slam.needs_new_submap((q0, np.array([0.49, 0.0, 0.0])), (q0, t0), cfg)
+    assert slam.needs_new_submap((q0, np.array([0.0, 0.51, 0.0])), (q0, t0), cfg)
+    assert not slam.needs_new_submap((_quat([1, 1, 0], np.deg2rad(49.5)), t0), (q0, t0), cfg)
+    assert slam.needs_new_submap((_quat([1, 1, 0], np.deg2rad(50.5)), t0), (q0, t0), cfg)
+
+
+def test_submap_save_load_round_trip(tmp_path):
+    rng = np.random.default_rng(2)
+    subs = [{k: rng.standard_normal(s) for k, s in (("mean", (n, 3)), ("log_scale", (n, 3)), ("quat", (n, 4)),
+                                                      ("opacity_logit", (n,)), ("rgb", (n, 3)))}
+            for n in (5, 0, 12)]
+    path = str(tmp_path / "s.npz")
+    slam.save_submaps(path, subs)
+    back = slam.load_submaps(path)
+    assert len(back) == 3
+    for a, b in zip(subs, back):
+        assert set(a) == set(b)
+        for k in a:
+            np.testing.assert_array_equal(a[k], b[k])
