@@ -44,3 +44,34 @@ def test_unit_scene_recipe():
     assert abs(ls.mean() + 3.0) < 0.02 and abs(ls.std() - 0.5) < 0.02
     assert np.all(sc["rgb"] >= 0) and np.all(sc["rgb"] <= 1)
     assert np.allclose(np.linalg.norm(sc["quat"].astype(np.float64), axis=1), 1.0, atol=1e-6)
+
+
+def test_trajectories_perturbations_and_sensor_noise():
+    from paper_2312_10070_gb300 import slam
+    # room trajectories: consecutive frames move about step_m or turn about max_step_deg, never much more
+    for step, deg in ((0.015, 1.0), (0.02, 1.5), (0.04, 3.0)):
+        qs, ts = S.room_trajectory(100, n_frames=30, step_m=step, max_step_deg=deg)
+        assert len(qs) == 30
+        for i in range(29):
+            d, ang = slam.relative_motion(qs[i + 1], ts[i + 1], qs[i], ts[i])
+            assert d <= step * 1.05 and ang <= deg * 1.05, (i, d, ang)
+            assert d >= step * 0.99 or ang >= deg * 0.99, (i, d, ang)
+            c = slam.camera_centre(qs[i], ts[i])
+            assert np.all(c > 0) and np.all(c < np.array(S.ROOM))
+    # target pose of the unit workload: within 2 cm per axis and 1 degree
+    for seed in (2, 22, 42):
+        q, t = S.perturbed_pose(seed)
+        assert np.all(np.abs(t) <= 0.02 + 1e-7)
+        _, ang = slam.relative_motion(q, np.zeros(3), np.array([1.0, 0, 0, 0]), np.zeros(3))
+        assert ang <= 1.0 + 1e-4
+    # sensor noise: N(0, 0.01) colour, 1 % depth, depth invalid where alpha < 0.5
+    rng = np.random.default_rng(0)
+    rgb = rng.random((3, 200, 300)).astype(np.float32)
+    dep = rng.uniform(1, 4, (200, 300)).astype(np.float32)
+    al = rng.random((200, 300)).astype(np.float32)
+    rn, dn = S.add_sensor_noise(rgb, dep, al, seed=1)
+    assert abs(float((rn - rgb).std()) - 0.01) < 5e-4 and abs(float((rn - rgb).mean())) < 2e-4
+    ok = al >= 0.5
+    assert np.all(dn[~ok] == 0) and np.all(dn[ok] > 0)
+    rel = dn[ok] / dep[ok] - 1
+    assert abs(float(rel.std()) - 0.01) < 5e-4
