@@ -107,3 +107,30 @@ def test_storage_rounding_hooks():
     np.testing.assert_array_equal(oz, np.broadcast_to(p["fc1.b"], (2, 6)))
     gz = C.backward(p, cz, d_out, rnd=zero)
     assert all(not np.any(v) for v in gz.values())
+
+
+def test_residual_input_worked_example():
+    """A render and a frame built so every channel is known: rendered RGB and
+    depth / scale, frame minus render, depth residual / scale where both
+    depths are valid and 0 where either is not; a doubled scale halves the
+    depth channels."""
+    H, W = 4, 5
+    rgb_r = np.full((3, H, W), 0.25)
+    rgb_r[1] = 0.5
+    rgb_i = rgb_r + np.array([0.125, -0.25, 0.0])[:, None, None]
+    d_r = np.full((H, W), 2.0)
+    d_i = np.full((H, W), 2.5)
+    d_r[0, 0] = 0.0           # render invalid
+    d_i[1, 2] = 0.0           # frame invalid
+    x = C.residual_input(rgb_r, d_r, rgb_i, d_i, depth_scale=5.0)
+    assert x.shape == (H, W, 8)
+    np.testing.assert_array_equal(x[..., 0:3], np.moveaxis(rgb_r, 0, -1))
+    np.testing.assert_array_equal(x[..., 3], d_r / 5.0)
+    np.testing.assert_allclose(x[..., 4:7], np.broadcast_to([0.125, -0.25, 0.0], (H, W, 3)))
+    expect = np.full((H, W), 0.1)
+    expect[0, 0] = expect[1, 2] = 0.0
+    np.testing.assert_allclose(x[..., 7], expect, atol=1e-15)
+    y = C.residual_input(rgb_r, d_r, rgb_i, d_i, depth_scale=10.0)
+    np.testing.assert_allclose(y[..., [3, 7]], x[..., [3, 7]] / 2, atol=1e-15)
+    z = C.residual_input(rgb_r, d_r, rgb_r, d_r)      # frame == render
+    assert np.all(z[..., 4:] == 0)

@@ -31,6 +31,13 @@ MUTATIONS = [
      "return float(np.sum(w * r * r) / B), 2.0 * w * r / B", "return float(np.sum(w * r * r) / B), w * r / B"),
     ("cnn: invalid depth averaged in the box downsample", "cnn.py", "test_oracle_cnn_pins.py",
      "out_d[i, j] = dv[m].mean() if m.any() else 0.0", "out_d[i, j] = dv.mean()"),
+    ("cnn: depth residual kept where the frame's depth is invalid", "cnn.py", "test_oracle_cnn_pins.py",
+     "valid = (d_r > 0) & (d_i > 0)", "valid = d_r > 0"),
+    ("cnn: rendered depth channel not scaled", "cnn.py", "test_oracle_cnn_pins.py",
+     "ch = [rgb_r[0], rgb_r[1], rgb_r[2], d_r / depth_scale,", "ch = [rgb_r[0], rgb_r[1], rgb_r[2], d_r,"),
+    ("seed: prune by sigmoid(-logit)", "seed.py", "test_oracle_seed_pins.py",
+     'o = 1.0 / (1.0 + np.exp(-np.asarray(params["opacity_logit"], np.float64)))',
+     'o = 1.0 / (1.0 + np.exp(np.asarray(params["opacity_logit"], np.float64)))'),
     ("seed: splitmix64 first multiplier", "seed.py", "test_oracle_seed_pins.py",
      "z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)",
      "z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B7)"),

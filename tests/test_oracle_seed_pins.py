@@ -140,3 +140,20 @@ def test_merge_rule_on_a_constructed_case():
     _, m = SD.merge([s1, s2], 0.01)
     d, _ = cKDTree(s1["mean"]).query(s2["mean"])
     np.testing.assert_array_equal(m[1], d >= 0.01)
+
+
+def test_prune_keeps_exactly_the_logits_above_the_threshold_in_order():
+    """Opacity sigmoid(logit) >= o_min  <=>  logit >= ln(o_min / (1 - o_min)):
+    the kept set is fixed by the closed-form inverse, order and pairing kept."""
+    rng = np.random.default_rng(4)
+    n = 5000
+    params = dict(mean=rng.standard_normal((n, 3)), log_scale=rng.standard_normal((n, 3)),
+                  quat=rng.standard_normal((n, 4)), opacity_logit=rng.normal(0.0, 3.0, n),
+                  rgb=rng.random((n, 3)))
+    for o_min in (0.1, 0.005, 0.6):
+        thr = np.log(o_min / (1 - o_min))
+        far = np.abs(params["opacity_logit"] - thr) > 1e-9
+        out, keep = SD.prune(params, o_min)
+        np.testing.assert_array_equal(keep[far], params["opacity_logit"][far] >= thr)
+        for k, v in params.items():
+            np.testing.assert_array_equal(out[k], v[keep])   # same rows, original order
