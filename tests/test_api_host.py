@@ -80,3 +80,25 @@ def test_pose_error_and_twist_sampling():
     for _ in range(200):
         xi = W.random_twist(rng, 0.05, 3.0)
         assert np.linalg.norm(xi[:3]) <= 0.05 + 1e-15 and np.linalg.norm(xi[3:]) <= np.deg2rad(3.0) + 1e-15
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """Without a CUDA device the rasterizer refuses to run instead of falling
+    back to host code (this container has none; on a GPU machine it is skipped)."""
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        api.Context()
+    from paper_2312_10070_gb300 import warmstart as W
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        W.WarmStartNet(max_batch=4)
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    """A missing libgsr.so raises on load (when not rebuilt) rather than
+    degrading to anything else."""
+    from paper_2312_10070_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libgsr.so"))
+    with pytest.raises(ImportError):
+        _lib.load(build_if_missing=False)
