@@ -75,6 +75,20 @@ MUTATIONS = [
     ("opacity: sigmoid of -logit", "o->opacity = 1.0 / (1.0 + exp(-logit));", "o->opacity = 1.0 / (1.0 + exp(logit));"),
     ("quaternion: sign of w z in R[0][1]", "R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);",
      "R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y + w * z);"),
+    ("backward: sign of the conic inverse's derivative",
+     "GS[2 * i + j] = -(T2[2 * i] * Q[j] + T2[2 * i + 1] * Q[2 + j]);",
+     "GS[2 * i + j] = (T2[2 * i] * Q[j] + T2[2 * i + 1] * Q[2 + j]);"),
+    ("backward: factor 2 of dL/dJ dropped",
+     "GJ[3 * r + k] = 2.0 * (GS[2 * r] * JSc[k] + GS[2 * r + 1] * JSc[3 + k]);",
+     "GJ[3 * r + k] = (GS[2 * r] * JSc[k] + GS[2 * r + 1] * JSc[3 + k]);"),
+    ("backward: off-diagonal conic gradient not halved", "double GQ[4] = {g2[2], 0.5 * g2[3], 0.5 * g2[3], g2[4]};",
+     "double GQ[4] = {g2[2], g2[3], g2[3], g2[4]};"),
+    ("pose adjoint: sign of the z-rotation term from Sigma_cam", "g_pose[5] += 2.0 * (Y[3] - Y[1]);",
+     "g_pose[5] += 2.0 * (Y[1] - Y[3]);"),
+    ("backward: factor 2 of dL/dM dropped", "for (int i = 0; i < 9; ++i) GM[i] *= 2.0;",
+     "for (int i = 0; i < 9; ++i) GM[i] *= 1.0;"),
+    ("backward: sign of dJ00/dz", "gp[2] += GJ[0] * (-fx / (pz * pz)) + GJ[2] * (fx * o->tx / (pz * pz))",
+     "gp[2] += GJ[0] * (fx / (pz * pz)) + GJ[2] * (fx * o->tx / (pz * pz))"),
     ("near plane at the camera centre",
      ("if (pz <= c->z_near && !z_amb) return;", "if (empty || pz <= c->z_near) return;"),
      ("if (pz <= 0.0 && !z_amb) return;", "if (empty || pz <= 0.0) return;")),
