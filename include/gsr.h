@@ -203,6 +203,34 @@ GSR_API gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *g, con
                                const float *d_rgb, const float *d_depth, const float *d_alpha,
                                gsr_gaussian_grads *dg, float *d_pose6, void *stream);
 
+/* Twist-perturbed render and its backward (Sec. 3.5: tracking optimises the
+ * camera pose by gradient descent; here the pose is perturbed on the left by a
+ * twist held in DEVICE memory, so an autograd graph over the twist needs no
+ * host round trip).  gsr_render_forward_xi renders at the float pose
+ * fl(exp(xi^) T), exp formed in double precision on the device from
+ * xi = (rho, phi) (device float[6], caller-owned; T = *pose).
+ * gsr_render_backward_xi returns the parameter gradients of that render and,
+ * in d_xi (device float[6], overwritten, NULL = none), dL/dxi =
+ * J_l(xi)^T g, where g is the left-perturbation pose gradient at exp(xi^) T
+ * and J_l the SE(3) left Jacobian (exp((xi + e)^) = exp((J_l e)^) exp(xi^)
+ * to first order).  xi must hold the same values in the backward as in the
+ * matching forward.  Otherwise as gsr_render_forward / gsr_render_backward;
+ * GSR_ERR_INVALID_ARG for a NULL xi. */
+GSR_API gsr_status gsr_render_forward_xi(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
+                                         const gsr_pose *pose, const float *xi, gsr_render_out *out, void *stream);
+GSR_API gsr_status gsr_render_backward_xi(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
+                                          const gsr_pose *pose, const float *xi, const gsr_render_out *saved,
+                                          const float *d_rgb, const float *d_depth, const float *d_alpha,
+                                          gsr_gaussian_grads *dg, float *d_xi, void *stream);
+
+/* Left retraction of a pose by a device twist (Sec. 3.5's pose update as the
+ * tracker applies it): pose_out (device float[7]) = (q', t') of
+ * fl(exp(xi^) T), q' normalised with w >= 0, formed in double precision on
+ * the device; xi = (rho, phi) device float[6].  Stream-ordered, no context,
+ * no allocation.  GSR_ERR_INVALID_ARG on NULL arguments, GSR_ERR_CUDA if the
+ * launch fails. */
+GSR_API gsr_status gsr_pose_retract(const gsr_pose *pose, const float *xi, float *pose_out, void *stream);
+
 /* -------------------------------------------------------------- losses */
 
 /* Mapping loss, Eq. (joint_loss) without L_reg (Sec. 3.4):
@@ -240,16 +268,23 @@ GSR_API gsr_status gsr_loss_track(gsr_ctx *ctx, int32_t width, int32_t height, c
  * outputs, scale and the result are those of gsr_loss_track.
  *
  * Its scratch (about 3.7 MB) is one static device array in libgsr.so, held
- * by every GPU that loads the library until the process exits.  The first
- * call on a device looks up that array's device address (with that device
- * current), so the first call on each device should come before any stream
- * capture.  Every call on a device shares the array, which keeps the last
- * call's contents: calls that overlap on the GPU (different streams, or
- * host threads) race and must be serialised by the caller.
+ * by every GPU that loads the library until the process exits.  Each call
+ * looks up that array's device address in the current CUDA context (no
+ * allocation; the first call in a context also loads the library's module
+ * there, so the first call on each device should come before any stream
+ * capture).  Every call on a device shares the array, which keeps the last
+ * call's contents (the call clears what must start at zero): calls that
+ * overlap on the GPU (different streams, or host threads) race and must be
+ * serialised by the caller.
  *
  * Errors: GSR_ERR_INVALID_ARG for a null pointer or a non-positive size,
  * GSR_ERR_CAPACITY when width * height > GSR_NOALLOC_MAX_PIXELS (nothing is
- * launched), GSR_ERR_CUDA if the address lookup or a launch fails. */
+ * launched), GSR_ERR_CUDA if the address lookup or one of this call's
+ * launches fails (an error left pending by earlier work is cleared first, not
+ * reported).  The call never synchronises, so unlike gsr_loss_track (whose
+ * context latches it for the next synchronising call) it does NOT report a
+ * non-finite loss as GSR_ERR_NONFINITE: check the value written to loss_dev,
+ * which is then NaN or Inf. */
 GSR_API gsr_status gsr_loss_track_noalloc(int32_t width, int32_t height, const float *rgb, const float *depth,
                                           const float *alpha, const float *rgb_target, const float *depth_target,
                                           float lambda_c, float k_median, float alpha_pow, float *d_rgb,

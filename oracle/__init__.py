@@ -122,6 +122,8 @@ def _load():
         lib.orc_adam.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int64] + [ctypes.c_double] * 4
         lib.orc_pose_retract.restype = None
         lib.orc_pose_retract.argtypes = [P] * 5
+        lib.orc_se3_left_jacobian.restype = None
+        lib.orc_se3_left_jacobian.argtypes = [P] * 2
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_num_threads.argtypes = []
         lib.orc_set_num_threads.restype = None
@@ -319,3 +321,19 @@ def pose_retract(pose_q, pose_t, xi):
     qo, to = np.zeros(4), np.zeros(3)
     lib.orc_pose_retract(_p(q), _p(t), _p(xi), _p(qo), _p(to))
     return qo, to
+
+
+def se3_left_jacobian(xi):
+    """SE(3) left Jacobian J_l(xi) (6x6, xi = (rho, phi)): to first order
+    exp((xi + e)^) = exp((J_l e)^) exp(xi^)."""
+    lib = _load()
+    xi = _f64(xi).reshape(6)
+    J = np.zeros((6, 6))
+    lib.orc_se3_left_jacobian(_p(xi), _p(J))
+    return J
+
+
+def twist_gradient(xi, pose_grad):
+    """dL/dxi of a loss of T(xi) = exp(xi^) T, from the left-perturbation pose
+    gradient at T(xi): J_l(xi)^T pose_grad."""
+    return se3_left_jacobian(xi).T @ _f64(pose_grad).reshape(6)

@@ -963,6 +963,59 @@ void orc_pose_retract(const double *q_in, const double *t_in, const double *xi, 
     q_out[0] = w; q_out[1] = x; q_out[2] = y; q_out[3] = z;
 }
 
+/* SE(3) left Jacobian J_l(xi), xi = (rho, phi), row major 6x6: to first
+ * order exp((xi + e)^) = exp((J_l e)^) exp(xi^).  With K = [phi]x,
+ * P = [rho]x and th = |phi| it is [[V, Q], [0, V]], V = I + B K + C K^2 the
+ * SO(3) left Jacobian (B, C of orc_pose_retract) and
+ *   Q = P/2 + c1 (K P + P K + K P K) + c2 (K K P + P K K - 3 K P K)
+ *         + c3 (K P K K + K K P K),
+ *   c1 = (th - sin th)/th^3, c2 = (th^2 + 2 cos th - 2)/(2 th^4),
+ *   c3 = (2 th - 3 sin th + th cos th)/(2 th^5)
+ * (their Taylor series near th = 0).  The gradient of a loss with respect to
+ * the twist of T(xi) = exp(xi^) T is J_l(xi)^T times its left-perturbation
+ * gradient at T(xi). */
+void orc_se3_left_jacobian(const double *xi, double *J)
+{
+    const double *rho = xi, *phi = xi + 3;
+    double th = sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]), t2 = th * th;
+    double B, Cc, c1, c2, c3;
+    if (th < 1e-2) {
+        B = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+        Cc = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+        c1 = Cc;
+        c2 = 1.0 / 24.0 - t2 / 720.0 + t2 * t2 / 40320.0;
+        c3 = 1.0 / 120.0 - t2 / 2520.0 + t2 * t2 / 120960.0;
+    } else {
+        B = (1 - cos(th)) / t2;
+        Cc = (th - sin(th)) / (t2 * th);
+        c1 = Cc;
+        c2 = (t2 + 2 * cos(th) - 2) / (2 * t2 * t2);
+        c3 = (2 * th - 3 * sin(th) + th * cos(th)) / (2 * t2 * t2 * th);
+    }
+    double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
+    double P[9] = {0, -rho[2], rho[1], rho[2], 0, -rho[0], -rho[1], rho[0], 0};
+    double KK[9], KP[9], PK[9], KPK[9], KKP[9], PKK[9], KPKK[9], KKPK[9];
+    matmul3(K, K, KK);
+    matmul3(K, P, KP);
+    matmul3(P, K, PK);
+    matmul3(KP, K, KPK);
+    matmul3(KK, P, KKP);
+    matmul3(P, KK, PKK);
+    matmul3(KPK, K, KPKK);
+    matmul3(K, KPK, KKPK);
+    memset(J, 0, sizeof(double) * 36);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            int i = 3 * r + c;
+            double V = (r == c ? 1.0 : 0.0) + B * K[i] + Cc * KK[i];
+            double Q = 0.5 * P[i] + c1 * (KP[i] + PK[i] + KPK[i]) + c2 * (KKP[i] + PKK[i] - 3 * KPK[i])
+                     + c3 * (KPKK[i] + KKPK[i]);
+            J[6 * r + c] = V;
+            J[6 * (r + 3) + (c + 3)] = V;
+            J[6 * r + (c + 3)] = Q;
+        }
+}
+
 /* number of OpenMP threads the oracle uses (1 without OpenMP) */
 int orc_num_threads(void)
 {

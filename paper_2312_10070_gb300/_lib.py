@@ -20,6 +20,7 @@ P_i32 = ctypes.POINTER(c_i32)
 c_vp = ctypes.c_void_p
 
 GSR_OK = 0
+NOALLOC_MAX_PIXELS = 921600  # GSR_NOALLOC_MAX_PIXELS of gsr.h (1280 x 720)
 STATUS = {0: "GSR_OK", -1: "GSR_ERR_INVALID_ARG", -2: "GSR_ERR_CUDA", -3: "GSR_ERR_OOM",
           -4: "GSR_ERR_CAPACITY", -5: "GSR_ERR_TIMEOUT", -6: "GSR_ERR_NONFINITE", -7: "GSR_ERR_STATE"}
 
@@ -131,6 +132,12 @@ PROTOTYPES = {
     "gsr_render_backward": (c_i32, [c_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Pose),
                                     ctypes.POINTER(RenderOut), c_vp, c_vp, c_vp, ctypes.POINTER(GaussianGrads),
                                     c_vp, c_vp]),
+    "gsr_render_forward_xi": (c_i32, [c_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Pose),
+                                      c_vp, ctypes.POINTER(RenderOut), c_vp]),
+    "gsr_render_backward_xi": (c_i32, [c_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), ctypes.POINTER(Pose),
+                                       c_vp, ctypes.POINTER(RenderOut), c_vp, c_vp, c_vp,
+                                       ctypes.POINTER(GaussianGrads), c_vp, c_vp]),
+    "gsr_pose_retract": (c_i32, [ctypes.POINTER(Pose), c_vp, c_vp, c_vp]),
     "gsr_loss_map": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_f, c_f, c_f, c_f, c_vp, c_vp, c_vp,
                              c_vp]),
     "gsr_loss_track": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_f, c_f, c_f, c_vp, c_vp,

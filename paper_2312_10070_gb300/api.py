@@ -8,7 +8,6 @@ stated), contiguous and on the context's CUDA device.
 from __future__ import annotations
 
 import ctypes
-import math
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -151,8 +150,11 @@ class GaussianParams:
         return L.GaussianGrads(*[_ptr(t) for t in self.check().tensors()])
 
 
-def render_forward(ctx: Context, g: GaussianParams, cam: L.Camera, pose: L.Pose, want_n_contrib=False) -> dict:
-    """gsr_render_forward: rgb [3,H,W], depth, alpha, final_T, last_idx (int32)."""
+def render_forward(ctx: Context, g: GaussianParams, cam: L.Camera, pose: L.Pose, want_n_contrib=False,
+                   xi: torch.Tensor = None) -> dict:
+    """gsr_render_forward: rgb [3,H,W], depth, alpha, final_T, last_idx (int32).
+    With a device twist xi (float32 [6]): gsr_render_forward_xi, the render at
+    exp(xi^) T formed on the device."""
     H, W = cam.height, cam.width
     dev = g.mean.device
     out = dict(rgb=torch.empty((3, H, W), device=dev), depth=torch.empty((H, W), device=dev),
@@ -160,9 +162,19 @@ def render_forward(ctx: Context, g: GaussianParams, cam: L.Camera, pose: L.Pose,
                last_idx=torch.empty((H, W), dtype=torch.int32, device=dev),
                n_contrib=torch.empty((H, W), dtype=torch.int32, device=dev) if want_n_contrib else None)
     ro = L.RenderOut(*[_ptr(out[k]) for k in ("rgb", "depth", "alpha", "final_T", "last_idx", "n_contrib")])
-    ctx.check(ctx.lib.gsr_render_forward(ctx.handle, ctypes.byref(g.c()), ctypes.byref(cam), ctypes.byref(pose),
-                                         ctypes.byref(ro), _stream()))
+    if xi is None:
+        ctx.check(ctx.lib.gsr_render_forward(ctx.handle, ctypes.byref(g.c()), ctypes.byref(cam), ctypes.byref(pose),
+                                             ctypes.byref(ro), _stream()))
+    else:
+        ctx.check(ctx.lib.gsr_render_forward_xi(ctx.handle, ctypes.byref(g.c()), ctypes.byref(cam),
+                                                ctypes.byref(pose), _twist(xi), ctypes.byref(ro), _stream()))
     return out
+
+
+def _twist(xi):
+    if xi.dtype != torch.float32 or xi.numel() != 6:
+        raise ValueError("the twist must be a float32 tensor of 6 elements (rho, phi)")
+    return _ptr(xi)
 
 
 def frame_stats(ctx: Context) -> dict:
@@ -193,17 +205,26 @@ def tile_lists(ctx: Context, n_tiles: int, n_gaussians: int, capacity: int = Non
 
 
 def render_backward(ctx: Context, g: GaussianParams, cam: L.Camera, pose: L.Pose, saved: dict, d_rgb=None,
-                    d_depth=None, d_alpha=None, want_params=True, want_pose=True, out: GaussianParams = None):
-    """gsr_render_backward: returns (GaussianParams of gradients or None, pose6 tensor or None)."""
+                    d_depth=None, d_alpha=None, want_params=True, want_pose=True, out: GaussianParams = None,
+                    xi: torch.Tensor = None):
+    """gsr_render_backward: returns (GaussianParams of gradients or None, pose6 tensor or None).
+    With a device twist xi: gsr_render_backward_xi, and pose6 is dL/dxi."""
     grads = None
     if want_params:
         grads = out if out is not None else g.zeros_like()
     pose6 = torch.empty(6, device=g.mean.device) if want_pose else None
     ro = L.RenderOut(None, None, None, _ptr(saved["final_T"]), _ptr(saved["last_idx"]), None)
     gg = grads.c_grads() if grads is not None else None
-    ctx.check(ctx.lib.gsr_render_backward(ctx.handle, ctypes.byref(g.c()), ctypes.byref(cam), ctypes.byref(pose),
-                                          ctypes.byref(ro), _ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha),
-                                          ctypes.byref(gg) if gg is not None else None, _ptr(pose6), _stream()))
+    if xi is None:
+        ctx.check(ctx.lib.gsr_render_backward(ctx.handle, ctypes.byref(g.c()), ctypes.byref(cam), ctypes.byref(pose),
+                                              ctypes.byref(ro), _ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha),
+                                              ctypes.byref(gg) if gg is not None else None, _ptr(pose6), _stream()))
+    else:
+        ctx.check(ctx.lib.gsr_render_backward_xi(ctx.handle, ctypes.byref(g.c()), ctypes.byref(cam),
+                                                 ctypes.byref(pose), _twist(xi), ctypes.byref(ro), _ptr(d_rgb),
+                                                 _ptr(d_depth), _ptr(d_alpha),
+                                                 ctypes.byref(gg) if gg is not None else None, _ptr(pose6),
+                                                 _stream()))
     return grads, pose6
 
 
@@ -448,32 +469,19 @@ def probe_peaks(blocks: int = 152 * 8, iters: int = 16384, reps: int = 5):
 
 
 # ----------------------------------------------------------- pose helpers
-def quat_mul(a, b):
-    aw, ax, ay, az = a
-    bw, bx, by, bz = b
-    return np.array([aw * bw - ax * bx - ay * by - az * bz, aw * bx + ax * bw + ay * bz - az * by,
-                     aw * by - ax * bz + ay * bw + az * bx, aw * bz + ax * by - ay * bx + az * bw])
+def pose_retract(pose: L.Pose, xi: torch.Tensor, out: torch.Tensor = None) -> torch.Tensor:
+    """gsr_pose_retract: (q', t') of exp(xi^) T as a device float32 [7]
+    tensor (stream-ordered; xi is a device float32 [6] twist (rho, phi))."""
+    out = out if out is not None else torch.empty(7, dtype=torch.float32, device=xi.device)
+    L.check(L.load().gsr_pose_retract(ctypes.byref(pose), _twist(xi.contiguous()), _ptr(out), _stream()))
+    return out
 
 
-def pose_exp_left(q, t, xi):
-    """exp(xi^) T on the host (xi = (rho, phi)); used by the autograd wrapper."""
-    xi = np.asarray(xi, np.float64)
-    rho, phi = xi[:3], xi[3:]
-    th = float(np.linalg.norm(phi))
-    K = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
-    if th < 1e-8:
-        A, B, C = 1.0, 0.5, 1.0 / 6.0
-        dq = np.array([1.0, *(0.5 * phi)])
-    else:
-        A, B, C = math.sin(th) / th, (1 - math.cos(th)) / th ** 2, (th - math.sin(th)) / th ** 3
-        dq = np.array([math.cos(th / 2), *(math.sin(th / 2) / th * phi)])
-    Rd = np.eye(3) + A * K + B * K @ K
-    V = np.eye(3) + B * K + C * K @ K
-    qn = quat_mul(dq, np.asarray(q, np.float64))
-    qn /= np.linalg.norm(qn)
-    if qn[0] < 0:
-        qn = -qn
-    return qn, Rd @ np.asarray(t, np.float64) + V @ rho
+def pose_from_tensor(p: torch.Tensor) -> L.Pose:
+    """A (q, t) float32 [7] tensor (e.g. from pose_retract) as a host pose
+    (reads it back, synchronising)."""
+    h = p.detach().cpu().numpy().astype(np.float64)
+    return make_pose(h[:4], h[4:7])
 
 
 def autotune(ctx: Context, g: GaussianParams, cam: L.Camera, poses, reps: int = 3):

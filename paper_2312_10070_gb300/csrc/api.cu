@@ -297,16 +297,19 @@ static gsr_status take_status(gsr_ctx *ctx, cudaStream_t s)
     return GSR_OK;
 }
 
-static bool same_forward(const gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *c, const gsr_pose *p)
+static bool same_forward(const gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *c, const gsr_pose *p,
+                         const float *xi)
 {
-    return ctx->fwd_n == g->n && ctx->fwd_ptrs[0] == g->mean && ctx->fwd_ptrs[1] == g->log_scale &&
+    return ctx->fwd_n == g->n && ctx->fwd_xi == xi && ctx->fwd_ptrs[0] == g->mean && ctx->fwd_ptrs[1] == g->log_scale &&
            ctx->fwd_ptrs[2] == g->quat && ctx->fwd_ptrs[3] == g->opacity_logit && ctx->fwd_ptrs[4] == g->rgb &&
            memcmp(&ctx->fwd_cam, c, sizeof(*c)) == 0 && memcmp(&ctx->fwd_pose, p, sizeof(*p)) == 0;
 }
 
-static void remember_forward(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *c, const gsr_pose *p)
+static void remember_forward(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *c, const gsr_pose *p,
+                             const float *xi)
 {
     ctx->fwd_n = g->n;
+    ctx->fwd_xi = xi;
     ctx->fwd_ptrs[0] = g->mean;
     ctx->fwd_ptrs[1] = g->log_scale;
     ctx->fwd_ptrs[2] = g->quat;
@@ -324,8 +327,8 @@ static gsr_status ensure_view_pose(gsr_ctx *ctx)
 }
 
 // ---------------------------------------------------------------- renderer
-extern "C" gsr_status gsr_render_forward(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
-                                         const gsr_pose *pose, gsr_render_out *out, void *stream)
+static gsr_status render_forward(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam, const gsr_pose *pose,
+                                 const float *xi, gsr_render_out *out, void *stream)
 {
     if (!ctx) return GSR_ERR_INVALID_ARG;
     GSR_TRY(check_gaussians(ctx, g));
@@ -337,6 +340,7 @@ extern "C" gsr_status gsr_render_forward(gsr_ctx *ctx, const gsr_gaussians *g, c
     GSR_TRY(ensure_view_pose(ctx));
     float *d_pose = (float *)ctx->view.pose.p;
     GSR_TRY(launch_set_pose(ctx, d_pose, *pose, s));
+    if (xi) GSR_TRY(launch_perturb_pose(ctx, d_pose, xi, s));
     CamK ck = make_camk(*cam, ctx->opt.tile_w, ctx->opt.tile_h);
     Params P = to_params(g);
     GSR_TRY(prof_mark(ctx, PROF_BIN, false, s));
@@ -345,8 +349,21 @@ extern "C" gsr_status gsr_render_forward(gsr_ctx *ctx, const gsr_gaussians *g, c
     GSR_TRY(prof_mark(ctx, PROF_FWD, false, s));
     GSR_TRY(run_blend_forward(ctx, P, ck, out, s));
     GSR_TRY(prof_mark(ctx, PROF_FWD, true, s));
-    remember_forward(ctx, g, cam, pose);
+    remember_forward(ctx, g, cam, pose, xi);
     return GSR_OK;
+}
+
+extern "C" gsr_status gsr_render_forward(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
+                                         const gsr_pose *pose, gsr_render_out *out, void *stream)
+{
+    return render_forward(ctx, g, cam, pose, nullptr, out, stream);
+}
+
+extern "C" gsr_status gsr_render_forward_xi(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
+                                            const gsr_pose *pose, const float *xi, gsr_render_out *out, void *stream)
+{
+    if (ctx && !xi) return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "null twist");
+    return render_forward(ctx, g, cam, pose, xi, out, stream);
 }
 
 extern "C" gsr_status gsr_frame_stats_get(gsr_ctx *ctx, gsr_frame_stats *st, void *stream)
@@ -393,10 +410,10 @@ extern "C" gsr_status gsr_tile_lists_get(gsr_ctx *ctx, uint32_t *ranges, int32_t
                            (cudaStream_t)stream);
 }
 
-extern "C" gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
-                                          const gsr_pose *pose, const gsr_render_out *saved, const float *d_rgb,
-                                          const float *d_depth, const float *d_alpha, gsr_gaussian_grads *dg,
-                                          float *d_pose6, void *stream)
+static gsr_status render_backward(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
+                                  const gsr_pose *pose, const float *xi, const gsr_render_out *saved,
+                                  const float *d_rgb, const float *d_depth, const float *d_alpha,
+                                  gsr_gaussian_grads *dg, float *d_pose6, void *stream)
 {
     if (!ctx) return GSR_ERR_INVALID_ARG;
     GSR_TRY(check_gaussians(ctx, g));
@@ -408,11 +425,12 @@ extern "C" gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *g, 
     Params P = to_params(g);
     GSR_TRY(ensure_view_pose(ctx));
     float *d_pose = (float *)ctx->view.pose.p;
-    if (ctx->opt.memory_saving || !same_forward(ctx, g, cam, pose)) {
+    if (ctx->opt.memory_saving || !same_forward(ctx, g, cam, pose, xi)) {
         // rebuild the (deterministic) tile lists instead of keeping them alive
         GSR_TRY(launch_set_pose(ctx, d_pose, *pose, s));
+        if (xi) GSR_TRY(launch_perturb_pose(ctx, d_pose, xi, s));
         GSR_TRY(run_binning(ctx, ctx->view, P, ck, d_pose, !ctx->opt.fixed_capacity, s));
-        remember_forward(ctx, g, cam, pose);
+        remember_forward(ctx, g, cam, pose, xi);
     }
     bool want_params = dg && (dg->mean || dg->log_scale || dg->quat || dg->opacity_logit || dg->rgb);
     GSR_TRY(prof_mark(ctx, PROF_BWD, false, s));
@@ -420,8 +438,26 @@ extern "C" gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *g, 
     GSR_TRY(prof_mark(ctx, PROF_BWD, true, s));
     GSR_TRY(prof_mark(ctx, PROF_PBWD, false, s));
     GSR_TRY(run_project_backward(ctx, ctx->view, P, ck, d_pose, want_params ? dg : nullptr, d_pose6, false, 1.f, s));
+    if (xi && d_pose6) GSR_TRY(launch_pose_grad_xi(ctx, d_pose6, xi, s));
     GSR_TRY(prof_mark(ctx, PROF_PBWD, true, s));
     return GSR_OK;
+}
+
+extern "C" gsr_status gsr_render_backward(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
+                                          const gsr_pose *pose, const gsr_render_out *saved, const float *d_rgb,
+                                          const float *d_depth, const float *d_alpha, gsr_gaussian_grads *dg,
+                                          float *d_pose6, void *stream)
+{
+    return render_backward(ctx, g, cam, pose, nullptr, saved, d_rgb, d_depth, d_alpha, dg, d_pose6, stream);
+}
+
+extern "C" gsr_status gsr_render_backward_xi(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
+                                             const gsr_pose *pose, const float *xi, const gsr_render_out *saved,
+                                             const float *d_rgb, const float *d_depth, const float *d_alpha,
+                                             gsr_gaussian_grads *dg, float *d_xi, void *stream)
+{
+    if (ctx && !xi) return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "null twist");
+    return render_backward(ctx, g, cam, pose, xi, saved, d_rgb, d_depth, d_alpha, dg, d_xi, stream);
 }
 
 // ------------------------------------------------------------------ losses

@@ -120,6 +120,7 @@ struct gsr_ctx {
     int64_t fwd_n = -1;
     gsr_camera fwd_cam{};
     gsr_pose fwd_pose{};
+    const float *fwd_xi = nullptr;  // device twist of the last forward (nullptr: none)
     // graphs
     cudaGraphExec_t track_graph = nullptr;
     uint64_t track_key = 0;
@@ -352,6 +353,10 @@ gsr_status run_blend_multi(gsr_ctx *ctx, const CamK &ck, bool backward, const Bl
                            int n_items, u32 *counter, cudaStream_t s);
 
 gsr_status launch_set_pose(gsr_ctx *ctx, float *d_pose, const gsr_pose &p, cudaStream_t s);
+// exp(xi^) applied to the (q, t) of a device pose record (xi: device float[6])
+gsr_status launch_perturb_pose(gsr_ctx *ctx, float *d_pose, const float *xi, cudaStream_t s);
+// g6 <- J_l(xi)^T g6 (device float[6] each)
+gsr_status launch_pose_grad_xi(gsr_ctx *ctx, float *g6, const float *xi, cudaStream_t s);
 // Projection + binning into V; returns after enqueueing (no sync unless
 // allow_grow, which reads the instance count back once to size V)
 gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK &ck, const float *d_pose,

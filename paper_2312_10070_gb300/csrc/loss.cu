@@ -20,7 +20,6 @@
 //
 // Reductions are deterministic: per-block partials, then one ordered pass.
 #include <algorithm>
-#include <mutex>
 
 #include "gsr_internal.cuh"
 
@@ -551,11 +550,6 @@ constexpr int64_t NA_WORDS = NA_CNT + 16;
 
 static __device__ __align__(256) u32 g_noalloc_scratch[NA_WORDS];
 
-namespace {
-std::mutex g_noalloc_mu;
-u32 *g_noalloc_ptr[256] = {};  // device address of g_noalloc_scratch per device ordinal
-}  // namespace
-
 extern "C" gsr_status gsr_loss_track_noalloc(int32_t width, int32_t height, const float *rgb, const float *depth,
                                              const float *alpha, const float *rgb_target, const float *depth_target,
                                              float lambda_c, float k_median, float alpha_pow, float *d_rgb,
@@ -565,26 +559,19 @@ extern "C" gsr_status gsr_loss_track_noalloc(int32_t width, int32_t height, cons
         return GSR_ERR_INVALID_ARG;
     const int64_t HW = (int64_t)width * height;
     if (HW > NA_MAXP) return GSR_ERR_CAPACITY;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    // an error left pending by earlier, unrelated work must not be reported as this call's
+    (void)cudaGetLastError();
+    // Host code only knows the array's host-side stand-in; the kernels need its
+    // device address in the CURRENT context.  The address is looked up on every
+    // call (a table lookup once the module is loaded in that context) rather
+    // than cached per device ordinal: a cached address would go stale after
+    // cudaDeviceReset or under another context of the same device.
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
         (void)cudaGetLastError();
         return GSR_ERR_CUDA;
     }
-    u32 *base = nullptr;
-    {
-        // set-up once per device: host code only knows the array's host-side
-        // stand-in; the kernels need its device address
-        std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-                (void)cudaGetLastError();
-                return GSR_ERR_CUDA;
-            }
-            g_noalloc_ptr[dev] = (u32 *)p;
-        }
-        base = g_noalloc_ptr[dev];
-    }
+    u32 *base = (u32 *)p;
     cudaStream_t s = (cudaStream_t)stream;
     u32 *ebits = base, *hist = base + NA_HIST, *cnt = base + NA_CNT;
     float *part = (float *)(base + NA_PART);

@@ -168,6 +168,148 @@ __global__ void k_set_pose(float *d, gsr_pose p)
     pose_rotation_split(d);
 }
 
+// ------------------------------------------ twist perturbation (Sec. 3.5)
+// The tracker optimises a left perturbation T(xi) = exp(xi^) T of the pose,
+// xi = (rho, phi).  exp(xi^) = [[R(phi), V(phi) rho], [0, 1]] with K = [phi]x,
+// th = |phi|, R = I + A K + B K^2, V = I + B K + C K^2, A = sin th / th,
+// B = (1 - cos th) / th^2, C = (th - sin th) / th^3 (series below 1e-3).
+__device__ __forceinline__ void so3_coeffs_d(double th, double &A, double &B, double &C)
+{
+    const double t2 = th * th;
+    if (th < 1e-3) {
+        A = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
+        B = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+        C = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+    } else {
+        A = sin(th) / th;
+        B = (1.0 - cos(th)) / t2;
+        C = (th - sin(th)) / (t2 * th);
+    }
+}
+
+__device__ __forceinline__ void skew_d(const double *w, double K[9])
+{
+    K[0] = 0.0;   K[1] = -w[2]; K[2] = w[1];
+    K[3] = w[2];  K[4] = 0.0;   K[5] = -w[0];
+    K[6] = -w[1]; K[7] = w[0];  K[8] = 0.0;
+}
+
+__device__ __forceinline__ void mat3_mul_d(const double *A, const double *B, double *C)
+{
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+}
+
+// Replaces the (q, t) of a pose record by exp(xi^) (q, t), in double
+// precision, then rounds q', t' to float and re-forms the split rotation, so
+// the record is that of the float pose fl(exp(xi^) T) like any other pose.
+__device__ void perturb_record(float *d, const float *__restrict__ xi)
+{
+    double x[6];
+    for (int k = 0; k < 6; ++k) x[k] = (double)xi[k];
+    const double th = sqrt(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]);
+    double A, B, C;
+    so3_coeffs_d(th, A, B, C);
+    double K[9], K2[9];
+    skew_d(x + 3, K);
+    mat3_mul_d(K, K, K2);
+    double Rd[9], V[9];
+    for (int i = 0; i < 9; ++i) {
+        const double I = (i % 4 == 0) ? 1.0 : 0.0;
+        Rd[i] = I + A * K[i] + B * K2[i];
+        V[i] = I + B * K[i] + C * K2[i];
+    }
+    // unit quaternion of the rotation by phi: (cos th/2, sin(th/2)/th phi)
+    const double hs = th < 1e-3 ? 0.5 - th * th / 48.0 : sin(0.5 * th) / th;
+    const double aw = cos(0.5 * th), ax = hs * x[3], ay = hs * x[4], az = hs * x[5];
+    double bw = d[0], bx = d[1], by = d[2], bz = d[3];
+    const double bn = sqrt(bw * bw + bx * bx + by * by + bz * bz);
+    bw /= bn;
+    bx /= bn;
+    by /= bn;
+    bz /= bn;
+    double q[4] = {aw * bw - ax * bx - ay * by - az * bz, aw * bx + ax * bw + ay * bz - az * by,
+                   aw * by - ax * bz + ay * bw + az * bx, aw * bz + ax * by - ay * bx + az * bw};
+    double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (q[0] < 0.0) qn = -qn;
+    const double t[3] = {d[4], d[5], d[6]};
+    for (int r = 0; r < 3; ++r) {
+        const double tr = Rd[3 * r] * t[0] + Rd[3 * r + 1] * t[1] + Rd[3 * r + 2] * t[2] + V[3 * r] * x[0] +
+                          V[3 * r + 1] * x[1] + V[3 * r + 2] * x[2];
+        d[4 + r] = (float)tr;
+    }
+    for (int k = 0; k < 4; ++k) d[k] = (float)(q[k] / qn);
+    pose_rotation_split(d);
+}
+
+__global__ void k_perturb_pose(float *d, const float *__restrict__ xi) { perturb_record(d, xi); }
+
+// (q', t') = fl(exp(xi^) (q, t)) written to out[0..7) (q' with w >= 0)
+__global__ void k_pose_retract(gsr_pose p, const float *__restrict__ xi, float *__restrict__ out)
+{
+    float d[GSR_POSE_WORDS];
+    for (int k = 0; k < 4; ++k) d[k] = p.q[k];
+    for (int k = 0; k < 3; ++k) d[4 + k] = p.t[k];
+    perturb_record(d, xi);
+    for (int k = 0; k < 7; ++k) out[k] = d[k];
+}
+
+// g6 <- J_l(xi)^T g6: the pose gradient at exp(xi^) T taken with respect to
+// xi itself.  exp((xi + e)^) = exp((J_l(xi) e)^) exp(xi^) + O(e^2), with the
+// SE(3) left Jacobian J_l = [[V, Q], [0, V]] (rho first) and
+//   Q = 1/2 P + c1 (K P + P K + K P K) + c2 (K K P + P K K - 3 K P K)
+//       + c3 (K P K K + K K P K),   P = [rho]x,
+//   c1 = (th - sin th) / th^3, c2 = (th^2 + 2 cos th - 2) / (2 th^4),
+//   c3 = (2 th - 3 sin th + th cos th) / (2 th^5)  (series below 1e-2).
+__global__ void k_pose_grad_xi(float *g6, const float *__restrict__ xi)
+{
+    double x[6], g[6];
+    for (int k = 0; k < 6; ++k) {
+        x[k] = (double)xi[k];
+        g[k] = (double)g6[k];
+    }
+    const double th = sqrt(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]), t2 = th * th;
+    double A, B, C;
+    so3_coeffs_d(th, A, B, C);
+    double c1, c2, c3;
+    if (th < 1e-2) {
+        c1 = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+        c2 = 1.0 / 24.0 - t2 / 720.0 + t2 * t2 / 40320.0;
+        c3 = 1.0 / 120.0 - t2 / 2520.0 + t2 * t2 / 120960.0;
+    } else {
+        c1 = (th - sin(th)) / (t2 * th);
+        c2 = (t2 + 2.0 * cos(th) - 2.0) / (2.0 * t2 * t2);
+        c3 = (2.0 * th - 3.0 * sin(th) + th * cos(th)) / (2.0 * t2 * t2 * th);
+    }
+    double K[9], P[9], KK[9], KP[9], PK[9], KPK[9], KKP[9], PKK[9], KPKK[9], KKPK[9], V[9], Q[9];
+    skew_d(x + 3, K);
+    skew_d(x, P);
+    mat3_mul_d(K, K, KK);
+    mat3_mul_d(K, P, KP);
+    mat3_mul_d(P, K, PK);
+    mat3_mul_d(KP, K, KPK);
+    mat3_mul_d(KK, P, KKP);
+    mat3_mul_d(P, KK, PKK);
+    mat3_mul_d(KPK, K, KPKK);
+    mat3_mul_d(K, KPK, KKPK);
+    for (int i = 0; i < 9; ++i) {
+        const double I = (i % 4 == 0) ? 1.0 : 0.0;
+        V[i] = I + B * K[i] + C * KK[i];
+        Q[i] = 0.5 * P[i] + c1 * (KP[i] + PK[i] + KPK[i]) + c2 * (KKP[i] + PKK[i] - 3.0 * KPK[i]) +
+               c3 * (KPKK[i] + KKPK[i]);
+    }
+    // [g_rho'; g_phi'] = [[V^T, 0], [Q^T, V^T]] [g_rho; g_phi]
+    for (int c = 0; c < 3; ++c) {
+        double r = 0.0, p = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            r += V[3 * k + c] * g[k];
+            p += Q[3 * k + c] * g[k] + V[3 * k + c] * g[3 + k];
+        }
+        g6[c] = (float)r;
+        g6[3 + c] = (float)p;
+    }
+}
+
 // K1: projection, culling, radius, tile rectangle.  rec[gid] holds
 // (u, v, conic a, conic b) (conic c, opacity, depth, rect lo) (r, g, b, rect hi).
 __global__ void __launch_bounds__(256) k_project(Params P, CamK ck, const float *__restrict__ pose,
@@ -805,6 +947,30 @@ __global__ void k_pose_reduce(const float *__restrict__ part, int nb, float *__r
 gsr_status launch_set_pose(gsr_ctx *ctx, float *d_pose, const gsr_pose &p, cudaStream_t s)
 {
     k_set_pose<<<1, 1, 0, s>>>(d_pose, p);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+gsr_status launch_perturb_pose(gsr_ctx *ctx, float *d_pose, const float *xi, cudaStream_t s)
+{
+    k_perturb_pose<<<1, 1, 0, s>>>(d_pose, xi);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+extern "C" gsr_status gsr_pose_retract(const gsr_pose *pose, const float *xi, float *pose_out, void *stream)
+{
+    if (!pose || !xi || !pose_out) return GSR_ERR_INVALID_ARG;
+    (void)cudaGetLastError();  // report only this call's launch
+    k_pose_retract<<<1, 1, 0, (cudaStream_t)stream>>>(*pose, xi, pose_out);
+    return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+gsr_status launch_pose_grad_xi(gsr_ctx *ctx, float *g6, const float *xi, cudaStream_t s)
+{
+    k_pose_grad_xi<<<1, 1, 0, s>>>(g6, xi);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     return GSR_OK;

@@ -224,7 +224,8 @@ def add_frames(data: Samples, ctx_full, ctx_low, g, spec, poses, per_frame: int,
                 break
             k = int(data.slots[data.n])
             xi = random_twist(rng, max_t, max_deg)
-            qi, ti = api.pose_exp_left(q, t, xi)
+            pi = api.pose_retract(api.make_pose(q, t), torch.tensor(xi, dtype=torch.float32, device="cuda"))
+            qi, ti = _host_pose(pi)
             lo = api.render_forward(ctx_low, g, cam_l, api.make_pose(qi, ti))
             make_input(lo["rgb"], lo["depth"], fr.rgb, fr.depth, depth_scale, out=data.x[k])
             data._y[k] = -xi
@@ -264,10 +265,20 @@ def predict(net: WarmStartNet, x: torch.Tensor, batch: int = 0) -> torch.Tensor:
     return out
 
 
+def _host_pose(p: torch.Tensor):
+    """(q, t) float64 arrays of a device (q, t) float32 [7] pose (synchronising)."""
+    h = p.cpu().numpy().astype(np.float64)
+    return h[:4], h[4:7]
+
+
 def corrected_poses(data: Samples, pred: torch.Tensor):
+    """exp(pred_i^) T_i for every sample's initial pose T_i (gsr_pose_retract)."""
     from . import api
-    p = pred.double().cpu().numpy()
-    return [api.pose_exp_left(q, t, p[i]) for i, (q, t) in enumerate(data.init)]
+    pred = pred.to(torch.float32).contiguous()
+    out = torch.empty((len(data.init), 7), dtype=torch.float32, device=pred.device)
+    for i, (q, t) in enumerate(data.init):
+        api.pose_retract(api.make_pose(q, t), pred[i], out=out[i])
+    return [_host_pose(p) for p in out]
 
 
 def pose_errors(data: Samples, poses):
@@ -308,5 +319,5 @@ def warm_start_pose(net: WarmStartNet, ctx_low, g, spec, frame: Frame, q, t, dep
     cam_l = api.camera_from_spec(low_res_camera(spec))
     lo = api.render_forward(ctx_low, g, cam_l, api.make_pose(q, t))
     x = make_input(lo["rgb"], lo["depth"], frame.rgb, frame.depth, depth_scale).unsqueeze(0)
-    xi = net.forward(x)[0].double().cpu().numpy()
-    return api.pose_exp_left(q, t, xi)
+    xi = net.forward(x)[0].contiguous()
+    return _host_pose(api.pose_retract(api.make_pose(q, t), xi))

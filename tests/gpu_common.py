@@ -28,6 +28,17 @@ def grad_close(g, ref, rel=1e-3, floor=0.1, rel_l2=1e-4):
     return bool((ratio <= 1.0).all() and l2 <= rel_l2), float(max(ratio.max(), l2 / rel_l2))
 
 
+def strict_pass_fraction(g, ref):
+    """Fraction of entries within the stricter elementwise bar
+    |g - ref| <= 1e-3 (|ref| + 1e-3 rms(ref)) (reported beside grad_close)."""
+    g = np.asarray(g, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    if ref.size == 0:
+        return 1.0
+    rms = np.sqrt(np.mean(ref * ref))
+    return float(np.mean(np.abs(g - ref) <= 1e-3 * (np.abs(ref) + 1e-3 * rms) + 1e-30))
+
+
 def tile_sequences_match(ranges, gids, ref_start, ref_gid, near_tie, skip):
     """Per tile, the GPU list must equal the oracle list once Gaussians with an
     ambiguous projection (`skip`) are removed; runs of float-depth near-ties

@@ -63,6 +63,7 @@ def test_struct_layouts_match_header(tmp_path):
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for fname, _ in py._fields_:
             lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('printf("GSR_NOALLOC_MAX_PIXELS value %d\\n", (int)GSR_NOALLOC_MAX_PIXELS);')
     lines.append("return 0;}")
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -71,6 +72,9 @@ def test_struct_layouts_match_header(tmp_path):
     out = subprocess.check_output([str(exe)]).decode().split("\n")
     for line in filter(None, out):
         cname, field, val = line.split()
+        if cname == "GSR_NOALLOC_MAX_PIXELS":
+            assert _lib.NOALLOC_MAX_PIXELS == int(val)
+            continue
         py = STRUCTS[cname]
         if field == "size":
             assert ctypes.sizeof(py) == int(val), cname

@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 
 import oracle as O
 from paper_2312_10070_gb300 import api, synth as S
-from tests.gpu_common import grad_close, ocam
+from tests.gpu_common import grad_close, ocam, strict_pass_fraction
 
 pytestmark = pytest.mark.gpu
 
@@ -74,7 +74,8 @@ def test_hires_memory_saving_backward_matches_central_fd():
         assert torch.equal(out[k], out2[k]), k
 
     h = 1e-6
-    fd_all, gpu_all = [], []
+    fd_all = {name: [] for name in NAMES}
+    gpu_all = {name: [] for name in NAMES}
     for gid, li, sub, cw, win in subsets:
         wr, wd = w_rgb[(slice(None),) + win].astype(np.float64), w_d[win].astype(np.float64)
         _, r0 = _linear(sub, q, t, cw, wr, wd)
@@ -90,11 +91,17 @@ def test_hires_memory_saving_backward_matches_central_fd():
                 if not (np.array_equal(rp["n_contrib"], r0["n_contrib"])
                         and np.array_equal(rm["n_contrib"], r0["n_contrib"])):
                     continue  # a discrete decision flips within +-h: FD not defined
-                fd_all.append((lp - lm) / (2 * h))
-                gpu_all.append(gpu[name].reshape(sc64.n, -1)[gid, k])
-    fd_all, gpu_all = np.array(fd_all), np.array(gpu_all)
-    assert len(fd_all) >= 0.9 * 64 * 14
-    ok, worst = grad_close(gpu_all, fd_all, rel=1e-3, floor=0.1, rel_l2=1e-3)
-    assert ok, worst
+                fd_all[name].append((lp - lm) / (2 * h))
+                gpu_all[name].append(gpu[name].reshape(sc64.n, -1)[gid, k])
+    assert sum(len(v) for v in fd_all.values()) >= 0.9 * 64 * 14
+    # each parameter kind against its own scale: the tolerance floor and the
+    # relative L2 error are taken per name, so small-magnitude kinds (colour,
+    # opacity) are held to 1e-3 of their own gradients, not of the mean's
+    worst = {}
+    for name in NAMES:
+        fd, gg = np.array(fd_all[name]), np.array(gpu_all[name])
+        ok, worst[name] = grad_close(gg, fd, rel=1e-3, floor=0.1, rel_l2=1e-3)
+        print(name, len(fd), "worst ratio", worst[name], "strict floor pass", strict_pass_fraction(gg, fd))
+        assert ok, (name, worst[name])
     ctx.close()
     ctx2.close()

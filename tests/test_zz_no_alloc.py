@@ -47,8 +47,11 @@ def noalloc(lib, H, W, rgb, d, a, rgb_t, d_t):
 def test_noalloc_track_loss_matches_context_entry_point():
     lib = _lib.load()
     ctx = api.Context()
-    # two calls in a row with different inputs and sizes (the second smaller)
-    for (H, W, seed, invalid) in ((680, 1200, 1, 0.05), (120, 160, 2, 0.3)):
+    # calls in a row with different inputs and sizes: the largest image the
+    # static scratch holds (1280 x 720 = GSR_NOALLOC_MAX_PIXELS), a smaller one
+    # that must not see the first call's leftovers, then a mid-sized one
+    assert 720 * 1280 == _lib.NOALLOC_MAX_PIXELS
+    for (H, W, seed, invalid) in ((720, 1280, 3, 0.1), (120, 160, 2, 0.3), (680, 1200, 1, 0.05)):
         inp = frame(H, W, seed, invalid)
         loss, med, g_rgb, g_d = noalloc(lib, H, W, *inp)
         ref_loss, ref_med, ref_rgb, ref_d = api.loss_track(ctx, *inp)
@@ -71,3 +74,18 @@ def test_noalloc_rejects_images_beyond_its_scratch():
     assert st == -4  # GSR_ERR_CAPACITY, nothing launched
     assert lib.gsr_loss_track_noalloc(0, 10, p(x), p(y), p(y), p(x), p(y), 0.5, 50.0, 3.0, p(x), p(y), None, None,
                                       None) == -1
+
+
+def test_noalloc_nonfinite_loss_shows_in_the_loss_value():
+    """The call does not synchronise, so a NaN input is not reported as a
+    status; it shows in the loss it writes (documented in gsr.h)."""
+    lib = _lib.load()
+    H, W = 64, 96
+    rgb, d, a, rgb_t, d_t = frame(H, W, 4, 0.1)
+    rgb_t[1, 5, 7] = float("nan")
+    loss, med, _, _ = noalloc(lib, H, W, rgb, d, a, rgb_t, d_t)
+    assert not np.isfinite(float(loss))
+    # the next call on clean inputs is unaffected
+    rgb_t[1, 5, 7] = 0.5
+    loss, med, _, _ = noalloc(lib, H, W, rgb, d, a, rgb_t, d_t)
+    assert np.isfinite(float(loss))
