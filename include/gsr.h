@@ -190,6 +190,17 @@ GSR_API gsr_status gsr_check_wait_timeout(gsr_ctx *ctx, int32_t polls, void *str
 GSR_API gsr_status gsr_tile_lists_get(gsr_ctx *ctx, uint32_t *ranges, int32_t *gids, int64_t capacity,
                                       uint32_t *depth_bits, int64_t *n_instances, void *stream);
 
+/* Copies the per-Gaussian image-space records of the last forward to HOST
+ * memory (synchronises; for tests and debugging).  rec: host float[12 n] =
+ * per Gaussian (u, v, conic a, conic b, conic c, opacity, camera depth,
+ * bits of the first tile column/row, r, g, b, bits of the last tile
+ * column/row) -- the projection of Sec. 3.1 (mean, inverse of the EWA
+ * covariance Sigma^I, activated opacity) as the blend kernels read it;
+ * visible: host uint32[n], 1 where the Gaussian survived culling (records of
+ * culled Gaussians are unspecified).  n must equal the last forward's count.
+ * GSR_ERR_STATE without a forward. */
+GSR_API gsr_status gsr_records_get(gsr_ctx *ctx, float *rec, uint32_t *visible, int64_t n, void *stream);
+
 /* Backward of gsr_render_forward (Sec. 3.4 adjoints, including the depth
  * adjoint dD/dalpha_j = mu^z_j T_j - sum_{u>j} mu^z_u alpha_u T_u /(1-alpha_j)).
  * `saved` must hold the final_T and last_idx of the matching forward.
@@ -502,6 +513,11 @@ GSR_API gsr_status gsr_merge_submap(gsr_ctx *ctx, gsr_gaussians_mut *global, int
  * GSR_ERR_CUDA if the launch fails. */
 GSR_API gsr_status gsr_probe_fma(float *out, int32_t blocks, int32_t iters, void *stream);
 GSR_API gsr_status gsr_probe_exp(float *out, int32_t blocks, int32_t iters, void *stream);
+/* y[i] = the single-precision exponential the blend kernels use for
+ * alpha = o exp(-sigma), at x[i] (device float[n] each), so a test can check
+ * its error against the bound the parity margins assume.
+ * GSR_ERR_INVALID_ARG on NULL or n <= 0. */
+GSR_API gsr_status gsr_probe_expf(const float *x, float *y, int64_t n, void *stream);
 
 #ifdef __cplusplus
 }

@@ -62,7 +62,7 @@ class Camera:
     guard: float = 1.3
     tile_w: int = 16
     tile_h: int = 16
-    amb_rel: float = 5e-4
+    amb_rel: float = 0.0
     guard_y: float = 0.0
 
     def c(self) -> _Cam:
@@ -103,10 +103,13 @@ def _load():
         lib.orc_bin.restype = ctypes.c_int64
         lib.orc_bin.argtypes = [ctypes.c_int64] + [P] * 6 + [ctypes.POINTER(_Cam), ctypes.c_int64, P, P, P]
         lib.orc_render.restype = ctypes.c_int
-        lib.orc_render.argtypes = [ctypes.c_int64] + [P] * 7 + [ctypes.POINTER(_Cam)] + [P] * 8
+        lib.orc_render.argtypes = [ctypes.c_int64] + [P] * 7 + [ctypes.POINTER(_Cam)] + [P] * 9
         lib.orc_render_backward.restype = ctypes.c_int
         lib.orc_render_backward.argtypes = ([ctypes.c_int64] + [P] * 7 + [ctypes.POINTER(_Cam)]
-                                            + [P] * 3 + [P] * 7)
+                                            + [P] * 3 + [P] * 7 + [P])
+        lib.orc_render_alternatives.restype = ctypes.c_int
+        lib.orc_render_alternatives.argtypes = ([ctypes.c_int64] + [P] * 7 + [ctypes.POINTER(_Cam), P,
+                                                ctypes.c_int64, ctypes.c_int, ctypes.c_int] + [P] * 8)
         lib.orc_project_backward.restype = ctypes.c_int
         lib.orc_project_backward.argtypes = ([ctypes.c_int64] + [P] * 6 + [ctypes.POINTER(_Cam)]
                                              + [P] * 7)
@@ -122,6 +125,8 @@ def _load():
         lib.orc_adam.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int64] + [ctypes.c_double] * 4
         lib.orc_pose_retract.restype = None
         lib.orc_pose_retract.argtypes = [P] * 5
+        lib.orc_error_model.restype = None
+        lib.orc_error_model.argtypes = [P]
         lib.orc_se3_left_jacobian.restype = None
         lib.orc_se3_left_jacobian.argtypes = [P] * 2
         lib.orc_num_threads.restype = ctypes.c_int
@@ -210,9 +215,12 @@ def bin_tiles(scene: Scene, pose_q, pose_t, cam: Camera) -> dict:
     return dict(start=start, gid=gid[:total], near_tie=tie[:total].astype(bool))
 
 
-def render(scene: Scene, pose_q, pose_t, cam: Camera) -> dict:
+def render(scene: Scene, pose_q, pose_t, cam: Camera, flips=None) -> dict:
     """Forward render: rgb [3,H,W], depth, alpha, final_T, last_idx, n_contrib,
-    amb (per-pixel ambiguity flags) and n_eval (list entries visited)."""
+    amb (per-pixel ambiguity flags: bit 0 a marginal decision, bit 1 a marginal
+    alpha cap, bit 3 a marginal decision other than a skip or stop) and n_eval
+    (list entries visited).  flips (uint32 [H,W], optional): per pixel, the
+    branches taken at its marginal skip / stop decisions."""
     lib = _load()
     q, t = _pose(pose_q, pose_t)
     H, W = cam.height, cam.width
@@ -221,17 +229,20 @@ def render(scene: Scene, pose_q, pose_t, cam: Camera) -> dict:
                n_contrib=np.zeros((H, W), np.int32), amb=np.zeros((H, W), np.int32))
     ne = np.zeros(1, np.int64)
     c = cam.c()
+    fl = None if flips is None else np.ascontiguousarray(np.asarray(flips, np.uint32).reshape(H, W))
     lib.orc_render(scene.n, *[_p(a) for a in scene.params()], _p(scene.rgb), _p(q), _p(t),
                    ctypes.byref(c), *[_p(out[k]) for k in ("rgb", "depth", "alpha", "final_T",
-                                                           "last_idx", "n_contrib", "amb")], _p(ne))
+                                                           "last_idx", "n_contrib", "amb")], _p(ne), _p(fl))
     out["n_eval"] = int(ne[0])
     return out
 
 
 def render_backward(scene: Scene, pose_q, pose_t, cam: Camera, d_rgb=None, d_depth=None,
-                    d_alpha=None) -> dict:
+                    d_alpha=None, flips=None) -> dict:
     """Exact gradient of sum(d_rgb*rgb + d_depth*depth + d_alpha*alpha) with respect
-    to every Gaussian parameter and the pose twist (rho, phi) of a left perturbation."""
+    to every Gaussian parameter and the pose twist (rho, phi) of a left perturbation.
+    flips (uint32 [H,W], optional): per pixel, the branches taken at its marginal
+    skip / stop decisions (the flip mask of one of render_alternatives' results)."""
     lib = _load()
     q, t = _pose(pose_q, pose_t)
     n = scene.n
@@ -242,11 +253,35 @@ def render_backward(scene: Scene, pose_q, pose_t, cam: Camera, d_rgb=None, d_dep
              opacity_logit=np.zeros(n), rgb=np.zeros((n, 3)), pose=np.zeros(6),
              g2d=np.zeros((n, 10)))
     c = cam.c()
+    fl = None if flips is None else np.ascontiguousarray(np.asarray(flips, np.uint32).reshape(cam.height, cam.width))
     lib.orc_render_backward(n, *[_p(a) for a in scene.params()], _p(scene.rgb), _p(q), _p(t),
                             ctypes.byref(c), _p(d_rgb), _p(d_depth), _p(d_alpha),
                             *[_p(g[k]) for k in ("mean", "log_scale", "quat", "opacity_logit",
-                                                 "rgb", "pose", "g2d")])
+                                                 "rgb", "pose", "g2d")], _p(fl))
     return g
+
+
+def render_alternatives(scene: Scene, pose_q, pose_t, cam: Camera, pixels, max_bits=4, kmax=16) -> dict:
+    """Every result a float32 implementation may produce at the given pixel
+    indices (row-major): per pixel up to kmax alternatives that take either
+    branch of its marginal skip / stop decisions.  Arrays [npix, kmax]:
+    rgb [npix, kmax, 3], depth, final_T, last_gid, n_contrib, flip; count
+    [npix]; amb [npix]."""
+    lib = _load()
+    q, t = _pose(pose_q, pose_t)
+    pix = np.ascontiguousarray(np.asarray(pixels, np.int64).reshape(-1))
+    m = pix.size
+    out = dict(rgb=np.zeros((m, kmax, 3)), depth=np.zeros((m, kmax)), final_T=np.zeros((m, kmax)),
+               last_gid=np.full((m, kmax), -2, np.int32), n_contrib=np.zeros((m, kmax), np.int32),
+               flip=np.zeros((m, kmax), np.uint32), count=np.zeros(m, np.int32), amb=np.zeros(m, np.int32))
+    if m == 0:
+        return out
+    c = cam.c()
+    lib.orc_render_alternatives(scene.n, *[_p(a) for a in scene.params()], _p(scene.rgb), _p(q), _p(t),
+                                ctypes.byref(c), _p(pix), m, int(max_bits), int(kmax),
+                                *[_p(out[k]) for k in ("rgb", "depth", "final_T", "last_gid", "n_contrib", "flip",
+                                                       "count", "amb")])
+    return out
 
 
 def project_backward(scene: Scene, pose_q, pose_t, cam: Camera, g2d) -> dict:
@@ -337,3 +372,13 @@ def twist_gradient(xi, pose_grad):
     """dL/dxi of a loss of T(xi) = exp(xi^) T, from the left-perturbation pose
     gradient at T(xi): J_l(xi)^T pose_grad."""
     return se3_left_jacobian(xi).T @ _f64(pose_grad).reshape(6)
+
+
+def error_model() -> dict:
+    """The float32 error bounds behind the ambiguity flags (see gsr_oracle.c):
+    unit roundoff u; compensated transform bound; u, v ratio and rounding
+    factors; conic quadratic-form factor (x u sqrt(kappa)); sigmoid factor;
+    sigma evaluation factor; relative error of the exponential."""
+    c = np.zeros(8)
+    _load().orc_error_model(_p(c))
+    return dict(zip(("u", "df", "ratio", "round", "conic", "opacity", "sigma", "exp"), c.tolist()))

@@ -51,6 +51,17 @@ typedef struct {
 #define ALPHA_MAX 0.99
 #define T_STOP 1e-4
 
+/* Rounding-error bounds of the float32 implementation, in units of the unit
+ * roundoff U32 = 2^-24 (used only to flag decisions as ambiguous). */
+#define U32 (1.0 / 16777216.0)
+#define ERR_DF 1e-13        /* compensated p = R mu + t, relative to sum |terms| */
+#define ERR_RATIO 5.0       /* u, v: on fx p_x / p_z (4 roundings) */
+#define ERR_ROUND 1.25      /* u, v: the final rounding */
+#define ERR_CONIC 32.0      /* conic as a quadratic form, x sqrt(kappa) */
+#define ERR_OPAC 4.0        /* sigmoid in float */
+#define ERR_SIGMA 6.0       /* sigma from the float conic and offsets, x sum |terms| */
+#define ERR_EXP 5e-7        /* relative error of the single-precision exponential for sigma in [0, 6] */
+
 /* per-Gaussian projection state (Sec. 3.1) */
 typedef struct {
     int visible, radius, x0, y0, x1, y1;
@@ -59,6 +70,8 @@ typedef struct {
     int vis_amb;      /* the cull decision itself is near its threshold */
     int ox0, oy0, ox1, oy1, ix0, iy0, ix1, iy1; /* outer / inner possible tile rectangles */
     double err_z, err_u, err_v; /* bounds of the float32 rounding error of p_z, u, v */
+    int key_unc;      /* the float depth key may differ from the float rounding of p_z */
+    double e_q;       /* relative error bound of the float conic as a quadratic form */
     int clamp_x, clamp_y;
     double u, v, depth, opacity;
     double cov[3];    /* Sigma^I + eps I:   a b c */
@@ -126,12 +139,23 @@ static void project_one(const orc_camera *c, const double Rcw[9], const double t
         o->p[i] = Rcw[3 * i] * mean[0] + Rcw[3 * i + 1] * mean[1] + Rcw[3 * i + 2] * mean[2] + tcw[i];
     double px = o->p[0], py = o->p[1], pz = o->p[2];
     o->depth = pz;
-    /* Error model of a float32 implementation that evaluates p = R mu + t
-     * faithfully rounded (compensated products): |error| < 1 ulp of p, bounded
-     * here by 2.4e-7 |p|.  The margins below derive from it: a decision closer
-     * to its threshold than the bound is flagged as ambiguous, not compared. */
-    o->err_z = 2.4e-7 * fabs(pz) + 1e-12;
-    int z_amb = fabs(pz - c->z_near) <= o->err_z;
+    /* Error model of the float32 implementation (each a bound; a decision
+     * closer to its threshold than its bound is flagged as ambiguous and not
+     * compared).  p = R mu + t is evaluated in compensated (double-float)
+     * arithmetic, so before its final rounding p_z is within
+     * ERR_DF (sum_j |R_zj mu_j| + |t_z|) of the exact value: the float depth
+     * key is the correctly rounded p_z unless p_z lies within that distance
+     * of a rounding midpoint (key_unc). */
+    {
+        double sabs = fabs(Rcw[6] * mean[0]) + fabs(Rcw[7] * mean[1]) + fabs(Rcw[8] * mean[2]) + fabs(tcw[2]);
+        o->err_z = ERR_DF * sabs + 1e-300;
+        float f = (float)pz;
+        double up = nextafterf(f, INFINITY), dn = nextafterf(f, -INFINITY);
+        double d1 = fabs(pz - 0.5 * ((double)f + up)), d2 = fabs(pz - 0.5 * ((double)f + dn));
+        o->key_unc = fmin(d1, d2) <= o->err_z;
+    }
+    /* the near-plane test compares the float key with the float z_near */
+    int z_amb = fabs(pz - c->z_near) <= o->err_z + 1.2e-7 * c->z_near;
     if (z_amb) { o->amb |= 1; o->vis_amb = 1; } /* its tiles (computed below) are marked */
     if (pz <= c->z_near && !z_amb) return;
 
@@ -168,6 +192,16 @@ static void project_one(const orc_camera *c, const double Rcw[9], const double t
     if (fabs(det) <= 1e-5 * fabs(a * cc)) { o->amb |= 1; o->vis_amb = 2; }
     if (det <= 0) return;
     o->conic[0] = cc / det; o->conic[1] = -b / det; o->conic[2] = a / det;
+    {
+        /* the float conic (inverse of Sigma^I = T T^T + eps I, T = J W R S
+         * formed from float inputs) errs as a quadratic form by at most
+         * ERR_CONIC u sqrt(kappa), kappa = the condition number of Sigma^I:
+         * first-order propagation of the entry errors of T through T T^T
+         * and the inverse scales with sqrt(kappa) */
+        double hm = 0.5 * (a + cc), hd = sqrt(0.25 * (a - cc) * (a - cc) + b * b);
+        double kappa = (hm + hd) / fmax(hm - hd, 1e-300);
+        o->e_q = ERR_CONIC * U32 * sqrt(kappa);
+    }
 
     /* screen radius: 3 sqrt(largest eigenvalue), rounded up */
     double lmax = 0.5 * (a + cc) + sqrt(0.25 * (a - cc) * (a - cc) + b * b);
@@ -184,9 +218,11 @@ static void project_one(const orc_camera *c, const double Rcw[9], const double t
     /* pinhole projection; pixel (i, j) has its centre at (i + 0.5, j + 0.5) */
     o->u = c->fx * px / pz + c->cx;
     o->v = c->fy * py / pz + c->cy;
-    /* u = fx (p_x / p_z) + c_x in float: ~4 ulp on the ratio, 0.5 ulp on u */
-    o->err_u = 5e-7 * c->fx * fabs(px / pz) + 1.2e-7 * fabs(o->u) + 1e-6;
-    o->err_v = 5e-7 * c->fy * fabs(py / pz) + 1.2e-7 * fabs(o->v) + 1e-6;
+    /* u = fx (p_x / p_z) + c_x in float from the rounded p_x, p_z: the ratio
+     * carries four roundings (p_x, p_z, the reciprocal, the product), the
+     * fused multiply-add one more on u */
+    o->err_u = ERR_RATIO * U32 * c->fx * fabs(px / pz) + ERR_ROUND * U32 * fabs(o->u) + 1e-9;
+    o->err_v = ERR_RATIO * U32 * c->fy * fabs(py / pz) + ERR_ROUND * U32 * fabs(o->v) + 1e-9;
 
     /* tile rectangle, inclusive, clamped to the tile grid */
     int tiles_x = (c->width + c->tile_w - 1) / c->tile_w;
@@ -292,38 +328,78 @@ static void free_lists(olists *L)
     free(L->gid);
 }
 
-/* two depths whose order a float32 evaluation may swap: within the sum of
- * their error bounds plus 2 ulp of float */
-static int depth_near_tie(double a, double ea, double b, double eb)
+/* two Gaussians whose float depth keys a float32 implementation may order
+ * differently from the oracle: the keys are the correctly rounded depths
+ * (ties broken by index on both sides) unless one of them is uncertain, and
+ * then only neighbouring keys can swap */
+static int depth_near_tie(const oproj *a, const oproj *b)
 {
-    return fabs(a - b) <= ea + eb + 2.5e-7 * fmax(fabs(a), fabs(b));
+    return (a->key_unc || b->key_unc) && fabs(a->depth - b->depth) <= 2.5e-7 * fmax(fabs(a->depth), fabs(b->depth));
 }
 
-/* Tiles whose list membership may differ because a projection decision is
- * within its margin: the tiles between the outer and inner possible
- * rectangles, all of the outer rectangle when the cull decision itself is
- * marginal, and the whole image when no rectangle exists (z or det). */
-static unsigned char *ambiguous_tiles(int64_t n, const oproj *P, const orc_camera *cam)
+/* Gaussians whose list membership in a tile may differ because a projection
+ * decision is within its margin, per tile (CSR): the tiles between the outer
+ * and inner possible rectangles, all of the outer rectangle when the cull
+ * decision itself is marginal.  `global` is set when a Gaussian with a
+ * marginal determinant has no rectangle at all (its membership may differ
+ * anywhere).  A pixel of such a tile is ambiguous only if the Gaussian could
+ * composite there (tile_pixel_ambiguous). */
+typedef struct { int64_t *start; int32_t *gid; int global; } oamb;
+
+static int amb_marks(const oproj *g, int tx, int ty)
+{
+    if (g->vis_amb == 2) return 0;  /* handled as global */
+    int outer = tx >= g->ox0 && tx <= g->ox1 && ty >= g->oy0 && ty <= g->oy1;
+    int inner = tx >= g->ix0 && tx <= g->ix1 && ty >= g->iy0 && ty <= g->iy1;
+    return outer && (g->vis_amb || !inner);
+}
+
+static void ambiguous_tiles(int64_t n, const oproj *P, const orc_camera *cam, oamb *A)
 {
     int tiles_x = (cam->width + cam->tile_w - 1) / cam->tile_w;
     int tiles_y = (cam->height + cam->tile_h - 1) / cam->tile_h;
-    unsigned char *m = (unsigned char *)calloc((size_t)tiles_x * tiles_y, 1);
-    for (int64_t i = 0; i < n; ++i) {
-        const oproj *g = &P[i];
-        if (!(g->amb & 1)) continue;
-        for (int ty = 0; ty < tiles_y; ++ty)
-            for (int tx = 0; tx < tiles_x; ++tx) {
-                int mark;
-                if (g->vis_amb == 2) mark = 1;
-                else {
-                    int outer = tx >= g->ox0 && tx <= g->ox1 && ty >= g->oy0 && ty <= g->oy1;
-                    int inner = tx >= g->ix0 && tx <= g->ix1 && ty >= g->iy0 && ty <= g->iy1;
-                    mark = outer && (g->vis_amb || !inner);
+    int64_t nt = (int64_t)tiles_x * tiles_y;
+    A->start = (int64_t *)calloc((size_t)nt + 1, sizeof(int64_t));
+    A->global = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t *fill = pass ? (int64_t *)calloc((size_t)nt, sizeof(int64_t)) : NULL;
+        for (int64_t i = 0; i < n; ++i) {
+            const oproj *g = &P[i];
+            if (!(g->amb & 1)) continue;
+            if (g->vis_amb == 2) { A->global = 1; continue; }
+            for (int ty = imax(0, g->oy0); ty <= imin(tiles_y - 1, g->oy1); ++ty)
+                for (int tx = imax(0, g->ox0); tx <= imin(tiles_x - 1, g->ox1); ++tx) {
+                    if (!amb_marks(g, tx, ty)) continue;
+                    int64_t t = (int64_t)ty * tiles_x + tx;
+                    if (pass == 0) A->start[t + 1]++;
+                    else A->gid[A->start[t] + fill[t]++] = (int32_t)i;
                 }
-                if (mark) m[(int64_t)ty * tiles_x + tx] = 1;
-            }
+        }
+        if (pass == 0) {
+            for (int64_t t = 0; t < nt; ++t) A->start[t + 1] += A->start[t];
+            A->gid = (int32_t *)malloc(sizeof(int32_t) * (size_t)(A->start[nt] > 0 ? A->start[nt] : 1));
+        }
+        free(fill);
     }
-    return m;
+}
+
+static void free_amb(oamb *A) { free(A->start); free(A->gid); }
+
+/* 1 when a Gaussian whose membership in the pixel's tile is marginal could
+ * composite at the pixel (alpha >= 1/255 up to a relative 1e-3): its presence
+ * or absence then may change the pixel; otherwise it cannot. */
+static int tile_pixel_ambiguous(const oamb *A, const oproj *P, int64_t t, int ix, int iy)
+{
+    if (A->global) return 1;
+    const double xc = ix + 0.5, yc = iy + 0.5;  /* the pixel's centre */
+    for (int64_t k = A->start[t]; k < A->start[t + 1]; ++k) {
+        const oproj *g = &P[A->gid[k]];
+        if (!(g->conic[0] > 0 && g->conic[2] > 0)) return 1;
+        double dx = xc - g->u, dy = yc - g->v;
+        double sigma = 0.5 * (g->conic[0] * dx * dx + g->conic[2] * dy * dy) + g->conic[1] * dx * dy;
+        if (g->opacity * exp(-sigma) >= ALPHA_MIN * (1.0 - 1e-3)) return 1;
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------ public API */
@@ -373,8 +449,7 @@ int64_t orc_bin(int64_t n, const double *mean, const double *log_scale, const do
         if (near_tie)
             for (int64_t t = 0; t < L.n_tiles; ++t)
                 for (int64_t k = L.start[t]; k < L.start[t + 1]; ++k)
-                    near_tie[k] = (k > L.start[t]) && depth_near_tie(P[L.gid[k]].depth, P[L.gid[k]].err_z,
-                                                                     P[L.gid[k - 1]].depth, P[L.gid[k - 1]].err_z);
+                    near_tie[k] = (k > L.start[t]) && depth_near_tie(&P[L.gid[k]], &P[L.gid[k - 1]]);
     } else {
         total = -1;
     }
@@ -396,14 +471,25 @@ typedef struct { int32_t gid; double alpha, G, T, dx, dy, ex; int clamped; } oco
 static void blend_pixel(const orc_camera *cam, const oproj *P, const double *rgb,
                         const int32_t *list, int64_t len, int ix, int iy,
                         double C[3], double *D, double *T_out, int32_t *last, int32_t *ncontrib,
-                        int64_t *neval, int *amb, ocontrib *trace)
+                        int64_t *neval, int *amb, ocontrib *trace, unsigned flip, int *n_enum)
 {
+    /* flip: bit k takes the other branch of the k-th marginal skip (alpha vs
+     * 1/255) or stop (T (1 - alpha) vs 1e-4) decision met on this walk, both
+     * branches being results a float32 implementation may produce; n_enum
+     * receives the number of such decisions met.  amb bit 0: some decision was
+     * marginal; bit 1: a marginal alpha cap (gradient only); bit 3: a marginal
+     * decision other than those two kinds (sigma sign, depth order). */
+    int ne_k = 0;
     double px = ix + 0.5, py = iy + 0.5;
     double T = 1.0;
     int32_t lastpos = -1, nc = 0;
     int64_t ne = 0;
-    int a = 0, have_prev = 0;
-    double prev_depth = 0, prev_err = 0, eps = cam->amb_rel;
+    int a = 0;
+    const oproj *prev = NULL;
+    /* relative error bound of the float transmittance so far (each composited
+     * entry adds its alpha error amplified by alpha / (1 - alpha), plus one
+     * rounding of the product), and an extra relative margin (amb_rel) */
+    double eT = 0.0, eps = cam->amb_rel;
     C[0] = C[1] = C[2] = 0;
     *D = 0;
     for (int64_t k = 0; k < len; ++k) {
@@ -413,27 +499,42 @@ static void blend_pixel(const orc_camera *cam, const oproj *P, const double *rgb
         double dx = px - g->u, dy = py - g->v;
         /* sigma = 1/2 Delta^T (Sigma^I)^-1 Delta */
         double sigma = 0.5 * (g->conic[0] * dx * dx + g->conic[2] * dy * dy) + g->conic[1] * dx * dy;
-        if (fabs(sigma) <= 1e-9) a |= 1;
+        if (fabs(sigma) <= 1e-9) a |= 1 | 8;
         if (sigma < 0) continue;
         double ex = exp(-sigma);
         double G = g->opacity * ex; /* alpha_j = o_j exp(-sigma_j) */
-        /* relative error bound of G from the float32 error of (u, v) */
+        /* relative error bound of the float G: the float (u, v) moves sigma by
+         * es, the float conic by e_q sigma, the float evaluation of sigma by
+         * ERR_SIGMA u (sum of the magnitudes of its terms); the exponential,
+         * the sigmoid and the product add their own */
         double es = fabs(g->conic[0] * dx + g->conic[1] * dy) * g->err_u
                   + fabs(g->conic[1] * dx + g->conic[2] * dy) * g->err_v;
-        double mg = eps + es;
-        if (fabs(G - ALPHA_MIN) <= mg * ALPHA_MIN) a |= 1;
+        double sabs = 0.5 * (fabs(g->conic[0]) * dx * dx + fabs(g->conic[2]) * dy * dy) + fabs(g->conic[1] * dx * dy);
+        double mg = eps + es + g->e_q * sigma + ERR_SIGMA * U32 * sabs + ERR_EXP + ERR_OPAC * U32 + U32;
         if (fabs(G - ALPHA_MAX) <= mg * ALPHA_MAX) a |= 2;
         int clamped = G > ALPHA_MAX;
         double alpha = clamped ? ALPHA_MAX : G;
-        if (alpha < ALPHA_MIN) continue;
+        int skip = alpha < ALPHA_MIN;
+        if (fabs(G - ALPHA_MIN) <= mg * ALPHA_MIN) {
+            a |= 1;
+            if ((flip >> ne_k) & 1u) skip = !skip;
+            ++ne_k;
+        }
+        if (skip) continue;
+        double ea = clamped ? 2e-8 : mg; /* the cap is 0.99 in float */
         double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - T_STOP) <= (eps + mg * alpha / (1.0 - alpha)) * T_STOP) a |= 1;
-        if (Tn < T_STOP) break;
+        double eTn = eT + ea * alpha / (1.0 - alpha) + 2 * U32;
+        int stop = Tn < T_STOP;
+        if (fabs(Tn - T_STOP) <= (eps + eTn) * T_STOP) {
+            a |= 1;
+            if ((flip >> ne_k) & 1u) stop = !stop;
+            ++ne_k;
+        }
+        if (stop) break;
         a |= g->amb & 2;
-        if (have_prev && depth_near_tie(prev_depth, prev_err, g->depth, g->err_z)) a |= 1;
-        prev_depth = g->depth;
-        prev_err = g->err_z;
-        have_prev = 1;
+        if (prev && depth_near_tie(prev, g)) a |= 1 | 8;
+        prev = g;
+        eT = eTn;
         if (trace) {
             ocontrib *t = &trace[nc];
             t->gid = gi; t->alpha = alpha; t->G = G; t->T = T; t->dx = dx; t->dy = dy; t->ex = ex;
@@ -451,22 +552,26 @@ static void blend_pixel(const orc_camera *cam, const oproj *P, const double *rgb
     *ncontrib = nc;
     *neval = ne;
     *amb = a;
+    if (n_enum) *n_enum = ne_k;
 }
 
 /* Render colour [3,H,W], depth [H,W], alpha = 1 - T_final [H,W], T_final,
  * last_idx (position in the tile list of the last composited entry, -1 if
  * none), n_contrib, pixel ambiguity flags, and the evaluation count E
- * (list entries visited over all pixels).  Any output may be NULL. */
+ * (list entries visited over all pixels).  Any output may be NULL.  flips
+ * [H,W] (NULL = none) selects, per pixel, the branches of its marginal skip
+ * / stop decisions (as orc_render_alternatives). */
 int orc_render(int64_t n, const double *mean, const double *log_scale, const double *quat,
                const double *logit, const double *rgb, const double *pose_q, const double *pose_t,
                const orc_camera *cam, double *out_rgb, double *out_depth, double *out_alpha,
                double *out_T, int32_t *out_last, int32_t *out_ncontrib, int32_t *out_amb,
-               int64_t *out_neval)
+               int64_t *out_neval, const uint32_t *flips)
 {
     oproj *P = project_all(n, mean, log_scale, quat, logit, pose_q, pose_t, cam);
     olists L;
     build_lists(n, P, cam, &L);
-    unsigned char *tamb = ambiguous_tiles(n, P, cam);
+    oamb A;
+    ambiguous_tiles(n, P, cam, &A);
     int W = cam->width, H = cam->height;
     int tiles_x = (W + cam->tile_w - 1) / cam->tile_w;
     int64_t HW = (int64_t)W * H, etotal = 0;
@@ -479,7 +584,7 @@ int orc_render(int64_t n, const double *mean, const double *log_scale, const dou
             int64_t ne;
             int a;
             blend_pixel(cam, P, rgb, L.gid + L.start[t], L.start[t + 1] - L.start[t], ix, iy, C, &D, &T,
-                        &last, &nc, &ne, &a, NULL);
+                        &last, &nc, &ne, &a, NULL, flips ? flips[(int64_t)iy * W + ix] : 0u, NULL);
             int64_t p = (int64_t)iy * W + ix;
             if (out_rgb) for (int ch = 0; ch < 3; ++ch) out_rgb[ch * HW + p] = C[ch];
             if (out_depth) out_depth[p] = D;
@@ -487,12 +592,66 @@ int orc_render(int64_t n, const double *mean, const double *log_scale, const dou
             if (out_T) out_T[p] = T;
             if (out_last) out_last[p] = last;
             if (out_ncontrib) out_ncontrib[p] = nc;
-            if (out_amb) out_amb[p] = a | (tamb[t] ? 1 : 0);
+            if (out_amb) out_amb[p] = a | (tile_pixel_ambiguous(&A, P, t, ix, iy) ? 1 | 8 : 0);
             etotal += ne;
         }
     }
     if (out_neval) *out_neval = etotal;
-    free(tamb);
+    free_amb(&A);
+    free_lists(&L);
+    free(P);
+    return 0;
+}
+
+/* Every result a float32 implementation may produce at the given pixels:
+ * per pixel, the walks that take either branch of each marginal skip / stop
+ * decision (bit k of a flip mask = the k-th such decision met, as
+ * blend_pixel), up to 2^max_bits of them and at most kmax.  Outputs, [npix,
+ * kmax] (colour [npix, kmax, 3]): colour, depth, final T, the Gaussian index
+ * of the last composited entry (-1 if none), n_contrib and the flip mask of
+ * each alternative; count [npix] the number of alternatives (1 where no
+ * decision is marginal); amb [npix] the pixel's ambiguity flags. */
+int orc_render_alternatives(int64_t n, const double *mean, const double *log_scale, const double *quat,
+                            const double *logit, const double *rgb, const double *pose_q, const double *pose_t,
+                            const orc_camera *cam, const int64_t *pix, int64_t npix, int max_bits, int kmax,
+                            double *out_rgb, double *out_depth, double *out_T, int32_t *out_lastgid,
+                            int32_t *out_nc, uint32_t *out_flip, int32_t *out_count, int32_t *out_amb)
+{
+    oproj *P = project_all(n, mean, log_scale, quat, logit, pose_q, pose_t, cam);
+    olists L;
+    build_lists(n, P, cam, &L);
+    oamb A;
+    ambiguous_tiles(n, P, cam, &A);
+    int W = cam->width;
+    int tiles_x = (W + cam->tile_w - 1) / cam->tile_w;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < npix; ++i) {
+        int ix = (int)(pix[i] % W), iy = (int)(pix[i] / W);
+        int64_t t = (int64_t)(iy / cam->tile_h) * tiles_x + ix / cam->tile_w;
+        const int32_t *list = L.gid + L.start[t];
+        int64_t len = L.start[t + 1] - L.start[t];
+        double C[3], D, T;
+        int32_t last, nc;
+        int64_t ne;
+        int a, nen = 0;
+        blend_pixel(cam, P, rgb, list, len, ix, iy, C, &D, &T, &last, &nc, &ne, &a, NULL, 0u, &nen);
+        out_amb[i] = a | (tile_pixel_ambiguous(&A, P, t, ix, iy) ? 1 | 8 : 0);
+        int bits = nen < max_bits ? nen : max_bits;
+        int cnt = 1 << bits;
+        if (cnt > kmax) cnt = kmax;
+        for (int m = 0; m < cnt; ++m) {
+            if (m > 0) blend_pixel(cam, P, rgb, list, len, ix, iy, C, &D, &T, &last, &nc, &ne, &a, NULL, (unsigned)m, NULL);
+            int64_t o = i * kmax + m;
+            for (int ch = 0; ch < 3; ++ch) out_rgb[3 * o + ch] = C[ch];
+            out_depth[o] = D;
+            out_T[o] = T;
+            out_lastgid[o] = last >= 0 ? list[last] : -1;
+            out_nc[o] = nc;
+            out_flip[o] = (uint32_t)m;
+        }
+        out_count[i] = cnt;
+    }
+    free_amb(&A);
     free_lists(&L);
     free(P);
     return 0;
@@ -610,7 +769,8 @@ static void project_backward_one(const orc_camera *cam, const double Rcw[9], con
 }
 
 /* Backward of the renderer.  Inputs dL/dC [3,H,W], dL/dD [H,W], dL/dA [H,W]
- * (any may be NULL = zero).  Outputs (NULL = not wanted): per-Gaussian
+ * (any may be NULL = zero); flips [H,W] (NULL = none) selects, per pixel,
+ * the branches of its marginal decisions (as orc_render_alternatives).  Outputs (NULL = not wanted): per-Gaussian
  * gradients of mean [n,3], log_scale [n,3], quat [n,4], opacity logit [n],
  * rgb [n,3], pose [6] (rho, phi), and the image-space gradients g2 [n,10]. */
 int orc_render_backward(int64_t n, const double *mean, const double *log_scale, const double *quat,
@@ -618,7 +778,7 @@ int orc_render_backward(int64_t n, const double *mean, const double *log_scale, 
                         const double *pose_t, const orc_camera *cam, const double *dL_drgb,
                         const double *dL_ddepth, const double *dL_dalpha, double *g_mean,
                         double *g_log_scale, double *g_quat, double *g_logit, double *g_rgb,
-                        double *g_pose, double *g2d_out)
+                        double *g_pose, double *g2d_out, const uint32_t *flips)
 {
     oproj *P = project_all(n, mean, log_scale, quat, logit, pose_q, pose_t, cam);
     olists L;
@@ -644,7 +804,7 @@ int orc_render_backward(int64_t n, const double *mean, const double *log_scale, 
                 int64_t ne;
                 int a;
                 blend_pixel(cam, P, rgb, L.gid + L.start[t], L.start[t + 1] - L.start[t], ix, iy, C, &D,
-                            &Tf, &last, &nc, &ne, &a, tr);
+                            &Tf, &last, &nc, &ne, &a, tr, flips ? flips[p] : 0u, NULL);
                 double dC[3], dD, dA;
                 for (int ch = 0; ch < 3; ++ch) dC[ch] = dL_drgb ? dL_drgb[ch * HW + p] : 0.0;
                 dD = dL_ddepth ? dL_ddepth[p] : 0.0;
@@ -1014,6 +1174,15 @@ void orc_se3_left_jacobian(const double *xi, double *J)
             J[6 * (r + 3) + (c + 3)] = V;
             J[6 * r + (c + 3)] = Q;
         }
+}
+
+/* The float32 error model behind the ambiguity flags, for the tests that
+ * check an implementation against it: U32, ERR_DF, ERR_RATIO, ERR_ROUND,
+ * ERR_CONIC, ERR_OPAC, ERR_SIGMA, ERR_EXP (in that order). */
+void orc_error_model(double *c)
+{
+    c[0] = U32; c[1] = ERR_DF; c[2] = ERR_RATIO; c[3] = ERR_ROUND;
+    c[4] = ERR_CONIC; c[5] = ERR_OPAC; c[6] = ERR_SIGMA; c[7] = ERR_EXP;
 }
 
 /* number of OpenMP threads the oracle uses (1 without OpenMP) */

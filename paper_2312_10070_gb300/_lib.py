@@ -138,6 +138,8 @@ PROTOTYPES = {
                                        c_vp, ctypes.POINTER(RenderOut), c_vp, c_vp, c_vp,
                                        ctypes.POINTER(GaussianGrads), c_vp, c_vp]),
     "gsr_pose_retract": (c_i32, [ctypes.POINTER(Pose), c_vp, c_vp, c_vp]),
+    "gsr_records_get": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp]),
+    "gsr_probe_expf": (c_i32, [c_vp, c_vp, c_i64, c_vp]),
     "gsr_loss_map": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_f, c_f, c_f, c_f, c_vp, c_vp, c_vp,
                              c_vp]),
     "gsr_loss_track": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_f, c_f, c_f, c_vp, c_vp,

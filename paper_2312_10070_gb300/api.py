@@ -204,6 +204,16 @@ def tile_lists(ctx: Context, n_tiles: int, n_gaussians: int, capacity: int = Non
     return ranges, gids[:ni.value], dbits[:n_gaussians]
 
 
+def records(ctx: Context, n: int):
+    """gsr_records_get: (rec float32 [n, 12], visible bool [n]) of the last
+    forward: u, v, conic (a, b, c), opacity, depth, ... per Gaussian."""
+    rec = np.zeros((max(n, 1), 12), np.float32)
+    vis = np.zeros(max(n, 1), np.uint32)
+    ctx.check(ctx.lib.gsr_records_get(ctx.handle, rec.ctypes.data_as(ctypes.c_void_p),
+                                      vis.ctypes.data_as(ctypes.c_void_p), int(n), _stream()))
+    return rec[:n], vis[:n].astype(bool)
+
+
 def render_backward(ctx: Context, g: GaussianParams, cam: L.Camera, pose: L.Pose, saved: dict, d_rgb=None,
                     d_depth=None, d_alpha=None, want_params=True, want_pose=True, out: GaussianParams = None,
                     xi: torch.Tensor = None):

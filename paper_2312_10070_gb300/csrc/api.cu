@@ -410,6 +410,19 @@ extern "C" gsr_status gsr_tile_lists_get(gsr_ctx *ctx, uint32_t *ranges, int32_t
                            (cudaStream_t)stream);
 }
 
+extern "C" gsr_status gsr_records_get(gsr_ctx *ctx, float *rec, uint32_t *visible, int64_t n, void *stream)
+{
+    if (!ctx || !rec || !visible || n < 0) return GSR_ERR_INVALID_ARG;
+    if (ctx->fwd_n < 0) return gsr_fail(ctx, GSR_ERR_STATE, "no forward on this context");
+    if (n != ctx->fwd_n) return gsr_fail(ctx, GSR_ERR_INVALID_ARG, "n differs from the last forward's count");
+    if (n == 0) return GSR_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    GSR_CUDA(ctx, cudaMemcpyAsync(rec, ctx->view.rec.p, sizeof(float) * 12 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    GSR_CUDA(ctx, cudaMemcpyAsync(visible, ctx->view.flag.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    GSR_CUDA(ctx, cudaStreamSynchronize(s));
+    return GSR_OK;
+}
+
 static gsr_status render_backward(gsr_ctx *ctx, const gsr_gaussians *g, const gsr_camera *cam,
                                   const gsr_pose *pose, const float *xi, const gsr_render_out *saved,
                                   const float *d_rgb, const float *d_depth, const float *d_alpha,

@@ -51,6 +51,14 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_exp(float *out, int ite
     out[(int64_t)blockIdx.x * PROBE_THREADS + threadIdx.x] = s;
 }
 
+// y = __expf(x): the exponential the blend kernels evaluate alpha with, for a
+// test that checks its error against the bound the parity margins assume
+__global__ void k_probe_expf(const float *__restrict__ x, float *__restrict__ y, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __expf(x[i]);
+}
+
 gsr_status probe_args(float *out, int32_t blocks, int32_t iters)
 {
     if (!out || blocks <= 0 || iters <= 0 || iters % PROBE_UNROLL) return GSR_ERR_INVALID_ARG;
@@ -74,6 +82,13 @@ GSR_API gsr_status gsr_probe_exp(float *out, int32_t blocks, int32_t iters, void
     const gsr_status st = probe_args(out, blocks, iters);
     if (st != GSR_OK) return st;
     k_probe_exp<<<(unsigned)blocks, PROBE_THREADS, 0, (cudaStream_t)stream>>>(out, iters);
+    return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
+}
+
+GSR_API gsr_status gsr_probe_expf(const float *x, float *y, int64_t n, void *stream)
+{
+    if (!x || !y || n <= 0) return GSR_ERR_INVALID_ARG;
+    k_probe_expf<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n);
     return cudaGetLastError() == cudaSuccess ? GSR_OK : GSR_ERR_CUDA;
 }
 

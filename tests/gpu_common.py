@@ -5,6 +5,8 @@ import numpy as np
 import oracle as O
 from paper_2312_10070_gb300 import synth as S
 
+TOL_IMAGE = 2e-4  # max-abs bar of RGB, depth, alpha and final T against the FP64 oracle
+
 
 def ocam(spec, tile=(16, 16), **kw):
     return O.Camera(spec.width, spec.height, spec.fx, spec.fy, spec.cx, spec.cy, tile_w=tile[0], tile_h=tile[1],
@@ -108,3 +110,63 @@ def box_min_sigma(u, v, ca, cb, cc, x0, x1, y0, y1):
     inside = (X0 <= 0) & (X1 >= 0) & (Y0 <= 0) & (Y1 >= 0)
     return np.where(inside, 0.0, m)
 
+
+
+def check_forward(ctx, out, sc64, q, t, oc, max_excluded=0.0, tol=TOL_IMAGE, label=""):
+    """Forward parity of one render on context `ctx` (outputs `out` as numpy,
+    with n_contrib) against the oracle at camera `oc` (same tile shape).
+
+    Pixels where no decision is marginal must match the oracle's render:
+    RGB, depth, alpha and final T within `tol`, n_contrib and the Gaussian
+    of the last composited entry bit-exact (the GPU's last_idx is mapped to
+    a Gaussian through its own tile lists, which may be culled).  At a pixel
+    with marginal skip / stop decisions every branch is a valid float32
+    result: the GPU's output must match one of the oracle's alternatives
+    (render_alternatives) to the same bar.  Pixels with another kind of
+    marginal decision (sigma sign, depth order, tile membership) are
+    excluded; their fraction must not exceed `max_excluded`.  Returns
+    (flips [H,W] uint32: the branches the GPU's output took, for the oracle's
+    backward; excluded [H,W] bool; the oracle's render)."""
+    from paper_2312_10070_gb300 import api
+    ref = O.render(sc64, q, t, oc)
+    H, W = oc.height, oc.width
+    tx, ty = oc.tiles
+    tile = (oc.tile_w, oc.tile_h)
+    ranges, gids, _ = api.tile_lists(ctx, tx * ty, sc64.n)
+    bins = O.bin_tiles(sc64, q, t, oc)
+    g_gpu = last_gids(out["last_idx"], ranges[:, 0], gids, tile, W)
+    g_ref = last_gids(ref["last_idx"], bins["start"][:-1], bins["gid"], tile, W)
+    ok = ref["amb"] == 0
+    for k in ("depth", "alpha", "final_T"):
+        err = np.abs(out[k][ok] - ref[k][ok]).max() if ok.any() else 0.0
+        assert err <= tol, (label, k, err)
+    err = np.abs(out["rgb"][:, ok] - ref["rgb"][:, ok]).max() if ok.any() else 0.0
+    assert err <= tol, (label, "rgb", err)
+    assert np.array_equal(out["n_contrib"][ok], ref["n_contrib"][ok]), label
+    assert np.array_equal(g_gpu[ok], g_ref[ok]), label
+    flips = np.zeros(H * W, np.uint32)
+    excluded = np.zeros(H * W, bool)
+    fl = np.nonzero(~ok.ravel())[0]
+    alt = O.render_alternatives(sc64, q, t, oc, fl)
+    o_rgb = out["rgb"].reshape(3, -1)
+    o_d, o_T, o_nc, o_g = out["depth"].ravel(), out["final_T"].ravel(), out["n_contrib"].ravel(), g_gpu.ravel()
+    unmatched = []
+    for i, p in enumerate(fl):
+        if alt["amb"][i] & 8:
+            excluded[p] = True
+            continue
+        c = alt["count"][i]
+        good = ((alt["n_contrib"][i, :c] == o_nc[p]) & (alt["last_gid"][i, :c] == o_g[p])
+                & (np.abs(alt["rgb"][i, :c] - o_rgb[:, p]).max(-1) <= tol)
+                & (np.abs(alt["depth"][i, :c] - o_d[p]) <= tol) & (np.abs(alt["final_T"][i, :c] - o_T[p]) <= tol))
+        k = np.nonzero(good)[0]
+        if k.size == 0:
+            unmatched.append(int(p))
+            continue
+        flips[p] = alt["flip"][i, k[0]]
+    print(f"forward parity {label}: {H * W} pixels, {fl.size} with marginal decisions "
+          f"({fl.size / (H * W):.4%}), matched to an alternative {fl.size - excluded.sum() - len(unmatched)}, "
+          f"excluded {excluded.sum()} ({excluded.mean():.5%}), unmatched {len(unmatched)}")
+    assert not unmatched, (label, unmatched[:10])
+    assert excluded.mean() <= max_excluded, (label, excluded.mean())
+    return flips.reshape(H, W), excluded.reshape(H, W), ref

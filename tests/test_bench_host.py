@@ -18,8 +18,11 @@ def tuned(tile, batch, ppt):
     return dict(tile=tile, batch=batch, ppt_fwd=ppt, ppt_bwd=ppt)
 
 
-def test_traffic_lookup_prefers_the_captured_configuration():
+def test_traffic_lookup_prefers_the_captured_configuration(monkeypatch):
     entries = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["blend_bwd"]
+    # the lookup logic, with the sources as they were at capture time
+    shas = {tuple(e["sources"]): e["sources_sha256"] for e in entries}
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda files: shas.get(tuple(files), "0" * 64))
     by_cfg = {(e["config"]["batch"], e["config"]["ppt"]): e["dram_bytes_per_launch"] for e in entries}
     for (batch, ppt), b in by_cfg.items():
         got, cfg = bench.measured_traffic("blend_bwd", tuned((8, 8), batch, ppt))

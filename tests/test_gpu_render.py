@@ -4,10 +4,14 @@ FP64 oracle on the same seeded inputs.
 Bars: tile keys / per-tile lists and per-pixel contributor counts bit-exact;
 RGB / depth / alpha within max-abs 2e-4; gradients within 1e-3 relative,
 |g - g_ref| <= 1e-3 |g_ref| + 1e-4 max|g_ref| elementwise and a per-tensor
-relative L2 error <= 1e-4.  Pixels and Gaussians whose
-discrete decisions the oracle flags as within its margin of a threshold
-(FP32 vs FP64 may legitimately decide them differently) are excluded; their
-count is asserted small.
+relative L2 error <= 1e-4 (the count of entries within the stricter
+1e-3 (|g| + 1e-3 rms) is printed).  Where the oracle finds a skip or stop
+decision within the float32 error bound of its threshold, each branch is a
+valid result: the GPU's pixel must equal one of the oracle's alternatives,
+and the oracle's backward then takes the same branch.  Pixels with another
+kind of marginal decision are excluded (none on the unit scenes, at most
+0.1 % on the 1200x680 view); Gaussians with a marginal projection decision
+are left out of the tile-list comparison.
 """
 import numpy as np
 import pytest
@@ -16,7 +20,8 @@ torch = pytest.importorskip("torch")
 
 import oracle as O
 from paper_2312_10070_gb300 import api, synth as S
-from tests.gpu_common import box_min_sigma, grad_close, last_gids, ocam, tile_sequences_match, unit_inputs
+from tests.gpu_common import (box_min_sigma, check_forward, grad_close, last_gids, ocam, strict_pass_fraction,
+                              tile_sequences_match, unit_inputs)
 
 pytestmark = pytest.mark.gpu
 
@@ -37,38 +42,23 @@ def run_forward(ctx, sc, spec, q, t, tile=(16, 16)):
     return g, cam, pose, {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}, out
 
 
-def check_forward(out, ref, max_amb=0.08, lists=None):
-    """lists = (ctx, scene64, q, t, oracle camera): the context's tile lists
-    are culled, so last_idx (a position in the list in use) is compared as the
-    Gaussian it names, against the oracle's rectangle lists."""
-    ok = ref["amb"] == 0
-    assert ok.mean() >= 1 - max_amb, ok.mean()
-    for k in ("depth", "alpha", "final_T"):
-        err = np.abs(out[k][ok] - ref[k][ok]).max()
-        assert err <= 2e-4, (k, err)
-    err = np.abs(out["rgb"][:, ok] - ref["rgb"][:, ok]).max()
-    assert err <= 2e-4, ("rgb", err)
-    assert np.array_equal(out["n_contrib"][ok], ref["n_contrib"][ok])
-    if lists is None:
-        assert np.array_equal(out["last_idx"][ok], ref["last_idx"][ok])
-        return
-    c, sc64, q, t, oc = lists
-    tx, ty = oc.tiles
-    ranges, gids, _ = api.tile_lists(c, tx * ty, sc64.n)
-    bins = O.bin_tiles(sc64, q, t, oc)
-    tile = (oc.tile_w, oc.tile_h)
-    g_gpu = last_gids(out["last_idx"], ranges[:, 0], gids, tile, oc.width)
-    g_ref = last_gids(ref["last_idx"], bins["start"][:-1], bins["gid"], tile, oc.width)
-    assert np.array_equal(g_gpu[ok], g_ref[ok])
+def grads_match(grads, pose6, ref, label=""):
+    for k in api.GaussianParams.NAMES:
+        g = getattr(grads, k).cpu().numpy()
+        ok, worst = grad_close(g, ref[k])
+        print(f"{label} {k}: worst ratio {worst:.3f}, strict-floor pass {strict_pass_fraction(g, ref[k]):.5f}")
+        assert ok, (label, k, worst)
+    if pose6 is not None:
+        ok, worst = grad_close(pose6.cpu().numpy(), ref["pose"])
+        print(f"{label} pose: worst ratio {worst:.3f}")
+        assert ok, (label, "pose", worst)
 
 
 @pytest.mark.parametrize("seed,pose_seed", [(1, 2), (7, 8)])
 def test_forward_unit_matches_oracle(ctx, seed, pose_seed):
     sc, spec, q, t = unit_inputs(seed, pose_seed)
     _, _, _, out, _ = run_forward(ctx, sc, spec, q, t)
-    sc64 = O.Scene.from_dict(sc)
-    ref = O.render(sc64, q, t, ocam(spec))
-    check_forward(out, ref, lists=(ctx, sc64, q, t, ocam(spec)))
+    check_forward(ctx, out, O.Scene.from_dict(sc), q, t, ocam(spec), label=f"unit {seed}")
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8), (32, 8)])
@@ -84,6 +74,7 @@ def test_tile_lists_bit_exact(tile):
     ref = O.bin_tiles(sc64, q, t, oc)
     pr = O.project(sc64, q, t, oc)
     skip = (pr["amb"] & 1).astype(bool)
+    print("Gaussians with a marginal projection decision:", skip.sum(), "depth near-ties:", ref["near_tie"].sum())
     assert skip.sum() <= 10
     assert tile_sequences_match(ranges, gids, ref["start"], ref["gid"], ref["near_tie"], skip) == 0
     # culling decisions and depth keys
@@ -91,49 +82,45 @@ def test_tile_lists_bit_exact(tile):
     assert np.array_equal(vis[~skip], pr["visible"][~skip].astype(bool))
     f32 = pr["depth"].astype(np.float32).view(np.uint32).astype(np.int64)
     ulp = np.abs(dbits.astype(np.int64) - f32)[vis & ~skip]
-    assert ulp.max() <= 1, ulp.max()  # faithfully rounded camera depth
+    assert ulp.max() == 0, ulp.max()  # the depth keys are the correctly rounded camera depths
     # forward outputs at this tile size
-    check_forward(out, O.render(sc64, q, t, oc))
+    check_forward(c, out, sc64, q, t, oc, label=f"rect lists {tile}")
     c.close()
 
 
 def test_backward_unit_matches_oracle(ctx):
+    """dL/dpixel is nonzero at every pixel: at pixels with marginal decisions
+    the oracle's backward takes the branches the GPU's forward took."""
     sc, spec, q, t = unit_inputs(1, 2)
     g, cam, pose, out, saved = run_forward(ctx, sc, spec, q, t)
     sc64 = O.Scene.from_dict(sc)
-    ref_f = O.render(sc64, q, t, ocam(spec))
+    flips, excl, _ = check_forward(ctx, out, sc64, q, t, ocam(spec), label="unit backward")
     rng = np.random.default_rng(5)
     H, W = spec.height, spec.width
     w = [rng.standard_normal((3, H, W)), rng.standard_normal((H, W)), rng.standard_normal((H, W))]
-    amb = ref_f["amb"] != 0
     for a in w:
-        a[..., amb] = 0.0
+        a[..., excl] = 0.0
     w = [a.astype(np.float32) for a in w]
     grads, pose6 = api.render_backward(ctx, g, cam, pose, saved, *[torch.from_numpy(a).cuda() for a in w])
     torch.cuda.synchronize()
-    ref = O.render_backward(sc64, q, t, ocam(spec), *w)
-    for k in api.GaussianParams.NAMES:
-        ok, worst = grad_close(getattr(grads, k).cpu().numpy(), ref[k])
-        assert ok, (k, worst)
-    ok, worst = grad_close(pose6.cpu().numpy(), ref["pose"])
-    assert ok, ("pose", worst)
+    ref = O.render_backward(sc64, q, t, ocam(spec), *w, flips=flips)
+    grads_match(grads, pose6, ref, "unit backward")
 
 
 def test_pose_only_backward(ctx):
     sc, spec, q, t = unit_inputs(11, 12)
     g, cam, pose, out, saved = run_forward(ctx, sc, spec, q, t)
     sc64 = O.Scene.from_dict(sc)
-    ref_f = O.render(sc64, q, t, ocam(spec))
+    flips, excl, _ = check_forward(ctx, out, sc64, q, t, ocam(spec), label="pose-only")
     rng = np.random.default_rng(6)
     H, W = spec.height, spec.width
     d_rgb, d_dep = rng.standard_normal((3, H, W)), rng.standard_normal((H, W))
-    amb = ref_f["amb"] != 0
-    d_rgb[:, amb] = 0
-    d_dep[amb] = 0
+    d_rgb[:, excl] = 0
+    d_dep[excl] = 0
     d_rgb, d_dep = d_rgb.astype(np.float32), d_dep.astype(np.float32)
     _, pose6 = api.render_backward(ctx, g, cam, pose, saved, torch.from_numpy(d_rgb).cuda(),
                                    torch.from_numpy(d_dep).cuda(), None, want_params=False)
-    ref = O.render_backward(sc64, q, t, ocam(spec), d_rgb, d_dep, None)
+    ref = O.render_backward(sc64, q, t, ocam(spec), d_rgb, d_dep, None, flips=flips)
     ok, worst = grad_close(pose6.cpu().numpy(), ref["pose"])
     assert ok, worst
 
@@ -161,8 +148,7 @@ def test_edge_cases(ctx):
     sc = S.random_scene(400, 4, box=((-0.6, 0.6), (-0.45, 0.45), (1, 3)), log_scale=(-3.0, 0.4))
     _, _, _, out, _ = run_forward(ctx, sc, spec, *S.IDENTITY_POSE)
     sc64 = O.Scene.from_dict(sc)
-    check_forward(out, O.render(sc64, *S.IDENTITY_POSE, ocam(spec)),
-                  lists=(ctx, sc64, *S.IDENTITY_POSE, ocam(spec)))
+    check_forward(ctx, out, sc64, *S.IDENTITY_POSE, ocam(spec), label="ragged")
 
 
 def test_memory_saving_mode_is_bit_identical():
@@ -197,25 +183,22 @@ def test_full_size_room_view_matches_oracle(tile, batch, ppt):
     q, t = S.submap_views()[S.HEADLINE_VIEW]
     g, cam, pose, out, saved = run_forward(ctx, sc, spec, q, t)
     sc64 = O.Scene.from_dict(sc)
-    ref = O.render(sc64, q, t, ocam(spec, tile))
-    check_forward(out, ref, max_amb=0.1, lists=(ctx, sc64, q, t, ocam(spec, tile)))
+    flips, excl, ref = check_forward(ctx, out, sc64, q, t, ocam(spec, tile), max_excluded=1e-3,
+                                     label=f"1200x680 {tile} {batch} {ppt}")
     st = api.frame_stats(ctx)
     pr = O.project(sc64, q, t, ocam(spec))
     assert abs(st["n_visible"] - pr["visible"].sum()) <= (pr["amb"] & 1).sum()
-    # backward on sampled outputs: dL/dpixel nonzero on a random 2% of unambiguous pixels
+    # backward on sampled outputs: dL/dpixel nonzero on a random 2% of the
+    # pixels (those with marginal decisions included, at the GPU's branches)
     rng = np.random.default_rng(9)
     H, W = spec.height, spec.width
-    mask = (rng.random((H, W)) < 0.02) & (ref["amb"] == 0)
+    mask = (rng.random((H, W)) < 0.02) & ~excl
     d_rgb = (rng.standard_normal((3, H, W)) * mask).astype(np.float32)
     d_dep = (rng.standard_normal((H, W)) * mask).astype(np.float32)
     grads, pose6 = api.render_backward(ctx, g, cam, pose, saved, torch.from_numpy(d_rgb).cuda(),
                                        torch.from_numpy(d_dep).cuda(), None)
-    refb = O.render_backward(sc64, q, t, ocam(spec, tile), d_rgb, d_dep, None)
-    for k in api.GaussianParams.NAMES:
-        ok, worst = grad_close(getattr(grads, k).cpu().numpy(), refb[k])
-        assert ok, (k, worst)
-    ok, worst = grad_close(pose6.cpu().numpy(), refb["pose"])
-    assert ok, ("pose", worst)
+    refb = O.render_backward(sc64, q, t, ocam(spec, tile), d_rgb, d_dep, None, flips=flips)
+    grads_match(grads, pose6, refb, f"1200x680 {tile}")
     ctx.close()
 
 

@@ -8,7 +8,7 @@ torch = pytest.importorskip("torch")
 import oracle as O
 from paper_2312_10070_gb300 import api, synth as S
 from paper_2312_10070_gb300.autograd import render
-from tests.gpu_common import grad_close, ocam, strict_pass_fraction, unit_inputs
+from tests.gpu_common import check_forward, grad_close, ocam, strict_pass_fraction, unit_inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -37,17 +37,21 @@ def test_autograd_function_matches_oracle(xi0):
                             np.float32(xi0).astype(np.float64))
     qx, tx = np.float32(qx).astype(np.float64), np.float32(tx).astype(np.float64)
     sc64 = O.Scene.from_dict(sc)
-    ref_f = O.render(sc64, qx, tx, ocam(spec))
-    ok = ref_f["amb"] == 0
-    assert np.abs(rgb.detach().cpu().numpy()[:, ok] - ref_f["rgb"][:, ok]).max() <= 2e-4
-    amb = torch.from_numpy(~ok).cuda()
+    # the same render with contributor counts, for the forward parity and the
+    # branches of marginal decisions the oracle's backward must take
+    chk = api.render_forward(ctx, api.GaussianParams(*[x.detach() for x in g.tensors()]), cam, api.make_pose(q, t),
+                             want_n_contrib=True, xi=xi.detach())
+    chk = {k: (v.cpu().numpy() if v is not None else None) for k, v in chk.items()}
+    assert np.array_equal(chk["rgb"], rgb.detach().cpu().numpy())
+    flips, excl, _ = check_forward(ctx, chk, sc64, qx, tx, ocam(spec), label=f"autograd xi={xi0}")
     rng = np.random.default_rng(1)
     w = [cu(rng.standard_normal(s)) for s in ((3, 120, 160), (120, 160), (120, 160))]
+    ex = torch.from_numpy(excl).cuda()
     for a in w:
-        a[..., amb] = 0
+        a[..., ex] = 0
     loss = (w[0] * rgb).sum() + (w[1] * depth).sum() + (w[2] * alpha).sum()
     loss.backward()
-    ref = O.render_backward(sc64, qx, tx, ocam(spec), *[a.cpu().numpy() for a in w])
+    ref = O.render_backward(sc64, qx, tx, ocam(spec), *[a.cpu().numpy() for a in w], flips=flips)
     for k in api.GaussianParams.NAMES:
         ok_, worst = grad_close(getattr(g, k).grad.cpu().numpy(), ref[k])
         assert ok_, (k, worst)
@@ -268,8 +272,6 @@ def test_autotune_picks_a_config_that_keeps_parity():
     assert best["tile"] in [(16, 16), (8, 8), (16, 8), (32, 8)] and best["batch"] in (32, 64, 128, 256)
     out = api.render_forward(ctx, g, cam, api.make_pose(q, t), want_n_contrib=True)
     torch.cuda.synchronize()
-    ref = O.render(O.Scene.from_dict(sc), q, t, ocam(spec, best["tile"]))
-    ok = ref["amb"] == 0
-    assert np.abs(out["rgb"].cpu().numpy()[:, ok] - ref["rgb"][:, ok]).max() <= 2e-4
-    assert np.array_equal(out["n_contrib"].cpu().numpy()[ok], ref["n_contrib"][ok])
+    out = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+    check_forward(ctx, out, O.Scene.from_dict(sc), q, t, ocam(spec, best["tile"]), label=f"autotuned {best}")
     ctx.close()

@@ -39,7 +39,7 @@ MUTATIONS = [
      "double a = JS[0] * J[0] + JS[1] * J[1] + JS[2] * J[2];"),
     ("pixel centre at the corner", "double px = ix + 0.5, py = iy + 0.5;", "double px = ix, py = iy;"),
     ("alpha cap 0.999", "#define ALPHA_MAX 0.99", "#define ALPHA_MAX 0.999"),
-    ("transmittance stop after compositing", "if (Tn < T_STOP) break;", "if (T < T_STOP) break;"),
+    ("transmittance stop after compositing", "int stop = Tn < T_STOP;", "int stop = T < T_STOP;"),
     ("blend adjoint: suffix sum not divided by 1 - alpha",
      "for (int ch = 0; ch < 3; ++ch) dLda += dC[ch] * (cj[ch] * e->T - Sc[ch] / om);",
      "for (int ch = 0; ch < 3; ++ch) dLda += dC[ch] * (cj[ch] * e->T - Sc[ch]);"),
@@ -92,6 +92,10 @@ MUTATIONS = [
     ("near plane at the camera centre",
      ("if (pz <= c->z_near && !z_amb) return;", "if (empty || pz <= c->z_near) return;"),
      ("if (pz <= 0.0 && !z_amb) return;", "if (empty || pz <= 0.0) return;")),
+    ("SE(3) left Jacobian: sign of the second coupling coefficient",
+     "c2 = (t2 + 2 * cos(th) - 2) / (2 * t2 * t2);", "c2 = -(t2 + 2 * cos(th) - 2) / (2 * t2 * t2);"),
+    ("SE(3) left Jacobian: coupling block transposed", "J[6 * r + (c + 3)] = Q;",
+     "J[6 * c + (r + 3)] = Q;"),
     ("guard band: gradient through the clamped coordinate",
      "if (!o->clamp_x) { gp[0] += gtx / pz; gp[2] += -gtx * px / (pz * pz); }",
      "{ gp[0] += gtx / pz; gp[2] += -gtx * px / (pz * pz); }"),

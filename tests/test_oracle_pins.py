@@ -612,3 +612,63 @@ def test_twist_gradient_at_nonzero_twist_matches_central_fd():
         assert abs(an[k] - fd) <= 1e-6 * (abs(fd) + 1.0), (k, an[k], fd)
     # the factor matters at this twist: the bare left gradient is off by more than the bar
     assert np.abs(g["pose"] - an).max() > 1e-3 * (np.abs(an).max() + 1.0)
+
+
+def test_marginal_decision_alternatives_take_the_other_branch():
+    """A skip decision (alpha within its error bound of 1/255) and a stop
+    decision (T (1 - alpha) within its bound of 1e-4) each yield two results:
+    the oracle's own branch, and the other branch, which equals the render
+    of the scene without that Gaussian (skip) or the render where it is
+    composited (stop).  The flip masks of render_alternatives reproduce
+    render(flips=...) and the backward takes the same branches."""
+    cam = O.Camera(16, 16, 40.0, 40.0, 8.0, 8.0, tile_w=16, tile_h=16, eps2d=0.0)
+    # skip decision at pixel (8, 8) (centre (8.5, 8.5)): a Gaussian centred
+    # 0.3 px off it (sigma clearly positive) whose alpha there is 1/255 (1 + 1e-9)
+    sc = one_gaussian_scene([[0.04, 0.025, 2.0], [0.05, 0.045, 3.0]], [0.05, 0.05], [0.5, 0.5],
+                            [[1, 0, 0], [0, 1, 0]])
+    pr = O.project(sc, ID_Q, ID_T, cam)
+    dx, dy = 8.5 - pr["uv"][0, 0], 8.5 - pr["uv"][0, 1]
+    a_, b_, c_ = pr["conic"][0]
+    sig = 0.5 * (a_ * dx * dx + c_ * dy * dy) + b_ * dx * dy
+    assert sig > 0.01
+    o = O.ALPHA_MIN * (1 + 1e-9) * np.exp(sig)
+    sc.opacity_logit[0] = logit(o)
+    pix = np.array([8 * 16 + 8])
+    r = O.render(sc, ID_Q, ID_T, cam)
+    assert r["amb"][8, 8] & 1 and not r["amb"][8, 8] & 8 and r["n_contrib"][8, 8] == 2
+    alt = O.render_alternatives(sc, ID_Q, ID_T, cam, pix)
+    assert alt["count"][0] == 2
+    without = O.Scene(sc.mean[1:], sc.log_scale[1:], sc.quat[1:], sc.opacity_logit[1:], sc.rgb[1:])
+    r1 = O.render(without, ID_Q, ID_T, cam)
+    assert alt["n_contrib"][0, 1] == 1 and alt["last_gid"][0, 1] == 1
+    np.testing.assert_array_equal(alt["rgb"][0, 1], r1["rgb"][:, 8, 8])
+    assert alt["depth"][0, 1] == r1["depth"][8, 8]
+    fl = np.zeros((16, 16), np.uint32)
+    fl[8, 8] = alt["flip"][0, 1]
+    rf = O.render(sc, ID_Q, ID_T, cam, flips=fl)
+    np.testing.assert_array_equal(rf["rgb"][:, 8, 8], r1["rgb"][:, 8, 8])
+    # the backward with the flip gives the first Gaussian no gradient from that pixel
+    w = np.zeros((3, 16, 16))
+    w[:, 8, 8] = 1.0
+    gb = O.render_backward(sc, ID_Q, ID_T, cam, w, None, None, flips=fl)
+    g1 = O.render_backward(without, ID_Q, ID_T, cam, w, None, None)
+    assert np.all(gb["rgb"][0] == 0) and np.allclose(gb["rgb"][1], g1["rgb"][0], rtol=0, atol=1e-15)
+    # stop decision: alphas 0.95 and 0.9 leave T = 0.005; a third entry with
+    # 1 - alpha = 0.02 (1 + 1e-9) brings T (1 - alpha) to 1e-4 (1 + 1e-9)
+    # (each Gaussian 0.2-0.3 px off the pixel centre, opacities set so that
+    # alpha at the pixel is exactly these values)
+    sc = one_gaussian_scene([[0.03, 0.028, 2.0], [0.04, 0.035, 2.5], [0.045, 0.04, 3.0]], [0.05, 0.05, 0.05],
+                            [0.5, 0.5, 0.5], [[1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    pr = O.project(sc, ID_Q, ID_T, cam)
+    for i, al in enumerate((0.95, 0.9, 1 - 0.02 * (1 + 1e-9))):
+        dx, dy = 8.5 - pr["uv"][i, 0], 8.5 - pr["uv"][i, 1]
+        a_, b_, c_ = pr["conic"][i]
+        sig = 0.5 * (a_ * dx * dx + c_ * dy * dy) + b_ * dx * dy
+        assert 1e-3 < sig < -np.log(al)
+        sc.opacity_logit[i] = logit(al * np.exp(sig))
+    r = O.render(sc, ID_Q, ID_T, cam)
+    assert r["amb"][8, 8] & 1 and not r["amb"][8, 8] & 8 and r["n_contrib"][8, 8] == 3
+    alt = O.render_alternatives(sc, ID_Q, ID_T, cam, pix)
+    assert alt["count"][0] == 2 and alt["n_contrib"][0, 1] == 2 and alt["last_gid"][0, 1] == 1
+    without = O.Scene(sc.mean[:2], sc.log_scale[:2], sc.quat[:2], sc.opacity_logit[:2], sc.rgb[:2])
+    np.testing.assert_array_equal(alt["rgb"][0, 1], O.render(without, ID_Q, ID_T, cam)["rgb"][:, 8, 8])
