@@ -232,10 +232,12 @@ def oracle_band_step(sc64, q, t, spec, band_index=0):
     return lm["loss"]
 
 
-def cpu_baseline(budget_s=30.0):
+def cpu_baseline(budget_s=30.0, other_configs=True):
     """The oracle as it stands, on the host cores: the bands of the frame in
     turn (each a full step on 1/8 of the pixels) until all 8 ran or the
-    budget is spent; iters/s scaled to the full frame."""
+    budget is spent; iters/s scaled to the full frame.  Also the same oracle
+    on one thread, and (other_configs) bounded samples of the other
+    configurations on all cores and on one thread."""
     import oracle as O
     from paper_2312_10070_gb300 import synth as S
     O.build()
@@ -260,12 +262,85 @@ def cpu_baseline(budget_s=30.0):
         dt1 = time.perf_counter() - t1
     finally:
         O.set_num_threads(cores)
-    return dict(value=done / (BAND_FRACTION * dt), unit="iters/s", cores=cores, kind="oracle",
-                sample=f"{done} of the 8 1200x85 bands of view {S.HEADLINE_VIEW} (each band: all 500k Gaussians "
-                       f"projected, render, loss, backward, Adam); iters/s = bands / (8 x seconds)",
-                seconds=dt,
-                single_thread=dict(value=1.0 / (BAND_FRACTION * dt1), unit="iters/s", cores=1, seconds=dt1,
-                                   sample="band 0 of the same view on one thread, scaled x1/8"))
+    out = dict(value=done / (BAND_FRACTION * dt), unit="iters/s", cores=cores, kind="oracle",
+               sample=f"{done} of the 8 1200x85 bands of view {S.HEADLINE_VIEW} (each band: all 500k Gaussians "
+                      f"projected, render, loss, backward, Adam); iters/s = bands / (8 x seconds)",
+               seconds=dt,
+               single_thread=dict(value=1.0 / (BAND_FRACTION * dt1), unit="iters/s", cores=1, seconds=dt1,
+                                  sample="band 0 of the same view on one thread, scaled x1/8"))
+    if other_configs:
+        del sc64
+        out["configs"] = oracle_other_configs(cores)
+    return out
+
+
+def oracle_other_configs(cores):
+    """The FP64 oracle's forward + backward on the other configurations, all
+    cores and one thread, each a bounded sample scaled to a full frame:
+    C1 160x120 / 5k unit scene (render, L1 colour + depth loss against the
+    identity-pose render, backward; full frame), C2 one tracking iteration
+    at 1200x680 / 300k (render, tracking loss with both masks, backward;
+    1/8 of the rows), C4 1752x1168 / 1.5M (render, backward of unit image
+    gradients; 1/16 of the rows)."""
+    import oracle as O
+    from paper_2312_10070_gb300 import synth as S
+
+    def band(spec, frac):
+        h = spec.height // frac
+        return O.Camera(spec.width, h, spec.fx, spec.fy, spec.cx, spec.cy)
+
+    def c1():
+        sc = O.Scene.from_dict(S.random_scene(5000, 1))
+        q, t = S.perturbed_pose(2)
+        spec = S.camera_unit()
+        cam = O.Camera(spec.width, spec.height, spec.fx, spec.fy, spec.cx, spec.cy)
+        tg = O.render(sc, *S.IDENTITY_POSE, cam)
+
+        def run():
+            r = O.render(sc, q, t, cam)
+            O.render_backward(sc, q, t, cam, np.sign(r["rgb"] - tg["rgb"]) / r["rgb"].size,
+                              np.sign(r["depth"] - tg["depth"]) / r["depth"].size, None)
+        return run, 1, "160x120, 5000 Gaussians, full frame"
+
+    def c2():
+        sc = O.Scene.from_dict(S.room_scene(300_000, seed=100))
+        qs, ts = S.room_trajectory(100, n_frames=6)
+        spec = S.camera_room()
+        cam = band(spec, 8)
+        tg = O.render(sc, qs[3], ts[3], cam)
+
+        def run():
+            r = O.render(sc, qs[4], ts[4], cam)
+            lt = O.loss_track(r["rgb"], r["depth"], r["alpha"], tg["rgb"], tg["depth"])
+            O.render_backward(sc, qs[4], ts[4], cam, lt["d_rgb"], lt["d_depth"], None)
+        return run, 8, "1200x85 band (1/8) of a 1200x680 tracking iteration, 300k Gaussians"
+
+    def c4():
+        sc = O.Scene.from_dict(S.hires_scene())
+        spec = S.camera_hires()
+        cam = band(spec, 16)
+        ones = np.ones((3, cam.height, cam.width))
+
+        def run():
+            O.render(sc, *S.IDENTITY_POSE, cam)
+            O.render_backward(sc, *S.IDENTITY_POSE, cam, ones, ones[0], None)
+        return run, 16, "1752x73 band (1/16) of the 1752x1168 frame, 1.5M Gaussians"
+
+    res = {}
+    for name, make in (("C1_unit", c1), ("C2_track", c2), ("C4_hires", c4)):
+        run, scale, sample = make()
+        d = dict(sample=sample + "; iters/s scaled to the full frame", unit="iters/s")
+        for label, n in (("all_cores", cores), ("single_thread", 1)):
+            O.set_num_threads(n)
+            try:
+                t0 = time.perf_counter()
+                run()
+                dt = time.perf_counter() - t0
+            finally:
+                O.set_num_threads(cores)
+            d[label] = dict(value=1.0 / (scale * dt), seconds=dt, cores=n)
+        res[name] = d
+    return res
 
 
 def run_reference(args, rank, world):
@@ -285,8 +360,12 @@ def run_reference(args, rank, world):
         oracle_band_step(sc64, q, t, spec, i % BAND_FRACTION)
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
     value = 1.0 / (dt * BAND_FRACTION)
+    # a step is one measured band: ms_per_step is its measured time; value
+    # scales it to full-frame iterations (8 bands per frame)
     line = dict(impl="reference", metric=METRIC, value=value, unit="iters/s", n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=dt * BAND_FRACTION * 1e3, higher_is_better=True, scaling="weak",
+                warmup=args.warmup, ms_per_step=dt * 1e3, ms_per_frame_scaled=dt * BAND_FRACTION * 1e3,
+                step="one 1200x85 band (1/8 of the frame) of the mapping iteration; value = 1 / (8 x seconds per band)",
+                higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
                 config=config_dict(None, None),
                 cpu_baseline=dict(kind="oracle", cores=O.num_threads(), value=value, unit="iters/s",
@@ -367,7 +446,6 @@ def run_gpu(args, rank, world):
         tuned = dict(tile=(o.tile_w, o.tile_h), batch=o.batch, ppt_fwd=o.ppt_fwd, ppt_bwd=o.ppt_bwd, source="--tuned")
     else:
         tuned, _ = api.autotune(ctx, g, cam, [pose], reps=6)
-    api.profile_enable(ctx, True)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -380,7 +458,6 @@ def run_gpu(args, rank, world):
 
     sampler = ClockSampler(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    phase_ms = {k: [] for k in api.PHASES}
     replicas.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.kernel_launches
@@ -391,13 +468,21 @@ def run_gpu(args, rank, world):
         ev[i][0].record()
         step()
         ev[i][1].record()
-        ph = api.profile_read(ctx)  # synchronises; the events of this replay
-        for k, v in ph.items():
-            phase_ms[k].append(v)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     launches = ctx.kernel_launches - launches0
+    # per-phase times from a separate profiled pass (the library's events
+    # recorded inside the graph), after the timed region
+    api.profile_enable(ctx, True)
+    phase_ms = {k: [] for k in api.PHASES}
+    step()  # the profiled graph is captured here
+    for i in range(max(args.steps // 2, 3)):
+        flush.fill_(float(i))
+        step()
+        for k, v in api.profile_read(ctx).items():  # synchronises; the events of this replay
+            phase_ms[k].append(v)
+    api.profile_enable(ctx, False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = replicas.max_over_ranks(sum(step_ms))  # the slowest replica
     replicas.barrier()
@@ -488,6 +573,11 @@ def run_gpu(args, rank, world):
                 data="synthetic", config=dict(config_dict(stats, None), autotuned=tuned), roofline=roof,
                 hbm_roofline_step=hbm,
                 phases_ms=avg, e2e=e2e, gpu_launches=int(launches), clocks=clocks)
+    if not args.no_extras and world == 1 and not args.tuned:
+        ctx.close()
+        del g, state, g_gt, flush
+        torch.cuda.empty_cache()
+        line["workloads"] = extra_workloads(args)
     if not args.no_cpu_baseline and world == 1:  # the oracle is timed in single-GPU runs only
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -509,10 +599,14 @@ def cnn_flops_per_sample():
     return fwd, 3 * fwd - first
 
 
-def run_warmstart(args):
+def run_warmstart(args, emit=True):
     """Training throughput of the warm-start CNN: Adam steps on batches of 256
     synthetic inputs (120x160x8), inputs resident in HBM (157 MB per batch,
-    larger than L2; a different batch each step)."""
+    larger than L2; a different batch each step).  Besides the BF16 tensor
+    roofline, the step's HBM traffic model: every layer's activations and
+    upstream gradients (BF16) written once and read by the next pass, the
+    im2col operands gathered on the fly (counted once), FP32 master weights,
+    gradients and Adam moments read and written."""
     import torch
     from paper_2312_10070_gb300 import warmstart as W
     B = 256
@@ -543,7 +637,35 @@ def run_warmstart(args):
                                      "input 120x160x8", flops_per_sample=train),
                 roofline=dict(bound="tensor", kernel="warmstart_train", achieved=tf, peak=peak, unit="TFLOP/s",
                               frac=tf / peak, traffic=measured_traffic("warmstart_train")[0], peak_note="measured bf16 burst" if d else "fallback"))
-    print(json.dumps(line), flush=True)
+    nbytes = cnn_bytes_per_step(B)
+    hb = peaks()["hbm"]
+    line["hbm_roofline"] = dict(bound="hbm", achieved=nbytes / (ms / 1e3) / 1e9, peak=hb, unit="GB/s",
+                                frac=nbytes / (ms / 1e3) / 1e9 / hb, traffic_model_bytes=nbytes)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def cnn_bytes_per_step(B):
+    """HBM bytes of one training step of batch B (model): the input (FP32,
+    read once by the first layer's gather), each layer's BF16 activation
+    written by the forward and read by the next layer and by the weight
+    gradient, each BF16 upstream gradient written and read once, and per
+    parameter FP32 weight, gradient and two Adam moments read and written
+    plus the BF16 weight copy."""
+    from paper_2312_10070_gb300 import warmstart as W
+    h, w = W.IN_H, W.IN_W
+    act = 0
+    params = 0
+    for ci, co in W.CONV:
+        h, w = (h - 1) // 2 + 1, (w - 1) // 2 + 1
+        act += h * w * co
+        params += 9 * ci * co + co
+    for a, b in W.DENSE:
+        act += b
+        params += a * b + b
+    inp = W.IN_H * W.IN_W * W.IN_C * 4
+    return B * (inp + act * 2 * 3 + act * 2 * 2) + params * (4 * 2 * 4 + 2)
 
 
 # ------------------------------------------------------------ seeding
@@ -589,7 +711,7 @@ def run_seed(args):
     print(json.dumps(line), flush=True)
 
 
-def run_map8(args):
+def run_map8(args, emit=True):
     """The batched sub-map mapping iteration: all 8 keyframes of the 500k
     sub-map (1200x680) in one gsr_map_step per iteration (persistent blend
     over a (keyframe, tile) queue, per-Gaussian gradients summed with uniform
@@ -644,10 +766,13 @@ def run_map8(args):
                 config=dict(workload="gsr_map_step over the 8 sub-map keyframes of room_scene seed 3, one Adam step "
                                      "per iteration", keyframes=8, autotuned=tuned, l2="flushed between steps"),
                 phases_ms=avg, roofline=roof, gpu_launches=int(ctx.kernel_launches - launches0))
-    print(json.dumps(line), flush=True)
+    ctx.close()
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_track(args):
+def run_track(args, emit=True):
     """Frame-to-model tracking at 1200x680 against 300k Gaussians
     (room_scene seed 100): each step tracks one frame of a smooth room
     trajectory (room_trajectory seed 100, ~1.5 cm / <= 1 degree apart) with
@@ -704,10 +829,13 @@ def run_track(args):
                             l2="flushed before every frame", ms_per_frame=ms_frame,
                             pose_error_max_cm=float(errs[:, 0].max() * 100), pose_error_max_deg=float(errs[:, 1].max())),
                 gpu_launches=int(launches))
-    print(json.dumps(line), flush=True)
+    ctx.close()
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_hires(args):
+def run_hires(args, emit=True):
     """The high-resolution configuration, 1752x1168 with 1.5M Gaussians
     (hires_scene seed 4, identity pose; target = render of the scene,
     optimised copy = scene + noise): the mapping iteration (gsr_map_step), and
@@ -768,7 +896,33 @@ def run_hires(args):
                 dtype="f32", data="synthetic",
                 config=dict(workload="hires_scene(1.5M, seed 4), identity pose, tile 8x8 / batch 128 / one pixel per "
                                      "thread", results=out, l2="flushed between steps (256 MB write)"))
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def extra_workloads(args):
+    """Short runs of the other configurations, reported beside the headline:
+    100-iteration tracking at 1200x680 / 300k (iterations/s), the batched
+    8-keyframe mapping iteration (iterations/s), 1752x1168 / 1.5M (mapping
+    iteration and the autograd-facing render pair in both modes), and the
+    warm-start network's training step.  Each keeps its own warm-up; the
+    numbers are CUDA-event timings like the headline's."""
+    import torch
+    out = {}
+    sub = argparse.Namespace(steps=5, warmup=3, gpus=1)
+    for name, fn, steps in (("track", run_track, 5), ("map8", run_map8, 5), ("hires", run_hires, 5),
+                            ("warmstart", run_warmstart, 20)):
+        sub.steps = steps
+        t0 = time.perf_counter()
+        line = fn(sub, emit=False)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        keep = {k: line[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "config", "phases_ms",
+                                      "roofline", "hbm_roofline", "gpu_launches") if k in line and line[k] is not None}
+        keep["wall_s"] = time.perf_counter() - t0
+        out[name] = keep
+    return out
 
 
 def main():
@@ -778,6 +932,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the short runs of the other workloads reported beside the headline")
     ap.add_argument("--tuned", default="",
                     help="tile_w,tile_h,batch,ppt_fwd,ppt_bwd: fixed blend configuration, no autotuning")
     ap.add_argument("--workload", default="map", choices=["map", "map8", "hires", "warmstart", "seed", "track"],

@@ -357,13 +357,248 @@ __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, in
     }
 }
 
+// ---------------------------------------------------- two pixels per thread
+// With two pixels per thread (vertically adjacent: same column, so dx is
+// shared) the per-pixel arithmetic runs on packed float pairs: add, mul and
+// fma.rn.f32x2 round each half exactly like the scalar operation, so every
+// sigma, alpha, transmittance and decision is bit-identical to the
+// one-pixel-per-thread kernels (eval_gaussian); only the order in which a
+// thread sums its two pixels' gradient contributions differs.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// sigma of one staged Gaussian at the pixel pair (px, py.x) / (px, py.y), in
+// eval_gaussian's order of operations; dx shared, dy / dy^2 / dx dy per pixel
+struct PairSigma {
+    float dx, dxdx;
+    float2 dy, dydy, dxdy, sig;
+};
+
+__device__ __forceinline__ PairSigma pair_sigma(float px, float2 py, const float4 &a, const float4 &b)
+{
+    PairSigma r;
+    r.dx = __fsub_rn(px, a.x);
+    r.dxdx = __fmul_rn(r.dx, r.dx);
+    r.dy = add2(py, f2(-a.y));
+    r.dydy = mul2(r.dy, r.dy);
+    const float2 q = fma2(f2(a.z), f2(r.dxdx), mul2(f2(b.x), r.dydy));
+    r.dxdy = mul2(f2(r.dx), r.dy);
+    r.sig = fma2(f2(a.w), r.dxdy, mul2(f2(0.5f), q));
+    return r;
+}
+
+template <int TW, int TH, int BATCH>
+__device__ __forceinline__ void fwd_tile2(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
+                                          float4 *sC, u32 *sR, int *sJ, int *s_cnt)
+{
+    constexpr int NT = TW * TH / 2;
+    const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
+    const int col = (int)threadIdx.x % TW, row0 = ((int)threadIdx.x / TW) * 2;
+    const int ix = tx * TW + col, iy0 = ty * TH + row0;
+    const float px = (float)ix + 0.5f;
+    const float2 py = make_float2((float)iy0 + 0.5f, (float)(iy0 + 1) + 0.5f);
+    float2 T = f2(1.f), c0 = f2(0.f), c1 = f2(0.f), c2 = f2(0.f), d = f2(0.f);
+    int last0 = -1, last1 = -1, nc0 = 0, nc1 = 0;
+    bool done0 = !(ix < ck.W && iy0 < ck.H), done1 = !(ix < ck.W && iy0 + 1 < ck.H);
+    bool tdone = done0 && done1;
+    const uint2 rg = vp.ranges[tile];
+    const int n = (int)(rg.y - rg.x);
+    const TileBox box = tile_box(ck, tile, TW, TH);
+    for (int base = 0; base < n; base += BATCH) {
+        if (__syncthreads_count(tdone) == NT) break;
+        const int cnt = stage_entries<NT>(vp, rg.x, base, min(n, base + BATCH), box, sA, sB, sC, sR, sJ, s_cnt);
+        __syncthreads();
+        for (int j = 0; j < cnt && !tdone; ++j) {
+            const float4 a = sA[j], b = sB[j];
+            const PairSigma S = pair_sigma(px, py, a, b);
+            const bool r0 = done0 || S.sig.x > b.w, r1 = done1 || S.sig.y > b.w;
+            if (r0 && r1) continue;
+            const float2 G = mul2(f2(b.y), make_float2(__expf(-S.sig.x), __expf(-S.sig.y)));
+            const float al0 = fminf(GSR_ALPHA_MAX, G.x), al1 = fminf(GSR_ALPHA_MAX, G.y);
+            const bool u0 = !r0 && S.sig.x >= 0.f && al0 >= GSR_ALPHA_MIN;
+            const bool u1 = !r1 && S.sig.y >= 0.f && al1 >= GSR_ALPHA_MIN;
+            if (!(u0 || u1)) continue;
+            const float2 al = make_float2(al0, al1);
+            const float2 Tn = mul2(T, add2(f2(1.f), make_float2(-al0, -al1)));
+            const bool s0 = u0 && Tn.x < GSR_T_STOP, s1 = u1 && Tn.y < GSR_T_STOP;
+            const bool k0 = u0 && !s0, k1 = u1 && !s1;  // composited
+            done0 = done0 || s0;
+            done1 = done1 || s1;
+            const float4 c = sC[j];
+            const float2 w = mul2(make_float2(k0 ? al.x : 0.f, k1 ? al.y : 0.f), T);
+            c0 = fma2(f2(c.x), w, c0);
+            c1 = fma2(f2(c.y), w, c1);
+            c2 = fma2(f2(c.z), w, c2);
+            d = fma2(f2(b.z), w, d);
+            T = make_float2(k0 ? Tn.x : T.x, k1 ? Tn.y : T.y);
+            const int jj = sJ[j];
+            last0 = k0 ? jj : last0;
+            last1 = k1 ? jj : last1;
+            nc0 += k0;
+            nc1 += k1;
+            tdone = done0 && done1;
+        }
+    }
+    const int64_t HW = (int64_t)ck.W * ck.H;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int iy = iy0 + k;
+        if (ix < ck.W && iy < ck.H) {
+            const int64_t p = (int64_t)iy * ck.W + ix;
+            const float Tk = k ? T.y : T.x;
+            vp.rgb[p] = k ? c0.y : c0.x;
+            vp.rgb[HW + p] = k ? c1.y : c1.x;
+            vp.rgb[2 * HW + p] = k ? c2.y : c2.x;
+            vp.depth[p] = k ? d.y : d.x;
+            vp.alpha[p] = 1.f - Tk;
+            vp.final_T[p] = Tk;
+            vp.last_idx[p] = k ? last1 : last0;
+            if (vp.n_contrib) vp.n_contrib[p] = k ? nc1 : nc0;
+        }
+    }
+}
+
+template <int TW, int TH, int BATCH, bool POSE_ONLY>
+__device__ __forceinline__ void bwd_tile2(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
+                                          float4 *sC, u32 *sR, int *sJ, int *s_cnt, int *s_max)
+{
+    constexpr int NT = TW * TH / 2;
+    const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
+    const int col = (int)threadIdx.x % TW, row0 = ((int)threadIdx.x / TW) * 2;
+    const int ix = tx * TW + col, iy0 = ty * TH + row0;
+    const float px = (float)ix + 0.5f;
+    const float2 py = make_float2((float)iy0 + 0.5f, (float)(iy0 + 1) + 0.5f);
+    const uint2 rg = vp.ranges[tile];
+    const int64_t HW = (int64_t)ck.W * ck.H;
+    // per pixel: T recovered back to front, the image gradients, and Q = the
+    // folded suffix sum of (dL/dC . c_u + dL/dD z_u) alpha_u T_u
+    float2 T = f2(1.f), g0 = f2(0.f), g1 = f2(0.f), g2 = f2(0.f), gd = f2(0.f), gaT = f2(0.f), Q = f2(0.f);
+    int L0 = -1, L1 = -1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int iy = iy0 + k;
+        if (ix < ck.W && iy < ck.H) {
+            const int64_t p = (int64_t)iy * ck.W + ix;
+            const int Lk = vp.last_idx[p];
+            const float Tk = vp.final_T[p];
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, ad = 0.f, aa = 0.f;
+            if (vp.d_rgb) {
+                a0 = vp.d_rgb[p];
+                a1 = vp.d_rgb[HW + p];
+                a2 = vp.d_rgb[2 * HW + p];
+            }
+            if (vp.d_depth) ad = vp.d_depth[p];
+            if (vp.d_alpha) aa = vp.d_alpha[p] * Tk;
+            if (k) {
+                L1 = Lk; T.y = Tk; g0.y = a0; g1.y = a1; g2.y = a2; gd.y = ad; gaT.y = aa;
+            } else {
+                L0 = Lk; T.x = Tk; g0.x = a0; g1.x = a1; g2.x = a2; gd.x = ad; gaT.x = aa;
+            }
+        }
+    }
+    const int lmax = max(L0, L1);
+    if (threadIdx.x == 0) *s_max = -1;
+    __syncthreads();
+    const int wmax = __reduce_max_sync(0xffffffffu, lmax);
+    if ((threadIdx.x & 31) == 0) atomicMax(s_max, wmax);
+    __syncthreads();
+    const int nend = min(*s_max + 1, (int)(rg.y - rg.x));  // saved state never reads past the list
+    const TileBox box = tile_box(ck, tile, TW, TH);
+    for (int bend = nend; bend > 0; bend -= BATCH) {
+        const int bstart = max(0, bend - BATCH);
+        __syncthreads();
+        const int cnt = stage_entries<NT>(vp, rg.x, bstart, bend, box, sA, sB, sC, sR, sJ, s_cnt);
+        __syncthreads();
+        for (int j = cnt - 1; j >= 0; --j) {
+            const int jj = sJ[j];
+            const float4 a = sA[j], b = sB[j];
+            float gu = 0.f, gv = 0.f, gca = 0.f, gcb = 0.f, gcc = 0.f, gop = 0.f, gr = 0.f, gg = 0.f, gb = 0.f,
+                  gz = 0.f;
+            bool contrib = false;
+            const bool n0 = jj <= L0, n1 = jj <= L1;
+            if (n0 || n1) {
+                const PairSigma S = pair_sigma(px, py, a, b);
+                const bool r0 = !n0 || S.sig.x > b.w, r1 = !n1 || S.sig.y > b.w;
+                if (!(r0 && r1)) {
+                    const float ex0 = __expf(-S.sig.x), ex1 = __expf(-S.sig.y);
+                    const float2 G = mul2(f2(b.y), make_float2(ex0, ex1));
+                    const float al0 = fminf(GSR_ALPHA_MAX, G.x), al1 = fminf(GSR_ALPHA_MAX, G.y);
+                    const bool u0 = !r0 && S.sig.x >= 0.f && al0 >= GSR_ALPHA_MIN;
+                    const bool u1 = !r1 && S.sig.y >= 0.f && al1 >= GSR_ALPHA_MIN;
+                    if (u0 || u1) {
+                        contrib = true;
+                        const float4 c = sC[j];
+                        const float2 al = make_float2(u0 ? al0 : 0.f, u1 ? al1 : 0.f);
+                        const float2 om = add2(f2(1.f), make_float2(-al.x, -al.y));
+                        // gradient-only use (decisions come from the forward's arithmetic): fast reciprocal
+                        const float2 iom = make_float2(u0 ? __fdividef(1.f, om.x) : 1.f, u1 ? __fdividef(1.f, om.y) : 1.f);
+                        T = mul2(T, iom);  // T_j
+                        const float2 w = mul2(al, T);
+                        // dL/dalpha_j = T_j P - (Q - gaT) / (1 - alpha_j),  P = g . (c_j, z_j)
+                        const float2 P = fma2(g0, f2(c.x), fma2(g1, f2(c.y), fma2(g2, f2(c.z), mul2(gd, f2(b.z)))));
+                        const float2 dLda = fma2(T, P, mul2(add2(gaT, make_float2(-Q.x, -Q.y)), iom));
+                        Q = fma2(P, w, Q);
+                        gz = fmaf(gd.y, w.y, gd.x * w.x);
+                        if (!POSE_ONLY) {
+                            gr = fmaf(g0.y, w.y, g0.x * w.x);
+                            gg = fmaf(g1.y, w.y, g1.x * w.x);
+                            gb = fmaf(g2.y, w.y, g2.x * w.x);
+                        }
+                        // the cap alpha = min(0.99, G) passes no gradient where it is active
+                        const bool l0 = u0 && G.x <= GSR_ALPHA_MAX, l1 = u1 && G.y <= GSR_ALPHA_MAX;
+                        if (!POSE_ONLY) gop = fmaf(dLda.y, l1 ? ex1 : 0.f, dLda.x * (l0 ? ex0 : 0.f));
+                        // nds = -dL/dsigma per pixel; the pixels share dx
+                        const float2 nds = mul2(dLda, make_float2(l0 ? G.x : 0.f, l1 ? G.y : 0.f));
+                        const float sn = nds.x + nds.y;
+                        const float sny = fmaf(nds.y, S.dy.y, nds.x * S.dy.x);
+                        gu = fmaf(a.z * S.dx, sn, a.w * sny);
+                        gv = fmaf(a.w * S.dx, sn, b.x * sny);
+                        gca = -0.5f * S.dxdx * sn;
+                        gcb = -S.dx * sny;
+                        gcc = -0.5f * fmaf(nds.y, S.dydy.y, nds.x * S.dydy.x);
+                    }
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, contrib);
+            if (bal) {
+                float *dst = vp.g2d + 12 * (int64_t)sR[j];
+                if (__popc(bal) <= SPARSE_LANES) {
+                    if (contrib) {  // slots as in warp_reduce_add10
+                        atomicAdd(dst + 0, gu);
+                        atomicAdd(dst + 1, gv);
+                        atomicAdd(dst + 2, gca);
+                        atomicAdd(dst + 3, gcb);
+                        atomicAdd(dst + 4, gcc);
+                        if (!POSE_ONLY) {
+                            atomicAdd(dst + 5, gop);
+                            atomicAdd(dst + 6, gr);
+                            atomicAdd(dst + 7, gg);
+                            atomicAdd(dst + 8, gb);
+                        }
+                        atomicAdd(dst + 9, gz);
+                    }
+                } else if (POSE_ONLY) {
+                    const float v[6] = {gu, gv, gca, gcb, gcc, gz};
+                    warp_reduce_add6(v, dst);
+                } else {
+                    const float v[10] = {gu, gv, gca, gcb, gcc, gop, gr, gg, gb, gz};
+                    warp_reduce_add10(v, dst);
+                }
+            }
+        }
+    }
+}
+
 template <int TW, int TH, int BATCH, int PPT>
 __global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd(CamK ck, BlendView vp)
 {
     __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
     __shared__ u32 sR[BATCH];
     __shared__ int sJ[BATCH], s_cnt[TW * TH / PPT / 32];
-    fwd_tile<TW, TH, BATCH, PPT>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt);
+    if constexpr (PPT == 2) fwd_tile2<TW, TH, BATCH>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt);
+    else fwd_tile<TW, TH, BATCH, PPT>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt);
 }
 
 template <int TW, int TH, int BATCH, int PPT, bool POSE_ONLY>
@@ -373,7 +608,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_bwd(CamK ck, BlendView v
     __shared__ u32 sR[BATCH];
     __shared__ int sJ[BATCH], s_cnt[TW * TH / PPT / 32];
     __shared__ int s_max;
-    bwd_tile<TW, TH, BATCH, PPT, POSE_ONLY>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt, &s_max);
+    if constexpr (PPT == 2) bwd_tile2<TW, TH, BATCH, POSE_ONLY>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt, &s_max);
+    else bwd_tile<TW, TH, BATCH, PPT, POSE_ONLY>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt, &s_max);
 }
 
 // Persistent forms: items[i] = (view << 16) | tile, longest lists first.
@@ -396,7 +632,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd_multi(CamK ck, const
     __shared__ int s_item;
     for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
         const u32 w = items[it];
-        fwd_tile<TW, TH, BATCH, PPT>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt);
+        if constexpr (PPT == 2) fwd_tile2<TW, TH, BATCH>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt);
+        else fwd_tile<TW, TH, BATCH, PPT>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt);
     }
 }
 
@@ -411,8 +648,11 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_bwd_multi(CamK ck, const
     __shared__ int s_max, s_item;
     for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
         const u32 w = items[it];
-        bwd_tile<TW, TH, BATCH, PPT, false>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt,
-                                            &s_max);
+        if constexpr (PPT == 2)
+            bwd_tile2<TW, TH, BATCH, false>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt, &s_max);
+        else
+            bwd_tile<TW, TH, BATCH, PPT, false>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt,
+                                                &s_max);
     }
 }
 
@@ -566,6 +806,11 @@ gsr_status run_blend_forward(gsr_ctx *ctx, const Params &, const CamK &ck, gsr_r
 
 gsr_status zero_g2d(gsr_ctx *ctx, ViewScratch &V, cudaStream_t s)
 {
+    // the binning zeroes the accumulators; a second backward on the same lists must start again from zero
+    if (V.g2d_zero) {
+        V.g2d_zero = false;
+        return GSR_OK;
+    }
     k_zero_g2d<<<(unsigned)ceil_div(V.cap_n * 3, 256), 256, 0, s>>>(V.cap_n, (u32 *)V.counters.p + CNT_VISIBLE,
                                                                     (float4 *)V.g2d.p);
     ctx->launches += 1;
