@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) k_adam_scalar(gsr_gaussians_mut g, gsr_ga
     }
 }
 
-__global__ void k_lreg_final(const float *__restrict__ part, int nb, float scale, float *out)
+__global__ void k_lreg_final(const float *__restrict__ part, int nb, float scale, float *out, int32_t *step)
 {
     __shared__ float red[32];
     float v = 0.f;
@@ -221,7 +221,8 @@ __global__ void k_lreg_final(const float *__restrict__ part, int nb, float scale
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int k = 0; k < 32; ++k) t += red[k];
-        *out += scale * t;
+        if (out) *out += scale * t;
+        if (step) *step += 1;
     }
 }
 
@@ -319,7 +320,8 @@ gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads
         ctx->launches += 2;
     }
     if (loss_reg_dev) {
-        k_lreg_final<<<1, 1024, 0, s>>>(part, (int)nb, o->w_reg / (float)(g->n > 0 ? g->n : 1), loss_reg_dev);
+        k_lreg_final<<<1, 1024, 0, s>>>(part, (int)nb, o->w_reg / (float)(g->n > 0 ? g->n : 1), loss_reg_dev,
+                                        nullptr);
         ctx->launches += 1;
     }
     GSR_LAUNCHED(ctx);
@@ -338,7 +340,16 @@ gsr_status adam_prep(gsr_ctx *ctx, gsr_adam_state *st, const gsr_adam_opts *o, f
 
 gsr_status adam_lreg_final(gsr_ctx *ctx, const float *part, int nb, float scale, float *loss_reg_dev, cudaStream_t s)
 {
-    k_lreg_final<<<1, 1024, 0, s>>>(part, nb, scale, loss_reg_dev);
+    k_lreg_final<<<1, 1024, 0, s>>>(part, nb, scale, loss_reg_dev, nullptr);
+    ctx->launches += 1;
+    GSR_LAUNCHED(ctx);
+    return GSR_OK;
+}
+
+gsr_status adam_lreg_final_step(gsr_ctx *ctx, const float *part, int nb, float scale, float *loss_reg_dev,
+                                int32_t *step, cudaStream_t s)
+{
+    k_lreg_final<<<1, 1024, 0, s>>>(part, nb, scale, loss_reg_dev, step);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     return GSR_OK;

@@ -65,6 +65,7 @@ struct ViewScratch {
     DevBuf loss_part;   // per-block partial sums of this view's mapping loss
     int64_t cap_n = 0, cap_i = 0, cap_t = 0;
     bool culled = false;  // the lists hold only entries that pass the tile test
+    bool g2d_zero = false;  // g2d was zeroed by the last binning and no backward has added to it since
     // identity of the last forward, to decide whether the saved lists are valid
     uint64_t generation = 0;
 };
@@ -260,11 +261,24 @@ __device__ __forceinline__ void adam_update(float &p, float g, float &m, float &
     p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
 }
 
+// The same update with the bias corrections passed as reciprocals and a fast
+// division (a few ulp; the fused projection backward + Adam).
+__device__ __forceinline__ void adam_update_fast(float &p, float g, float &m, float &v, float lr, float b1, float b2,
+                                                 float eps, float ib1, float ib2)
+{
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    p -= __fdividef(lr * (m * ib1), sqrtf(v * ib2) + eps);
+}
+
 __device__ __forceinline__ float sign_of(float x) { return (x > 0.f) ? 1.f : ((x < 0.f) ? -1.f : 0.f); }
 
 // One Gaussian's three log-scales p (in registers) with gradient g plus the
 // gradient of rw * |s - mean(s)|_1 (s = exp(p), Sec. 3.4 L_reg); returns the
 // unweighted L_reg term.
+// FAST: bc1, bc2 are the reciprocals of the bias corrections and the update
+// is adam_update_fast
+template <bool FAST = false>
 __device__ __forceinline__ float adam_log_scales3(float *p, const float *g, float *m, float *v, float rw, float lr,
                                                   const gsr_adam_opts &o, float bc1, float bc2)
 {
@@ -285,7 +299,8 @@ __device__ __forceinline__ float adam_log_scales3(float *p, const float *g, floa
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float gk = g[k] + rw * (sg[k] - ssum * (1.f / 3.f)) * sc[k];
-        adam_update(p[k], gk, m[k], v[k], lr, o.beta1, o.beta2, o.eps, bc1, bc2);
+        if (FAST) adam_update_fast(p[k], gk, m[k], v[k], lr, o.beta1, o.beta2, o.eps, bc1, bc2);
+        else adam_update(p[k], gk, m[k], v[k], lr, o.beta1, o.beta2, o.eps, bc1, bc2);
     }
     return lsum;
 }
@@ -396,6 +411,10 @@ gsr_status run_loss_track(gsr_ctx *ctx, int W, int H, const float *rgb, const fl
 // and the final L_reg reduction into *loss_reg_dev (part: nb block partial sums)
 gsr_status adam_prep(gsr_ctx *ctx, gsr_adam_state *st, const gsr_adam_opts *o, float **bc, cudaStream_t s);
 gsr_status adam_lreg_final(gsr_ctx *ctx, const float *part, int nb, float scale, float *loss_reg_dev, cudaStream_t s);
+// as adam_lreg_final, and then advances the Adam step counter (for the fused
+// projection backward + Adam, which reads the counter without advancing it)
+gsr_status adam_lreg_final_step(gsr_ctx *ctx, const float *part, int nb, float scale, float *loss_reg_dev,
+                                int32_t *step, cudaStream_t s);
 // one-keyframe step: projection backward of every Gaussian fused with its Adam
 // update and L_reg (the gradients never reach memory)
 gsr_status run_project_backward_adam(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians_mut *g, gsr_adam_state *st,

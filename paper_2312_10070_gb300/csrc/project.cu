@@ -451,7 +451,8 @@ __device__ __forceinline__ void row_cols(const RowCull &q, const CamK &ck, int t
 template <bool CULL>
 __global__ void k_gather(int64_t cap, const u32 *__restrict__ d_v, const u32 *__restrict__ vals,
                          const float4 *__restrict__ rec, float4 *__restrict__ rec_sorted,
-                         int32_t *__restrict__ rank_of_gid, CamK ck, u32 *__restrict__ tcount)
+                         int32_t *__restrict__ rank_of_gid, CamK ck, u32 *__restrict__ tcount,
+                         float4 *__restrict__ g2d)
 {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= cap || r >= (int64_t)*d_v) return;
@@ -460,6 +461,11 @@ __global__ void k_gather(int64_t cap, const u32 *__restrict__ d_v, const u32 *__
     rec_sorted[3 * r] = a;
     rec_sorted[3 * r + 1] = b;
     rec_sorted[3 * r + 2] = c;
+    // the rank's image-space gradient accumulator starts at zero for the next backward
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    g2d[3 * r] = z;
+    g2d[3 * r + 1] = z;
+    g2d[3 * r + 2] = z;
     rank_of_gid[gid] = (int32_t)r;
     const u32 lo = __float_as_uint(b.w), hi = __float_as_uint(c.w);
     const int x0 = (int)(lo & 0xffffu), y0 = (int)(lo >> 16), x1 = (int)(hi & 0xffffu), y1 = (int)(hi >> 16);
@@ -780,16 +786,24 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd(Params P, CamK ck, const
 // gradients stay in registers: the parameters are read once, the moments
 // read and written once, and no gradient array is written or read back.
 // Gaussians outside the view have zero gradients and still take their Adam
-// step.  Per-block sums of the L_reg terms go to lreg_part.
+// step.  Per-block sums of the L_reg terms go to lreg_part.  The kernel reads
+// the Adam step counter t - 1 (the bias corrections of step t are formed per
+// block); the kernel after it advances the counter.
 __global__ void __launch_bounds__(256, 4) k_project_bwd_adam(Params P, gsr_gaussians_mut gw, CamK ck,
                                                           const float *__restrict__ pose,
                                                           const int32_t *__restrict__ rank_of_gid,
                                                           const float *__restrict__ g2d, gsr_adam_state st,
-                                                          gsr_adam_opts o, const float *__restrict__ bc,
-                                                          float *__restrict__ lreg_part)
+                                                          gsr_adam_opts o, float *__restrict__ lreg_part)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float lreg = 0.f;
+    __shared__ float s_bc[2];
+    if (threadIdx.x == 0) {
+        const int t = *st.step + 1;
+        s_bc[0] = 1.f / (1.f - powf(o.beta1, (float)t));
+        s_bc[1] = 1.f / (1.f - powf(o.beta2, (float)t));
+    }
+    __syncthreads();
     if (i < P.n) {
         asm volatile("prefetch.global.L2 [%0];" ::"l"(P.mean + 3 * i));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(P.log_scale + 3 * i));
@@ -809,7 +823,7 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd_adam(Params P, gsr_gauss
             grgb[2] = q2.x;
             chain_to_params(ck, pr, g, q0, q1, q2, gm, gls, gq, &glog, nullptr);
         }
-        const float bc1 = bc[0], bc2 = bc[1];
+        const float ib1 = s_bc[0], ib2 = s_bc[1];  // reciprocal bias corrections
         float p[4], m[4], v[4];
         // log-scales with L_reg
 #pragma unroll
@@ -818,7 +832,7 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd_adam(Params P, gsr_gauss
             m[k] = st.m_log_scale[3 * i + k];
             v[k] = st.v_log_scale[3 * i + k];
         }
-        lreg = adam_log_scales3(p, gls, m, v, o.w_reg / (float)P.n, o.lr_log_scale, o, bc1, bc2);
+        lreg = adam_log_scales3<true>(p, gls, m, v, o.w_reg / (float)P.n, o.lr_log_scale, o, ib1, ib2);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             gw.log_scale[3 * i + k] = p[k];
@@ -829,12 +843,12 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd_adam(Params P, gsr_gauss
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             float pm = gw.mean[3 * i + k], mm = st.m_mean[3 * i + k], vm = st.v_mean[3 * i + k];
-            adam_update(pm, gm[k], mm, vm, o.lr_mean, o.beta1, o.beta2, o.eps, bc1, bc2);
+            adam_update_fast(pm, gm[k], mm, vm, o.lr_mean, o.beta1, o.beta2, o.eps, ib1, ib2);
             gw.mean[3 * i + k] = pm;
             st.m_mean[3 * i + k] = mm;
             st.v_mean[3 * i + k] = vm;
             float pc = gw.rgb[3 * i + k], mc = st.m_rgb[3 * i + k], vc = st.v_rgb[3 * i + k];
-            adam_update(pc, grgb[k], mc, vc, o.lr_rgb, o.beta1, o.beta2, o.eps, bc1, bc2);
+            adam_update_fast(pc, grgb[k], mc, vc, o.lr_rgb, o.beta1, o.beta2, o.eps, ib1, ib2);
             gw.rgb[3 * i + k] = pc;
             st.m_rgb[3 * i + k] = mc;
             st.v_rgb[3 * i + k] = vc;
@@ -842,13 +856,13 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd_adam(Params P, gsr_gauss
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float pq = gw.quat[4 * i + k], mq = st.m_quat[4 * i + k], vq = st.v_quat[4 * i + k];
-            adam_update(pq, gq[k], mq, vq, o.lr_quat, o.beta1, o.beta2, o.eps, bc1, bc2);
+            adam_update_fast(pq, gq[k], mq, vq, o.lr_quat, o.beta1, o.beta2, o.eps, ib1, ib2);
             gw.quat[4 * i + k] = pq;
             st.m_quat[4 * i + k] = mq;
             st.v_quat[4 * i + k] = vq;
         }
         float po = gw.opacity_logit[i], mo = st.m_opacity_logit[i], vo = st.v_opacity_logit[i];
-        adam_update(po, glog, mo, vo, o.lr_opacity, o.beta1, o.beta2, o.eps, bc1, bc2);
+        adam_update_fast(po, glog, mo, vo, o.lr_opacity, o.beta1, o.beta2, o.eps, ib1, ib2);
         gw.opacity_logit[i] = po;
         st.m_opacity_logit[i] = mo;
         st.v_opacity_logit[i] = vo;
@@ -1027,12 +1041,13 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
     const bool cull = !ctx->opt.rect_lists;
     if (cull)
         k_gather<true><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, dv[0], (float4 *)V.rec.p, (float4 *)V.rec_sorted.p,
-                                          (int32_t *)V.rank_of_gid.p, ck, (u32 *)V.tcount.p);
+                                          (int32_t *)V.rank_of_gid.p, ck, (u32 *)V.tcount.p, (float4 *)V.g2d.p);
     else
         k_gather<false><<<nb, 256, 0, s>>>(n, cnt + CNT_VISIBLE, dv[0], (float4 *)V.rec.p, (float4 *)V.rec_sorted.p,
-                                           (int32_t *)V.rank_of_gid.p, ck, (u32 *)V.tcount.p);
+                                           (int32_t *)V.rank_of_gid.p, ck, (u32 *)V.tcount.p, (float4 *)V.g2d.p);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
+    V.g2d_zero = true;
     GSR_TRY(scan_exclusive(ctx, (u32 *)V.tcount.p, (u32 *)V.inst_off.p, n, cnt + CNT_VISIBLE,
                            cnt + CNT_INSTANCES, s, &V.scan_tmp));
     V.culled = cull;
@@ -1103,14 +1118,13 @@ gsr_status run_project_backward_adam(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians
     const unsigned nb = (unsigned)ceil_div(n > 0 ? n : 1, 256);
     GSR_TRY(ensure_buf(ctx, ctx->pose_part, sizeof(float) * 6 * nb));
     float *part = (float *)ctx->pose_part.p;
-    float *bc = nullptr;
-    GSR_TRY(adam_prep(ctx, st, o, &bc, s));
     const Params P{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, n};
     k_project_bwd_adam<<<nb, 256, 0, s>>>(P, *g, ck, d_pose, (const int32_t *)V.rank_of_gid.p, (const float *)V.g2d.p,
-                                          *st, *o, bc, part);
+                                          *st, *o, part);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
-    if (loss_reg_dev) GSR_TRY(adam_lreg_final(ctx, part, (int)nb, o->w_reg / (float)(n > 0 ? n : 1), loss_reg_dev, s));
+    if (loss_reg_dev)
+        GSR_TRY(adam_lreg_final_step(ctx, part, (int)nb, o->w_reg / (float)(n > 0 ? n : 1), loss_reg_dev, st->step, s));
     return GSR_OK;
 }
 

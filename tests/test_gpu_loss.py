@@ -92,3 +92,19 @@ def test_adam_and_lreg_match_oracle(ctx):
     for k in api.GaussianParams.NAMES:
         np.testing.assert_allclose(getattr(g, k).cpu().numpy(), ref_p[k], rtol=1e-5, atol=1e-6)
     assert int(st.step) == 3
+
+
+@pytest.mark.parametrize("alpha_pow,k_median", [(0.0, 1e30), (3.0, 1e30), (0.0, 50.0), (3.0, 50.0), (1.0, 5.0)])
+def test_loss_track_ablation_variants_match_oracle(ctx, alpha_pow, k_median):
+    """The tracking-loss variants of the mask ablation (the alpha mask off:
+    exponent 0; the inlier mask off: an infinite factor) and an off-default
+    pair, each against the oracle with the same parameters."""
+    rgb, d, a, rgb_t, d_t = images(120, 160, 4, 0.1)
+    d[7, 9] = d_t[7, 9] + 30.0
+    d[50, 60] = d_t[50, 60] * 0.3
+    loss, med, g_rgb, g_d = api.loss_track(ctx, cu(rgb), cu(d), cu(a), cu(rgb_t), cu(d_t), 0.5, k_median, alpha_pow)
+    ref = O.loss_track(rgb, d, a, rgb_t, d_t, 0.5, k_median, alpha_pow)
+    assert float(med) == np.float32(ref["median"])
+    assert abs(float(loss) - ref["loss"]) <= 1e-5 * abs(ref["loss"]) + 1e-6
+    np.testing.assert_allclose(g_rgb.cpu().numpy(), ref["d_rgb"], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(g_d.cpu().numpy(), ref["d_depth"], rtol=1e-5, atol=1e-6)
