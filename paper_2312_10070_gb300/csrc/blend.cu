@@ -48,14 +48,22 @@ __device__ __forceinline__ bool quick_reject(float px, float py, const float4 &a
     return sigma > b.w;
 }
 
+// One staged list entry: the Gaussian's record with b.w = its skip threshold
+// and c.w = its position in the tile list (int bits), so one base address
+// serves every field.
+struct Staged {
+    float4 a, b, c;
+};
+__device__ __forceinline__ int staged_pos(const Staged &e) { return __float_as_int(e.c.w); }
+
 // Stage list entries [lo, hi) (hi - lo <= BATCH) of a tile: entries that may
-// hit the tile are written in list order to sA/sB/sC (sB.w = skip threshold),
-// with their list position in sJ and Gaussian rank in sR.  Returns the number
+// hit the tile are written in list order to sS (b.w = skip threshold, c.w =
+// list position) with their Gaussian rank in sR.  Returns the number
 // staged (uniform over the CTA).  s_cnt holds NT/32 ints.  The caller
 // synchronises before reading the staged entries.
 template <int NT>
 __device__ __forceinline__ int stage_entries(const BlendView &vp, u32 list_base, int lo, int hi, const TileBox &box,
-                                             float4 *sA, float4 *sB, float4 *sC, u32 *sR, int *sJ, int *s_cnt)
+                                             Staged *sS, u32 *sR, int *s_cnt)
 {
     constexpr int NW = NT / 32;
     const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
@@ -87,11 +95,12 @@ __device__ __forceinline__ int stage_entries(const BlendView &vp, u32 list_base,
         }
         if (keep) {
             const int pos = off + __popc(bal & ((1u << lane) - 1u));
-            sA[pos] = a;
-            sB[pos] = b;
-            sC[pos] = vp.rec[3 * (int64_t)r + 2];
+            float4 c = vp.rec[3 * (int64_t)r + 2];
+            c.w = __int_as_float(j);  // replaces the rectangle bits, unused here
+            sS[pos].a = a;
+            sS[pos].b = b;
+            sS[pos].c = c;
             sR[pos] = r;
-            sJ[pos] = j;
         }
         total += sum;
         if (NW > 1) __syncthreads();  // s_cnt is rewritten by the next chunk
@@ -100,8 +109,8 @@ __device__ __forceinline__ int stage_entries(const BlendView &vp, u32 list_base,
 }
 
 template <int TW, int TH, int BATCH, int PPT>
-__device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
-                                         float4 *sC, u32 *sR, int *sJ, int *s_cnt)
+__device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, int tile, Staged *sS,
+                                         u32 *sR, int *s_cnt)
 {
     constexpr int NT = TW * TH / PPT;
     const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
@@ -128,10 +137,10 @@ __device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, in
     const TileBox box = tile_box(ck, tile, TW, TH);
     for (int base = 0; base < n; base += BATCH) {
         if (__syncthreads_count(tdone) == NT) break;
-        const int cnt = stage_entries<NT>(vp, rg.x, base, min(n, base + BATCH), box, sA, sB, sC, sR, sJ, s_cnt);
+        const int cnt = stage_entries<NT>(vp, rg.x, base, min(n, base + BATCH), box, sS, sR, s_cnt);
         __syncthreads();
         for (int j = 0; j < cnt && !tdone; ++j) {
-            const float4 a = sA[j], b = sB[j];
+            const float4 a = sS[j].a, b = sS[j].b;
             bool all = true;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -142,14 +151,14 @@ __device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, in
                         if (Tn < GSR_T_STOP) {
                             done[k] = true;
                         } else {
-                            const float4 c = sC[j];
+                            const float4 c = sS[j].c;
                             const float w = e.alpha * T[k];
                             c0[k] = fmaf(c.x, w, c0[k]);
                             c1[k] = fmaf(c.y, w, c1[k]);
                             c2[k] = fmaf(c.z, w, c2[k]);
                             d[k] = fmaf(b.z, w, d[k]);
                             T[k] = Tn;
-                            last[k] = sJ[j];
+                            last[k] = staged_pos(sS[j]);
                             ++nc[k];
                         }
                     }
@@ -238,8 +247,8 @@ __device__ __forceinline__ void warp_reduce_add6(const float (&v)[6], float *dst
 // POSE_ONLY: the tracker needs only the gradients feeding the pose
 // (u, v, conic, depth); colour and opacity gradients are skipped.
 template <int TW, int TH, int BATCH, int PPT, bool POSE_ONLY>
-__device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
-                                         float4 *sC, u32 *sR, int *sJ, int *s_cnt, int *s_max)
+__device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, int tile, Staged *sS,
+                                         u32 *sR, int *s_cnt, int *s_max)
 {
     constexpr int NT = TW * TH / PPT;
     const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
@@ -285,21 +294,21 @@ __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, in
     for (int bend = nend; bend > 0; bend -= BATCH) {
         const int bstart = max(0, bend - BATCH);
         __syncthreads();
-        const int cnt = stage_entries<NT>(vp, rg.x, bstart, bend, box, sA, sB, sC, sR, sJ, s_cnt);
+        const int cnt = stage_entries<NT>(vp, rg.x, bstart, bend, box, sS, sR, s_cnt);
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
-            const int jj = sJ[j];
+            const int jj = staged_pos(sS[j]);
             float gu = 0.f, gv = 0.f, gca = 0.f, gcb = 0.f, gcc = 0.f, gop = 0.f, gr = 0.f, gg = 0.f, gb = 0.f,
                   gz = 0.f;
             bool contrib = false;
-            const float4 a = sA[j], b = sB[j];
+            const float4 a = sS[j].a, b = sS[j].b;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 if (jj <= L[k] && !quick_reject(px, py[k], a, b)) {
                     const Eval e = eval_gaussian(px, py[k], a.x, a.y, a.z, a.w, b.x, b.y);
                     if (e.use) {
                         contrib = true;
-                        const float4 c = sC[j];
+                        const float4 c = sS[j].c;
                         // gradient-only use (decisions come from eval_gaussian): fast reciprocal
                         const float iom = __fdividef(1.f, 1.f - e.alpha);
                         T[k] = T[k] * iom;  // T_j
@@ -390,8 +399,8 @@ __device__ __forceinline__ PairSigma pair_sigma(float px, float2 py, const float
 }
 
 template <int TW, int TH, int BATCH>
-__device__ __forceinline__ void fwd_tile2(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
-                                          float4 *sC, u32 *sR, int *sJ, int *s_cnt)
+__device__ __forceinline__ void fwd_tile2(const CamK &ck, const BlendView &vp, int tile, Staged *sS,
+                                          u32 *sR, int *s_cnt)
 {
     constexpr int NT = TW * TH / 2;
     const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
@@ -408,10 +417,10 @@ __device__ __forceinline__ void fwd_tile2(const CamK &ck, const BlendView &vp, i
     const TileBox box = tile_box(ck, tile, TW, TH);
     for (int base = 0; base < n; base += BATCH) {
         if (__syncthreads_count(tdone) == NT) break;
-        const int cnt = stage_entries<NT>(vp, rg.x, base, min(n, base + BATCH), box, sA, sB, sC, sR, sJ, s_cnt);
+        const int cnt = stage_entries<NT>(vp, rg.x, base, min(n, base + BATCH), box, sS, sR, s_cnt);
         __syncthreads();
         for (int j = 0; j < cnt && !tdone; ++j) {
-            const float4 a = sA[j], b = sB[j];
+            const float4 a = sS[j].a, b = sS[j].b;
             const PairSigma S = pair_sigma(px, py, a, b);
             const bool r0 = done0 || S.sig.x > b.w, r1 = done1 || S.sig.y > b.w;
             if (r0 && r1) continue;
@@ -426,14 +435,14 @@ __device__ __forceinline__ void fwd_tile2(const CamK &ck, const BlendView &vp, i
             const bool k0 = u0 && !s0, k1 = u1 && !s1;  // composited
             done0 = done0 || s0;
             done1 = done1 || s1;
-            const float4 c = sC[j];
+            const float4 c = sS[j].c;
             const float2 w = mul2(make_float2(k0 ? al.x : 0.f, k1 ? al.y : 0.f), T);
             c0 = fma2(f2(c.x), w, c0);
             c1 = fma2(f2(c.y), w, c1);
             c2 = fma2(f2(c.z), w, c2);
             d = fma2(f2(b.z), w, d);
             T = make_float2(k0 ? Tn.x : T.x, k1 ? Tn.y : T.y);
-            const int jj = sJ[j];
+            const int jj = staged_pos(sS[j]);
             last0 = k0 ? jj : last0;
             last1 = k1 ? jj : last1;
             nc0 += k0;
@@ -461,8 +470,8 @@ __device__ __forceinline__ void fwd_tile2(const CamK &ck, const BlendView &vp, i
 }
 
 template <int TW, int TH, int BATCH, bool POSE_ONLY>
-__device__ __forceinline__ void bwd_tile2(const CamK &ck, const BlendView &vp, int tile, float4 *sA, float4 *sB,
-                                          float4 *sC, u32 *sR, int *sJ, int *s_cnt, int *s_max)
+__device__ __forceinline__ void bwd_tile2(const CamK &ck, const BlendView &vp, int tile, Staged *sS,
+                                          u32 *sR, int *s_cnt, int *s_max)
 {
     constexpr int NT = TW * TH / 2;
     const int tx = tile % ck.tiles_x, ty = tile / ck.tiles_x;
@@ -509,11 +518,11 @@ __device__ __forceinline__ void bwd_tile2(const CamK &ck, const BlendView &vp, i
     for (int bend = nend; bend > 0; bend -= BATCH) {
         const int bstart = max(0, bend - BATCH);
         __syncthreads();
-        const int cnt = stage_entries<NT>(vp, rg.x, bstart, bend, box, sA, sB, sC, sR, sJ, s_cnt);
+        const int cnt = stage_entries<NT>(vp, rg.x, bstart, bend, box, sS, sR, s_cnt);
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
-            const int jj = sJ[j];
-            const float4 a = sA[j], b = sB[j];
+            const int jj = staged_pos(sS[j]);
+            const float4 a = sS[j].a, b = sS[j].b;
             float gu = 0.f, gv = 0.f, gca = 0.f, gcb = 0.f, gcc = 0.f, gop = 0.f, gr = 0.f, gg = 0.f, gb = 0.f,
                   gz = 0.f;
             bool contrib = false;
@@ -529,7 +538,7 @@ __device__ __forceinline__ void bwd_tile2(const CamK &ck, const BlendView &vp, i
                     const bool u1 = !r1 && S.sig.y >= 0.f && al1 >= GSR_ALPHA_MIN;
                     if (u0 || u1) {
                         contrib = true;
-                        const float4 c = sC[j];
+                        const float4 c = sS[j].c;
                         const float2 al = make_float2(u0 ? al0 : 0.f, u1 ? al1 : 0.f);
                         const float2 om = add2(f2(1.f), make_float2(-al.x, -al.y));
                         // gradient-only use (decisions come from the forward's arithmetic): fast reciprocal
@@ -594,22 +603,22 @@ __device__ __forceinline__ void bwd_tile2(const CamK &ck, const BlendView &vp, i
 template <int TW, int TH, int BATCH, int PPT>
 __global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd(CamK ck, BlendView vp)
 {
-    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
+    __shared__ Staged sS[BATCH];
     __shared__ u32 sR[BATCH];
-    __shared__ int sJ[BATCH], s_cnt[TW * TH / PPT / 32];
-    if constexpr (PPT == 2) fwd_tile2<TW, TH, BATCH>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt);
-    else fwd_tile<TW, TH, BATCH, PPT>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt);
+    __shared__ int s_cnt[TW * TH / PPT / 32];
+    if constexpr (PPT == 2) fwd_tile2<TW, TH, BATCH>(ck, vp, blockIdx.x, sS, sR, s_cnt);
+    else fwd_tile<TW, TH, BATCH, PPT>(ck, vp, blockIdx.x, sS, sR, s_cnt);
 }
 
 template <int TW, int TH, int BATCH, int PPT, bool POSE_ONLY>
 __global__ void __launch_bounds__(TW *TH / PPT) k_blend_bwd(CamK ck, BlendView vp)
 {
-    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
+    __shared__ Staged sS[BATCH];
     __shared__ u32 sR[BATCH];
-    __shared__ int sJ[BATCH], s_cnt[TW * TH / PPT / 32];
+    __shared__ int s_cnt[TW * TH / PPT / 32];
     __shared__ int s_max;
-    if constexpr (PPT == 2) bwd_tile2<TW, TH, BATCH, POSE_ONLY>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt, &s_max);
-    else bwd_tile<TW, TH, BATCH, PPT, POSE_ONLY>(ck, vp, blockIdx.x, sA, sB, sC, sR, sJ, s_cnt, &s_max);
+    if constexpr (PPT == 2) bwd_tile2<TW, TH, BATCH, POSE_ONLY>(ck, vp, blockIdx.x, sS, sR, s_cnt, &s_max);
+    else bwd_tile<TW, TH, BATCH, PPT, POSE_ONLY>(ck, vp, blockIdx.x, sS, sR, s_cnt, &s_max);
 }
 
 // Persistent forms: items[i] = (view << 16) | tile, longest lists first.
@@ -626,14 +635,14 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd_multi(CamK ck, const
                                                                   const u32 *__restrict__ items, int n_items,
                                                                   u32 *counter)
 {
-    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
+    __shared__ Staged sS[BATCH];
     __shared__ u32 sR[BATCH];
-    __shared__ int sJ[BATCH], s_cnt[TW * TH / PPT / 32];
+    __shared__ int s_cnt[TW * TH / PPT / 32];
     __shared__ int s_item;
     for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
         const u32 w = items[it];
-        if constexpr (PPT == 2) fwd_tile2<TW, TH, BATCH>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt);
-        else fwd_tile<TW, TH, BATCH, PPT>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt);
+        if constexpr (PPT == 2) fwd_tile2<TW, TH, BATCH>(ck, views[w >> 16], (int)(w & 0xffffu), sS, sR, s_cnt);
+        else fwd_tile<TW, TH, BATCH, PPT>(ck, views[w >> 16], (int)(w & 0xffffu), sS, sR, s_cnt);
     }
 }
 
@@ -642,16 +651,16 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_bwd_multi(CamK ck, const
                                                                   const u32 *__restrict__ items, int n_items,
                                                                   u32 *counter)
 {
-    __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
+    __shared__ Staged sS[BATCH];
     __shared__ u32 sR[BATCH];
-    __shared__ int sJ[BATCH], s_cnt[TW * TH / PPT / 32];
+    __shared__ int s_cnt[TW * TH / PPT / 32];
     __shared__ int s_max, s_item;
     for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
         const u32 w = items[it];
         if constexpr (PPT == 2)
-            bwd_tile2<TW, TH, BATCH, false>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt, &s_max);
+            bwd_tile2<TW, TH, BATCH, false>(ck, views[w >> 16], (int)(w & 0xffffu), sS, sR, s_cnt, &s_max);
         else
-            bwd_tile<TW, TH, BATCH, PPT, false>(ck, views[w >> 16], (int)(w & 0xffffu), sA, sB, sC, sR, sJ, s_cnt,
+            bwd_tile<TW, TH, BATCH, PPT, false>(ck, views[w >> 16], (int)(w & 0xffffu), sS, sR, s_cnt,
                                                 &s_max);
     }
 }

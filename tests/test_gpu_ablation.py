@@ -1,26 +1,35 @@
-"""The synthetic mask / L_reg ablations run end to end (20-frame sequence with
-2 % gross depth outliers); the full configuration tracks within 3 cm.  The
-printed table is the synthetic counterpart of the paper's ablations, not a
-reproduction of its numbers."""
+"""Synthetic counterparts of the paper's tracking-mask and L_reg ablations.
+
+Sequences (ablation.ablations_over_seeds): room scenes of 300k Gaussians,
+seeds 100-102, 24 frames each with about 3 cm / 2 degrees between frames (so
+each frame shows regions the map has not seen yet, which the alpha mask is
+there to discount), 2 % gross depth outliers and flying pixels at half of the
+depth-edge pixels (which the inlier mask is there to reject).  Both
+ablations run the online SLAM loop once per variant and seed.
+
+Measured on GB300 (mean over the three seeds): the alpha mask raises the
+merged map's PSNR in every seed, with and without the inlier mask; no
+direction of the tracking error (ATE) or of the L_reg weight holds across
+the seeds.  The test asserts what held: the alpha mask's mean PSNR gain, with
+and without the inlier mask, and tracking within 3 cm in every run.  The
+variants' tracking losses themselves are compared with the oracle in
+test_gpu_loss.py."""
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 
-def test_tracking_mask_and_lreg_ablations_run():
-    from paper_2312_10070_gb300 import ablation, api, slam, synth as S
-    spec = S.camera_room()
-    scene = S.room_scene(300_000, seed=100)
-    qs, ts = S.room_trajectory(seed=100, n_frames=20, step_m=0.02, max_step_deg=1.5)
-    gt = [(np.asarray(q, np.float64), np.asarray(t, np.float64)) for q, t in zip(qs, ts)]
-    frames = ablation.synthetic_frames(scene, (qs, ts), spec, seed=500, outlier_frac=0.02)
-    base = slam.SLAMConfig(track_iters=60, map_iters_first=100, map_iters=40, capacity=1_500_000,
-                           seed=api.SeedConfig(m_u=100_000, m_c=50_000, m_k=30_000))
-    masks = ablation.tracking_mask_ablation(frames, gt, spec, base)
-    lreg = ablation.lreg_ablation(frames, gt, spec, base)
-    print(masks, lreg)
-    assert [(r["alpha_mask"], r["inlier_mask"]) for r in masks] == list(ablation.MASK_VARIANTS)
-    for r in masks + lreg:
-        assert np.isfinite(r["ate_cm"]) and np.isfinite(r["psnr_db"])
-    assert masks[-1]["ate_cm"] < 3.0 and lreg[0]["ate_cm"] < 3.0
+def test_tracking_mask_and_lreg_ablations_over_seeds():
+    from paper_2312_10070_gb300 import ablation
+    per_seed, summary = ablation.ablations_over_seeds([100, 101, 102], n_frames=24)
+    for k, v in summary.items():
+        print(f"{k}: ATE {v['ate_cm_mean']:.2f} +- {v['ate_cm_std']:.2f} cm {np.round(v['ate_cm'], 2).tolist()}, "
+              f"PSNR {v['psnr_db_mean']:.2f} +- {v['psnr_db_std']:.2f} dB {np.round(v['psnr_db'], 2).tolist()}")
+    for p in per_seed:
+        assert [(r["alpha_mask"], r["inlier_mask"]) for r in p["tracking_masks"]] == list(ablation.MASK_VARIANTS)
+        for r in p["tracking_masks"] + p["l_reg"]:
+            assert np.isfinite(r["ate_cm"]) and np.isfinite(r["psnr_db"]) and r["ate_cm"] < 3.0, (p["seed"], r)
+    for inlier in (0, 1):
+        off, on = summary[f"alpha=0,inlier={inlier}"], summary[f"alpha=1,inlier={inlier}"]
+        assert on["psnr_db_mean"] > off["psnr_db_mean"], (inlier, off, on)
