@@ -374,10 +374,8 @@ gsr_status launch_perturb_pose(gsr_ctx *ctx, float *d_pose, const float *xi, cud
 gsr_status launch_pose_grad_xi(gsr_ctx *ctx, float *g6, const float *xi, cudaStream_t s);
 // Projection + binning into V; returns after enqueueing (no sync unless
 // allow_grow, which reads the instance count back once to size V)
-// after_project (nullable): recorded on s once the projection (visibility
-// flags, records) is enqueued, before the rest of the binning
 gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK &ck, const float *d_pose,
-                       bool allow_grow, cudaStream_t s, cudaEvent_t after_project = nullptr);
+                       bool allow_grow, cudaStream_t s);
 gsr_status run_blend_forward(gsr_ctx *ctx, const Params &P, const CamK &ck, gsr_render_out *out,
                              cudaStream_t s);
 gsr_status run_blend_backward(gsr_ctx *ctx, const CamK &ck, const gsr_render_out *saved,
@@ -419,16 +417,9 @@ gsr_status adam_lreg_final_step(gsr_ctx *ctx, const float *part, int nb, float s
                                 int32_t *step, cudaStream_t s);
 // one-keyframe step: projection backward of every Gaussian fused with its Adam
 // update and L_reg (the gradients never reach memory)
-// visible_only: Gaussians outside the view are left to run_adam_culled
 gsr_status run_project_backward_adam(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians_mut *g, gsr_adam_state *st,
                                      const gsr_adam_opts *o, const CamK &ck, const float *d_pose,
-                                     float *loss_reg_dev, cudaStream_t s, bool visible_only = false);
-// The one-keyframe step's Adam + L_reg of the Gaussians the projection culled
-// (zero render gradient), from the visibility flags alone, so it can run
-// beside the binning and the blends; its L_reg partial sums follow the fused
-// kernel's in the context's partial-sum buffer.
-gsr_status run_adam_culled(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians_mut *g, gsr_adam_state *st,
-                           const gsr_adam_opts *o, cudaStream_t s);
+                                     float *loss_reg_dev, cudaStream_t s);
 gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads *gr,
                     gsr_adam_state *st, const gsr_adam_opts *o, float *loss_reg_dev, cudaStream_t s);
 gsr_status run_pose_adam(gsr_ctx *ctx, float *d_pose, const float *d_grad6, float *m6, float *v6,

@@ -793,8 +793,7 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd_adam(Params P, gsr_gauss
                                                           const float *__restrict__ pose,
                                                           const int32_t *__restrict__ rank_of_gid,
                                                           const float *__restrict__ g2d, gsr_adam_state st,
-                                                          gsr_adam_opts o, float *__restrict__ lreg_part,
-                                                          int visible_only)
+                                                          gsr_adam_opts o, float *__restrict__ lreg_part)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float lreg = 0.f;
@@ -805,8 +804,8 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd_adam(Params P, gsr_gauss
         s_bc[1] = 1.f / (1.f - powf(o.beta2, (float)t));
     }
     __syncthreads();
-    const int32_t r = i < P.n ? rank_of_gid[i] : -1;
-    if (i < P.n && (r >= 0 || !visible_only)) {
+    if (i < P.n) {
+        const int32_t r = rank_of_gid[i];
         asm volatile("prefetch.global.L2 [%0];" ::"l"(P.mean + 3 * i));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(P.log_scale + 3 * i));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(P.quat + 4 * i));
@@ -932,79 +931,6 @@ __global__ void k_lists_to_gid(int64_t cap_i, const u32 *__restrict__ d_n, const
     if (i < cap_i && i < (int64_t)*d_n) out[i] = rank2gid[tvals[i]];
 }
 
-// Adam + L_reg of the Gaussians the projection culled (flag 0): their render
-// gradient is zero, so only the log-scales' L_reg gradient drives them; the
-// same arithmetic as the fused kernel's culled Gaussians.  Reads the step
-// counter t - 1 like the fused kernel; the final reduction advances it.
-__global__ void __launch_bounds__(256) k_adam_culled(gsr_gaussians_mut gw, const u32 *__restrict__ flag,
-                                                     gsr_adam_state st, gsr_adam_opts o,
-                                                     float *__restrict__ lreg_part)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float lreg = 0.f;
-    __shared__ float s_bc[2];
-    if (threadIdx.x == 0) {
-        const int t = *st.step + 1;
-        s_bc[0] = 1.f / (1.f - powf(o.beta1, (float)t));
-        s_bc[1] = 1.f / (1.f - powf(o.beta2, (float)t));
-    }
-    __syncthreads();
-    if (i < gw.n && !flag[i]) {
-        const float ib1 = s_bc[0], ib2 = s_bc[1];
-        float p[3], m[3], v[3];
-        const float gls[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            p[k] = gw.log_scale[3 * i + k];
-            m[k] = st.m_log_scale[3 * i + k];
-            v[k] = st.v_log_scale[3 * i + k];
-        }
-        lreg = adam_log_scales3<true>(p, gls, m, v, o.w_reg / (float)gw.n, o.lr_log_scale, o, ib1, ib2);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            gw.log_scale[3 * i + k] = p[k];
-            st.m_log_scale[3 * i + k] = m[k];
-            st.v_log_scale[3 * i + k] = v[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float pm = gw.mean[3 * i + k], mm = st.m_mean[3 * i + k], vm = st.v_mean[3 * i + k];
-            adam_update_fast(pm, 0.f, mm, vm, o.lr_mean, o.beta1, o.beta2, o.eps, ib1, ib2);
-            gw.mean[3 * i + k] = pm;
-            st.m_mean[3 * i + k] = mm;
-            st.v_mean[3 * i + k] = vm;
-            float pc = gw.rgb[3 * i + k], mc = st.m_rgb[3 * i + k], vc = st.v_rgb[3 * i + k];
-            adam_update_fast(pc, 0.f, mc, vc, o.lr_rgb, o.beta1, o.beta2, o.eps, ib1, ib2);
-            gw.rgb[3 * i + k] = pc;
-            st.m_rgb[3 * i + k] = mc;
-            st.v_rgb[3 * i + k] = vc;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float pq = gw.quat[4 * i + k], mq = st.m_quat[4 * i + k], vq = st.v_quat[4 * i + k];
-            adam_update_fast(pq, 0.f, mq, vq, o.lr_quat, o.beta1, o.beta2, o.eps, ib1, ib2);
-            gw.quat[4 * i + k] = pq;
-            st.m_quat[4 * i + k] = mq;
-            st.v_quat[4 * i + k] = vq;
-        }
-        float po = gw.opacity_logit[i], mo = st.m_opacity_logit[i], vo = st.v_opacity_logit[i];
-        adam_update_fast(po, 0.f, mo, vo, o.lr_opacity, o.beta1, o.beta2, o.eps, ib1, ib2);
-        gw.opacity_logit[i] = po;
-        st.m_opacity_logit[i] = mo;
-        st.v_opacity_logit[i] = vo;
-    }
-    __shared__ float red[8];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) lreg += __shfl_down_sync(0xffffffffu, lreg, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lreg;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int k = 0; k < 8; ++k) t += red[k];
-        lreg_part[blockIdx.x] = t;
-    }
-}
-
 __global__ void k_depth_bits(int64_t n, const u32 *__restrict__ flag, const float4 *__restrict__ rec,
                              u32 *__restrict__ out)
 {
@@ -1072,7 +998,7 @@ static int bits_for(int64_t v)
 }
 
 gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK &ck, const float *d_pose,
-                       bool allow_grow, cudaStream_t s, cudaEvent_t after_project)
+                       bool allow_grow, cudaStream_t s)
 {
     const int64_t n = P.n;
     const int64_t tiles = (int64_t)ck.tiles_x * ck.tiles_y;
@@ -1103,7 +1029,6 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
     k_project<<<nb, 256, 0, s>>>(P, ck, d_pose, (float4 *)V.rec.p, (u32 *)V.flag.p, (int32_t *)V.rank_of_gid.p);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
-    if (after_project) GSR_CUDA(ctx, cudaEventRecord(after_project, s));
     GSR_TRY(scan_exclusive(ctx, (u32 *)V.flag.p, (u32 *)V.compact.p, n, nullptr, cnt + CNT_VISIBLE, s,
                            &V.scan_tmp));
     k_compact<<<nb, 256, 0, s>>>(n, (u32 *)V.flag.p, (u32 *)V.compact.p, (float4 *)V.rec.p, (u32 *)V.dkeys[0].p,
@@ -1187,7 +1112,7 @@ gsr_status run_project_backward(gsr_ctx *ctx, ViewScratch &V, const Params &P, c
 
 gsr_status run_project_backward_adam(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians_mut *g, gsr_adam_state *st,
                                      const gsr_adam_opts *o, const CamK &ck, const float *d_pose,
-                                     float *loss_reg_dev, cudaStream_t s, bool visible_only)
+                                     float *loss_reg_dev, cudaStream_t s)
 {
     const int64_t n = g->n;
     const unsigned nb = (unsigned)ceil_div(n > 0 ? n : 1, 256);
@@ -1195,24 +1120,11 @@ gsr_status run_project_backward_adam(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians
     float *part = (float *)ctx->pose_part.p;
     const Params P{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, n};
     k_project_bwd_adam<<<nb, 256, 0, s>>>(P, *g, ck, d_pose, (const int32_t *)V.rank_of_gid.p, (const float *)V.g2d.p,
-                                          *st, *o, part, visible_only ? 1 : 0);
+                                          *st, *o, part);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     if (loss_reg_dev)
         GSR_TRY(adam_lreg_final_step(ctx, part, (int)nb, o->w_reg / (float)(n > 0 ? n : 1), loss_reg_dev, st->step, s));
-    return GSR_OK;
-}
-
-gsr_status run_adam_culled(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians_mut *g, gsr_adam_state *st,
-                           const gsr_adam_opts *o, cudaStream_t s)
-{
-    const int64_t n = g->n;
-    const unsigned nb = (unsigned)ceil_div(n > 0 ? n : 1, 256);
-    GSR_TRY(ensure_buf(ctx, ctx->pose_part, sizeof(float) * 6 * nb));
-    float *part = (float *)ctx->pose_part.p + nb;  // after the fused kernel's partial sums
-    k_adam_culled<<<nb, 256, 0, s>>>(*g, (const u32 *)V.flag.p, *st, *o, part);
-    ctx->launches += 1;
-    GSR_LAUNCHED(ctx);
     return GSR_OK;
 }
 

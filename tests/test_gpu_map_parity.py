@@ -100,9 +100,10 @@ def check_first_step(g, st, sc0, grads, cfg, label):
         m = getattr(st.m, k).cpu().numpy().reshape(-1).astype(np.float64)
         v = getattr(st.v, k).cpu().numpy().reshape(-1).astype(np.float64)
         ok, worst = grad_close(m / (1 - a.beta1), gr)
-        print(f"{label} {k}: gradient (first moment) worst ratio {worst:.3f}, strict-floor pass "
-              f"{strict_pass_fraction(m / (1 - a.beta1), gr):.5f}")
+        strict = strict_pass_fraction(m / (1 - a.beta1), gr)
+        print(f"{label} {k}: gradient (first moment) worst ratio {worst:.3f}, strict-floor pass {strict:.5f}")
         assert ok, (label, k, "first moment", worst)
+        assert strict >= 0.995, (label, k, "strict floor", strict)
         ok, worst = grad_close(np.sqrt(v / (1 - a.beta2)), np.abs(gr))
         assert ok, (label, k, "second moment", worst)
         th0 = getattr(sc0, k).reshape(-1)
