@@ -520,6 +520,8 @@ __device__ __forceinline__ void bwd_tile2(const CamK &ck, const BlendView &vp, i
         __syncthreads();
         const int cnt = stage_entries<NT>(vp, rg.x, bstart, bend, box, sS, sR, s_cnt);
         __syncthreads();
+        // two entries per trip: the next entry's loads and sigma overlap this one's reduction
+#pragma unroll 2
         for (int j = cnt - 1; j >= 0; --j) {
             const int jj = staged_pos(sS[j]);
             const float4 a = sS[j].a, b = sS[j].b;

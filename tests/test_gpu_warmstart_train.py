@@ -4,10 +4,10 @@ tracker (falling back to the plain initial pose when the network's pose has
 the larger tracking loss) needs no more iterations and fewer wall-clock ms
 per frame than the plain one, network and fallback test included.
 
-Training rooms: room_scene(200k Gaussians), seeds 1000-1063, 24 frames each
+Training rooms: room_scene(200k Gaussians), seeds 1000-1095, 24 frames each
 (trajectories with about 4 cm / 3 degrees between frames), 32 initial poses
-per frame (49152 samples, 30 GB of inputs on the device); initial pose = true
-pose moved by a random twist of up to 5 cm / 3 degrees; 4000 Adam steps of
+per frame (73728 samples, 45 GB of inputs on the device); initial pose = true
+pose moved by a random twist of up to 5 cm / 3 degrees; 6000 Adam steps of
 256.  Held-out rooms: seeds 2000-2002, 16 frames x 4 initial poses.
 """
 import time
@@ -27,7 +27,7 @@ def trained():
     ctx_f = api.Context(tile=(16, 16), batch=256)
     ctx_l = api.Context(tile=(16, 16), batch=64)
     rng = np.random.default_rng(5)
-    n_rooms, frames, per_frame = 64, 24, 32
+    n_rooms, frames, per_frame = 96, 24, 32
     train = W.Samples(n_rooms * frames * per_frame, seed=1)
     for r in range(n_rooms):
         seed = 1000 + r
@@ -42,7 +42,7 @@ def trained():
         W.add_frames(ev, ctx_f, ctx_l, g, spec, poses, 4, np.random.default_rng(seed), noise_seed=10 * seed)
         evals.append((g, ev))
     net = W.WarmStartNet(max_batch=256, seed=7)
-    losses = W.train(net, train, steps=4000, batch=256, lr=5e-4, seed=8, log_every=500)
+    losses = W.train(net, train, steps=6000, batch=256, lr=5e-4, seed=8, log_every=500)
     return dict(W=W, api=api, spec=spec, ctx_f=ctx_f, ctx_l=ctx_l, net=net, evals=evals, losses=losses)
 
 
