@@ -32,6 +32,16 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// 8-byte form (both addresses 8-byte aligned); ok = false writes zeros
+__device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src, bool ok)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 constexpr int SHALO = 5;                 // window radius
 constexpr int TX = 32, TY = 48;          // output tile
@@ -119,17 +129,67 @@ __device__ __forceinline__ void vsum(const float (*hq)[LH][HP], int r0, int c, c
     }
 }
 
-// The five window sums are formed in two groups (mu_x, mu_y, E[x^2]) and
-// (E[y^2], E[xy]) through three horizontal-sum planes, so a block needs
-// 43 KB of shared memory and the whole 1200x680 grid (570 blocks) fits in one
-// wave at four blocks per SM.
+// Packed forms: two planes summed at once in float pairs (fma.rn.f32x2 rounds
+// each half like fmaf, in the same order, so the sums equal the scalar ones).
+__device__ __forceinline__ float2 wfma2(float w, float2 q, float2 a) { return __ffma2_rn(make_float2(w, w), q, a); }
+
+template <typename F>
+__device__ __forceinline__ void hsum2(const float2 (&v)[HSEG + 10], const float (&wk)[11], F f, float2 (&out)[HSEG])
+{
+#pragma unroll
+    for (int j = 0; j < HSEG; ++j) out[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < HSEG + 10; ++i) {
+        const float2 q = f(v[i]);
+#pragma unroll
+        for (int j = 0; j < HSEG; ++j)
+            if (i - j >= 0 && i - j <= 10) out[j] = wfma2(wk[i - j], q, out[j]);
+    }
+}
+
+__device__ __forceinline__ void vsum2(const float2 (*hq)[HP], int r0, int c, const float (&wk)[11], float2 (&out)[VSEG])
+{
+    float2 col[VSEG + 10];
+#pragma unroll
+    for (int i = 0; i < VSEG + 10; ++i) col[i] = hq[r0 + i][c];
+#pragma unroll
+    for (int j = 0; j < VSEG; ++j) {
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 11; ++k) a = wfma2(wk[k], col[j + k], a);
+        out[j] = a;
+    }
+}
+
+__device__ __forceinline__ void vsum1(const float (*hq)[HP], int r0, int c, const float (&wk)[11], float (&out)[VSEG])
+{
+    float col[VSEG + 10];
+#pragma unroll
+    for (int i = 0; i < VSEG + 10; ++i) col[i] = hq[r0 + i][c];
+#pragma unroll
+    for (int j = 0; j < VSEG; ++j) {
+        float a = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) a = fmaf(wk[k], col[j + k], a);
+        out[j] = a;
+    }
+}
+
+// The five window sums are formed in two groups through float-pair planes:
+// (mu_x, mu_y) packed plus E[x^2] scalar, then (E[y^2], E[xy]) packed; the
+// inputs sit in shared memory as (x, y) pairs.  A block needs 43 KB of shared
+// memory and the whole 1200x680 grid (570 blocks) fits in one wave at four
+// blocks per SM.  The adjoint maps are written as the pair (dS/dmu_x,
+// dS/dE[x^2]) per channel (planes 2 ch, 2 ch + 1, interleaved) and dS/dE[xy]
+// (plane 6 + ch).
 __global__ void __launch_bounds__(256, 4) k_ssim_fwd(int W, int H, const float *__restrict__ x, const float *__restrict__ y,
                                                   const float *__restrict__ dep, const float *__restrict__ dep_t,
                                                   float gscale, float *__restrict__ P, float *__restrict__ part,
                                                   u32 *__restrict__ nvalid)
 {
-    __shared__ float sx[LH][LP], sy[LH][LP];
-    __shared__ float hq[3][LH][HP];
+    __shared__ float2 sxy[LH][LP];
+    __shared__ float2 hp[LH][HP];
+    __shared__ float hs[LH][HP];
     float wk[11];
 #pragma unroll
     for (int k = 0; k < 11; ++k) wk[k] = wtap(k);
@@ -140,7 +200,7 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(int W, int H, const float *
     const float C1 = 1e-4f, C2 = 9e-4f;
     float acc[3] = {0.f, 0.f, 0.f};  // SSIM sum, |x - y| sum, valid |D^ - D| sum
     const int hc = ((int)threadIdx.x >> 5) * HSEG, hlane = (int)threadIdx.x & 31;
-    // channel ch + 1's halo is copied into sx / sy asynchronously while channel
+    // channel ch + 1's halo is copied into sxy asynchronously while channel
     // ch's vertical sums and outputs are computed (its planes are read out by then)
     auto load_channel = [&](int ch) {
 #pragma unroll 1
@@ -149,8 +209,8 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(int W, int H, const float *
             const int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
             const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
             const int64_t q = ok ? (int64_t)ch * HW + (int64_t)yy * W + xx : 0;
-            cp_async4(&sx[rr][cc], x + q, ok);
-            cp_async4(&sy[rr][cc], y + q, ok);
+            cp_async4(&sxy[rr][cc].x, x + q, ok);
+            cp_async4(&sxy[rr][cc].y, y + q, ok);
         }
     };
     load_channel(0);
@@ -158,65 +218,65 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(int W, int H, const float *
         cp_async_wait_all();
         __syncthreads();
         for (int hr = hlane; hr < LH; hr += 32) {
-            float xv[HSEG + 10], yv[HSEG + 10], o[HSEG];
+            float2 v[HSEG + 10], o[HSEG];
+            float xv[HSEG + 10], o1[HSEG];
 #pragma unroll
             for (int i = 0; i < HSEG + 10; ++i) {
-                xv[i] = sx[hr][hc + i];
-                yv[i] = sy[hr][hc + i];
+                v[i] = sxy[hr][hc + i];
+                xv[i] = v[i].x;
             }
-            hsum(xv, yv, wk, [](float a, float) { return a; }, o);
+            hsum2(v, wk, [](float2 a) { return a; }, o);
 #pragma unroll
-            for (int j = 0; j < HSEG; ++j) hq[0][hr][hc + j] = o[j];
-            hsum(xv, yv, wk, [](float, float b) { return b; }, o);
+            for (int j = 0; j < HSEG; ++j) hp[hr][hc + j] = o[j];
+            hsum(xv, xv, wk, [](float a, float) { return a * a; }, o1);
 #pragma unroll
-            for (int j = 0; j < HSEG; ++j) hq[1][hr][hc + j] = o[j];
-            hsum(xv, yv, wk, [](float a, float) { return a * a; }, o);
-#pragma unroll
-            for (int j = 0; j < HSEG; ++j) hq[2][hr][hc + j] = o[j];
+            for (int j = 0; j < HSEG; ++j) hs[hr][hc + j] = o1[j];
         }
         __syncthreads();
-        float ma[3][VSEG];
-        vsum<3>(hq, r0, c, wk, ma);
+        float2 mxy[VSEG];
+        float e11[VSEG];
+        vsum2(hp, r0, c, wk, mxy);
+        vsum1(hs, r0, c, wk, e11);
         __syncthreads();
         for (int hr = hlane; hr < LH; hr += 32) {
-            float xv[HSEG + 10], yv[HSEG + 10], o[HSEG];
+            float2 v[HSEG + 10], o[HSEG];
 #pragma unroll
-            for (int i = 0; i < HSEG + 10; ++i) {
-                xv[i] = sx[hr][hc + i];
-                yv[i] = sy[hr][hc + i];
-            }
-            hsum(xv, yv, wk, [](float, float b) { return b * b; }, o);
+            for (int i = 0; i < HSEG + 10; ++i) v[i] = sxy[hr][hc + i];
+            // (y^2, x y)
+            hsum2(v, wk, [](float2 a) { return __fmul2_rn(make_float2(a.y, a.x), make_float2(a.y, a.y)); }, o);
 #pragma unroll
-            for (int j = 0; j < HSEG; ++j) hq[0][hr][hc + j] = o[j];
-            hsum(xv, yv, wk, [](float a, float b) { return a * b; }, o);
-#pragma unroll
-            for (int j = 0; j < HSEG; ++j) hq[1][hr][hc + j] = o[j];
+            for (int j = 0; j < HSEG; ++j) hp[hr][hc + j] = o[j];
         }
-        float l1 = 0.f;  // this thread's |x - y| of the channel, read before sx / sy are refilled
+        float l1 = 0.f;  // this thread's |x - y| of the channel, read before sxy is refilled
 #pragma unroll
         for (int j = 0; j < VSEG; ++j)
-            if (gx < W && oy + r0 + j < H) l1 += fabsf(sx[r0 + j + SHALO][c + SHALO] - sy[r0 + j + SHALO][c + SHALO]);
+            if (gx < W && oy + r0 + j < H) {
+                const float2 v = sxy[r0 + j + SHALO][c + SHALO];
+                l1 += fabsf(v.x - v.y);
+            }
         acc[1] += l1;
         __syncthreads();
         if (ch < 2) load_channel(ch + 1);
-        float mb[2][VSEG];
-        vsum<2>(hq, r0, c, wk, mb);
+        float2 m22[VSEG];  // (E[y^2], E[xy])
+        vsum2(hp, r0, c, wk, m22);
+        float2 *P01 = reinterpret_cast<float2 *>(P) + (int64_t)ch * HW;
+        float *P2 = P + (int64_t)(6 + ch) * HW;
 #pragma unroll
         for (int j = 0; j < VSEG; ++j) {
             const int gy = oy + r0 + j;
             if (gx < W && gy < H) {
-                const float m1 = ma[0][j], m2 = ma[1][j], e11 = ma[2][j], e22 = mb[0][j], e12 = mb[1][j];
+                const float m1 = mxy[j].x, m2 = mxy[j].y, e22 = m22[j].x, e12 = m22[j].y;
                 const float A1 = 2.f * m1 * m2 + C1, A2 = 2.f * (e12 - m1 * m2) + C2;
-                const float B1 = m1 * m1 + m2 * m2 + C1, B2 = (e11 - m1 * m1) + (e22 - m2 * m2) + C2;
+                const float B1 = m1 * m1 + m2 * m2 + C1, B2 = (e11[j] - m1 * m1) + (e22 - m2 * m2) + C2;
                 // B1, B2 >= C1, C2 > 0: fast reciprocals (2 ulp) are ample here
                 const float iB1 = __fdividef(1.f, B1), iB2 = __fdividef(1.f, B2);
                 const float iB = iB1 * iB2;
                 const float S = A1 * A2 * iB;
                 acc[0] += S;
                 const int64_t p = (int64_t)gy * W + gx;
-                P[(3 * ch + 0) * HW + p] = gscale * (2.f * m2 * (A2 - A1) * iB - 2.f * m1 * S * (iB1 - iB2));
-                P[(3 * ch + 1) * HW + p] = gscale * (-S * iB2);
-                P[(3 * ch + 2) * HW + p] = gscale * (2.f * A1 * iB);
+                P01[p] = make_float2(gscale * (2.f * m2 * (A2 - A1) * iB - 2.f * m1 * S * (iB1 - iB2)),
+                                     gscale * (-S * iB2));
+                P2[p] = gscale * (2.f * A1 * iB);
             }
         }
         __syncthreads();
@@ -245,16 +305,21 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(int W, int H, const float *
     }
 }
 
-// The three adjoint maps are blurred one at a time through one loaded plane
-// and one horizontal-sum plane (18 KB of shared memory per block).
-__global__ void __launch_bounds__(256) k_ssim_bwd(int W, int H, const float *__restrict__ x, const float *__restrict__ y,
+// The adjoint maps are blurred per channel in two passes, the pair
+// (dS/dmu_x, dS/dE[x^2]) packed, then dS/dE[xy], each through its own loaded
+// plane and one shared horizontal-sum plane (45 KB of shared memory per
+// block).  The six plane loads are asynchronous copies issued one stage
+// ahead: plane k + 2 is copied while planes k and k + 1 are summed.
+__global__ void __launch_bounds__(256, 4) k_ssim_bwd(int W, int H, const float *__restrict__ x, const float *__restrict__ y,
                                                   const float *__restrict__ dep, const float *__restrict__ dep_t,
                                                   const float *__restrict__ P, float l1s, float dscale,
                                                   const u32 *__restrict__ nvalid, float *__restrict__ d_rgb,
                                                   float *__restrict__ d_dep)
 {
-    __shared__ float sp[LH][LP];
-    __shared__ float hq[1][LH][HP];
+    __shared__ float2 sa[LH][LP];  // (dS/dmu_x, dS/dE[x^2]) of the loaded tile
+    __shared__ float sb[LH][LP];   // dS/dE[xy] of the loaded tile
+    __shared__ float2 hq2[LH][HP];
+    float (*hq)[HP] = reinterpret_cast<float (*)[HP]>(&hq2[0][0]);
     float wk[11];
 #pragma unroll
     for (int k = 0; k < 11; ++k) wk[k] = wtap(k);
@@ -263,51 +328,90 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(int W, int H, const float *__r
     const int gx = ox + c;
     const int64_t HW = (int64_t)W * H;
     const int hc = ((int)threadIdx.x >> 5) * HSEG, hlane = (int)threadIdx.x & 31;
-    for (int ch = 0; ch < 3; ++ch) {
-        float b[3][VSEG];
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            for (int i = threadIdx.x; i < LH * LW; i += 256) {
-                const int rr = i / LW, cc = i % LW;
-                const int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
-                const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
-                sp[rr][cc] = ok ? P[(3 * ch + m) * HW + (int64_t)yy * W + xx] : 0.f;
-            }
-            __syncthreads();
-            for (int hr = hlane; hr < LH; hr += 32) {
-                float v[HSEG + 10], o[HSEG];
-#pragma unroll
-                for (int i = 0; i < HSEG + 10; ++i) v[i] = sp[hr][hc + i];
-                hsum(v, v, wk, [](float a, float) { return a; }, o);
-#pragma unroll
-                for (int j = 0; j < HSEG; ++j) hq[0][hr][hc + j] = o[j];
-            }
-            __syncthreads();
-            float bm[1][VSEG];
-            vsum<1>(hq, r0, c, wk, bm);
-#pragma unroll
-            for (int j = 0; j < VSEG; ++j) b[m][j] = bm[0][j];
-            __syncthreads();
+    const float2 *P01 = reinterpret_cast<const float2 *>(P);
+    const float *P2 = P + 6 * HW;
+    auto load01 = [&](int ch) {
+#pragma unroll 1
+        for (int i = threadIdx.x; i < LH * LW; i += 256) {
+            const int rr = i / LW, cc = i % LW;
+            const int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
+            const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
+            cp_async8(&sa[rr][cc], P01 + (ok ? (int64_t)ch * HW + (int64_t)yy * W + xx : 0), ok);
         }
+        cp_async_commit();
+    };
+    auto load2 = [&](int ch) {
+#pragma unroll 1
+        for (int i = threadIdx.x; i < LH * LW; i += 256) {
+            const int rr = i / LW, cc = i % LW;
+            const int yy = oy - SHALO + rr, xx = ox - SHALO + cc;
+            const bool ok = xx >= 0 && xx < W && yy >= 0 && yy < H;
+            cp_async4(&sb[rr][cc], P2 + (ok ? (int64_t)ch * HW + (int64_t)yy * W + xx : 0), ok);
+        }
+        cp_async_commit();
+    };
+    load01(0);
+    load2(0);
+    {  // depth gradient while the first planes arrive
+        const u32 nv = *nvalid;
+        const float dsn = nv > 0 ? dscale / (float)nv : 0.f;
 #pragma unroll
         for (int j = 0; j < VSEG; ++j) {
             const int gy = oy + r0 + j;
             if (gx < W && gy < H) {
                 const int64_t p = (int64_t)gy * W + gx;
-                const float xv = x[ch * HW + p], yv = y[ch * HW + p];
-                d_rgb[ch * HW + p] = l1s * sgnf(xv - yv) + b[0][j] + 2.f * xv * b[1][j] + yv * b[2][j];
+                const float dt = dep_t[p];
+                d_dep[p] = dt > 0.f ? dsn * sgnf(dep[p] - dt) : 0.f;
             }
         }
     }
-    const u32 nv = *nvalid;
-    const float dsn = nv > 0 ? dscale / (float)nv : 0.f;
+    for (int ch = 0; ch < 3; ++ch) {
+        float xv[VSEG], yv[VSEG];  // this thread's pixels, read while the planes are summed
 #pragma unroll
-    for (int j = 0; j < VSEG; ++j) {
-        const int gy = oy + r0 + j;
-        if (gx < W && gy < H) {
-            const int64_t p = (int64_t)gy * W + gx;
-            const float dt = dep_t[p];
-            d_dep[p] = dt > 0.f ? dsn * sgnf(dep[p] - dt) : 0.f;
+        for (int j = 0; j < VSEG; ++j) {
+            const int gy = oy + r0 + j;
+            const int64_t p = (gx < W && gy < H) ? ch * HW + (int64_t)gy * W + gx : 0;
+            xv[j] = x[p];
+            yv[j] = y[p];
+        }
+        cp_async_wait<1>();  // (dS/dmu_x, dS/dE[x^2]) of channel ch has landed
+        __syncthreads();
+        for (int hr = hlane; hr < LH; hr += 32) {
+            float2 v[HSEG + 10], o[HSEG];
+#pragma unroll
+            for (int i = 0; i < HSEG + 10; ++i) v[i] = sa[hr][hc + i];
+            hsum2(v, wk, [](float2 a) { return a; }, o);
+#pragma unroll
+            for (int j = 0; j < HSEG; ++j) hq2[hr][hc + j] = o[j];
+        }
+        __syncthreads();
+        if (ch < 2) load01(ch + 1);
+        float2 b01[VSEG];
+        vsum2(hq2, r0, c, wk, b01);
+        if (ch < 2)
+            cp_async_wait<1>();  // dS/dE[xy] of channel ch has landed
+        else
+            cp_async_wait<0>();
+        __syncthreads();
+        for (int hr = hlane; hr < LH; hr += 32) {
+            float v[HSEG + 10], o[HSEG];
+#pragma unroll
+            for (int i = 0; i < HSEG + 10; ++i) v[i] = sb[hr][hc + i];
+            hsum(v, v, wk, [](float a, float) { return a; }, o);
+#pragma unroll
+            for (int j = 0; j < HSEG; ++j) hq[hr][hc + j] = o[j];
+        }
+        __syncthreads();
+        if (ch < 2) load2(ch + 1);
+        float b2[VSEG];
+        vsum1(hq, r0, c, wk, b2);
+#pragma unroll
+        for (int j = 0; j < VSEG; ++j) {
+            const int gy = oy + r0 + j;
+            if (gx < W && gy < H) {
+                const int64_t p = (int64_t)gy * W + gx;
+                d_rgb[ch * HW + p] = l1s * sgnf(xv[j] - yv[j]) + b01[j].x + 2.f * xv[j] * b01[j].y + yv[j] * b2[j];
+            }
         }
     }
 }
