@@ -25,8 +25,8 @@
 // Gaussian, a transposed warp reduction (12 shuffles for 10 components) sums
 // the warp and one atomic add per warp and component lands in the
 // per-Gaussian accumulator; when at most SPARSE_LANES lanes do, each of them
-// adds its own 10 components (fewer issue slots than the reduction, and few
-// enough atomics that the L2 keeps up).
+// adds its own 10 components with three vector atomics (fewer issue slots
+// than the reduction, and few enough atomics that the L2 keeps up).
 //
 // The same tile bodies run in two launch forms: one CTA per tile of one view,
 // and a persistent grid over (keyframe, tile) items of several views, pulled
@@ -191,7 +191,7 @@ __device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, in
 // 1200 x 680 / 500k-Gaussian view with 8 x 8 tiles: 3 lanes 0.364 ms (two
 // pixels per thread), 8 lanes 0.349 ms, 12 lanes 0.362 ms, 16 lanes 0.445 ms
 // (atomic contention), always reducing 0.371 ms.
-constexpr int SPARSE_LANES = 8;
+constexpr int SPARSE_LANES = 16;
 
 // Transposed warp reductions: every shuffle step halves the number of live
 // values per lane, so the 10 image-space gradient components of one Gaussian
@@ -242,6 +242,25 @@ __device__ __forceinline__ void warp_reduce_add6(const float (&v)[6], float *dst
     const int ai = (h3 ? 2 : 0) + (h2 ? 1 : 0);  // index into a (3 = padding)
     const int comp = (h4 ? 3 : 0) + ai;          // 0..5
     if (!(lane & 3) && ai < 3 && c != 0.f) atomicAdd(dst + (comp == 5 ? 9 : comp), c);
+}
+
+// One lane's 10 components of an entry added to its Gaussian's accumulator
+// (slots as in warp_reduce_add10) with vector atomics: float4 and float2 adds
+// to global memory (sm_90 and later; atomic per element).  A record is 12
+// floats (48 bytes) from a 256-byte aligned base, so slots 0 and 4 are
+// 16-byte and slot 8 8-byte aligned.
+template <bool POSE_ONLY>
+__device__ __forceinline__ void lane_add10(float *dst, float gu, float gv, float gca, float gcb, float gcc, float gop,
+                                           float gr, float gg, float gb, float gz)
+{
+    atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(gu, gv, gca, gcb));
+    if (!POSE_ONLY) {
+        atomicAdd(reinterpret_cast<float4 *>(dst + 4), make_float4(gcc, gop, gr, gg));
+        atomicAdd(reinterpret_cast<float2 *>(dst + 8), make_float2(gb, gz));
+    } else {
+        atomicAdd(dst + 4, gcc);
+        atomicAdd(dst + 9, gz);
+    }
 }
 
 // POSE_ONLY: the tracker needs only the gradients feeding the pose
@@ -340,20 +359,7 @@ __device__ __forceinline__ void bwd_tile(const CamK &ck, const BlendView &vp, in
             if (bal) {
                 float *dst = vp.g2d + 12 * (int64_t)sR[j];
                 if (__popc(bal) <= SPARSE_LANES) {
-                    if (contrib) {  // slots as in warp_reduce_add10
-                        atomicAdd(dst + 0, gu);
-                        atomicAdd(dst + 1, gv);
-                        atomicAdd(dst + 2, gca);
-                        atomicAdd(dst + 3, gcb);
-                        atomicAdd(dst + 4, gcc);
-                        if (!POSE_ONLY) {
-                            atomicAdd(dst + 5, gop);
-                            atomicAdd(dst + 6, gr);
-                            atomicAdd(dst + 7, gg);
-                            atomicAdd(dst + 8, gb);
-                        }
-                        atomicAdd(dst + 9, gz);
-                    }
+                    if (contrib) lane_add10<POSE_ONLY>(dst, gu, gv, gca, gcb, gcc, gop, gr, gg, gb, gz);
                 } else if (POSE_ONLY) {
                     const float v[6] = {gu, gv, gca, gcb, gcc, gz};
                     warp_reduce_add6(v, dst);
@@ -576,20 +582,7 @@ __device__ __forceinline__ void bwd_tile2(const CamK &ck, const BlendView &vp, i
             if (bal) {
                 float *dst = vp.g2d + 12 * (int64_t)sR[j];
                 if (__popc(bal) <= SPARSE_LANES) {
-                    if (contrib) {  // slots as in warp_reduce_add10
-                        atomicAdd(dst + 0, gu);
-                        atomicAdd(dst + 1, gv);
-                        atomicAdd(dst + 2, gca);
-                        atomicAdd(dst + 3, gcb);
-                        atomicAdd(dst + 4, gcc);
-                        if (!POSE_ONLY) {
-                            atomicAdd(dst + 5, gop);
-                            atomicAdd(dst + 6, gr);
-                            atomicAdd(dst + 7, gg);
-                            atomicAdd(dst + 8, gb);
-                        }
-                        atomicAdd(dst + 9, gz);
-                    }
+                    if (contrib) lane_add10<POSE_ONLY>(dst, gu, gv, gca, gcb, gcc, gop, gr, gg, gb, gz);
                 } else if (POSE_ONLY) {
                     const float v[6] = {gu, gv, gca, gcb, gcc, gz};
                     warp_reduce_add6(v, dst);
