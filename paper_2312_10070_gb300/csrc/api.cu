@@ -680,7 +680,7 @@ static gsr_status map_iter(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_state *s
             GSR_TRY(run_project_backward_adam(ctx, ctx->view, g, st, &o->adam, ck, d_pose, nullptr, s));
             GSR_TRY(prof_mark(ctx, PROF_PBWD, true, s));
             GSR_TRY(prof_mark(ctx, PROF_ADAM, false, s));
-            const unsigned nb = (unsigned)ceil_div(n > 0 ? n : 1, 256);
+            const unsigned nb = (unsigned)project_bwd_adam_partials(n);
             GSR_TRY(adam_lreg_final_step(ctx, (const float *)ctx->pose_part.p, (int)nb,
                                          o->adam.w_reg / (float)(n > 0 ? n : 1), sm + SM_MAPLOSS, st->step, s));
             GSR_TRY(prof_mark(ctx, PROF_ADAM, true, s));

@@ -188,9 +188,11 @@ __device__ __forceinline__ void fwd_tile(const CamK &ck, const BlendView &vp, in
 
 // Largest number of compositing lanes for which a warp skips the reduction and
 // the lanes add their gradients with their own atomics.  Measured on the
-// 1200 x 680 / 500k-Gaussian view with 8 x 8 tiles: 3 lanes 0.364 ms (two
-// pixels per thread), 8 lanes 0.349 ms, 12 lanes 0.362 ms, 16 lanes 0.445 ms
-// (atomic contention), always reducing 0.371 ms.
+// 1200 x 680 / 500k-Gaussian view with 8 x 8 tiles and two pixels per thread,
+// with the three vector atomics per lane: 8 lanes 0.283 ms, 12 lanes 0.275 ms,
+// 16 lanes 0.266 ms, 20 and 24 lanes 0.265 ms, never reducing 0.330 ms (atomic
+// contention); the 8-keyframe step, with more contention, runs 10 % slower at
+// 24 lanes than at 16.  (With ten scalar atomics per lane 8 lanes was best.)
 constexpr int SPARSE_LANES = 16;
 
 // Transposed warp reductions: every shuffle step halves the number of live

@@ -420,6 +420,8 @@ gsr_status adam_lreg_final_step(gsr_ctx *ctx, const float *part, int nb, float s
 gsr_status run_project_backward_adam(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians_mut *g, gsr_adam_state *st,
                                      const gsr_adam_opts *o, const CamK &ck, const float *d_pose,
                                      float *loss_reg_dev, cudaStream_t s);
+// number of per-block L_reg partials run_project_backward_adam writes for n Gaussians
+int64_t project_bwd_adam_partials(int64_t n);
 gsr_status run_adam(gsr_ctx *ctx, gsr_gaussians_mut *g, const gsr_gaussian_grads *gr,
                     gsr_adam_state *st, const gsr_adam_opts *o, float *loss_reg_dev, cudaStream_t s);
 gsr_status run_pose_adam(gsr_ctx *ctx, float *d_pose, const float *d_grad6, float *m6, float *v6,

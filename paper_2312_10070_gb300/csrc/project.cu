@@ -781,42 +781,112 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd(Params P, CamK ck, const
     }
 }
 
+// Asynchronous global -> shared copies (cp.async): 16 bytes (both addresses
+// 16-byte aligned) or 4 bytes.
+__device__ __forceinline__ void cpa16(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa4(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// count consecutive floats from global src into shared dst by the whole block
+// (V16: src 16-byte aligned, 16-byte copies and 4-byte ones for the last
+// count % 4)
+template <bool V16>
+__device__ __forceinline__ void stage_in(float *dst, const float *src, int count)
+{
+    int q0 = 0;
+    if (V16) {
+        const int n4 = count >> 2;
+        for (int q = threadIdx.x; q < n4; q += blockDim.x) cpa16(dst + 4 * q, src + 4 * q);
+        q0 = 4 * n4;
+    }
+    for (int q = q0 + (int)threadIdx.x; q < count; q += blockDim.x) cpa4(dst + q, src + q);
+}
+
+template <bool V16>
+__device__ __forceinline__ void stage_out(float *dst, const float *src, int count)
+{
+    int q0 = 0;
+    if (V16) {
+        const int n4 = count >> 2;
+        for (int q = threadIdx.x; q < n4; q += blockDim.x)
+            reinterpret_cast<float4 *>(dst)[q] = reinterpret_cast<const float4 *>(src)[q];
+        q0 = 4 * n4;
+    }
+    for (int q = q0 + (int)threadIdx.x; q < count; q += blockDim.x) dst[q] = src[q];
+}
+
 // One-keyframe mapping step: the projection backward of Gaussian i (as in
 // k_project_bwd) followed at once by its Adam update with L_reg, so its 14
-// gradients stay in registers: the parameters are read once, the moments
+// gradients never leave the block: the parameters are read once, the moments
 // read and written once, and no gradient array is written or read back.
 // Gaussians outside the view have zero gradients and still take their Adam
 // step.  Per-block sums of the L_reg terms go to lreg_part.  The kernel reads
 // the Adam step counter t - 1 (the bias corrections of step t are formed per
 // block); the kernel after it advances the counter.
-__global__ void __launch_bounds__(256, 4) k_project_bwd_adam(Params P, gsr_gaussians_mut gw, CamK ck,
-                                                          const float *__restrict__ pose,
-                                                          const int32_t *__restrict__ rank_of_gid,
-                                                          const float *__restrict__ g2d, gsr_adam_state st,
-                                                          gsr_adam_opts o, float *__restrict__ lreg_part)
+//
+// None of the loads depends on a computed value except the image-gradient
+// row (it needs the Gaussian's depth rank), so a block of PBA Gaussians first
+// copies its slice of all 15 parameter and moment arrays and its gathered
+// image-gradient rows into shared memory with asynchronous copies (27 KB in
+// flight per block), then updates them there and writes the slices back with
+// coalesced stores.  V16: every array base is 16-byte aligned.
+constexpr int PBA = 128;
+
+template <bool V16>
+__global__ void __launch_bounds__(PBA, 8) k_project_bwd_adam(gsr_gaussians_mut gw, CamK ck,
+                                                             const float *__restrict__ pose,
+                                                             const int32_t *__restrict__ rank_of_gid,
+                                                             const float *__restrict__ g2d, gsr_adam_state st,
+                                                             gsr_adam_opts o, float *__restrict__ lreg_part)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float lreg = 0.f;
+    // [params | m | v] x [mean 3 | log_scale 3 | quat 4 | opacity 1 | rgb 3] x PBA, then the image-gradient rows
+    constexpr int OM = 0, OL = 3 * PBA, OQ = 6 * PBA, OO = 10 * PBA, OC = 11 * PBA, GROUP = 14 * PBA;
+    __shared__ __align__(16) float sh[3 * GROUP + 12 * PBA];
     __shared__ float s_bc[2];
-    if (threadIdx.x == 0) {
-        const int t = *st.step + 1;
-        s_bc[0] = 1.f / (1.f - powf(o.beta1, (float)t));
-        s_bc[1] = 1.f / (1.f - powf(o.beta2, (float)t));
+    float *sg = sh + 3 * GROUP;
+    const int t = (int)threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * PBA, i = i0 + t;
+    const int nloc = (int)min((int64_t)PBA, gw.n - i0);
+    const float *arr[3][5] = {{gw.mean, gw.log_scale, gw.quat, gw.opacity_logit, gw.rgb},
+                              {st.m_mean, st.m_log_scale, st.m_quat, st.m_opacity_logit, st.m_rgb},
+                              {st.v_mean, st.v_log_scale, st.v_quat, st.v_opacity_logit, st.v_rgb}};
+    constexpr int width[5] = {3, 3, 4, 1, 3}, off[5] = {OM, OL, OQ, OO, OC};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int f = 0; f < 5; ++f)
+            stage_in<V16>(sh + a * GROUP + off[f], arr[a][f] + width[f] * i0, width[f] * nloc);
+    const int32_t r = t < nloc ? rank_of_gid[i] : -1;
+    if (r >= 0) {
+        const float *row = g2d + 12 * (int64_t)r;
+        cpa16(sg + 12 * t, row);
+        cpa16(sg + 12 * t + 4, row + 4);
+        cpa16(sg + 12 * t + 8, row + 8);
     }
+    if (t == 0) {
+        const int ts = *st.step + 1;
+        s_bc[0] = 1.f / (1.f - powf(o.beta1, (float)ts));
+        s_bc[1] = 1.f / (1.f - powf(o.beta2, (float)ts));
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
-    if (i < P.n) {
-        const int32_t r = rank_of_gid[i];
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.mean + 3 * i));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.log_scale + 3 * i));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.quat + 4 * i));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.opacity_logit + i));
+    float lreg = 0.f;
+    if (t < nloc) {
+        float *sp = sh, *smo = sh + GROUP, *svo = sh + 2 * GROUP;
         float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
         float glog = 0.f, grgb[3] = {0.f, 0.f, 0.f};
         if (r >= 0) {
             const PoseR pr = load_pose(pose);
             GProj g;
-            project_core(ck, pr, P.mean, P.log_scale, P.quat, P.opacity_logit[i], i, g);
-            const float4 *G4 = reinterpret_cast<const float4 *>(g2d + 12 * (int64_t)r);
+            project_core(ck, pr, sp + OM, sp + OL, sp + OQ, sp[OO + t], t, g);
+            const float4 *G4 = reinterpret_cast<const float4 *>(sg + 12 * t);
             const float4 q0 = G4[0], q1 = G4[1], q2 = G4[2];
             grgb[0] = q1.z;
             grgb[1] = q1.w;
@@ -824,58 +894,52 @@ __global__ void __launch_bounds__(256, 4) k_project_bwd_adam(Params P, gsr_gauss
             chain_to_params(ck, pr, g, q0, q1, q2, gm, gls, gq, &glog, nullptr);
         }
         const float ib1 = s_bc[0], ib2 = s_bc[1];  // reciprocal bias corrections
-        float p[4], m[4], v[4];
         // log-scales with L_reg
+        float p[3], m[3], v[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            p[k] = gw.log_scale[3 * i + k];
-            m[k] = st.m_log_scale[3 * i + k];
-            v[k] = st.v_log_scale[3 * i + k];
+            p[k] = sp[OL + 3 * t + k];
+            m[k] = smo[OL + 3 * t + k];
+            v[k] = svo[OL + 3 * t + k];
         }
-        lreg = adam_log_scales3<true>(p, gls, m, v, o.w_reg / (float)P.n, o.lr_log_scale, o, ib1, ib2);
+        lreg = adam_log_scales3<true>(p, gls, m, v, o.w_reg / (float)gw.n, o.lr_log_scale, o, ib1, ib2);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            gw.log_scale[3 * i + k] = p[k];
-            st.m_log_scale[3 * i + k] = m[k];
-            st.v_log_scale[3 * i + k] = v[k];
+            sp[OL + 3 * t + k] = p[k];
+            smo[OL + 3 * t + k] = m[k];
+            svo[OL + 3 * t + k] = v[k];
         }
         // means, colours, quaternion, opacity
+        auto upd = [&](int idx, float gk, float lr) {
+            adam_update_fast(sp[idx], gk, smo[idx], svo[idx], lr, o.beta1, o.beta2, o.eps, ib1, ib2);
+        };
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            float pm = gw.mean[3 * i + k], mm = st.m_mean[3 * i + k], vm = st.v_mean[3 * i + k];
-            adam_update_fast(pm, gm[k], mm, vm, o.lr_mean, o.beta1, o.beta2, o.eps, ib1, ib2);
-            gw.mean[3 * i + k] = pm;
-            st.m_mean[3 * i + k] = mm;
-            st.v_mean[3 * i + k] = vm;
-            float pc = gw.rgb[3 * i + k], mc = st.m_rgb[3 * i + k], vc = st.v_rgb[3 * i + k];
-            adam_update_fast(pc, grgb[k], mc, vc, o.lr_rgb, o.beta1, o.beta2, o.eps, ib1, ib2);
-            gw.rgb[3 * i + k] = pc;
-            st.m_rgb[3 * i + k] = mc;
-            st.v_rgb[3 * i + k] = vc;
+            upd(OM + 3 * t + k, gm[k], o.lr_mean);
+            upd(OC + 3 * t + k, grgb[k], o.lr_rgb);
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float pq = gw.quat[4 * i + k], mq = st.m_quat[4 * i + k], vq = st.v_quat[4 * i + k];
-            adam_update_fast(pq, gq[k], mq, vq, o.lr_quat, o.beta1, o.beta2, o.eps, ib1, ib2);
-            gw.quat[4 * i + k] = pq;
-            st.m_quat[4 * i + k] = mq;
-            st.v_quat[4 * i + k] = vq;
-        }
-        float po = gw.opacity_logit[i], mo = st.m_opacity_logit[i], vo = st.v_opacity_logit[i];
-        adam_update_fast(po, glog, mo, vo, o.lr_opacity, o.beta1, o.beta2, o.eps, ib1, ib2);
-        gw.opacity_logit[i] = po;
-        st.m_opacity_logit[i] = mo;
-        st.v_opacity_logit[i] = vo;
+        for (int k = 0; k < 4; ++k) upd(OQ + 4 * t + k, gq[k], o.lr_quat);
+        upd(OO + t, glog, o.lr_opacity);
     }
-    __shared__ float red[8];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) lreg += __shfl_down_sync(0xffffffffu, lreg, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lreg;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int k = 0; k < 8; ++k) t += red[k];
-        lreg_part[blockIdx.x] = t;
+    float *const warr[3][5] = {{gw.mean, gw.log_scale, gw.quat, gw.opacity_logit, gw.rgb},
+                               {st.m_mean, st.m_log_scale, st.m_quat, st.m_opacity_logit, st.m_rgb},
+                               {st.v_mean, st.v_log_scale, st.v_quat, st.v_opacity_logit, st.v_rgb}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int f = 0; f < 5; ++f)
+            stage_out<V16>(warr[a][f] + width[f] * i0, sh + a * GROUP + off[f], width[f] * nloc);
+    __shared__ float red[PBA / 32];
+#pragma unroll
+    for (int offs = 16; offs > 0; offs >>= 1) lreg += __shfl_down_sync(0xffffffffu, lreg, offs);
+    if ((t & 31) == 0) red[t >> 5] = lreg;
+    __syncthreads();
+    if (t == 0) {
+        float tot = 0.f;
+        for (int k = 0; k < PBA / 32; ++k) tot += red[k];
+        lreg_part[blockIdx.x] = tot;
     }
 }
 
@@ -1110,17 +1174,27 @@ gsr_status run_project_backward(gsr_ctx *ctx, ViewScratch &V, const Params &P, c
     return GSR_OK;
 }
 
+int64_t project_bwd_adam_partials(int64_t n) { return ceil_div(n > 0 ? n : 1, PBA); }
+
 gsr_status run_project_backward_adam(gsr_ctx *ctx, ViewScratch &V, gsr_gaussians_mut *g, gsr_adam_state *st,
                                      const gsr_adam_opts *o, const CamK &ck, const float *d_pose,
                                      float *loss_reg_dev, cudaStream_t s)
 {
     const int64_t n = g->n;
-    const unsigned nb = (unsigned)ceil_div(n > 0 ? n : 1, 256);
+    const unsigned nb = (unsigned)project_bwd_adam_partials(n);
     GSR_TRY(ensure_buf(ctx, ctx->pose_part, sizeof(float) * 6 * nb));
     float *part = (float *)ctx->pose_part.p;
-    const Params P{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, n};
-    k_project_bwd_adam<<<nb, 256, 0, s>>>(P, *g, ck, d_pose, (const int32_t *)V.rank_of_gid.p, (const float *)V.g2d.p,
-                                          *st, *o, part);
+    const void *ptrs[15] = {g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb,
+                            st->m_mean, st->m_log_scale, st->m_quat, st->m_opacity_logit, st->m_rgb,
+                            st->v_mean, st->v_log_scale, st->v_quat, st->v_opacity_logit, st->v_rgb};
+    bool v16 = true;
+    for (const void *q : ptrs) v16 = v16 && ((uintptr_t)q & 15u) == 0;
+    if (v16)
+        k_project_bwd_adam<true><<<nb, PBA, 0, s>>>(*g, ck, d_pose, (const int32_t *)V.rank_of_gid.p,
+                                                   (const float *)V.g2d.p, *st, *o, part);
+    else
+        k_project_bwd_adam<false><<<nb, PBA, 0, s>>>(*g, ck, d_pose, (const int32_t *)V.rank_of_gid.p,
+                                                    (const float *)V.g2d.p, *st, *o, part);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
     if (loss_reg_dev)
