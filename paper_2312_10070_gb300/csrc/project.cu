@@ -838,6 +838,7 @@ __device__ __forceinline__ void stage_out(float *dst, const float *src, int coun
 // flight per block), then updates them there and writes the slices back with
 // coalesced stores.  V16: every array base is 16-byte aligned.
 constexpr int PBA = 128;
+static_assert(PBA >= GSR_POSE_WORDS, "the pose record is staged by one thread per word");
 
 template <bool V16>
 __global__ void __launch_bounds__(PBA, 8) k_project_bwd_adam(gsr_gaussians_mut gw, CamK ck,
@@ -849,7 +850,7 @@ __global__ void __launch_bounds__(PBA, 8) k_project_bwd_adam(gsr_gaussians_mut g
     // [params | m | v] x [mean 3 | log_scale 3 | quat 4 | opacity 1 | rgb 3] x PBA, then the image-gradient rows
     constexpr int OM = 0, OL = 3 * PBA, OQ = 6 * PBA, OO = 10 * PBA, OC = 11 * PBA, GROUP = 14 * PBA;
     __shared__ __align__(16) float sh[3 * GROUP + 12 * PBA];
-    __shared__ float s_bc[2];
+    __shared__ float s_bc[2], s_pose[GSR_POSE_WORDS];
     float *sg = sh + 3 * GROUP;
     const int t = (int)threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * PBA, i = i0 + t;
@@ -870,6 +871,7 @@ __global__ void __launch_bounds__(PBA, 8) k_project_bwd_adam(gsr_gaussians_mut g
         cpa16(sg + 12 * t + 4, row + 4);
         cpa16(sg + 12 * t + 8, row + 8);
     }
+    if (t < GSR_POSE_WORDS) cpa4(s_pose + t, pose + t);
     if (t == 0) {
         const int ts = *st.step + 1;
         s_bc[0] = 1.f / (1.f - powf(o.beta1, (float)ts));
@@ -883,7 +885,7 @@ __global__ void __launch_bounds__(PBA, 8) k_project_bwd_adam(gsr_gaussians_mut g
         float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
         float glog = 0.f, grgb[3] = {0.f, 0.f, 0.f};
         if (r >= 0) {
-            const PoseR pr = load_pose(pose);
+            const PoseR pr = load_pose(s_pose);
             GProj g;
             project_core(ck, pr, sp + OM, sp + OL, sp + OQ, sp[OO + t], t, g);
             const float4 *G4 = reinterpret_cast<const float4 *>(sg + 12 * t);
