@@ -113,6 +113,7 @@ constexpr int RX_TILE = RX_THREADS * RX_ROUNDS;      // 2048 keys per block
 constexpr int RX_MAX_PASSES = 4;
 constexpr u32 LB_AGG = 1u << 30, LB_INC = 2u << 30, LB_MASK = (1u << 30) - 1u;
 constexpr int LB_SPIN_LIMIT = 1 << 24;               // bounded look-back wait
+static_assert(RX_THREADS == RX, "one thread per digit in the look-back and the digit scan");
 constexpr int LB_WINDOW = 4;                         // predecessors read per look-back step
 
 // Bounded wait for a look-back word: polls *p (through L2) until one of the
@@ -292,18 +293,20 @@ __global__ void __launch_bounds__(RX_THREADS, 4) k_radix_onesweep(const u32 *__r
         }
         __stcg(my, LB_INC | (prefix + tot));
     }
-    // block-local digit starts (exclusive scan over digits of tot)
+    // block-local digit starts (exclusive scan over digits of tot): a
+    // shuffle scan within each warp of 32 digits, then the warp totals
     {
-        __shared__ u32 sc[RX];
-        sc[d] = tot;
-        __syncthreads();
-        for (int o = 1; o < RX; o <<= 1) {
-            const u32 t = d >= o ? sc[d - o] : 0u;
-            __syncthreads();
-            sc[d] += t;
-            __syncthreads();
+        __shared__ u32 s_wt[RX / 32];
+        u32 x = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        const u32 lstart = sc[d] - tot;
+        if (lane == 31) s_wt[w] = x;
+        __syncthreads();
+        for (int k = 0; k < w; ++k) x += s_wt[k];
+        const u32 lstart = x - tot;
         s_gpos[d] = digit_base[d] + prefix - lstart;  // global slot of local position i: s_gpos + i
         u32 run = lstart;  // per-warp starts inside the block
 #pragma unroll
