@@ -212,7 +212,7 @@ void gsr_destroy(gsr_ctx *c)
     ViewScratch &V = c->view;
     DevBuf *bufs[] = {&V.rec, &V.flag, &V.compact, &V.rank_of_gid, &V.dkeys[0], &V.dkeys[1], &V.dvals[0], &V.dvals[1],
                       &V.rec_sorted, &V.tcount, &V.inst_off, &V.tkeys[0], &V.tkeys[1], &V.tvals[0], &V.tvals[1],
-                      &V.ranges, &V.g2d, &V.counters, &V.pose, &V.scan_tmp, &V.radix_hist, &V.loss_maps,
+                      &V.ranges, &V.order, &V.order_hist, &V.g2d, &V.counters, &V.pose, &V.scan_tmp, &V.radix_hist, &V.loss_maps,
                       &V.loss_part, &c->scan_tmp,
                       &c->radix_hist, &c->pose_part,
                       &c->loss_part, &c->loss_maps, &c->img_tmp, &c->small, &c->grads};
@@ -220,12 +220,11 @@ void gsr_destroy(gsr_ctx *c)
     for (ViewScratch &W : c->mv) {
         DevBuf *vb[] = {&W.rec, &W.flag, &W.compact, &W.rank_of_gid, &W.dkeys[0], &W.dkeys[1], &W.dvals[0],
                         &W.dvals[1], &W.rec_sorted, &W.tcount, &W.inst_off, &W.tkeys[0], &W.tkeys[1], &W.tvals[0],
-                        &W.tvals[1], &W.ranges, &W.g2d, &W.counters, &W.pose, &W.scan_tmp, &W.radix_hist,
+                        &W.tvals[1], &W.ranges, &W.order, &W.order_hist, &W.g2d, &W.counters, &W.pose, &W.scan_tmp, &W.radix_hist,
                         &W.loss_maps, &W.loss_part};
         for (DevBuf *b : vb) free_buf(*b);
     }
-    DevBuf *mb[] = {&c->mv_frames, &c->mv_desc, &c->mv_pview, &c->mv_keys[0], &c->mv_keys[1], &c->mv_items[0],
-                    &c->mv_items[1], &c->mv_counter};
+    DevBuf *mb[] = {&c->mv_frames, &c->mv_desc, &c->mv_pview, &c->mv_items, &c->mv_order_hist, &c->mv_counter};
     for (DevBuf *b : mb) free_buf(*b);
     SeedScratch &S = c->seed;
     DevBuf *sb[] = {&S.flag, &S.sel, &S.off, &S.keys[0], &S.keys[1], &S.vals[0], &S.vals[1], &S.cnt, &S.cand_pix,
@@ -715,10 +714,8 @@ static gsr_status map_iter_multi(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_st
     GSR_TRY(ensure_buf(ctx, ctx->mv_frames, sizeof(float) * 12 * (size_t)HW * n_kf));
     GSR_TRY(ensure_buf(ctx, ctx->mv_desc, sizeof(BlendView) * n_kf));
     GSR_TRY(ensure_buf(ctx, ctx->mv_pview, sizeof(ProjView) * n_kf));
-    for (int k = 0; k < 2; ++k) {
-        GSR_TRY(ensure_buf(ctx, ctx->mv_keys[k], sizeof(u32) * (size_t)tiles * n_kf));
-        GSR_TRY(ensure_buf(ctx, ctx->mv_items[k], sizeof(u32) * (size_t)tiles * n_kf));
-    }
+    GSR_TRY(ensure_buf(ctx, ctx->mv_items, sizeof(u32) * (size_t)tiles * n_kf));
+    GSR_TRY(ensure_buf(ctx, ctx->mv_order_hist, order_hist_bytes((int64_t)tiles * n_kf)));
     GSR_TRY(ensure_buf(ctx, ctx->mv_counter, sizeof(u32)));
     float *G = (float *)ctx->grads.p;
     gsr_gaussian_grads gr{G, G + 3 * n, G + 6 * n, G + 10 * n, G + 11 * n};
@@ -746,7 +743,7 @@ static gsr_status map_iter_multi(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_st
         cudaStream_t sk = ctx->side[k % ns];
         GSR_TRY(ensure_buf(ctx, V.pose, GSR_POSE_WORDS * sizeof(float)));
         GSR_TRY(launch_set_pose(ctx, (float *)V.pose.p, kfs[k].pose, sk));
-        GSR_TRY(run_binning(ctx, V, P, ck, (float *)V.pose.p, grow, sk));
+        GSR_TRY(run_binning(ctx, V, P, ck, (float *)V.pose.p, grow, sk, false));
     }
     for (int i = 0; i < ns; ++i) {
         GSR_CUDA(ctx, cudaEventRecord(ctx->join_ev[i], ctx->side[i]));
@@ -775,13 +772,12 @@ static gsr_status map_iter_multi(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_st
         ctx->mv_pview_host = pv;
     }
     const BlendView *dv = (const BlendView *)ctx->mv_desc.p;
-    u32 *keys[2] = {(u32 *)ctx->mv_keys[0].p, (u32 *)ctx->mv_keys[1].p};
-    u32 *items[2] = {(u32 *)ctx->mv_items[0].p, (u32 *)ctx->mv_items[1].p};
-    GSR_TRY(run_make_items(ctx, dv, n_kf, tiles, keys, items, s));
+    u32 *items = (u32 *)ctx->mv_items.p;
+    GSR_TRY(run_make_items(ctx, dv, n_kf, tiles, items, s));
     GSR_TRY(prof_mark(ctx, PROF_BIN, true, s));
 
     GSR_TRY(prof_mark(ctx, PROF_FWD, false, s));
-    GSR_TRY(run_blend_multi(ctx, ck, false, dv, items[0], n_kf * tiles, (u32 *)ctx->mv_counter.p, s));
+    GSR_TRY(run_blend_multi(ctx, ck, false, dv, items, n_kf * tiles, (u32 *)ctx->mv_counter.p, s));
     GSR_TRY(prof_mark(ctx, PROF_FWD, true, s));
     GSR_TRY(prof_mark(ctx, PROF_LOSS, false, s));
     // per-keyframe losses on the side streams (own scratch), the scalar sums in order here
@@ -803,7 +799,7 @@ static gsr_status map_iter_multi(gsr_ctx *ctx, gsr_gaussians_mut *g, gsr_adam_st
     GSR_TRY(prof_mark(ctx, PROF_LOSS, true, s));
     GSR_TRY(prof_mark(ctx, PROF_BWD, false, s));
     for (int k = 0; k < n_kf; ++k) GSR_TRY(zero_g2d(ctx, ctx->mv[k], s));
-    GSR_TRY(run_blend_multi(ctx, ck, true, dv, items[0], n_kf * tiles, (u32 *)ctx->mv_counter.p, s));
+    GSR_TRY(run_blend_multi(ctx, ck, true, dv, items, n_kf * tiles, (u32 *)ctx->mv_counter.p, s));
     GSR_TRY(prof_mark(ctx, PROF_BWD, true, s));
     GSR_TRY(prof_mark(ctx, PROF_PBWD, false, s));
     GSR_TRY(run_project_backward_multi(ctx, P, ck, (const ProjView *)ctx->mv_pview.p, n_kf, &gr, s));

@@ -29,8 +29,10 @@
 // than the reduction, and few enough atomics that the L2 keeps up).
 //
 // The same tile bodies run in two launch forms: one CTA per tile of one view,
-// and a persistent grid over (keyframe, tile) items of several views, pulled
-// from a longest-first work list through an atomic counter (no waits).
+// block b taking tile order[b] (tiles by list length, longest first, written
+// by the binning), and a persistent grid over (keyframe, tile) items of
+// several views, pulled from a longest-first work list through an atomic
+// counter (no waits).
 #include <algorithm>
 
 #include "gsr_internal.cuh"
@@ -597,14 +599,17 @@ __device__ __forceinline__ void bwd_tile2(const CamK &ck, const BlendView &vp, i
     }
 }
 
+// the tile this block renders (launch order: longest lists first)
+__device__ __forceinline__ int block_tile(const BlendView &vp) { return vp.order ? (int)vp.order[blockIdx.x] : (int)blockIdx.x; }
+
 template <int TW, int TH, int BATCH, int PPT>
 __global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd(CamK ck, BlendView vp)
 {
     __shared__ Staged sS[BATCH];
     __shared__ u32 sR[BATCH];
     __shared__ int s_cnt[TW * TH / PPT / 32];
-    if constexpr (PPT == 2) fwd_tile2<TW, TH, BATCH>(ck, vp, blockIdx.x, sS, sR, s_cnt);
-    else fwd_tile<TW, TH, BATCH, PPT>(ck, vp, blockIdx.x, sS, sR, s_cnt);
+    if constexpr (PPT == 2) fwd_tile2<TW, TH, BATCH>(ck, vp, block_tile(vp), sS, sR, s_cnt);
+    else fwd_tile<TW, TH, BATCH, PPT>(ck, vp, block_tile(vp), sS, sR, s_cnt);
 }
 
 template <int TW, int TH, int BATCH, int PPT, bool POSE_ONLY>
@@ -614,8 +619,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_bwd(CamK ck, BlendView v
     __shared__ u32 sR[BATCH];
     __shared__ int s_cnt[TW * TH / PPT / 32];
     __shared__ int s_max;
-    if constexpr (PPT == 2) bwd_tile2<TW, TH, BATCH, POSE_ONLY>(ck, vp, blockIdx.x, sS, sR, s_cnt, &s_max);
-    else bwd_tile<TW, TH, BATCH, PPT, POSE_ONLY>(ck, vp, blockIdx.x, sS, sR, s_cnt, &s_max);
+    if constexpr (PPT == 2) bwd_tile2<TW, TH, BATCH, POSE_ONLY>(ck, vp, block_tile(vp), sS, sR, s_cnt, &s_max);
+    else bwd_tile<TW, TH, BATCH, PPT, POSE_ONLY>(ck, vp, block_tile(vp), sS, sR, s_cnt, &s_max);
 }
 
 // Persistent forms: items[i] = (view << 16) | tile, longest lists first.
@@ -662,16 +667,93 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_bwd_multi(CamK ck, const
     }
 }
 
-__global__ void k_make_items(const BlendView *__restrict__ views, int n_views, int tiles, u32 *__restrict__ keys,
-                             u32 *__restrict__ items)
+
+// Launch order of the blend kernels: (view, tile) items by list length,
+// longest first, so the long tiles start in the first wave instead of ending
+// the launch on them.  A counting sort over length buckets on a log scale
+// (four per octave; bucket 0 = empty tiles, placed last), in two launches of
+// ORDER_ITEMS items per block: k_order_count writes each block's bucket
+// counts, k_order_place derives its bucket starts from all blocks' counts
+// and places its items.  The order within a bucket follows shared-memory
+// atomics: only the schedule depends on it, since every tile's result is
+// computed by one block wherever it is placed.  Item i = view * tiles + tile
+// is written as (view << 16) | tile.
+constexpr int ORDER_BUCKETS = 72, ORDER_THREADS = 256, ORDER_PER_THREAD = 4;
+constexpr int ORDER_ITEMS = ORDER_THREADS * ORDER_PER_THREAD;
+
+__device__ __forceinline__ int length_bucket(u32 len)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_views * tiles) return;
-    const int v = i / tiles, t = i % tiles;
-    const uint2 rg = views[v].ranges[t];
-    const u32 len = min(rg.y - rg.x, 0xffffu);
-    keys[i] = 0xffffu - len;  // ascending sort = longest first
-    items[i] = ((u32)v << 16) | (u32)t;
+    if (len == 0) return 0;
+    const int l = 31 - __clz(len);                                // floor(log2 len)
+    const int frac = l >= 2 ? (int)((len >> (l - 2)) & 3u) : 0;  // two bits below the leading one
+    return min(1 + 4 * l + frac, ORDER_BUCKETS - 1);
+}
+
+// The views' tile ranges: one view's array, or the descriptors of several.
+struct ItemLen {
+    const uint2 *ranges;       // one view (views == nullptr)
+    const BlendView *views;
+    int tiles;
+    __device__ __forceinline__ u32 operator()(int i) const
+    {
+        const uint2 rg = views ? views[i / tiles].ranges[i % tiles] : ranges[i];
+        return rg.y - rg.x;
+    }
+};
+
+__global__ void __launch_bounds__(ORDER_THREADS) k_order_count(ItemLen len, int n, u32 *__restrict__ hist)
+{
+    __shared__ u32 cnt[ORDER_BUCKETS];
+    for (int b = threadIdx.x; b < ORDER_BUCKETS; b += ORDER_THREADS) cnt[b] = 0;
+    __syncthreads();
+    int bk[ORDER_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < ORDER_PER_THREAD; ++k) {
+        const int i = blockIdx.x * ORDER_ITEMS + k * ORDER_THREADS + (int)threadIdx.x;
+        bk[k] = i < n ? length_bucket(len(i)) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < ORDER_PER_THREAD; ++k)
+        if (bk[k] >= 0) atomicAdd(&cnt[bk[k]], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < ORDER_BUCKETS; b += ORDER_THREADS)
+        hist[(int64_t)blockIdx.x * ORDER_BUCKETS + b] = cnt[b];
+}
+
+__global__ void __launch_bounds__(ORDER_THREADS) k_order_place(ItemLen len, int n, const u32 *__restrict__ hist,
+                                                               u32 *__restrict__ items)
+{
+    __shared__ u32 total[ORDER_BUCKETS], start[ORDER_BUCKETS];
+    int bk[ORDER_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < ORDER_PER_THREAD; ++k) {
+        const int i = blockIdx.x * ORDER_ITEMS + k * ORDER_THREADS + (int)threadIdx.x;
+        bk[k] = i < n ? length_bucket(len(i)) : -1;
+    }
+    const int b = threadIdx.x;
+    u32 before = 0;  // items of bucket b in earlier blocks
+    if (b < ORDER_BUCKETS) {
+        u32 tot = 0;
+        for (int blk = 0; blk < (int)gridDim.x; ++blk) {
+            const u32 h = hist[(int64_t)blk * ORDER_BUCKETS + b];
+            tot += h;
+            before += blk < (int)blockIdx.x ? h : 0u;
+        }
+        total[b] = tot;
+    }
+    __syncthreads();
+    if (b < ORDER_BUCKETS) {  // longer buckets first
+        u32 s = before;
+        for (int c = b + 1; c < ORDER_BUCKETS; ++c) s += total[c];
+        start[b] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ORDER_PER_THREAD; ++k) {
+        if (bk[k] < 0) continue;
+        const int i = blockIdx.x * ORDER_ITEMS + k * ORDER_THREADS + (int)threadIdx.x;
+        items[atomicAdd(&start[bk[k]], 1u)] = ((u32)(i / len.tiles) << 16) | (u32)(i % len.tiles);
+    }
 }
 
 __global__ void k_zero_g2d(int64_t cap, const u32 *__restrict__ d_v, float4 *__restrict__ g2d)
@@ -795,6 +877,7 @@ BlendView blend_view(const ViewScratch &V, const gsr_render_out *o, const float 
     b.d_depth = d_depth;
     b.d_alpha = d_alpha;
     b.g2d = (float *)V.g2d.p;
+    b.order = V.order_valid ? (const u32 *)V.order.p : nullptr;
     b.culled = V.culled ? 1 : 0;
     return b;
 }
@@ -863,12 +946,26 @@ gsr_status run_blend_multi(gsr_ctx *ctx, const CamK &ck, bool backward, const Bl
     return dispatch(ctx, L, s);
 }
 
-gsr_status run_make_items(gsr_ctx *ctx, const BlendView *views, int n_views, int tiles, u32 *keys[2], u32 *items[2],
-                          cudaStream_t s)
+size_t order_hist_bytes(int64_t n) { return sizeof(u32) * ORDER_BUCKETS * (size_t)ceil_div(n > 0 ? n : 1, ORDER_ITEMS); }
+
+static gsr_status run_order(gsr_ctx *ctx, const ItemLen &len, int n, u32 *items, DevBuf &hist, cudaStream_t s)
 {
-    const int n = n_views * tiles;
-    k_make_items<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(views, n_views, tiles, keys[0], items[0]);
-    ctx->launches += 1;
+    const int nb = (int)ceil_div(n > 0 ? n : 1, ORDER_ITEMS);
+    GSR_TRY(ensure_buf(ctx, hist, order_hist_bytes(n)));
+    k_order_count<<<nb, ORDER_THREADS, 0, s>>>(len, n, (u32 *)hist.p);
+    k_order_place<<<nb, ORDER_THREADS, 0, s>>>(len, n, (const u32 *)hist.p, items);
+    ctx->launches += 2;
     GSR_LAUNCHED(ctx);
-    return radix_sort_pairs(ctx, keys, items, n, nullptr, 16, s);
+    return GSR_OK;
+}
+
+gsr_status run_order_tiles(gsr_ctx *ctx, ViewScratch &V, int tiles, cudaStream_t s)
+{
+    return run_order(ctx, ItemLen{(const uint2 *)V.ranges.p, nullptr, tiles}, tiles, (u32 *)V.order.p, V.order_hist,
+                     s);
+}
+
+gsr_status run_make_items(gsr_ctx *ctx, const BlendView *views, int n_views, int tiles, u32 *items, cudaStream_t s)
+{
+    return run_order(ctx, ItemLen{nullptr, views, tiles}, n_views * tiles, items, ctx->mv_order_hist, s);
 }

@@ -56,6 +56,8 @@ struct ViewScratch {
     DevBuf tkeys[2];    // u32 tile id per instance
     DevBuf tvals[2];    // u32 depth rank per instance
     DevBuf ranges;      // uint2 per tile
+    DevBuf order;       // u32 per tile: tile ids by list length, longest first (blend launch order)
+    DevBuf order_hist;  // u32 per length bucket and block of the launch-order sort
     DevBuf g2d;         // float x12 per rank: image-space gradients
     DevBuf counters;    // u32[CNT_WORDS]
     DevBuf pose;        // float[8]: q(4), t(3)
@@ -66,6 +68,7 @@ struct ViewScratch {
     int64_t cap_n = 0, cap_i = 0, cap_t = 0;
     bool culled = false;  // the lists hold only entries that pass the tile test
     bool g2d_zero = false;  // g2d was zeroed by the last binning and no backward has added to it since
+    bool order_valid = false;  // order holds the launch order of the last binning
     // identity of the last forward, to decide whether the saved lists are valid
     uint64_t generation = 0;
 };
@@ -79,6 +82,7 @@ struct BlendView {
     int32_t *last_idx, *n_contrib;
     const float *d_rgb, *d_depth, *d_alpha;
     float *g2d;
+    const u32 *order;  // the tile of block b is order[b] (nullptr: b)
     int culled;    // 1: every list entry passed the tile test when the lists were built
     int reserved;  // explicit padding (descriptors are compared bytewise)
 };
@@ -134,7 +138,7 @@ struct gsr_ctx {
     u32 *host_pinned = nullptr; // small pinned readback buffer
     // batched multi-keyframe mapping: per-keyframe scratch and frames
     std::vector<ViewScratch> mv;
-    DevBuf mv_frames, mv_desc, mv_pview, mv_keys[2], mv_items[2], mv_counter;
+    DevBuf mv_frames, mv_desc, mv_pview, mv_items, mv_order_hist, mv_counter;
     // side streams of the batched binning (one chain of binning kernels per
     // keyframe runs on each; forked from and joined to the caller's stream)
     static constexpr int N_SIDE = 8;
@@ -373,9 +377,11 @@ gsr_status launch_perturb_pose(gsr_ctx *ctx, float *d_pose, const float *xi, cud
 // g6 <- J_l(xi)^T g6 (device float[6] each)
 gsr_status launch_pose_grad_xi(gsr_ctx *ctx, float *g6, const float *xi, cudaStream_t s);
 // Projection + binning into V; returns after enqueueing (no sync unless
-// allow_grow, which reads the instance count back once to size V)
+// allow_grow, which reads the instance count back once to size V).
+// launch_order: also write V.order, the one-view blend launch order (the
+// persistent multi-view blend builds its own work list instead)
 gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK &ck, const float *d_pose,
-                       bool allow_grow, cudaStream_t s);
+                       bool allow_grow, cudaStream_t s, bool launch_order = true);
 gsr_status run_blend_forward(gsr_ctx *ctx, const Params &P, const CamK &ck, gsr_render_out *out,
                              cudaStream_t s);
 gsr_status run_blend_backward(gsr_ctx *ctx, const CamK &ck, const gsr_render_out *saved,
@@ -435,6 +441,11 @@ enum { PROF_BIN = 0, PROF_FWD = 1, PROF_LOSS = 2, PROF_BWD = 3, PROF_PBWD = 4, P
 // records the start (end = false) or end event of a phase on `s` when profiling
 gsr_status prof_mark(gsr_ctx *ctx, int phase, bool end, cudaStream_t s);
 // work list of the persistent blend: items (view << 16 | tile) of n_views
-// views, sorted longest tile list first (stable), into items[0]
-gsr_status run_make_items(gsr_ctx *ctx, const BlendView *views, int n_views, int tiles, u32 *keys[2], u32 *items[2],
-                          cudaStream_t s);
+// views (descriptors in device memory), longest tile list first by length
+// bucket (order within a bucket unspecified)
+gsr_status run_make_items(gsr_ctx *ctx, const BlendView *views, int n_views, int tiles, u32 *items, cudaStream_t s);
+// launch order of one view's blend kernels: tile ids, longest list first
+// (as run_make_items, one view)
+gsr_status run_order_tiles(gsr_ctx *ctx, ViewScratch &V, int tiles, cudaStream_t s);
+// scratch bytes of the launch-order sort of n items (sized before graph capture)
+size_t order_hist_bytes(int64_t n);

@@ -607,6 +607,7 @@ __global__ void k_ranges(int64_t cap_i, const u32 *__restrict__ d_n, const u32 *
     }
 }
 
+
 // --------------------------------------------------------------- backward
 // Chain of one Gaussian's image-space gradients
 //   q0 = (u, v, conic a, conic b), q1 = (conic c, opacity, r, g), q2 = (b, z, -, -)
@@ -1064,8 +1065,9 @@ static int bits_for(int64_t v)
 }
 
 gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK &ck, const float *d_pose,
-                       bool allow_grow, cudaStream_t s)
+                       bool allow_grow, cudaStream_t s, bool launch_order)
 {
+    V.order_valid = false;  // until this binning writes the order
     const int64_t n = P.n;
     const int64_t tiles = (int64_t)ck.tiles_x * ck.tiles_y;
     if (n > V.cap_n) {
@@ -1086,6 +1088,8 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
     }
     if (tiles > V.cap_t) {
         GSR_TRY(ensure_buf(ctx, V.ranges, sizeof(uint2) * tiles));
+        GSR_TRY(ensure_buf(ctx, V.order, sizeof(u32) * tiles));
+        GSR_TRY(ensure_buf(ctx, V.order_hist, order_hist_bytes(tiles)));
         V.cap_t = tiles;
     }
     GSR_TRY(ensure_buf(ctx, V.counters, sizeof(u32) * CNT_WORDS));
@@ -1143,6 +1147,8 @@ gsr_status run_binning(gsr_ctx *ctx, ViewScratch &V, const Params &P, const CamK
                                                                           (uint2 *)V.ranges.p);
     ctx->launches += 1;
     GSR_LAUNCHED(ctx);
+    V.order_valid = launch_order;
+    if (launch_order) GSR_TRY(run_order_tiles(ctx, V, tiles, s));
     return GSR_OK;
 }
 
