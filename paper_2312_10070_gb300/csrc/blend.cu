@@ -408,7 +408,8 @@ __device__ __forceinline__ PairSigma pair_sigma(float px, float2 py, const float
     return r;
 }
 
-template <int TW, int TH, int BATCH>
+// COUNT: also count each pixel's compositing entries (n_contrib requested)
+template <int TW, int TH, int BATCH, bool COUNT>
 __device__ __forceinline__ void fwd_tile2(const CamK &ck, const BlendView &vp, int tile, Staged *sS,
                                           u32 *sR, int *s_cnt)
 {
@@ -455,8 +456,10 @@ __device__ __forceinline__ void fwd_tile2(const CamK &ck, const BlendView &vp, i
             const int jj = staged_pos(sS[j]);
             last0 = k0 ? jj : last0;
             last1 = k1 ? jj : last1;
-            nc0 += k0;
-            nc1 += k1;
+            if (COUNT) {
+                nc0 += k0;
+                nc1 += k1;
+            }
             tdone = done0 && done1;
         }
     }
@@ -474,7 +477,7 @@ __device__ __forceinline__ void fwd_tile2(const CamK &ck, const BlendView &vp, i
             vp.alpha[p] = 1.f - Tk;
             vp.final_T[p] = Tk;
             vp.last_idx[p] = k ? last1 : last0;
-            if (vp.n_contrib) vp.n_contrib[p] = k ? nc1 : nc0;
+            if (COUNT) vp.n_contrib[p] = k ? nc1 : nc0;
         }
     }
 }
@@ -608,7 +611,10 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd(CamK ck, BlendView v
     __shared__ Staged sS[BATCH];
     __shared__ u32 sR[BATCH];
     __shared__ int s_cnt[TW * TH / PPT / 32];
-    if constexpr (PPT == 2) fwd_tile2<TW, TH, BATCH>(ck, vp, block_tile(vp), sS, sR, s_cnt);
+    if constexpr (PPT == 2) {
+        if (vp.n_contrib) fwd_tile2<TW, TH, BATCH, true>(ck, vp, block_tile(vp), sS, sR, s_cnt);
+        else fwd_tile2<TW, TH, BATCH, false>(ck, vp, block_tile(vp), sS, sR, s_cnt);
+    }
     else fwd_tile<TW, TH, BATCH, PPT>(ck, vp, block_tile(vp), sS, sR, s_cnt);
 }
 
@@ -643,7 +649,11 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend_fwd_multi(CamK ck, const
     __shared__ int s_item;
     for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
         const u32 w = items[it];
-        if constexpr (PPT == 2) fwd_tile2<TW, TH, BATCH>(ck, views[w >> 16], (int)(w & 0xffffu), sS, sR, s_cnt);
+        if constexpr (PPT == 2) {
+            const BlendView &v = views[w >> 16];
+            if (v.n_contrib) fwd_tile2<TW, TH, BATCH, true>(ck, v, (int)(w & 0xffffu), sS, sR, s_cnt);
+            else fwd_tile2<TW, TH, BATCH, false>(ck, v, (int)(w & 0xffffu), sS, sR, s_cnt);
+        }
         else fwd_tile<TW, TH, BATCH, PPT>(ck, views[w >> 16], (int)(w & 0xffffu), sS, sR, s_cnt);
     }
 }
