@@ -294,14 +294,17 @@ __global__ void __launch_bounds__(256, 4) k_ssim_fwd(int W, int H, const float *
             }
         }
     }
-    const u32 wsum = __reduce_add_sync(0xffffffffu, nv);
-    if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(nvalid, wsum);
-    block_sum256<3>(acc);
+    // the block's valid-depth count rides along the float sums (exact: at most
+    // TX * TY = 1536 per block) and reaches the counter in one atomic per block
+    float sums[4] = {acc[0], acc[1], acc[2], (float)nv};
+    block_sum256<4>(sums);
     if (threadIdx.x == 0) {
         const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-        part[3 * b] = acc[0];
-        part[3 * b + 1] = acc[1];
-        part[3 * b + 2] = acc[2];
+        part[3 * b] = sums[0];
+        part[3 * b + 1] = sums[1];
+        part[3 * b + 2] = sums[2];
+        const u32 bn = (u32)sums[3];
+        if (bn) atomicAdd(nvalid, bn);
     }
 }
 
@@ -452,8 +455,10 @@ __global__ void k_track_resid(int64_t HW, const float *__restrict__ dep, const f
         valid = dt > 0.f;
         ebits[p] = valid ? __float_as_uint(fabsf(dep[p] - dt)) : 0xffffffffu;
     }
-    u32 bal = __ballot_sync(0xffffffffu, valid);
-    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(nvalid, (u32)__popc(bal));
+    // one atomic per block on the shared counter (per warp, the blocks of this
+    // short kernel queued on one L2 address)
+    const int bn = __syncthreads_count(valid);
+    if (threadIdx.x == 0 && bn) atomicAdd(nvalid, (u32)bn);
 }
 
 // state: sel[0] = prefix bits, sel[1] = remaining rank
