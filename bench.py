@@ -768,7 +768,11 @@ def run_track(args, emit=True):
     iters = 100
     spec = S.camera_room()
     cam = api.camera_from_spec(spec)
-    ctx = api.Context()
+    if args.tuned:  # fixed launch configuration (profiler runs)
+        tw, th, batch, pf, pb = (int(x) for x in args.tuned.split(","))
+        ctx = api.Context(tile=(tw, th), batch=batch, ppt_fwd=pf, ppt_bwd=pb)
+    else:
+        ctx = api.Context()
     g = api.GaussianParams.from_numpy(S.room_scene(300_000, seed=100))
     n_frames = max(args.warmup, 3) + args.steps
     qs, ts = S.room_trajectory(100, n_frames=n_frames + 2)
@@ -785,7 +789,11 @@ def run_track(args, emit=True):
         frames.append((torch.from_numpy(rgb).cuda(), torch.from_numpy(dep).cuda(), qi / np.linalg.norm(qi), ti, k))
     # tile shape, batch and pixels per thread from the autotuner at the first
     # frame's pose (untimed), as for the mapping step
-    tuned, _ = api.autotune(ctx, g, cam, [api.make_pose(qs[2], ts[2])], reps=3)
+    if args.tuned:
+        o = ctx.options
+        tuned = dict(tile=(o.tile_w, o.tile_h), batch=o.batch, ppt_fwd=o.ppt_fwd, ppt_bwd=o.ppt_bwd, source="--tuned")
+    else:
+        tuned, _ = api.autotune(ctx, g, cam, [api.make_pose(qs[2], ts[2])], reps=3)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     ms, errs, launches = [], [], 0

@@ -472,6 +472,12 @@ __global__ void k_sel_init(const u32 *__restrict__ nvalid, u32 *__restrict__ sel
     hist[threadIdx.x] = 0u;
 }
 
+// SEL_UNROLL residuals per thread are loaded before their histogram updates;
+// the loop's trip count is uniform over the block, and each warp adds one
+// shared-memory atomic per distinct bin (the first pass bins the exponent
+// byte, which few values share, so per-lane atomics would queue on them)
+constexpr int SEL_UNROLL = 4;
+
 __global__ void __launch_bounds__(256) k_sel_hist(int64_t HW, const u32 *__restrict__ ebits, int shift,
                                                   const u32 *__restrict__ sel, u32 *__restrict__ hist)
 {
@@ -480,9 +486,22 @@ __global__ void __launch_bounds__(256) k_sel_hist(int64_t HW, const u32 *__restr
     __syncthreads();
     const u32 prefix = sel[0];
     const u32 hmask = shift == 24 ? 0u : (0xffffffffu << (shift + 8));
-    for (int64_t p = (int64_t)blockIdx.x * 256 + threadIdx.x; p < HW; p += (int64_t)gridDim.x * 256) {
-        u32 b = ebits[p];
-        if (b != 0xffffffffu && (b & hmask) == (prefix & hmask)) atomicAdd(&h[(b >> shift) & 255u], 1u);
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * 256 * SEL_UNROLL; base < HW;
+         base += (int64_t)gridDim.x * 256 * SEL_UNROLL) {
+        u32 bv[SEL_UNROLL];
+#pragma unroll
+        for (int u = 0; u < SEL_UNROLL; ++u) {
+            const int64_t p = base + u * 256 + threadIdx.x;
+            bv[u] = p < HW ? ebits[p] : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < SEL_UNROLL; ++u) {
+            const u32 b = bv[u];
+            const int bin = (b != 0xffffffffu && (b & hmask) == (prefix & hmask)) ? (int)((b >> shift) & 255u) : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[bin], (u32)__popc(peers));
+        }
     }
     __syncthreads();
     if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
@@ -490,20 +509,22 @@ __global__ void __launch_bounds__(256) k_sel_hist(int64_t HW, const u32 *__restr
 
 __global__ void __launch_bounds__(256) k_sel_pick(int shift, u32 *__restrict__ sel, u32 *__restrict__ hist)
 {
-    __shared__ u32 s[256];
+    __shared__ u32 s_wt[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const u32 v = hist[threadIdx.x];
-    s[threadIdx.x] = v;
-    __syncthreads();
-    // inclusive scan (Hillis-Steele, 256 entries)
-    for (int o = 1; o < 256; o <<= 1) {
-        u32 t = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0u;
-        __syncthreads();
-        s[threadIdx.x] += t;
-        __syncthreads();
+    // inclusive scan of the 256 bins: shuffles within each warp, then the warp totals
+    u32 incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
     }
-    const u32 k = sel[1];
-    const u32 incl = s[threadIdx.x], excl = incl - v;
+    if (lane == 31) s_wt[w] = incl;
     __syncthreads();
+    for (int k = 0; k < w; ++k) incl += s_wt[k];
+    const u32 k = sel[1];
+    const u32 excl = incl - v;
+    __syncthreads();  // every thread has read sel before the one below writes it
     if (v > 0 && excl <= k && k < incl) {
         sel[0] |= (u32)threadIdx.x << shift;
         sel[1] = k - excl;
@@ -629,7 +650,7 @@ gsr_status run_loss_track(gsr_ctx *ctx, int W, int H, const float *rgb, const fl
     GSR_CUDA(ctx, cudaMemsetAsync(cnt + CNT_TRACK_N, 0, sizeof(u32), s));
     k_track_resid<<<nb, 256, 0, s>>>(HW, depth, depth_t, ebits, cnt + CNT_TRACK_N);
     k_sel_init<<<1, 256, 0, s>>>(cnt + CNT_TRACK_N, cnt + CNT_SEL, hist);
-    const unsigned hb = (unsigned)std::min<int64_t>(nb, 1216);
+    const unsigned hb = (unsigned)std::min<int64_t>(ceil_div(HW, 256 * SEL_UNROLL), 1216);
     for (int shift = 24; shift >= 0; shift -= 8) {
         k_sel_hist<<<hb, 256, 0, s>>>(HW, ebits, shift, cnt + CNT_SEL, hist);
         k_sel_pick<<<1, 256, 0, s>>>(shift, cnt + CNT_SEL, hist);
@@ -693,7 +714,7 @@ extern "C" gsr_status gsr_loss_track_noalloc(int32_t width, int32_t height, cons
     }
     k_track_resid<<<nb, 256, 0, s>>>(HW, depth, depth_target, ebits, nvalid);
     k_sel_init<<<1, 256, 0, s>>>(nvalid, sel, hist);
-    const unsigned hb = (unsigned)std::min<int64_t>(nb, 1216);
+    const unsigned hb = (unsigned)std::min<int64_t>(ceil_div(HW, 256 * SEL_UNROLL), 1216);
     for (int shift = 24; shift >= 0; shift -= 8) {
         k_sel_hist<<<hb, 256, 0, s>>>(HW, ebits, shift, sel, hist);
         k_sel_pick<<<1, 256, 0, s>>>(shift, sel, hist);
