@@ -186,6 +186,7 @@ gsr_status grow_instance_capacity(gsr_ctx *ctx, ViewScratch &V, int64_t c);
 struct CamK {
     int W, H, tw, th, tiles_x, tiles_y;
     float fx, fy, cx, cy, z_near, eps2d, limx, limy;
+    float inv_tw;  // 1 / tw, exact: tile widths are powers of two
 };
 
 CamK make_camk(const gsr_camera &c, int tw, int th);

@@ -14,6 +14,7 @@ CamK make_camk(const gsr_camera &c, int tw, int th)
     k.H = c.height;
     k.tw = tw;
     k.th = th;
+    k.inv_tw = 1.f / (float)tw;
     k.tiles_x = (c.width + tw - 1) / tw;
     k.tiles_y = (c.height + th - 1) / th;
     k.fx = c.fx;
@@ -440,9 +441,10 @@ __device__ __forceinline__ void row_cols(const RowCull &q, const CamK &ck, int t
     R = __fadd_rn(R, d);
     // column tx's box spans x offsets [tx tw + 0.5 - u, tx tw + tw - 0.5 - u] (the
     // last column unclipped: conservative); clamp before converting to int
-    const float tw = (float)ck.tw;
-    const float flo = fmaxf(ceilf(__fsub_rn(__fdiv_rn(__fadd_rn(__fadd_rn(L, q.u), 0.5f), tw), 1.f)), (float)rx0);
-    const float fhi = fminf(floorf(__fdiv_rn(__fsub_rn(__fadd_rn(R, q.u), 0.5f), tw)), (float)rx1);
+    // x / tw as x * (1 / tw): the same float, since tw is a power of two
+    const float itw = ck.inv_tw;
+    const float flo = fmaxf(ceilf(__fsub_rn(__fmul_rn(__fadd_rn(__fadd_rn(L, q.u), 0.5f), itw), 1.f)), (float)rx0);
+    const float fhi = fminf(floorf(__fmul_rn(__fsub_rn(__fadd_rn(R, q.u), 0.5f), itw)), (float)rx1);
     *lo = (int)flo;
     *hi = fhi < flo ? *lo - 1 : (int)fhi;
 }
