@@ -768,8 +768,9 @@ def run_track(args, emit=True):
     iters = 100
     spec = S.camera_room()
     cam = api.camera_from_spec(spec)
-    if args.tuned:  # fixed launch configuration (profiler runs)
-        tw, th, batch, pf, pb = (int(x) for x in args.tuned.split(","))
+    fixed = getattr(args, "tuned", "")
+    if fixed:  # fixed launch configuration (profiler runs)
+        tw, th, batch, pf, pb = (int(x) for x in fixed.split(","))
         ctx = api.Context(tile=(tw, th), batch=batch, ppt_fwd=pf, ppt_bwd=pb)
     else:
         ctx = api.Context()
@@ -789,7 +790,7 @@ def run_track(args, emit=True):
         frames.append((torch.from_numpy(rgb).cuda(), torch.from_numpy(dep).cuda(), qi / np.linalg.norm(qi), ti, k))
     # tile shape, batch and pixels per thread from the autotuner at the first
     # frame's pose (untimed), as for the mapping step
-    if args.tuned:
+    if fixed:
         o = ctx.options
         tuned = dict(tile=(o.tile_w, o.tile_h), batch=o.batch, ppt_fwd=o.ppt_fwd, ppt_bwd=o.ppt_bwd, source="--tuned")
     else:
@@ -901,7 +902,7 @@ def extra_workloads(args):
     numbers are CUDA-event timings like the headline's."""
     import torch
     out = {}
-    sub = argparse.Namespace(steps=5, warmup=3, gpus=1)
+    sub = argparse.Namespace(steps=5, warmup=3, gpus=1, tuned="")  # each workload autotunes its own context
     for name, fn, steps in (("track", run_track, 5), ("map8", run_map8, 5), ("hires", run_hires, 5),
                             ("warmstart", run_warmstart, 20)):
         sub.steps = steps

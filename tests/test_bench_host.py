@@ -65,3 +65,20 @@ def test_reference_arm_other_ranks_exit_without_work():
                        env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_extra_workloads_namespace_has_every_argument_the_workloads_read():
+    """The default bench line runs the other workloads with a namespace of
+    its own: every args.<name> those functions read must be in it (a missing
+    one crashes the default run only on a GPU machine)."""
+    import ast
+    import inspect
+    import re
+    import bench
+    src = inspect.getsource(bench.extra_workloads)
+    call = next(n for n in ast.walk(ast.parse(src)) if isinstance(n, ast.Call)
+                and getattr(n.func, "attr", "") == "Namespace")
+    given = {kw.arg for kw in call.keywords}
+    for fn in (bench.run_track, bench.run_map8, bench.run_hires, bench.run_warmstart):
+        read = set(re.findall(r"\bargs\.([a-z_]+)", inspect.getsource(fn)))
+        assert read <= given, (fn.__name__, sorted(read - given))
